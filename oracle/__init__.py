@@ -1,0 +1,272 @@
+"""Oracle: a plain FP64 CPU reference of the particle hot path (arXiv 1804.07598).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  The product library (``paper_1804_07598_gb300``) never imports it and
+shares no code with it: the arithmetic lives in ``fpm_oracle.c`` (plain C,
+compiled by gcc with ``-ffp-contract=off``) and in ``sph.py`` / ``adjoint.py``
+of this package; this module only marshals numpy arrays.
+
+Every function cites the passage of the paper it follows; the conventions the
+paper leaves open are listed at the top of ``fpm_oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fpm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle's C part with gcc (no GPU, no nvcc)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _P(dtype):
+    return np.ctypeslib.ndpointer(dtype=dtype, flags="C_CONTIGUOUS")
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            i32, f64, i64 = ctypes.c_int, ctypes.c_double, ctypes.c_int64
+            sig = {
+                "orc_cell_grid": (i32, [_P(np.float64), _P(np.int32), f64, _P(np.int32), _P(np.float32)]),
+                "orc_wrap_f32": (None, [i32, _P(np.float32), _P(np.float64), _P(np.int32)]),
+                "orc_wrap_f64": (None, [i32, _P(np.float64), _P(np.float64), _P(np.int32)]),
+                "orc_cell_index_f32": (i32, [i32, _P(np.float32), _P(np.int32), _P(np.float32),
+                                             _P(np.float64), _P(np.uint32)]),
+                "orc_cell_index_f64": (i32, [i32, _P(np.float64), _P(np.int32), _P(np.float32),
+                                             _P(np.float64), _P(np.uint32)]),
+                "orc_counting_sort": (None, [i32, i32, _P(np.uint32), _P(np.uint32), _P(np.uint32)]),
+                "orc_neighbors_f32": (i64, [i32, _P(np.float32), _P(np.float64), _P(np.int32), f64, i64,
+                                            _P(np.int64), _P(np.uint32)]),
+                "orc_neighbors_f64": (i64, [i32, _P(np.float64), _P(np.float64), _P(np.int32), f64, i64,
+                                            _P(np.int64), _P(np.uint32)]),
+                "orc_neighbors_one_f32": (i32, [i32, _P(np.float32), _P(np.float64), _P(np.int32), f64, i32,
+                                                i32, _P(np.uint32)]),
+                "orc_neighbors_one_f64": (i32, [i32, _P(np.float64), _P(np.float64), _P(np.int32), f64, i32,
+                                                i32, _P(np.uint32)]),
+                "orc_max_disp_f32": (i32, [i32, _P(np.float32), _P(np.float32), _P(np.float64), _P(np.int32),
+                                           f64, ctypes.POINTER(f64)]),
+                "orc_max_disp_f64": (i32, [i32, _P(np.float64), _P(np.float64), _P(np.float64), _P(np.int32),
+                                           f64, ctypes.POINTER(f64)]),
+                "orc_lj_forces": (i32, [i32, _P(np.float64), _P(np.float64), _P(np.int32), f64, f64, f64, i32,
+                                        _P(np.float64), _P(np.float64)]),
+                "orc_lj_force_one": (None, [i32, _P(np.float64), _P(np.float64), _P(np.int32), f64, f64, f64,
+                                            i32, i32, _P(np.float64)]),
+                "orc_vv_kick_drift": (None, [i32, f64, _P(np.float64), _P(np.float64), _P(np.float64),
+                                             _P(np.float64), _P(np.int32)]),
+                "orc_vv_kick": (None, [i32, f64, _P(np.float64), _P(np.float64)]),
+                "orc_lj_nve": (i32, [i32, _P(np.float64), _P(np.float64), _P(np.float64), _P(np.int32), f64, f64,
+                                     f64, f64, i32, ctypes.c_void_p]),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+        return _lib
+
+
+def _box(L, periodic):
+    L = np.ascontiguousarray(np.broadcast_to(np.asarray(L, np.float64), (3,)))
+    p = np.ascontiguousarray(np.broadcast_to(np.asarray(periodic, np.int32), (3,)))
+    return L, p
+
+
+def _pos4(x, dtype):
+    x = np.asarray(x)
+    if x.ndim != 2 or x.shape[1] not in (3, 4):
+        raise ValueError("positions must be [n,3] or [n,4]")
+    out = np.zeros((x.shape[0], 4), dtype)
+    out[:, :3] = x[:, :3]
+    if x.shape[1] == 4:
+        out[:, 3] = x[:, 3]
+    return out
+
+
+# --------------------------------------------------------------------------
+# Cell lists (Sec. 2; getCellListSym / updateCellListSym in Listing 4.1)
+# --------------------------------------------------------------------------
+
+def cell_grid(L, periodic, r_cell):
+    """Cells per dimension and the single-precision inverse cell width."""
+    Lb, pb = _box(L, periodic)
+    nc = np.zeros(3, np.int32)
+    inv = np.zeros(3, np.float32)
+    if lib().orc_cell_grid(Lb, pb, float(r_cell), nc, inv):
+        raise ValueError("box too small for the cutoff (periodic L must exceed 2*r_cell)")
+    return nc, inv
+
+
+def wrap(pos, L, periodic):
+    """One-step periodic wrap into [0, L) in the positions' own precision."""
+    dtype = np.float32 if np.asarray(pos).dtype == np.float32 else np.float64
+    p = _pos4(pos, dtype)
+    Lb, pb = _box(L, periodic)
+    (lib().orc_wrap_f32 if dtype == np.float32 else lib().orc_wrap_f64)(p.shape[0], p, Lb, pb)
+    return p
+
+
+def cell_index(pos, L, periodic, r_cell):
+    """Cell id of every (already wrapped) particle; returns (cell, nbad, nc)."""
+    nc, inv = cell_grid(L, periodic, r_cell)
+    dtype = np.float32 if np.asarray(pos).dtype == np.float32 else np.float64
+    p = _pos4(pos, dtype)
+    Lb, _ = _box(L, periodic)
+    cell = np.zeros(p.shape[0], np.uint32)
+    fn = lib().orc_cell_index_f32 if dtype == np.float32 else lib().orc_cell_index_f64
+    nbad = fn(p.shape[0], p, nc, inv, Lb, cell)
+    return cell, nbad, nc
+
+
+def counting_sort(cell, ncell):
+    """Stable counting sort (Sec. 3.6 re-sorting): (cell_start[ncell+1], perm)."""
+    cell = np.ascontiguousarray(cell, np.uint32)
+    cs = np.zeros(int(ncell) + 1, np.uint32)
+    perm = np.zeros(cell.shape[0], np.uint32)
+    lib().orc_counting_sort(cell.shape[0], int(ncell), cell, cs, perm)
+    return cs, perm
+
+
+def celllist_build(pos, L, periodic, r_cell, vel=None, ids=None):
+    """The whole cell-list build: wrap -> cell index -> counting sort -> reorder.
+
+    Returns dict(pos, vel, ids, cell_start, perm, nc, nbad) with every
+    per-particle array in sorted order (pos wrapped)."""
+    pw = wrap(pos, L, periodic)
+    cell, nbad, nc = cell_index(pw, L, periodic, r_cell)
+    cs, perm = counting_sort(cell, int(np.prod(nc)))
+    out = dict(pos=pw[perm], cell_start=cs, perm=perm, nc=nc, nbad=nbad, cell=cell[perm])
+    if vel is not None:
+        out["vel"] = np.asarray(vel)[perm]
+    if ids is not None:
+        out["ids"] = np.asarray(ids)[perm]
+    return out
+
+
+# --------------------------------------------------------------------------
+# Verlet lists (Sec. 2, Sec. 4.1)
+# --------------------------------------------------------------------------
+
+def neighbors(pos, L, periodic, r_list):
+    """Full neighbour lists (CSR) of every particle within r_list, decided in the
+    positions' precision. Returns (offsets[n+1] int64, nbr uint32)."""
+    dtype = np.float32 if np.asarray(pos).dtype == np.float32 else np.float64
+    p = _pos4(pos, dtype)
+    Lb, pb = _box(L, periodic)
+    n = p.shape[0]
+    fn = lib().orc_neighbors_f32 if dtype == np.float32 else lib().orc_neighbors_f64
+    offs = np.zeros(n + 1, np.int64)
+    cap = max(1, 96 * n)
+    while True:
+        nbr = np.zeros(cap, np.uint32)
+        tot = fn(n, p, Lb, pb, float(r_list), cap, offs, nbr)
+        if tot == -2:
+            raise ValueError("box too small for the cutoff")
+        if tot >= 0:
+            return offs, nbr[:tot]
+        cap = int(offs[n]) + 1
+
+
+def neighbors_one(pos, L, periodic, r_list, i):
+    """Neighbour set of one particle by an O(n) scan (sampled checks)."""
+    dtype = np.float32 if np.asarray(pos).dtype == np.float32 else np.float64
+    p = _pos4(pos, dtype)
+    Lb, pb = _box(L, periodic)
+    fn = lib().orc_neighbors_one_f32 if dtype == np.float32 else lib().orc_neighbors_one_f64
+    out = np.zeros(4096, np.uint32)
+    k = fn(p.shape[0], p, Lb, pb, float(r_list), int(i), out.shape[0], out)
+    if k > out.shape[0]:
+        out = np.zeros(k, np.uint32)
+        k = fn(p.shape[0], p, Lb, pb, float(r_list), int(i), out.shape[0], out)
+    return out[:k]
+
+
+def max_disp(pos, ref, L, periodic, skin):
+    """Rebuild test: (flag, max squared minimum-image displacement)."""
+    dtype = np.float32 if np.asarray(pos).dtype == np.float32 else np.float64
+    p, r = _pos4(pos, dtype), _pos4(ref, dtype)
+    Lb, pb = _box(L, periodic)
+    m = ctypes.c_double(0.0)
+    fn = lib().orc_max_disp_f32 if dtype == np.float32 else lib().orc_max_disp_f64
+    flag = fn(p.shape[0], p, r, Lb, pb, float(skin), ctypes.byref(m))
+    return int(flag), float(m.value)
+
+
+# --------------------------------------------------------------------------
+# Lennard-Jones (Sec. 4.1, its potential and Listing 4.1's pair force)
+# --------------------------------------------------------------------------
+
+def lj_forces(pos, L, periodic, eps, sigma, rc, mask_f32=False):
+    """FP64 forces [n,4] (w = per-particle half pair energy), U, W, pairs.
+
+    mask_f32: decide r < rc in single precision on the (single-precision)
+    positions, as a single-precision path does."""
+    p = _pos4(pos, np.float64)
+    Lb, pb = _box(L, periodic)
+    f = np.zeros_like(p)
+    out = np.zeros(3, np.float64)
+    if lib().orc_lj_forces(p.shape[0], p, Lb, pb, float(eps), float(sigma), float(rc), int(bool(mask_f32)),
+                           f, out):
+        raise ValueError("box too small for the cutoff")
+    return f, float(out[0]), float(out[1]), int(out[2])
+
+
+def lj_force_one(pos, L, periodic, eps, sigma, rc, i, mask_f32=False):
+    p = _pos4(pos, np.float64)
+    Lb, pb = _box(L, periodic)
+    out = np.zeros(4, np.float64)
+    lib().orc_lj_force_one(p.shape[0], p, Lb, pb, float(eps), float(sigma), float(rc), int(bool(mask_f32)),
+                           int(i), out)
+    return out
+
+
+# --------------------------------------------------------------------------
+# Velocity Verlet (Listing 4.1 time loop, unit mass)
+# --------------------------------------------------------------------------
+
+def vv_kick_drift(pos, vel, force, dt, L, periodic):
+    """v += dt/2 F; x += dt v; wrap. Returns new (pos, vel) as FP64 [n,4]."""
+    p, v, f = _pos4(pos, np.float64), _pos4(vel, np.float64), _pos4(force, np.float64)
+    Lb, pb = _box(L, periodic)
+    lib().orc_vv_kick_drift(p.shape[0], float(dt), p, v, f, Lb, pb)
+    return p, v
+
+
+def vv_kick(vel, force, dt):
+    v, f = _pos4(vel, np.float64), _pos4(force, np.float64)
+    lib().orc_vv_kick(v.shape[0], float(dt), v, f)
+    return v
+
+
+def lj_nve(pos, vel, L, periodic, eps, sigma, rc, dt, nsteps, record=True):
+    """nsteps of NVE velocity Verlet in FP64. Returns (pos, vel, energies) with
+    energies[s] = (KE, U, W, pairs) after step s (s=0: initial state)."""
+    p, v = _pos4(pos, np.float64), _pos4(vel, np.float64)
+    Lb, pb = _box(L, periodic)
+    e = np.zeros((nsteps + 1, 4), np.float64) if record else None
+    ptr = e.ctypes.data_as(ctypes.c_void_p) if record else None
+    if lib().orc_lj_nve(p.shape[0], p, v, Lb, pb, float(eps), float(sigma), float(rc), float(dt), int(nsteps),
+                        ptr):
+        raise ValueError("box too small for the cutoff")
+    return p, v, e

@@ -1,0 +1,560 @@
+/*
+ * fpm_oracle.c -- plain, slow, obviously-correct CPU reference of the particle
+ * hot path of OpenFPM (arXiv 1804.07598).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this file's library.  It shares no
+ * code, header, table or helper with the CUDA library; it is compiled by gcc
+ * with -ffp-contract=off so that every floating-point operation written here
+ * is the operation executed.
+ *
+ * Conventions (readings of the paper, which is silent on them):
+ *   - The domain is the box [0,L0)x[0,L1)x[0,L2) with a per-dimension
+ *     periodic flag (the paper's Box + bc, Listing 4.1 of Sec. 4.1).
+ *   - Positions and velocities are stored as 4-vectors (x,y,z,w); w is unused.
+ *   - Cell grid: nc = floor(L / (r_cell*(1+2^-12))); a periodic dimension with
+ *     nc < 3 uses nc = 1 (all particles of that dimension are candidates);
+ *     a periodic dimension needs L > 2*r_cell*(1+2^-10) so that the minimum
+ *     image is unique inside r_cell.
+ *   - Cell coordinate: ci = min((int)((float)x * inv), nc-1) with
+ *     inv = (float)(nc/L), in single precision for both position precisions.
+ *   - Minimum image per periodic dimension: if (d > L/2) d -= L;
+ *     else if (d < -L/2) d += L.
+ *   - Squared distance: r2 = fma(dz,dz, fma(dy,dy, dx*dx)) in the precision
+ *     of the positions; a pair is inside a radius r iff r2 < (T)(r*r).
+ *
+ * Each function names the passage of the paper it follows.  Functions whose
+ * parity is pinned by an independent test say so in the test-suite; none of
+ * the functions here is "parity unpinned".
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MARGIN_CELL (1.0 + 1.0 / 4096.0)
+#define ORC_MARGIN_HALF (1.0 + 1.0 / 1024.0)
+
+/* ------------------------------------------------------------------------ */
+/* Cell grid (cell lists, Sec. 2; getCellListSym in Listing 4.1)             */
+/* ------------------------------------------------------------------------ */
+
+/* Returns 0 on success, 1 if the box cannot hold the cutoff sphere. */
+int orc_cell_grid(const double L[3], const int periodic[3], double r_cell,
+                  int nc[3], float inv[3])
+{
+    if (!(r_cell > 0.0)) return 1;
+    for (int d = 0; d < 3; ++d) {
+        if (!(L[d] > 0.0)) return 1;
+        if (periodic[d] && !(L[d] > 2.0 * r_cell * ORC_MARGIN_HALF)) return 1;
+        double q = floor(L[d] / (r_cell * ORC_MARGIN_CELL));
+        int n = (q > 1048576.0) ? 1048576 : (int)q;
+        if (n < 1) n = 1;
+        if (periodic[d] && n < 3) n = 1;
+        nc[d] = n;
+        inv[d] = (float)((double)n / L[d]);
+    }
+    return 0;
+}
+
+/* Wrap one coordinate into [0,L): one correction step each way. */
+static float wrap_f32(float x, float L)
+{
+    if (x < 0.0f) x = x + L;
+    if (x >= L) x = x - L;
+    return x;
+}
+
+static double wrap_f64(double x, double L)
+{
+    if (x < 0.0) x = x + L;
+    if (x >= L) x = x - L;
+    return x;
+}
+
+void orc_wrap_f32(int n, float *pos4, const double L[3], const int periodic[3])
+{
+    for (int i = 0; i < n; ++i)
+        for (int d = 0; d < 3; ++d)
+            if (periodic[d]) pos4[4 * i + d] = wrap_f32(pos4[4 * i + d], (float)L[d]);
+}
+
+void orc_wrap_f64(int n, double *pos4, const double L[3], const int periodic[3])
+{
+    for (int i = 0; i < n; ++i)
+        for (int d = 0; d < 3; ++d)
+            if (periodic[d]) pos4[4 * i + d] = wrap_f64(pos4[4 * i + d], L[d]);
+}
+
+/* Cell coordinate of one (already wrapped) coordinate.  *bad is set when the
+ * coordinate lies outside [0,L) (only possible in a non-periodic dimension). */
+static int cell_coord(float xf, float inv, int nc, int *bad)
+{
+    if (!(xf >= 0.0f)) { *bad = 1; return 0; }
+    float s = xf * inv;
+    int c = (s >= (float)nc) ? nc : (int)s;
+    if (c > nc - 1) c = nc - 1;
+    return c;
+}
+
+static uint32_t linear_cell(const int c[3], const int nc[3])
+{
+    return (uint32_t)(((int64_t)c[2] * nc[1] + c[1]) * nc[0] + c[0]);
+}
+
+/* Cell id of every particle; positions must already be wrapped.  Returns the
+ * number of particles found outside a non-periodic dimension's [0,L). */
+int orc_cell_index_f32(int n, const float *pos4, const int nc[3], const float inv[3],
+                       const double L[3], uint32_t *cell)
+{
+    int nbad = 0;
+    for (int i = 0; i < n; ++i) {
+        int c[3], bad = 0;
+        for (int d = 0; d < 3; ++d) {
+            float x = pos4[4 * i + d];
+            if (x >= (float)L[d]) bad = 1;
+            c[d] = cell_coord(x, inv[d], nc[d], &bad);
+        }
+        nbad += bad;
+        cell[i] = linear_cell(c, nc);
+    }
+    return nbad;
+}
+
+int orc_cell_index_f64(int n, const double *pos4, const int nc[3], const float inv[3],
+                       const double L[3], uint32_t *cell)
+{
+    int nbad = 0;
+    for (int i = 0; i < n; ++i) {
+        int c[3], bad = 0;
+        for (int d = 0; d < 3; ++d) {
+            double x = pos4[4 * i + d];
+            if (x >= L[d] || x < 0.0) bad = 1;
+            c[d] = cell_coord((float)x, inv[d], nc[d], &bad);
+        }
+        nbad += bad;
+        cell[i] = linear_cell(c, nc);
+    }
+    return nbad;
+}
+
+/* Stable counting sort by cell (the re-sorting of Sec. 3.6): perm lists the
+ * particles cell by cell, ties in ascending input index; cell_start[c] is the
+ * exclusive prefix sum of the cell counts, cell_start[ncell] = n. */
+void orc_counting_sort(int n, int ncell, const uint32_t *cell,
+                       uint32_t *cell_start, uint32_t *perm)
+{
+    uint32_t *fill = (uint32_t *)calloc((size_t)ncell + 1, sizeof(uint32_t));
+    for (int c = 0; c <= ncell; ++c) cell_start[c] = 0;
+    for (int i = 0; i < n; ++i) cell_start[cell[i] + 1] += 1;
+    for (int c = 0; c < ncell; ++c) cell_start[c + 1] += cell_start[c];
+    for (int i = 0; i < n; ++i) {
+        uint32_t c = cell[i];
+        perm[cell_start[c] + fill[c]] = (uint32_t)i;
+        fill[c] += 1;
+    }
+    free(fill);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pair geometry                                                             */
+/* ------------------------------------------------------------------------ */
+
+static float min_image_f32(float d, float L)
+{
+    float h = 0.5f * L;
+    if (d > h) d = d - L;
+    else if (d < -h) d = d + L;
+    return d;
+}
+
+static double min_image_f64(double d, double L)
+{
+    double h = 0.5 * L;
+    if (d > h) d = d - L;
+    else if (d < -h) d = d + L;
+    return d;
+}
+
+/* Separation x_i - x_j (minimum image) and its squared length, float. */
+static float sep_f32(const float *xi, const float *xj, const double L[3],
+                     const int periodic[3], float dv[3])
+{
+    for (int d = 0; d < 3; ++d) {
+        float t = xi[d] - xj[d];
+        if (periodic[d]) t = min_image_f32(t, (float)L[d]);
+        dv[d] = t;
+    }
+    return fmaf(dv[2], dv[2], fmaf(dv[1], dv[1], dv[0] * dv[0]));
+}
+
+static double sep_f64(const double *xi, const double *xj, const double L[3],
+                      const int periodic[3], double dv[3])
+{
+    for (int d = 0; d < 3; ++d) {
+        double t = xi[d] - xj[d];
+        if (periodic[d]) t = min_image_f64(t, L[d]);
+        dv[d] = t;
+    }
+    return fma(dv[2], dv[2], fma(dv[1], dv[1], dv[0] * dv[0]));
+}
+
+/* An oracle-private cell list over arbitrary-order positions. */
+typedef struct {
+    int nc[3];
+    float inv[3];
+    int ncell;
+    uint32_t *cell;        /* [n] */
+    uint32_t *cell_start;  /* [ncell+1] */
+    uint32_t *perm;        /* [n] */
+} orc_cells;
+
+static int cells_build(orc_cells *cl, int n, const float *pf, const double *pd,
+                       const double L[3], const int periodic[3], double r_cell)
+{
+    memset(cl, 0, sizeof(*cl));
+    if (orc_cell_grid(L, periodic, r_cell, cl->nc, cl->inv)) return 1;
+    cl->ncell = cl->nc[0] * cl->nc[1] * cl->nc[2];
+    cl->cell = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    cl->perm = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    cl->cell_start = (uint32_t *)malloc(sizeof(uint32_t) * ((size_t)cl->ncell + 1));
+    /* bin wrapped copies, so callers may pass positions one box length out */
+    size_t m = 4 * (size_t)(n > 0 ? n : 1);
+    if (pf) {
+        float *w = (float *)malloc(sizeof(float) * m);
+        memcpy(w, pf, sizeof(float) * 4 * (size_t)n);
+        orc_wrap_f32(n, w, L, periodic);
+        orc_cell_index_f32(n, w, cl->nc, cl->inv, L, cl->cell);
+        free(w);
+    } else {
+        double *w = (double *)malloc(sizeof(double) * m);
+        memcpy(w, pd, sizeof(double) * 4 * (size_t)n);
+        orc_wrap_f64(n, w, L, periodic);
+        orc_cell_index_f64(n, w, cl->nc, cl->inv, L, cl->cell);
+        free(w);
+    }
+    orc_counting_sort(n, cl->ncell, cl->cell, cl->cell_start, cl->perm);
+    return 0;
+}
+
+static void cells_free(orc_cells *cl)
+{
+    free(cl->cell);
+    free(cl->perm);
+    free(cl->cell_start);
+}
+
+/* The stencil offsets of one dimension: {-1,0,1}, or {0} when nc == 1. */
+static int stencil_dim(int nc, int periodic, int c, int out[3])
+{
+    int k = 0;
+    if (nc == 1) { out[k++] = 0; return k; }
+    for (int o = -1; o <= 1; ++o) {
+        int cc = c + o;
+        if (periodic) cc = (cc + nc) % nc;
+        else if (cc < 0 || cc >= nc) continue;
+        out[k++] = cc;
+    }
+    return k;
+}
+
+/* Candidates of particle i: every particle of the 27 (or fewer) cells around
+ * cell `ci`, in stencil order (z, then y, then x, each from -1 to 1), then in
+ * ascending input index inside each cell.  Writes them to out (room for n
+ * entries: a cell stencil never repeats a cell) and returns how many. */
+static int stencil_candidates(const orc_cells *cl, const int periodic[3], uint32_t ci,
+                              uint32_t *out)
+{
+    int c3[3], cz[3], cy[3], cx[3];
+    c3[0] = (int)(ci % (uint32_t)cl->nc[0]);
+    c3[1] = (int)((ci / (uint32_t)cl->nc[0]) % (uint32_t)cl->nc[1]);
+    c3[2] = (int)(ci / ((uint32_t)cl->nc[0] * (uint32_t)cl->nc[1]));
+    int kz = stencil_dim(cl->nc[2], periodic[2], c3[2], cz);
+    int ky = stencil_dim(cl->nc[1], periodic[1], c3[1], cy);
+    int kx = stencil_dim(cl->nc[0], periodic[0], c3[0], cx);
+    int k = 0;
+    for (int a = 0; a < kz; ++a)
+        for (int b = 0; b < ky; ++b)
+            for (int e = 0; e < kx; ++e) {
+                int cc[3] = {cx[e], cy[b], cz[a]};
+                uint32_t c = linear_cell(cc, cl->nc);
+                for (uint32_t s = cl->cell_start[c]; s < cl->cell_start[c + 1]; ++s)
+                    out[k++] = cl->perm[s];
+            }
+    return k;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Verlet lists (Sec. 2 "Verlet Lists [46]"; Sec. 4.1)                       */
+/* ------------------------------------------------------------------------ */
+
+/* Full neighbour lists: for every particle i, every j != i with
+ * r2(i,j) < (T)(r_list^2), listed in stencil order.  CSR output: offsets[n+1],
+ * nbr[offsets[i] .. offsets[i+1]).  Returns the total count, or -1 if it
+ * exceeds cap_total (offsets are then still complete, nbr truncated), or -2
+ * on an invalid box. */
+static int64_t neighbors_impl(int n, const float *pf, const double *pd,
+                              const double L[3], const int periodic[3],
+                              double r_list, int64_t cap_total,
+                              int64_t *offsets, uint32_t *nbr)
+{
+    orc_cells cl;
+    if (cells_build(&cl, n, pf, pd, L, periodic, r_list)) return -2;
+    float rl2f = (float)(r_list * r_list);
+    double rl2d = r_list * r_list;
+    int64_t total = 0;
+    uint32_t *cand = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) {
+        offsets[i] = total;
+        int m = stencil_candidates(&cl, periodic, cl.cell[i], cand);
+        for (int t = 0; t < m; ++t) {
+            uint32_t j = cand[t];
+            if (j != (uint32_t)i) {
+                int inside;
+                if (pf) {
+                    float dv[3];
+                    inside = sep_f32(pf + 4 * (size_t)i, pf + 4 * (size_t)j, L, periodic, dv) < rl2f;
+                } else {
+                    double dv[3];
+                    inside = sep_f64(pd + 4 * (size_t)i, pd + 4 * (size_t)j, L, periodic, dv) < rl2d;
+                }
+                if (inside) {
+                    if (total < cap_total) nbr[total] = j;
+                    total += 1;
+                }
+            }
+        }
+    }
+    offsets[n] = total;
+    free(cand);
+    cells_free(&cl);
+    return total > cap_total ? -1 : total;
+}
+
+int64_t orc_neighbors_f32(int n, const float *pos4, const double L[3], const int periodic[3],
+                          double r_list, int64_t cap_total, int64_t *offsets, uint32_t *nbr)
+{
+    return neighbors_impl(n, pos4, NULL, L, periodic, r_list, cap_total, offsets, nbr);
+}
+
+int64_t orc_neighbors_f64(int n, const double *pos4, const double L[3], const int periodic[3],
+                          double r_list, int64_t cap_total, int64_t *offsets, uint32_t *nbr)
+{
+    return neighbors_impl(n, NULL, pos4, L, periodic, r_list, cap_total, offsets, nbr);
+}
+
+/* Neighbour set of a single particle i by scanning all n particles (used for
+ * sampled checks on large systems).  Returns the count written (up to cap). */
+int orc_neighbors_one_f32(int n, const float *pos4, const double L[3], const int periodic[3],
+                          double r_list, int i, int cap, uint32_t *out)
+{
+    float rl2f = (float)(r_list * r_list);
+    int k = 0;
+    for (int j = 0; j < n; ++j) {
+        float dv[3];
+        if (j != i && sep_f32(pos4 + 4 * (size_t)i, pos4 + 4 * (size_t)j, L, periodic, dv) < rl2f) {
+            if (k < cap) out[k] = (uint32_t)j;
+            k++;
+        }
+    }
+    return k;
+}
+
+int orc_neighbors_one_f64(int n, const double *pos4, const double L[3], const int periodic[3],
+                          double r_list, int i, int cap, uint32_t *out)
+{
+    double rl2d = r_list * r_list;
+    int k = 0;
+    for (int j = 0; j < n; ++j) {
+        double dv[3];
+        if (j != i && sep_f64(pos4 + 4 * (size_t)i, pos4 + 4 * (size_t)j, L, periodic, dv) < rl2d) {
+            if (k < cap) out[k] = (uint32_t)j;
+            k++;
+        }
+    }
+    return k;
+}
+
+/* Verlet rebuild test: 1 iff some particle moved (minimum image) by more than
+ * skin/2 since the reference positions, judged as d2 > (T)((skin/2)^2).  The
+ * largest squared displacement is returned through max_d2. */
+int orc_max_disp_f32(int n, const float *pos4, const float *ref4, const double L[3],
+                     const int periodic[3], double skin, double *max_d2)
+{
+    float th = (float)(0.25 * skin * skin);
+    float m = 0.0f;
+    int flag = 0;
+    for (int i = 0; i < n; ++i) {
+        float dv[3];
+        float d2 = sep_f32(pos4 + 4 * (size_t)i, ref4 + 4 * (size_t)i, L, periodic, dv);
+        if (d2 > m) m = d2;
+        if (d2 > th) flag = 1;
+    }
+    *max_d2 = m;
+    return flag;
+}
+
+int orc_max_disp_f64(int n, const double *pos4, const double *ref4, const double L[3],
+                     const int periodic[3], double skin, double *max_d2)
+{
+    double th = 0.25 * skin * skin;
+    double m = 0.0;
+    int flag = 0;
+    for (int i = 0; i < n; ++i) {
+        double dv[3];
+        double d2 = sep_f64(pos4 + 4 * (size_t)i, ref4 + 4 * (size_t)i, L, periodic, dv);
+        if (d2 > m) m = d2;
+        if (d2 > th) flag = 1;
+    }
+    *max_d2 = m;
+    return flag;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Lennard-Jones interaction (Sec. 4.1: V(r) = 4 eps [(s/r)^12 - (s/r)^6];    */
+/* pair force 24 eps (2 s^12/r^14 - s^6/r^8) (x_p - x_q), truncated at r_cut) */
+/* ------------------------------------------------------------------------ */
+
+/* Pair inclusion test.  With mask_f32 != 0 the decision r2 < rc^2 is taken in
+ * single precision on the single-precision positions (which the FP64 input
+ * holds exactly), as a single-precision caller decides it; otherwise in FP64. */
+static int pair_inside(const double *xi, const double *xj, const double L[3],
+                       const int periodic[3], double rc, int mask_f32, double dv[3])
+{
+    double r2 = sep_f64(xi, xj, L, periodic, dv);
+    if (mask_f32) {
+        float a[3] = {(float)xi[0], (float)xi[1], (float)xi[2]};
+        float b[3] = {(float)xj[0], (float)xj[1], (float)xj[2]};
+        float df[3];
+        return sep_f32(a, b, L, periodic, df) < (float)(rc * rc);
+    }
+    return r2 < rc * rc;
+}
+
+/* Forces, potential energy U = sum_{i<j} V(r_ij), virial
+ * W = sum_{i<j} r_ij . F_ij and the number of interacting pairs.  Each pair
+ * is visited once and applied to both particles (Newton's third law, the
+ * symmetric interaction of Sec. 4.1).  force4 is [n][4] (w = per-particle
+ * half pair energy).  out[0]=U, out[1]=W, out[2]=pairs. Returns 0 or 1. */
+int orc_lj_forces(int n, const double *pos4, const double L[3], const int periodic[3],
+                  double eps, double sigma, double rc, int mask_f32,
+                  double *force4, double out[3])
+{
+    orc_cells cl;
+    double r_cell = mask_f32 ? rc * (1.0 + 1.0 / 65536.0) : rc;
+    if (cells_build(&cl, n, NULL, pos4, L, periodic, r_cell)) return 1;
+    memset(force4, 0, sizeof(double) * 4 * (size_t)n);
+    double U = 0.0, W = 0.0, pairs = 0.0;
+    double s2 = sigma * sigma, s6 = s2 * s2 * s2, s12 = s6 * s6;
+    uint32_t *cand = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) {
+        const double *xi = pos4 + 4 * (size_t)i;
+        int m = stencil_candidates(&cl, periodic, cl.cell[i], cand);
+        for (int t = 0; t < m; ++t) {
+            uint32_t j = cand[t];
+            if (j > (uint32_t)i) {
+                double dv[3];
+                const double *xj = pos4 + 4 * (size_t)j;
+                if (pair_inside(xi, xj, L, periodic, rc, mask_f32, dv)) {
+                    double r2 = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2];
+                    double r6 = r2 * r2 * r2;
+                    double r8 = r6 * r2, r14 = r6 * r6 * r2;
+                    double f = 24.0 * eps * (2.0 * s12 / r14 - s6 / r8);
+                    double v = 4.0 * eps * (s12 / (r6 * r6) - s6 / r6);
+                    for (int d = 0; d < 3; ++d) {
+                        force4[4 * (size_t)i + d] += f * dv[d];
+                        force4[4 * (size_t)j + d] -= f * dv[d];
+                    }
+                    force4[4 * (size_t)i + 3] += 0.5 * v;
+                    force4[4 * (size_t)j + 3] += 0.5 * v;
+                    U += v;
+                    W += f * r2;
+                    pairs += 1.0;
+                }
+            }
+        }
+    }
+    free(cand);
+    cells_free(&cl);
+    out[0] = U;
+    out[1] = W;
+    out[2] = pairs;
+    return 0;
+}
+
+/* Forces on one particle i by scanning all n particles (sampled checks). */
+void orc_lj_force_one(int n, const double *pos4, const double L[3], const int periodic[3],
+                      double eps, double sigma, double rc, int mask_f32, int i, double f_out[4])
+{
+    double s2 = sigma * sigma, s6 = s2 * s2 * s2, s12 = s6 * s6;
+    f_out[0] = f_out[1] = f_out[2] = f_out[3] = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double dv[3];
+        if (j == i) continue;
+        if (!pair_inside(pos4 + 4 * (size_t)i, pos4 + 4 * (size_t)j, L, periodic, rc, mask_f32, dv))
+            continue;
+        double r2 = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2];
+        double r6 = r2 * r2 * r2;
+        double f = 24.0 * eps * (2.0 * s12 / (r6 * r6 * r2) - s6 / (r6 * r2));
+        for (int d = 0; d < 3; ++d) f_out[d] += f * dv[d];
+        f_out[3] += 0.5 * 4.0 * eps * (s12 / (r6 * r6) - s6 / r6);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Velocity Verlet (Listing 4.1 time loop; unit mass)                        */
+/* ------------------------------------------------------------------------ */
+
+/* First half: v += dt/2 F; x += dt v; wrap into the periodic box. */
+void orc_vv_kick_drift(int n, double dt, double *pos4, double *vel4, const double *force4,
+                       const double L[3], const int periodic[3])
+{
+    for (int i = 0; i < n; ++i)
+        for (int d = 0; d < 3; ++d) {
+            size_t k = 4 * (size_t)i + d;
+            vel4[k] = vel4[k] + 0.5 * dt * force4[k];
+            pos4[k] = pos4[k] + dt * vel4[k];
+            if (periodic[d]) pos4[k] = wrap_f64(pos4[k], L[d]);
+        }
+}
+
+/* Second half: v += dt/2 F. */
+void orc_vv_kick(int n, double dt, double *vel4, const double *force4)
+{
+    for (int i = 0; i < n; ++i)
+        for (int d = 0; d < 3; ++d) {
+            size_t k = 4 * (size_t)i + d;
+            vel4[k] = vel4[k] + 0.5 * dt * force4[k];
+        }
+}
+
+/* nsteps of NVE velocity Verlet from (pos4, vel4), in place.  Forces are
+ * recomputed from the positions every step (no Verlet list: the force is the
+ * sum over all pairs inside rc, which a correct Verlet list reproduces).
+ * energies (optional, [nsteps+1][4]) receives KE, U, W, pairs after each
+ * force evaluation, starting with the initial state. */
+int orc_lj_nve(int n, double *pos4, double *vel4, const double L[3], const int periodic[3],
+               double eps, double sigma, double rc, double dt, int nsteps, double *energies)
+{
+    double *f = (double *)malloc(sizeof(double) * 4 * (size_t)(n > 0 ? n : 1));
+    double out[3];
+    if (orc_lj_forces(n, pos4, L, periodic, eps, sigma, rc, 0, f, out)) { free(f); return 1; }
+    for (int s = 0; s <= nsteps; ++s) {
+        if (s > 0) {
+            orc_vv_kick_drift(n, dt, pos4, vel4, f, L, periodic);
+            orc_lj_forces(n, pos4, L, periodic, eps, sigma, rc, 0, f, out);
+            orc_vv_kick(n, dt, vel4, f);
+        }
+        if (energies) {
+            double ke = 0.0;
+            for (int i = 0; i < n; ++i)
+                for (int d = 0; d < 3; ++d) ke += 0.5 * vel4[4 * (size_t)i + d] * vel4[4 * (size_t)i + d];
+            energies[4 * (size_t)s + 0] = ke;
+            energies[4 * (size_t)s + 1] = out[0];
+            energies[4 * (size_t)s + 2] = out[1];
+            energies[4 * (size_t)s + 3] = out[2];
+        }
+    }
+    free(f);
+    return 0;
+}
