@@ -18,8 +18,9 @@
  *     image is unique inside r_cell.
  *   - Cell coordinate: ci = min((int)((float)x * inv), nc-1) with
  *     inv = (float)(nc/L), in single precision for both position precisions.
- *   - Minimum image per periodic dimension: if (d > L/2) d -= L;
- *     else if (d < -L/2) d += L.
+ *   - Minimum image per periodic dimension, d = x_i - x_j: if d > L/2 the
+ *     separation is (x_i - L) - x_j, if d < -L/2 it is x_i - (x_j - L)
+ *     (the exact image shift first, then one rounded subtraction).
  *   - Squared distance: r2 = fma(dz,dz, fma(dy,dy, dx*dx)) in the precision
  *     of the positions; a pair is inside a radius r iff r2 < (T)(r*r).
  *
@@ -160,19 +161,28 @@ void orc_counting_sort(int n, int ncell, const uint32_t *cell,
 /* Pair geometry                                                             */
 /* ------------------------------------------------------------------------ */
 
-static float min_image_f32(float d, float L)
+/* Minimum-image separation of one periodic coordinate, x_i - x_j.  When the
+ * plain difference exceeds L/2 the image shift is applied to the coordinate
+ * lying above L/2 before subtracting: (x_i - L) - x_j or x_i - (x_j - L).
+ * That shift is exact (both operands within a factor 2), so the separation
+ * carries one rounding, like a pair inside the box; shifting after the
+ * subtraction would round twice and lose the low bits of the small
+ * coordinate. */
+static float sep1_f32(float xi, float xj, float L)
 {
     float h = 0.5f * L;
-    if (d > h) d = d - L;
-    else if (d < -h) d = d + L;
+    float d = xi - xj;
+    if (d > h) d = (xi - L) - xj;
+    else if (d < -h) d = xi - (xj - L);
     return d;
 }
 
-static double min_image_f64(double d, double L)
+static double sep1_f64(double xi, double xj, double L)
 {
     double h = 0.5 * L;
-    if (d > h) d = d - L;
-    else if (d < -h) d = d + L;
+    double d = xi - xj;
+    if (d > h) d = (xi - L) - xj;
+    else if (d < -h) d = xi - (xj - L);
     return d;
 }
 
@@ -180,22 +190,16 @@ static double min_image_f64(double d, double L)
 static float sep_f32(const float *xi, const float *xj, const double L[3],
                      const int periodic[3], float dv[3])
 {
-    for (int d = 0; d < 3; ++d) {
-        float t = xi[d] - xj[d];
-        if (periodic[d]) t = min_image_f32(t, (float)L[d]);
-        dv[d] = t;
-    }
+    for (int d = 0; d < 3; ++d)
+        dv[d] = periodic[d] ? sep1_f32(xi[d], xj[d], (float)L[d]) : xi[d] - xj[d];
     return fmaf(dv[2], dv[2], fmaf(dv[1], dv[1], dv[0] * dv[0]));
 }
 
 static double sep_f64(const double *xi, const double *xj, const double L[3],
                       const int periodic[3], double dv[3])
 {
-    for (int d = 0; d < 3; ++d) {
-        double t = xi[d] - xj[d];
-        if (periodic[d]) t = min_image_f64(t, L[d]);
-        dv[d] = t;
-    }
+    for (int d = 0; d < 3; ++d)
+        dv[d] = periodic[d] ? sep1_f64(xi[d], xj[d], L[d]) : xi[d] - xj[d];
     return fma(dv[2], dv[2], fma(dv[1], dv[1], dv[0] * dv[0]));
 }
 
