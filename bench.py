@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark of the LJ hot path (the MD test case of Sec. 4.1) on GB300.
+
+Workload: 1,000,188 LJ particles (FCC 63^3 x 4, density 0.8442, T* = 0.72,
+rc = 2.5, skin 0.3, dt = 0.005), FP32 pair math with FP64 energy / virial
+reductions; one step = VV kick+drift, rebuild test, device-gated cell-list +
+Verlet rebuild, LJ force sweep, VV kick, replayed from a CUDA graph.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line (rank 0).  Under torchrun (N > 1) every rank advances its
+own independent replica (the path does not shard); timing is the max over
+ranks and `value` is all ranks' steps / that time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LJ steps/s & pair-interactions/s at 1M atoms (FP32 vs FP64) ; adjoint/forward cost"
+UNIT = "steps/s"
+WORKLOAD = "lj_1m"
+FALLBACK_HBM_GBS = 6800.0
+
+# DRAM traffic per launch of the force kernel from one ncu capture, valid only
+# while the kernel source hashes to the recorded value (else reported null).
+# Filled from the ncu summary under profiles/ (see the design doc).
+NCU_TRAFFIC = {"lj.cu": {"sha": None, "bytes_per_launch": None}}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=100)
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--kernel-reps", type=int, default=50)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ dist ---
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks ---
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while active."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.idx), "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.f is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------- peaks ---
+
+def hbm_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def traffic_for(kernel_file: str):
+    rec = NCU_TRAFFIC.get(kernel_file)
+    if not rec or not rec["sha"]:
+        return None
+    src = os.path.join(ROOT, "paper_1804_07598_gb300", "csrc", kernel_file)
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return rec["bytes_per_launch"] if sha == rec["sha"] else None
+
+
+# -------------------------------------------------------------- the arms ---
+
+def cpu_baseline(nsteps: int):
+    """The oracle as it stands (single-threaded plain C, FP64) on the host:
+    `nsteps` NVE steps of the full 1,000,188-particle workload."""
+    import numpy as np  # noqa: F401
+    import oracle
+    from paper_1804_07598_gb300 import inputs
+    wl = inputs.WORKLOADS[WORKLOAD]
+    pos, vel, L = inputs.lj_state(wl)
+    t0 = time.perf_counter()
+    oracle.lj_nve(pos, vel, L, (1, 1, 1), wl.eps, wl.sigma, wl.rc, wl.dt, nsteps, record=False)
+    dt = time.perf_counter() - t0
+    # lj_nve evaluates nsteps + 1 force sweeps; count nsteps steps over the whole time
+    return {"value": nsteps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{nsteps} FP64 NVE steps of the full {wl.n}-particle workload "
+                      f"(+1 initial force sweep), plain C oracle, single thread, {dt:.1f} s"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    from paper_1804_07598_gb300 import inputs
+    import oracle
+    wl = inputs.WORKLOADS[WORKLOAD]
+    pos, vel, L = inputs.lj_state(wl)
+    oracle.build()
+    # warm-up steps, then K timed steps (each one oracle NVE step of the full workload)
+    import numpy as np
+    p, v = pos, vel
+    for _ in range(args.warmup):
+        p, v, _ = oracle.lj_nve(p, v, L, (1, 1, 1), wl.eps, wl.sigma, wl.rc, wl.dt, 1, record=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        p, v, _ = oracle.lj_nve(p, v, L, (1, 1, 1), wl.eps, wl.sigma, wl.rc, wl.dt, 1, record=False)
+    dt = time.perf_counter() - t0
+    val = args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD}: {wl.n} LJ particles, FCC 63^3x4, rho 0.8442, rc 2.5, skin 0.3, "
+                                   f"dt 0.005", "l2": "n/a (host)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"each step = one FP64 oracle NVE step (two force sweeps) of the full "
+                                       f"{wl.n}-particle workload, single thread"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+    from paper_1804_07598_gb300 import build as fbuild
+    from paper_1804_07598_gb300 import fpm, inputs
+    from paper_1804_07598_gb300.md import LJSystem
+
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    fbuild.build()
+    wl = inputs.WORKLOADS[WORKLOAD]
+    pos, vel, L = inputs.lj_state(wl, jitter_seed=7 + rank)
+    s = LJSystem(pos, vel, L, eps=wl.eps, sigma=wl.sigma, rc=wl.rc, skin=wl.skin, dt=wl.dt, precision="f32")
+    # warm-up (eager steps, then graph capture of one step and replays)
+    s.step(max(0, args.warmup // 2))
+    g = s.capture(steps_per_graph=1)
+    for _ in range(args.warmup - args.warmup // 2):
+        g.replay()
+    s.check_status()
+    torch.cuda.synchronize()
+    l0 = fpm.launches
+    s.step(1)  # count the kernels of one step (eager, same calls as the graph)
+    per_step_launches = fpm.launches - l0
+    torch.cuda.synchronize()
+    st0 = s.device_status().nrebuild
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier(ws)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        barrier(ws)
+    ms_local = e0.elapsed_time(e1)
+    ms = max_over_ranks(ms_local, ws)
+    st = s.check_status()
+    rebuilds = st.nrebuild - st0
+    obs = s.observables()
+    pairs = obs["pairs"]
+    steps_per_s = ws * args.steps / (ms / 1e3)
+
+    # force kernel alone: burst timing on the launching stream, same inputs
+    nn_sum = int(s.nn[: s.n].sum().item())
+    torch.cuda.synchronize()
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        s.compute_forces()
+    k0.record()
+    for _ in range(args.kernel_reps):
+        s.compute_forces()
+    k1.record()
+    torch.cuda.synchronize()
+    force_us = 1e3 * k0.elapsed_time(k1) / args.kernel_reps
+    alg_bytes = 4 * nn_sum + 4 * s.n + 16 * s.n + 16 * s.n  # list + counts + own position + force
+    peak, peak_kind = hbm_peak()
+    achieved = alg_bytes / (force_us * 1e-6) / 1e9
+
+    # FP64 path, same workload
+    s64 = LJSystem(pos, vel, L, eps=wl.eps, sigma=wl.sigma, rc=wl.rc, skin=wl.skin, dt=wl.dt, precision="f64")
+    s64.step(3)
+    g64 = s64.capture(steps_per_graph=1)
+    for _ in range(3):
+        g64.replay()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.fp64_steps):
+        g64.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    fp64_steps_per_s = args.fp64_steps / (e1_ms := e0.elapsed_time(e1)) * 1e3
+    del s64, g64
+
+    # end to end through the public API with host buffers: every step copies the
+    # state in from pinned host memory and reads state + energies back
+    hp = torch.empty_like(s.pos, device="cpu").pin_memory()
+    hv = torch.empty_like(s.vel, device="cpu").pin_memory()
+    he = torch.empty(3, dtype=torch.float64).pin_memory()
+    hp.copy_(s.pos)
+    hv.copy_(s.vel)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        s.pos.copy_(hp, non_blocking=True)
+        s.vel.copy_(hv, non_blocking=True)
+        g.replay()
+        hp.copy_(s.pos, non_blocking=True)
+        hv.copy_(s.vel, non_blocking=True)
+        he.copy_(s.energy, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(e2e_s, ws)
+    h2d = hp.numel() * hp.element_size() + hv.numel() * hv.element_size()
+    d2h = h2d + he.numel() * he.element_size()
+    s.check_status()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        cpu = cpu_baseline(args.cpu_steps)
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": steps_per_s, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: {wl.n} LJ particles (FCC 63^3 x 4), rho 0.8442, T* 0.72, rc 2.5, "
+                               f"skin 0.3, dt 0.005, FP32 pair math + FP64 reductions, CUDA graph of 1 step",
+                   "l2": "inputs larger than L2 (neighbour list %d MB)" % (4 * nn_sum // 2 ** 20),
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "1 gpu"},
+        "pair_interactions_per_s": pairs * steps_per_s,
+        "pairs_per_step": pairs,
+        "list_slots_per_step": nn_sum,
+        "rebuilds_in_timed_region": int(rebuilds),
+        "fp64_steps_per_s": fp64_steps_per_s * ws,
+        "fp32_over_fp64": steps_per_s / (fp64_steps_per_s * ws),
+        "roofline": {"kernel": "k_lj_forces<float>", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "peak_kind": f"{peak_kind} (burst, kernel timed alone)", "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic_for("lj.cu"),
+                     "alg_bytes_per_launch": alg_bytes, "launch_us": force_us},
+        "e2e": {"value": ws * args.e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": per_step_launches * args.steps,
+        "clocks": clk.summary(),
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

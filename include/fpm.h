@@ -1,0 +1,236 @@
+/*
+ * fpm.h -- C ABI of libfpm, the GB300 (sm_103a) particle hot path of
+ * OpenFPM (arXiv 1804.07598): cell lists, Verlet lists, the Lennard-Jones and
+ * SPH pair sweeps, velocity Verlet and the adjoint of the LJ force.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every array argument is a DEVICE pointer owned by the caller (the library
+ *    allocates nothing).  The library never frees or retains a pointer after
+ *    the call returns.
+ *  - Calls are asynchronous on the given stream (0 = the legacy default
+ *    stream).  FPM_OK means the arguments were valid and the work was
+ *    enqueued; conditions found on the device (neighbour-list overflow, a
+ *    particle outside a non-periodic box, a device wait that gave up) are
+ *    latched in the caller's fpm_dev_status block, read back by the caller
+ *    and turned into a status by fpm_status_from_device().
+ *  - Host-side argument errors return FPM_ERR_INVALID (or FPM_ERR_WORKSPACE)
+ *    and enqueue nothing; a failed launch returns FPM_ERR_CUDA.  The text of
+ *    the last error of the calling thread is returned by fpm_last_error().
+ *  - No call synchronises the device, allocates, or touches host memory other
+ *    than its by-value / by-pointer host arguments, so every call may be
+ *    captured into a CUDA graph.
+ *  - Particle arrays are 4-vectors: FPM_F32 -> float4 (16 B, 16-B aligned),
+ *    FPM_F64 -> double4 (32 B, 32-B aligned), component w unused on input
+ *    unless stated.  Positions
+ *    live in the box [0,L0) x [0,L1) x [0,L2); mass is 1 (reduced units).
+ *  - Neighbour lists are "ELL" column-major: entry k of particle i is
+ *    nbr[k*ld + i] with ld = fpm_nbr_ld(n), so that consecutive particles
+ *    read consecutive words.
+ */
+#ifndef FPM_H
+#define FPM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque CUDA stream (a cudaStream_t / CUstream). */
+typedef struct CUstream_st *fpm_stream;
+
+typedef enum {
+    FPM_OK = 0,
+    FPM_ERR_INVALID = 1,   /* bad argument; nothing enqueued                     */
+    FPM_ERR_CAPACITY = 2,  /* a neighbour list needed more than `cap` entries    */
+    FPM_ERR_DOMAIN = 3,    /* a particle lay outside a non-periodic dimension    */
+    FPM_ERR_CUDA = 4,      /* CUDA launch / runtime error                        */
+    FPM_ERR_TIMEOUT = 5,   /* a bounded device wait gave up                      */
+    FPM_ERR_WORKSPACE = 6  /* workspace pointer null or smaller than required    */
+} fpm_status;
+
+typedef enum { FPM_F32 = 0, FPM_F64 = 1 } fpm_prec;
+
+/* The simulation domain: the paper's Box and per-dimension boundary
+ * conditions (Listing 4.1, Sec. 4.1: Box<3> + bc[3] = {PERIODIC,...}).
+ * The box starts at the origin; a periodic dimension requires
+ * L > 2 * r_cell * (1 + 2^-10) for the cutoff r_cell it is used with. */
+typedef struct {
+    double L[3];
+    int32_t periodic[3];
+} fpm_box;
+
+/* Cell grid of a cell list (Sec. 2 "Cell Lists [45]"; getCellListSym,
+ * Listing 4.1).  nc[d] = floor(L[d] / (r_cell * (1 + 2^-12))), forced to 1 in
+ * a periodic dimension where it would be < 3 (every particle of that
+ * dimension is then a candidate); inv[d] = (float)(nc[d] / L[d]). */
+typedef struct {
+    int32_t nc[3];
+    int32_t ncell;
+    float inv[3];
+    float pad;
+} fpm_grid;
+
+/* Device-side status block (caller-allocated in device memory, 64 bytes,
+ * zero-filled before first use).  Written by the kernels with atomics. */
+typedef struct {
+    uint32_t flags;        /* bit 0 capacity, bit 1 domain, bit 2 timeout        */
+    uint32_t max_nn;       /* largest neighbour count seen by a Verlet build      */
+    uint32_t rebuild;      /* 1 after fpm_verlet_check found a displacement > skin/2 */
+    uint32_t nrebuild;     /* number of gated rebuilds performed                  */
+    uint32_t max_disp2;    /* float bits of the largest squared displacement      */
+    uint32_t bad_index;    /* a particle index that raised FPM_ERR_DOMAIN         */
+    uint32_t reserved[10];
+} fpm_dev_status;
+
+#define FPM_FLAG_CAPACITY 1u
+#define FPM_FLAG_DOMAIN 2u
+#define FPM_FLAG_TIMEOUT 4u
+
+/* ------------------------------------------------------------------ */
+/* Errors and helpers (host only)                                       */
+/* ------------------------------------------------------------------ */
+
+/* Static text of a status code. */
+const char *fpm_status_string(fpm_status s);
+
+/* Text of the last error raised on the calling thread ("" if none). */
+const char *fpm_last_error(void);
+
+/* Maps a host copy of the device status block to the first latched error
+ * (CAPACITY, then DOMAIN, then TIMEOUT) or FPM_OK. */
+fpm_status fpm_status_from_device(const fpm_dev_status *host_copy);
+
+/* Leading dimension of an ELL neighbour list for n particles:
+ * (n + 31) rounded down to a multiple of 32. */
+int64_t fpm_nbr_ld(int32_t n);
+
+/* Cell grid for cutoff r_cell in box (see fpm_grid).  Host only.
+ * FPM_ERR_INVALID if r_cell <= 0, a length <= 0, a periodic length below
+ * 2 r_cell (1 + 2^-10) or more than 2^31 - 1 cells. */
+fpm_status fpm_grid_make(const fpm_box *box, double r_cell, fpm_grid *out);
+
+/* ------------------------------------------------------------------ */
+/* Cell list (Sec. 2, cell lists [45]; Sec. 3.6, cache-friendly         */
+/* re-sorting; getCellListSym / updateCellListSym, Listing 4.1)         */
+/* ------------------------------------------------------------------ */
+
+/* Bytes of device workspace fpm_celllist_build needs for n particles on the
+ * given grid at precision prec (16-byte aligned base required). */
+fpm_status fpm_celllist_workspace(int32_t n, const fpm_grid *grid, fpm_prec prec, size_t *bytes);
+
+/* Builds the cell list of n particles:
+ *   1. wrap every periodic coordinate into [0,L) (one correction step),
+ *   2. cell coordinate ci = min((int)((float)x * inv), nc-1) per dimension,
+ *      linear cell id (cz*ncy + cy)*ncx + cx,
+ *   3. stable counting sort by cell (ties keep the input order),
+ *   4. exclusive scan of the cell counts into cell_start[ncell+1],
+ *   5. reorder: pos_out[k] = wrapped pos_in[perm[k]], vel_out[k] =
+ *      vel_in[perm[k]], id_out[k] = id_in[perm[k]] (or perm[k] when id_in is
+ *      NULL).
+ * pos_in/pos_out : [n] float4|double4; may alias (in-place reorder).
+ * vel_in/vel_out : [n] float4|double4 or both NULL; may alias.
+ * id_in          : [n] uint32 or NULL; id_out : [n] uint32 or NULL; may alias.
+ * cell_start     : [grid->ncell + 1] uint32 (output).
+ * perm           : [n] uint32 (output), input index of sorted slot k.
+ * workspace      : >= fpm_celllist_workspace() bytes, contents need no init.
+ * d_status       : device status block or NULL; FPM_FLAG_DOMAIN is latched
+ *                  (and the particle binned into the nearest cell) for a
+ *                  particle outside a non-periodic dimension.
+ * d_gate         : NULL, or a device word; when it holds 0 at run time every
+ *                  kernel of the call returns at once (device-gated rebuild).
+ * Deterministic: identical inputs give bit-identical outputs. */
+fpm_status fpm_celllist_build(const fpm_box *box, const fpm_grid *grid, int32_t n, fpm_prec prec,
+                              const void *pos_in, const void *vel_in, const uint32_t *id_in,
+                              void *pos_out, void *vel_out, uint32_t *id_out,
+                              uint32_t *cell_start, uint32_t *perm,
+                              void *workspace, size_t workspace_bytes,
+                              fpm_dev_status *d_status, const uint32_t *d_gate, fpm_stream stream);
+
+/* Gathers a per-particle property into sorted order: dst[k] = src[perm[k]],
+ * elem_bytes in {4, 8, 16, 32}; src and dst must not alias. */
+fpm_status fpm_reorder(int32_t n, int32_t elem_bytes, const uint32_t *perm, const void *src, void *dst,
+                       const uint32_t *d_gate, fpm_stream stream);
+
+/* ------------------------------------------------------------------ */
+/* Verlet lists (Sec. 2, Verlet lists [46]; Sec. 4.1)                   */
+/* ------------------------------------------------------------------ */
+
+/* Full Verlet list of n particles sorted by fpm_celllist_build on a grid
+ * made with r_cell >= r_list: for every i, every j != i of the 27 (or fewer)
+ * neighbouring cells with r2 < (T)(r_list^2), where per periodic dimension
+ * d = x_i - x_j, replaced by (x_i - L) - x_j if d > L/2 and by
+ * x_i - (x_j - L) if d < -L/2 (the exact image shift first, then one rounded
+ * subtraction), and r2 = fma(dz,dz, fma(dy,dy, dx*dx)), all in the
+ * positions' precision.
+ * pos     : [n] sorted, wrapped positions.   cell_start : [ncell+1].
+ * cap     : entries reserved per particle; nbr : [cap * fpm_nbr_ld(n)] uint32
+ *           (ELL, entry k of i at nbr[k*ld + i]); nn : [n] uint32, the number
+ *           of stored entries (min(count, cap)).  A count above cap latches
+ *           FPM_FLAG_CAPACITY; d_status->max_nn receives the largest count.
+ * pos_ref : [n] (same type as pos) receives pos, the reference positions of
+ *           the displacement test (may be NULL).
+ * d_gate  : as in fpm_celllist_build.  After a gated build the gate word is
+ *           cleared and d_status->nrebuild incremented.
+ * The order of entries within a list is not part of the contract; the set is. */
+fpm_status fpm_verlet_build(const fpm_box *box, const fpm_grid *grid, int32_t n, fpm_prec prec,
+                            const void *pos, const uint32_t *cell_start, double r_list, int32_t cap,
+                            uint32_t *nbr, uint32_t *nn, void *pos_ref,
+                            fpm_dev_status *d_status, uint32_t *d_gate, fpm_stream stream);
+
+/* Verlet rebuild test: sets d_status->rebuild = 1 when some particle moved
+ * (minimum image) by more than skin/2 since pos_ref, judged in the
+ * positions' precision as d2 > (T)(skin^2 / 4); d_status->max_disp2 receives
+ * the largest d2 (atomic max; as float bits).  Never clears the flag. */
+fpm_status fpm_verlet_check(const fpm_box *box, int32_t n, fpm_prec prec, const void *pos,
+                            const void *pos_ref, double skin, fpm_dev_status *d_status,
+                            fpm_stream stream);
+
+/* ------------------------------------------------------------------ */
+/* Lennard-Jones pair sweep (Sec. 4.1: V(r) = 4 eps[(s/r)^12 - (s/r)^6],  */
+/* pair force 24 eps (2 s^12 / r^14 - s^6 / r^8) (x_p - x_q) of           */
+/* Listing 4.1, truncated at r_cut, applied over the Verlet list)          */
+/* ------------------------------------------------------------------ */
+
+/* Bytes of workspace for fpm_lj_forces / fpm_kinetic (partial sums and a
+ * completion counter).  The workspace must be ZERO-FILLED once before its
+ * first use; every call leaves its counter at zero again. */
+fpm_status fpm_reduce_workspace(int32_t n, size_t *bytes);
+
+/* Forces of the truncated (unshifted) LJ potential over the full Verlet
+ * list: F_i = sum_j 24 eps (2 s^12/r^14 - s^6/r^8) (x_i - x_j) over entries
+ * with r2 < (T)(rc^2) (r2 as in fpm_verlet_build).  Pair arithmetic and the
+ * per-particle accumulation run in the positions' precision.
+ * force     : [n] float4|double4; w = 1/2 sum_j V(r_ij), the particle's share
+ *             of the potential energy.
+ * d_energy  : [3] double: U = sum_{i<j} V, W = sum_{i<j} r_ij . F_ij and
+ *             the number of interacting pairs.  Reduced in FP64 in a fixed
+ *             order (bit-reproducible).  May be NULL (no reduction).
+ * workspace : fpm_reduce_workspace() bytes (zero-filled once).            */
+fpm_status fpm_lj_forces(const fpm_box *box, int32_t n, fpm_prec prec, const void *pos,
+                         const uint32_t *nbr, const uint32_t *nn, int32_t cap,
+                         double eps, double sigma, double rc,
+                         void *force, double *d_energy, void *workspace, size_t workspace_bytes,
+                         fpm_stream stream);
+
+/* ------------------------------------------------------------------ */
+/* Velocity Verlet (Listing 4.1 time loop: v += dt/2 F; x += dt v; ...;   */
+/* v += dt/2 F), unit mass                                                */
+/* ------------------------------------------------------------------ */
+
+/* half = 0: v += dt/2 F; x += dt v; wrap periodic coordinates into [0,L).
+ * half = 1: v += dt/2 F.  pos is untouched when half = 1 (may be NULL). */
+fpm_status fpm_vv_step(const fpm_box *box, int32_t n, fpm_prec prec, int32_t half, double dt,
+                       void *pos, void *vel, const void *force, fpm_stream stream);
+
+/* Kinetic energy and momentum in FP64 (fixed-order, bit-reproducible):
+ * d_out[0] = 1/2 sum |v|^2, d_out[1..3] = sum v. */
+fpm_status fpm_kinetic(int32_t n, fpm_prec prec, const void *vel, double *d_out,
+                       void *workspace, size_t workspace_bytes, fpm_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FPM_H */

@@ -1,0 +1,214 @@
+// fpm_common.cuh -- device helpers shared by the libfpm kernels (not by the
+// oracle).  Geometry conventions are those stated in include/fpm.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fpm.h"
+
+namespace fpm {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4_32a; };
+template <typename T> using V4 = typename Vec4<T>::type;
+
+// The box as the kernels see it, in the path's precision.  h = L/2 exactly.
+template <typename T> struct BoxT {
+    T L[3];
+    T h[3];
+    int per[3];
+};
+
+template <typename T> inline BoxT<T> make_box(const fpm_box &b)
+{
+    BoxT<T> o;
+    for (int d = 0; d < 3; ++d) {
+        o.L[d] = (T)b.L[d];
+        o.h[d] = (T)0.5 * o.L[d];
+        o.per[d] = b.periodic[d] ? 1 : 0;
+    }
+    return o;
+}
+
+struct GridD {
+    int nc[3];
+    float inv[3];
+};
+
+inline GridD make_grid(const fpm_grid &g)
+{
+    GridD o;
+    for (int d = 0; d < 3; ++d) {
+        o.nc[d] = g.nc[d];
+        o.inv[d] = g.inv[d];
+    }
+    return o;
+}
+
+// Read-only cached loads of a 4-vector.
+__device__ __forceinline__ float4 ldg4(const float4 *p) { return __ldg(p); }
+__device__ __forceinline__ double4_32a ldg4(const double4_32a *p)
+{
+    const double2 a = __ldg((const double2 *)p), b = __ldg((const double2 *)p + 1);
+    double4_32a r;
+    r.x = a.x;
+    r.y = a.y;
+    r.z = b.x;
+    r.w = b.y;
+    return r;
+}
+
+// Explicitly rounded arithmetic so that no contraction changes a decision the
+// oracle takes with the same operations.
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
+
+// One-step periodic wrap into [0, L).
+template <typename T> __device__ __forceinline__ T wrap1(T x, T L)
+{
+    if (x < (T)0) x = radd(x, L);
+    if (x >= L) x = rsub(x, L);
+    return x;
+}
+
+// Minimum-image separation of one periodic coordinate, x_i - x_j: past L/2
+// the image shift is applied to the coordinate above L/2 first (exact), so the
+// separation carries a single rounding, as for a pair inside the box.
+template <typename T> __device__ __forceinline__ T sep1(T xi, T xj, T L, T h)
+{
+    const T d = rsub(xi, xj);
+    if (d > h) return rsub(rsub(xi, L), xj);
+    if (d < -h) return rsub(xi, rsub(xj, L));
+    return d;
+}
+
+// Separation x_i - x_j under the box and its squared length
+// r2 = fma(dz,dz, fma(dy,dy, dx*dx)).
+template <typename T, typename P>
+__device__ __forceinline__ T separation(const P &pi, const P &pj, const BoxT<T> &b, T &dx, T &dy, T &dz)
+{
+    dx = b.per[0] ? sep1(pi.x, pj.x, b.L[0], b.h[0]) : rsub(pi.x, pj.x);
+    dy = b.per[1] ? sep1(pi.y, pj.y, b.L[1], b.h[1]) : rsub(pi.y, pj.y);
+    dz = b.per[2] ? sep1(pi.z, pj.z, b.L[2], b.h[2]) : rsub(pi.z, pj.z);
+    return rfma(dz, dz, rfma(dy, dy, rmul(dx, dx)));
+}
+
+// Cell coordinate of one wrapped coordinate; bad |= out of [0, L).
+// The decision is taken in single precision for both position precisions.
+__device__ __forceinline__ int cell_coord(float xf, float inv, int nc, bool &bad)
+{
+    if (!(xf >= 0.0f)) {
+        bad = true;
+        return 0;
+    }
+    float s = __fmul_rn(xf, inv);
+    int c = (s >= (float)nc) ? nc : (int)s;
+    return c > nc - 1 ? nc - 1 : c;
+}
+
+template <typename T, typename P>
+__device__ __forceinline__ void cell_of(const P &p, const BoxT<T> &b, const GridD &g, int c[3], bool &bad)
+{
+    const T x[3] = {p.x, p.y, p.z};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        if (x[d] >= b.L[d] || x[d] < (T)0) bad = true;
+        c[d] = cell_coord((float)x[d], g.inv[d], g.nc[d], bad);
+    }
+}
+
+__device__ __forceinline__ uint32_t linear_cell(int cx, int cy, int cz, const GridD &g)
+{
+    return (uint32_t)(((int64_t)cz * g.nc[1] + cy) * g.nc[0] + cx);
+}
+
+__device__ __forceinline__ bool gated_off(const uint32_t *gate)
+{
+    return gate != nullptr && *(volatile const uint32_t *)gate == 0u;
+}
+
+__device__ __forceinline__ void latch_flag(fpm_dev_status *st, uint32_t flag)
+{
+    if (st) atomicOr(&st->flags, flag);
+}
+
+// Warp-level double sum with a fixed shuffle tree (deterministic).
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Deterministic FP64 reduction of NV values per thread across the grid.
+// Every block writes its partial sums to part[blockIdx][NV]; the last block
+// to finish (completion counter) sums the partials in index order and writes
+// out[0..NV); it then resets the counter.  blockDim must be a multiple of 32
+// and <= 1024.  All threads of the block must call it.
+template <int NV>
+__device__ void grid_reduce(double (&v)[NV], double *part, unsigned *counter, double *out)
+{
+    __shared__ double sh[32][NV];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double s = warp_sum(v[k]);
+        if (lane == 0) sh[warp][k] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = lane < nw ? sh[lane][k] : 0.0;
+            s = warp_sum(s);
+            if (lane == 0) part[(size_t)blockIdx.x * NV + k] = s;
+        }
+        if (lane == 0) {
+            __threadfence();
+            unsigned t = atomicAdd(counter, 1u);
+            last = (t == gridDim.x - 1);
+        }
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] += __ldcg(part + (size_t)b * NV + k);
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        double s = warp_sum(acc[k]);
+        if (lane == 0) sh[warp][k] = s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = lane < nw ? sh[lane][k] : 0.0;
+            s = warp_sum(s);
+            if (lane == 0 && out) out[k] = s;
+        }
+        if (lane == 0) *counter = 0u;
+    }
+}
+
+}  // namespace fpm
+
+// Host-side error plumbing (api.cu).
+fpm_status fpm_fail(fpm_status s, const char *fmt, ...);
+fpm_status fpm_check_launch(const char *what);

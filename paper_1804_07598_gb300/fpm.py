@@ -1,0 +1,247 @@
+"""Thin ctypes binding of libfpm (include/fpm.h): same names, argument
+marshalling only.  Every step of the hot path runs in the library's CUDA
+kernels; there is no Python or CPU fallback.  Tensors are torch CUDA tensors
+(device memory and streams are PyTorch's); ``None`` passes NULL.
+
+A call that returns a status other than FPM_OK raises ``FpmError`` carrying
+the library's last-error text.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SO_PATH = os.path.join(HERE, "libfpm.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "fpm.h")
+
+FPM_OK, FPM_ERR_INVALID, FPM_ERR_CAPACITY, FPM_ERR_DOMAIN, FPM_ERR_CUDA, FPM_ERR_TIMEOUT, FPM_ERR_WORKSPACE = range(7)
+FPM_F32, FPM_F64 = 0, 1
+FPM_FLAG_CAPACITY, FPM_FLAG_DOMAIN, FPM_FLAG_TIMEOUT = 1, 2, 4
+STATUS_BYTES = 64
+
+_c = ctypes
+_VP = _c.c_void_p
+
+
+class FpmError(RuntimeError):
+    def __init__(self, status: int, text: str):
+        super().__init__(f"fpm status {status}: {text}")
+        self.status = status
+
+
+class fpm_box(_c.Structure):
+    _fields_ = [("L", _c.c_double * 3), ("periodic", _c.c_int32 * 3)]
+
+
+class fpm_grid(_c.Structure):
+    _fields_ = [("nc", _c.c_int32 * 3), ("ncell", _c.c_int32), ("inv", _c.c_float * 3), ("pad", _c.c_float)]
+
+    @property
+    def shape(self):
+        return tuple(self.nc)
+
+
+class fpm_dev_status(_c.Structure):
+    _fields_ = [("flags", _c.c_uint32), ("max_nn", _c.c_uint32), ("rebuild", _c.c_uint32),
+                ("nrebuild", _c.c_uint32), ("max_disp2", _c.c_uint32), ("bad_index", _c.c_uint32),
+                ("reserved", _c.c_uint32 * 10)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# Number of kernels the wrappers below have enqueued (each wrapper knows how
+# many kernels its C call launches); benchmarks read it to report launches.
+launches = 0
+
+
+def _count(k: int):
+    global launches
+    launches += int(k)
+
+# name -> (restype, argtypes); mirrors include/fpm.h
+_SIG = {
+    "fpm_status_string": (_c.c_char_p, [_c.c_int]),
+    "fpm_last_error": (_c.c_char_p, []),
+    "fpm_status_from_device": (_c.c_int, [_c.POINTER(fpm_dev_status)]),
+    "fpm_nbr_ld": (_c.c_int64, [_c.c_int32]),
+    "fpm_grid_make": (_c.c_int, [_c.POINTER(fpm_box), _c.c_double, _c.POINTER(fpm_grid)]),
+    "fpm_celllist_workspace": (_c.c_int, [_c.c_int32, _c.POINTER(fpm_grid), _c.c_int, _c.POINTER(_c.c_size_t)]),
+    "fpm_celllist_build": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _c.c_int,
+                                      _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _c.c_size_t, _VP, _VP, _VP]),
+    "fpm_reorder": (_c.c_int, [_c.c_int32, _c.c_int32, _VP, _VP, _VP, _VP, _VP]),
+    "fpm_verlet_build": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _c.c_int, _VP, _VP,
+                                    _c.c_double, _c.c_int32, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "fpm_verlet_check": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.c_int, _VP, _VP, _c.c_double, _VP, _VP]),
+    "fpm_reduce_workspace": (_c.c_int, [_c.c_int32, _c.POINTER(_c.c_size_t)]),
+    "fpm_lj_forces": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.c_int, _VP, _VP, _VP, _c.c_int32,
+                                 _c.c_double, _c.c_double, _c.c_double, _VP, _VP, _VP, _c.c_size_t, _VP]),
+    "fpm_vv_step": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.c_int, _c.c_int32, _c.c_double, _VP, _VP, _VP,
+                               _VP]),
+    "fpm_kinetic": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _VP, _VP, _c.c_size_t, _VP]),
+}
+
+
+def header_functions() -> list:
+    """Names of every function declared in include/fpm.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fpm_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib():
+    """Load libfpm.so (built in-tree by paper_1804_07598_gb300.build).  Fails
+    loudly when the library is missing: there is no fallback path."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(SO_PATH):
+                raise RuntimeError(f"libfpm.so not built ({SO_PATH}); run paper_1804_07598_gb300.build.build()")
+            L = _c.CDLL(SO_PATH)
+            for name, (res, args) in _SIG.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+        return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("libfpm takes device tensors only")
+    if not t.is_contiguous():
+        raise ValueError("libfpm takes contiguous tensors only")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(status: int):
+    if status != FPM_OK:
+        raise FpmError(status, lib().fpm_last_error().decode())
+
+
+def _nbytes(t):
+    return 0 if t is None else t.numel() * t.element_size()
+
+
+def make_box(L, periodic=(1, 1, 1)) -> fpm_box:
+    b = fpm_box()
+    for d in range(3):
+        b.L[d] = float(L[d] if hasattr(L, "__len__") else L)
+        b.periodic[d] = int(periodic[d] if hasattr(periodic, "__len__") else periodic)
+    return b
+
+
+def prec_of(t) -> int:
+    import torch
+    return FPM_F64 if t.dtype == torch.float64 else FPM_F32
+
+
+# ------------------------------------------------------------------ helpers
+
+def fpm_status_string(s: int) -> str:
+    return lib().fpm_status_string(int(s)).decode()
+
+
+def fpm_last_error() -> str:
+    return lib().fpm_last_error().decode()
+
+
+def fpm_status_from_device(host_status: fpm_dev_status) -> int:
+    return lib().fpm_status_from_device(_c.byref(host_status))
+
+
+def fpm_nbr_ld(n: int) -> int:
+    return int(lib().fpm_nbr_ld(int(n)))
+
+
+def fpm_grid_make(box: fpm_box, r_cell: float) -> fpm_grid:
+    g = fpm_grid()
+    _check(lib().fpm_grid_make(_c.byref(box), float(r_cell), _c.byref(g)))
+    return g
+
+
+def fpm_celllist_workspace(n: int, grid: fpm_grid, prec: int) -> int:
+    b = _c.c_size_t(0)
+    _check(lib().fpm_celllist_workspace(int(n), _c.byref(grid), int(prec), _c.byref(b)))
+    return b.value
+
+
+def fpm_reduce_workspace(n: int) -> int:
+    b = _c.c_size_t(0)
+    _check(lib().fpm_reduce_workspace(int(n), _c.byref(b)))
+    return b.value
+
+
+def read_status(d_status) -> fpm_dev_status:
+    """Copy a device status block (a 64-byte tensor) to the host."""
+    h = d_status.detach().cpu().contiguous()
+    s = fpm_dev_status()
+    _c.memmove(_c.addressof(s), h.data_ptr(), STATUS_BYTES)
+    return s
+
+
+# ------------------------------------------------------------------ kernels
+
+def fpm_celllist_build(box, grid, n, prec, pos_in, vel_in, id_in, pos_out, vel_out, id_out, cell_start, perm,
+                       workspace, d_status=None, d_gate=None, stream=None):
+    _check(lib().fpm_celllist_build(_c.byref(box), _c.byref(grid), int(n), int(prec), _ptr(pos_in), _ptr(vel_in),
+                                    _ptr(id_in), _ptr(pos_out), _ptr(vel_out), _ptr(id_out), _ptr(cell_start),
+                                    _ptr(perm), _ptr(workspace), _nbytes(workspace), _ptr(d_status), _ptr(d_gate),
+                                    _stream(stream)))
+    _count(6 if n > 0 else 3)
+
+
+def fpm_reorder(n, elem_bytes, perm, src, dst, d_gate=None, stream=None):
+    _check(lib().fpm_reorder(int(n), int(elem_bytes), _ptr(perm), _ptr(src), _ptr(dst), _ptr(d_gate),
+                             _stream(stream)))
+    _count(1 if n > 0 else 0)
+
+
+def fpm_verlet_build(box, grid, n, prec, pos, cell_start, r_list, cap, nbr, nn, pos_ref=None, d_status=None,
+                     d_gate=None, stream=None):
+    _check(lib().fpm_verlet_build(_c.byref(box), _c.byref(grid), int(n), int(prec), _ptr(pos), _ptr(cell_start),
+                                  float(r_list), int(cap), _ptr(nbr), _ptr(nn), _ptr(pos_ref), _ptr(d_status),
+                                  _ptr(d_gate), _stream(stream)))
+    _count((1 if n > 0 else 0) + (1 if d_gate is not None else 0))
+
+
+def fpm_verlet_check(box, n, prec, pos, pos_ref, skin, d_status, stream=None):
+    _check(lib().fpm_verlet_check(_c.byref(box), int(n), int(prec), _ptr(pos), _ptr(pos_ref), float(skin),
+                                  _ptr(d_status), _stream(stream)))
+    _count(1 if n > 0 else 0)
+
+
+def fpm_lj_forces(box, n, prec, pos, nbr, nn, cap, eps, sigma, rc, force, d_energy=None, workspace=None,
+                  stream=None):
+    _check(lib().fpm_lj_forces(_c.byref(box), int(n), int(prec), _ptr(pos), _ptr(nbr), _ptr(nn), int(cap),
+                               float(eps), float(sigma), float(rc), _ptr(force), _ptr(d_energy), _ptr(workspace),
+                               _nbytes(workspace), _stream(stream)))
+    _count(1 if (n > 0 or d_energy is not None) else 0)
+
+
+def fpm_vv_step(box, n, prec, half, dt, pos, vel, force, stream=None):
+    _check(lib().fpm_vv_step(_c.byref(box), int(n), int(prec), int(half), float(dt), _ptr(pos), _ptr(vel),
+                             _ptr(force), _stream(stream)))
+    _count(1 if n > 0 else 0)
+
+
+def fpm_kinetic(n, prec, vel, d_out, workspace, stream=None):
+    _check(lib().fpm_kinetic(int(n), int(prec), _ptr(vel), _ptr(d_out), _ptr(workspace), _nbytes(workspace),
+                             _stream(stream)))
+    _count(1)

@@ -1,0 +1,146 @@
+"""Lennard-Jones NVE driver over libfpm (the MD test case of Sec. 4.1 /
+Listing 4.1): state buffers in device memory, the velocity-Verlet step with a
+device-gated Verlet rebuild, and CUDA-graph capture of whole steps.
+
+One step (all on the current stream, no host synchronisation):
+    fpm_vv_step(half=0)         v += dt/2 F; x += dt v; wrap
+    fpm_verlet_check            rebuild flag := max |x - x_ref| > skin/2
+    fpm_celllist_build [gated]  re-bin and reorder in place
+    fpm_verlet_build   [gated]  new list, x_ref := x, flag cleared
+    fpm_lj_forces               F, U, W, pairs
+    fpm_vv_step(half=1)         v += dt/2 F
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import torch
+
+from . import fpm
+
+
+def default_cap(rho: float, r_list: float) -> int:
+    """Neighbour-list capacity: 1.5x the mean full-list count at density rho,
+    rounded up to a multiple of 8 (at least 32)."""
+    mean = 4.0 / 3.0 * math.pi * r_list ** 3 * rho
+    return max(32, int(math.ceil(1.5 * mean / 8.0)) * 8)
+
+
+class LJSystem:
+    def __init__(self, pos, vel, L, periodic=(1, 1, 1), eps=1.0, sigma=1.0, rc=2.5, skin=0.3, dt=0.005,
+                 precision="f32", cap=None, device="cuda"):
+        self.dtype = torch.float32 if precision == "f32" else torch.float64
+        self.prec = fpm.FPM_F32 if precision == "f32" else fpm.FPM_F64
+        self.device = torch.device(device)
+        pos = torch.as_tensor(np.asarray(pos), dtype=torch.float64)
+        vel = torch.as_tensor(np.asarray(vel), dtype=torch.float64)
+        n = pos.shape[0]
+        self.n = n
+        self.L = np.broadcast_to(np.asarray(L, np.float64), (3,)).copy()
+        self.periodic = tuple(int(p) for p in periodic)
+        self.eps, self.sigma, self.rc, self.skin, self.dt = float(eps), float(sigma), float(rc), float(skin), float(dt)
+        self.r_list = self.rc + self.skin
+        self.box = fpm.make_box(self.L, self.periodic)
+        self.grid = fpm.fpm_grid_make(self.box, self.r_list)
+        vol = float(np.prod(self.L))
+        self.cap = int(cap) if cap else default_cap(max(n, 1) / vol, self.r_list)
+        self.ld = fpm.fpm_nbr_ld(n)
+        dev, dt_ = self.device, self.dtype
+        self.pos = torch.zeros((n, 4), dtype=dt_, device=dev)
+        self.vel = torch.zeros((n, 4), dtype=dt_, device=dev)
+        self.pos[:, :pos.shape[1]] = pos[:, :4].to(dt_)
+        self.vel[:, :vel.shape[1]] = vel[:, :4].to(dt_)
+        self.pos[:, 3] = 0
+        self.vel[:, 3] = 0
+        self.force = torch.zeros((n, 4), dtype=dt_, device=dev)
+        self.pos_ref = torch.zeros((n, 4), dtype=dt_, device=dev)
+        self.ids = torch.arange(n, dtype=torch.int32, device=dev)
+        self.perm = torch.zeros(max(n, 1), dtype=torch.int32, device=dev)
+        self.cell_start = torch.zeros(self.grid.ncell + 1, dtype=torch.int32, device=dev)
+        self.nbr = torch.zeros(max(1, self.cap * self.ld), dtype=torch.int32, device=dev)
+        self.nn = torch.zeros(max(n, 1), dtype=torch.int32, device=dev)
+        self.status = torch.zeros(fpm.STATUS_BYTES // 4, dtype=torch.int32, device=dev)
+        self.ws_cell = torch.zeros(fpm.fpm_celllist_workspace(n, self.grid, self.prec), dtype=torch.uint8, device=dev)
+        self.ws_red = torch.zeros(fpm.fpm_reduce_workspace(n), dtype=torch.uint8, device=dev)
+        self.energy = torch.zeros(3, dtype=torch.float64, device=dev)
+        self.kin = torch.zeros(4, dtype=torch.float64, device=dev)
+        self._graph = None
+        self.rebuild()
+        self.compute_forces()
+
+    # -- pieces ---------------------------------------------------------
+    @property
+    def gate_ptr(self) -> int:
+        return self.status.data_ptr() + 8  # fpm_dev_status.rebuild
+
+    def rebuild(self, gated: bool = False):
+        gate = self.gate_ptr if gated else None
+        fpm.fpm_celllist_build(self.box, self.grid, self.n, self.prec, self.pos, self.vel, self.ids, self.pos,
+                               self.vel, self.ids, self.cell_start, self.perm, self.ws_cell, self.status, gate)
+        fpm.fpm_verlet_build(self.box, self.grid, self.n, self.prec, self.pos, self.cell_start, self.r_list,
+                             self.cap, self.nbr, self.nn, self.pos_ref, self.status, gate)
+
+    def compute_forces(self):
+        fpm.fpm_lj_forces(self.box, self.n, self.prec, self.pos, self.nbr, self.nn, self.cap, self.eps, self.sigma,
+                          self.rc, self.force, self.energy, self.ws_red)
+
+    def _step(self):
+        fpm.fpm_vv_step(self.box, self.n, self.prec, 0, self.dt, self.pos, self.vel, self.force)
+        fpm.fpm_verlet_check(self.box, self.n, self.prec, self.pos, self.pos_ref, self.skin, self.status)
+        self.rebuild(gated=True)
+        self.compute_forces()
+        fpm.fpm_vv_step(self.box, self.n, self.prec, 1, self.dt, None, self.vel, self.force)
+
+    # -- public -----------------------------------------------------------
+    def step(self, nsteps: int = 1):
+        for _ in range(int(nsteps)):
+            self._step()
+
+    def capture(self, steps_per_graph: int = 1):
+        """Capture `steps_per_graph` whole steps into one CUDA graph."""
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                for _ in range(steps_per_graph):
+                    self._step()
+        torch.cuda.current_stream().wait_stream(s)
+        self._graph = (g, steps_per_graph)
+        return g
+
+    def run(self, nsteps: int):
+        """nsteps steps, through the captured graph when there is one."""
+        if self._graph is None:
+            self.step(nsteps)
+            return
+        g, k = self._graph
+        for _ in range(nsteps // k):
+            g.replay()
+        self.step(nsteps % k)
+
+    def kinetic(self):
+        fpm.fpm_kinetic(self.n, self.prec, self.vel, self.kin, self.ws_red)
+        return self.kin
+
+    def observables(self) -> dict:
+        """KE, U, W, pairs, momentum (host values; synchronises)."""
+        k = self.kinetic().cpu().numpy()
+        e = self.energy.cpu().numpy()
+        return dict(KE=float(k[0]), U=float(e[0]), W=float(e[1]), pairs=int(round(e[2])), P=k[1:4].copy())
+
+    def device_status(self) -> fpm.fpm_dev_status:
+        return fpm.read_status(self.status)
+
+    def check_status(self):
+        st = self.device_status()
+        code = fpm.fpm_status_from_device(st)
+        if code != fpm.FPM_OK:
+            raise fpm.FpmError(code, f"device status flags={st.flags} max_nn={st.max_nn} cap={self.cap}")
+        return st
+
+    def state_numpy(self):
+        """(pos, vel, ids) in the current (sorted) order, as numpy."""
+        return (self.pos.cpu().numpy(), self.vel.cpu().numpy(), self.ids.cpu().numpy().view(np.uint32))

@@ -25,3 +25,18 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def fpm_lib():
+    """libfpm built in-tree (compiled on demand) and loaded."""
+    from paper_1804_07598_gb300 import build, fpm
+    build.build()
+    return fpm.lib()
+
+
+@pytest.fixture(scope="session")
+def cuda(fpm_lib):
+    import torch
+    torch.cuda.init()
+    return torch.device("cuda:0")

@@ -1,0 +1,70 @@
+"""The C ABI library builds, loads and exports every function its header
+declares; host-side argument checks work without a GPU."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_1804_07598_gb300 import fpm
+
+
+def test_header_symbols_exported(fpm_lib):
+    names = fpm.header_functions()
+    assert len(names) >= 14
+    missing = [n for n in names if not hasattr(fpm_lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_header():
+    """The Python binding declares every header function (same names)."""
+    assert set(fpm.header_functions()) <= set(fpm._SIG)
+
+
+def test_grid_rule(fpm_lib):
+    import oracle
+    for L, per, r in [((16.79596, 16.79596, 16.79596), (1, 1, 1), 2.8), ((105.81456,) * 3, (1, 1, 1), 2.8),
+                      ((6.46, 6.46, 6.46), (1, 1, 1), 2.8), ((1.6, 0.67, 0.4), (0, 0, 0), 0.0098),
+                      ((9.0, 12.0, 5.7), (1, 1, 1), 2.8), ((6.0, 6.0, 6.0), (0, 0, 0), 2.8)]:
+        g = fpm.fpm_grid_make(fpm.make_box(L, per), r)
+        nc, inv = oracle.cell_grid(L, per, r)
+        assert tuple(g.nc) == tuple(int(x) for x in nc)
+        assert np.array_equal(np.array(g.inv, np.float32), inv)
+        assert g.ncell == int(np.prod(nc))
+
+
+def test_invalid_arguments_rejected(fpm_lib):
+    with pytest.raises(fpm.FpmError) as e:
+        fpm.fpm_grid_make(fpm.make_box((5.0, 5.0, 5.0)), 2.8)
+    assert e.value.status == fpm.FPM_ERR_INVALID
+    assert "2*r_cell" in fpm.fpm_last_error()
+    with pytest.raises(fpm.FpmError):
+        fpm.fpm_grid_make(fpm.make_box((5.0, 5.0, 5.0)), -1.0)
+    g = fpm.fpm_grid_make(fpm.make_box((10.0, 10.0, 10.0)), 2.8)
+    # null pointers / bad sizes return before touching the device
+    assert fpm_lib.fpm_celllist_build(ctypes.byref(fpm.make_box((10.0,) * 3)), ctypes.byref(g), 10, 0, None, None,
+                                      None, None, None, None, None, None, None, 0, None, None, None) \
+        == fpm.FPM_ERR_INVALID
+    assert fpm_lib.fpm_lj_forces(ctypes.byref(fpm.make_box((10.0,) * 3)), 10, 0, None, None, None, 0, 1.0, 1.0, 2.5,
+                                 None, None, None, 0, None) == fpm.FPM_ERR_INVALID
+    assert fpm_lib.fpm_vv_step(ctypes.byref(fpm.make_box((10.0,) * 3)), 10, 0, 2, 0.005, None, None, None, None) \
+        == fpm.FPM_ERR_INVALID
+    assert fpm.fpm_status_string(fpm.FPM_ERR_CAPACITY).startswith("neighbour")
+
+
+def test_status_decode(fpm_lib):
+    s = fpm.fpm_dev_status()
+    assert fpm.fpm_status_from_device(s) == fpm.FPM_OK
+    s.flags = fpm.FPM_FLAG_DOMAIN
+    assert fpm.fpm_status_from_device(s) == fpm.FPM_ERR_DOMAIN
+    s.flags = fpm.FPM_FLAG_DOMAIN | fpm.FPM_FLAG_CAPACITY
+    assert fpm.fpm_status_from_device(s) == fpm.FPM_ERR_CAPACITY
+    assert ctypes.sizeof(fpm.fpm_dev_status) == fpm.STATUS_BYTES
+
+
+def test_workspace_sizes(fpm_lib):
+    g = fpm.fpm_grid_make(fpm.make_box((105.81456,) * 3), 2.8)
+    b32 = fpm.fpm_celllist_workspace(1000188, g, fpm.FPM_F32)
+    b64 = fpm.fpm_celllist_workspace(1000188, g, fpm.FPM_F64)
+    assert b64 > b32 > 1000188 * 16
+    assert fpm.fpm_reduce_workspace(1000188) >= 256 + (1000188 // 256) * 24
+    assert fpm.fpm_nbr_ld(1000188) % 32 == 0 and fpm.fpm_nbr_ld(1000188) >= 1000188
