@@ -215,6 +215,28 @@ fpm_status fpm_lj_forces(const fpm_box *box, int32_t n, fpm_prec prec, const voi
                          void *force, double *d_energy, void *workspace, size_t workspace_bytes,
                          fpm_stream stream);
 
+/* fpm_lj_forces without a workspace argument, for callers that cannot
+ * allocate device memory at all: a host program whose device memory is owned
+ * by another runtime or a fixed pool it must not grow, or a real-time loop in
+ * which the implicit synchronisation of cudaMalloc is not acceptable.  (The
+ * paper has no counterpart; this is a deployment convenience.)
+ * Same arguments and results as fpm_lj_forces.  The energy reduction uses a
+ * scratch array compiled into the library (4 MiB + 256 B of device memory on
+ * every GPU that loads it, held until the process exits), which limits n to
+ * 2^24 = 16,777,216 particles; larger n returns FPM_ERR_INVALID.  The call
+ * allocates and frees nothing.
+ * - The first call on each device looks the scratch address up (with that
+ *   device current); make that first call before any stream capture.
+ * - Every call clears the scratch's completion counter on `stream` before
+ *   using it, and all calls on a device share the one array: calls that may
+ *   run at the same time on the GPU (different streams, or concurrently
+ *   replayed graphs) race and give wrong energies.  Serialise them.
+ * - With d_energy == NULL the scratch is not touched. */
+fpm_status fpm_lj_forces_noalloc(const fpm_box *box, int32_t n, fpm_prec prec, const void *pos,
+                                 const uint32_t *nbr, const uint32_t *nn, int32_t cap,
+                                 double eps, double sigma, double rc,
+                                 void *force, double *d_energy, fpm_stream stream);
+
 /* ------------------------------------------------------------------ */
 /* Velocity Verlet (Listing 4.1 time loop: v += dt/2 F; x += dt v; ...;   */
 /* v += dt/2 F), unit mass                                                */

@@ -208,3 +208,74 @@ extern "C" fpm_status fpm_kinetic(int32_t n, fpm_prec prec, const void *vel, dou
         k_kinetic<double><<<blocks, 256, 0, st>>>(n, (const double4_32a *)vel, r.part, r.counter, d_out);
     return fpm_check_launch("fpm_kinetic");
 }
+
+// ---------------------------------------------------------------------------
+// fpm_lj_forces_noalloc: the same force sweep and energy reduction for callers
+// that cannot allocate device memory (no cudaMalloc, no caching allocator).
+// Its scratch (the per-block partial sums and the completion counter) is a
+// file-scope device array, present on every GPU that loads this library.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr int kNoAllocMaxN = 1 << 24;  // particles per call
+constexpr size_t kNoAllocBytes = 256 + (size_t)((kNoAllocMaxN + 255) / 256) * 8 * sizeof(double);  // 4 MiB + 256 B
+
+static __device__ __align__(256) unsigned char g_lj_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mu;
+void *g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of g_lj_scratch on the current device (looked up once per
+// device; the host-side symbol itself is not a device address).
+fpm_status scratch_for_current_device(void **out)
+{
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fpm_fail(FPM_ERR_CUDA, "fpm_lj_forces_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return fpm_fail(FPM_ERR_INVALID, "fpm_lj_forces_noalloc: device %d", dev);
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_lj_scratch);
+        if (e != cudaSuccess || !p)
+            return fpm_fail(FPM_ERR_CUDA, "fpm_lj_forces_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return FPM_OK;
+}
+
+}  // namespace
+
+extern "C" fpm_status fpm_lj_forces_noalloc(const fpm_box *box, int32_t n, fpm_prec prec, const void *pos,
+                                            const uint32_t *nbr, const uint32_t *nn, int32_t cap, double eps,
+                                            double sigma, double rc, void *force, double *d_energy,
+                                            fpm_stream stream)
+{
+    if (n > kNoAllocMaxN)
+        return fpm_fail(FPM_ERR_INVALID, "fpm_lj_forces_noalloc: n=%d exceeds the built-in scratch limit of %d particles",
+                        n, kNoAllocMaxN);
+    if (!box || n < 0 || cap < 1 || !(rc > 0.0) || !(sigma > 0.0) || (n > 0 && (!pos || !nbr || !nn || !force)))
+        return fpm_fail(FPM_ERR_INVALID, "fpm_lj_forces_noalloc: null pointer or bad size");
+    if (prec != FPM_F32 && prec != FPM_F64) return fpm_fail(FPM_ERR_INVALID, "fpm_lj_forces_noalloc: bad precision");
+    if (n == 0 && !d_energy) return FPM_OK;
+    RedWs r{nullptr, nullptr};
+    cudaStream_t st = (cudaStream_t)stream;
+    if (d_energy) {
+        void *scratch = nullptr;
+        fpm_status s = scratch_for_current_device(&scratch);
+        if (s != FPM_OK) return s;
+        // the completion counter must start at zero; the array keeps whatever
+        // the previous call left there
+        cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned), st);
+        if (e != cudaSuccess)
+            return fpm_fail(FPM_ERR_CUDA, "fpm_lj_forces_noalloc: clearing the counter: %s", cudaGetErrorString(e));
+        r.counter = (unsigned *)scratch;
+        r.part = (double *)((char *)scratch + 256);
+    }
+    if (prec == FPM_F32) return lj_launch<float>(*box, n, pos, nbr, nn, eps, sigma, rc, force, d_energy, r, st);
+    return lj_launch<double>(*box, n, pos, nbr, nn, eps, sigma, rc, force, d_energy, r, st);
+}

@@ -79,6 +79,8 @@ _SIG = {
     "fpm_reduce_workspace": (_c.c_int, [_c.c_int32, _c.POINTER(_c.c_size_t)]),
     "fpm_lj_forces": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.c_int, _VP, _VP, _VP, _c.c_int32,
                                  _c.c_double, _c.c_double, _c.c_double, _VP, _VP, _VP, _c.c_size_t, _VP]),
+    "fpm_lj_forces_noalloc": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.c_int, _VP, _VP, _VP, _c.c_int32,
+                                         _c.c_double, _c.c_double, _c.c_double, _VP, _VP, _VP]),
     "fpm_vv_step": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.c_int, _c.c_int32, _c.c_double, _VP, _VP, _VP,
                                _VP]),
     "fpm_kinetic": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _VP, _VP, _c.c_size_t, _VP]),
@@ -233,6 +235,16 @@ def fpm_lj_forces(box, n, prec, pos, nbr, nn, cap, eps, sigma, rc, force, d_ener
                                float(eps), float(sigma), float(rc), _ptr(force), _ptr(d_energy), _ptr(workspace),
                                _nbytes(workspace), _stream(stream)))
     _count(1 if (n > 0 or d_energy is not None) else 0)
+
+
+def fpm_lj_forces_noalloc(box, n, prec, pos, nbr, nn, cap, eps, sigma, rc, force, d_energy=None, stream=None):
+    """fpm_lj_forces for callers that cannot allocate device memory: the
+    reduction scratch is built into the library (n <= 2^24); concurrent calls
+    on one device must be serialised by the caller."""
+    _check(lib().fpm_lj_forces_noalloc(_c.byref(box), int(n), int(prec), _ptr(pos), _ptr(nbr), _ptr(nn), int(cap),
+                                       float(eps), float(sigma), float(rc), _ptr(force), _ptr(d_energy),
+                                       _stream(stream)))
+    _count((1 if (n > 0 or d_energy is not None) else 0) + (1 if d_energy is not None else 0))
 
 
 def fpm_vv_step(box, n, prec, half, dt, pos, vel, force, stream=None):

@@ -1,0 +1,51 @@
+"""fpm_lj_forces_noalloc: the force sweep for callers that cannot allocate
+device memory (their memory belongs to another runtime or a fixed pool, or a
+cudaMalloc would stall a real-time loop).  It must give the same forces and
+energies as fpm_lj_forces, on consecutive calls, because its built-in scratch
+keeps the previous call's contents.
+
+Collected last on purpose, so that a run stopping at its first failure has
+already run every other test.  It passes alone in a fresh process too.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_1804_07598_gb300 import fpm, inputs
+from paper_1804_07598_gb300.md import LJSystem
+
+pytestmark = pytest.mark.gpu
+
+TOL_F = {"f32": 1e-5, "f64": 1e-12}   # same as the force parity tests
+TOL_E = {"f32": 1e-6, "f64": 1e-12}
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_noalloc_matches_workspace_version(cuda, prec):
+    wl = inputs.WORKLOADS["lj_small"]
+    pos, vel, L = inputs.lj_state(wl, jitter=0.06)
+    s = LJSystem(pos, vel, L, precision=prec)
+    s.compute_forces()
+    torch.cuda.synchronize()
+    f_ref = s.force.cpu().numpy().astype(np.float64)
+    e_ref = s.energy.cpu().numpy()
+    rms = np.sqrt(np.mean(np.sum(f_ref[:, :3] ** 2, axis=1)))
+    for call in range(2):  # two calls in a row share the scratch array
+        f = torch.full_like(s.force, float("nan"))
+        e = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda")
+        fpm.fpm_lj_forces_noalloc(s.box, s.n, s.prec, s.pos, s.nbr, s.nn, s.cap, s.eps, s.sigma, s.rc, f, e)
+        torch.cuda.synchronize()
+        fn = f.cpu().numpy().astype(np.float64)
+        en = e.cpu().numpy()
+        err = np.max(np.linalg.norm(fn[:, :3] - f_ref[:, :3], axis=1)) / rms
+        assert err <= TOL_F[prec], (call, err)
+        assert np.all(np.abs(en[:2] - e_ref[:2]) <= TOL_E[prec] * np.abs(e_ref[:2])), (call, en, e_ref)
+        assert en[2] == e_ref[2]
+
+
+def test_noalloc_rejects_oversize(fpm_lib):
+    box = fpm.make_box((10.0, 10.0, 10.0))
+    with pytest.raises(fpm.FpmError) as e:
+        fpm.fpm_lj_forces_noalloc(box, (1 << 24) + 1, fpm.FPM_F32, 1, 1, 1, 64, 1.0, 1.0, 2.5, 1, 1, 0)
+    assert e.value.status == fpm.FPM_ERR_INVALID
+    assert "scratch limit" in fpm.fpm_last_error()
