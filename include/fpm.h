@@ -24,9 +24,12 @@
  *    FPM_F64 -> double4 (32 B, 32-B aligned), component w unused on input
  *    unless stated.  Positions
  *    live in the box [0,L0) x [0,L1) x [0,L2); mass is 1 (reduced units).
- *  - Neighbour lists are "ELL" column-major: entry k of particle i is
- *    nbr[k*ld + i] with ld = fpm_nbr_ld(n), so that consecutive particles
- *    read consecutive words.
+ *  - A Verlet list is an object in caller memory (fpm_verlet_list_bytes):
+ *    per-tile descriptors followed by 16-bit entries laid out column-major
+ *    (entry k of particle i in word (k/2)*ld + i, ld = fpm_nbr_ld(n)), so
+ *    that consecutive particles read consecutive words.  Entries index the
+ *    tile's staged neighbourhood, not particles; fpm_verlet_decode turns a
+ *    list into particle indices.
  */
 #ifndef FPM_H
 #define FPM_H
@@ -65,12 +68,15 @@ typedef struct {
 /* Cell grid of a cell list (Sec. 2 "Cell Lists [45]"; getCellListSym,
  * Listing 4.1).  nc[d] = floor(L[d] / (r_cell * (1 + 2^-12))), forced to 1 in
  * a periodic dimension where it would be < 3 (every particle of that
- * dimension is then a candidate); inv[d] = (float)(nc[d] / L[d]). */
+ * dimension is then a candidate); inv[d] = (float)(nc[d] / L[d]).
+ * tiles_x: the pair sweeps work on tiles of consecutive cells along x; each
+ * row of nc[0] cells is split into tiles_x tiles of near-equal width (at most
+ * 14 cells).  ntiles = tiles_x * nc[1] * nc[2]. */
 typedef struct {
     int32_t nc[3];
     int32_t ncell;
     float inv[3];
-    float pad;
+    int32_t tiles_x;
 } fpm_grid;
 
 /* Device-side status block (caller-allocated in device memory, 64 bytes,
@@ -107,10 +113,12 @@ fpm_status fpm_status_from_device(const fpm_dev_status *host_copy);
  * (n + 31) rounded down to a multiple of 32. */
 int64_t fpm_nbr_ld(int32_t n);
 
-/* Cell grid for cutoff r_cell in box (see fpm_grid).  Host only.
+/* Cell grid for cutoff r_cell in box (see fpm_grid).  Host only.  n_hint,
+ * the expected particle count (<= 0: unknown), only sets the tile width:
+ * about 170 particles per tile, i.e. round(170 ncell / n_hint) cells.
  * FPM_ERR_INVALID if r_cell <= 0, a length <= 0, a periodic length below
- * 2 r_cell (1 + 2^-10) or more than 2^31 - 1 cells. */
-fpm_status fpm_grid_make(const fpm_box *box, double r_cell, fpm_grid *out);
+ * 2 r_cell (1 + 2^-10) or more than 2^24 cells. */
+fpm_status fpm_grid_make(const fpm_box *box, double r_cell, int32_t n_hint, fpm_grid *out);
 
 /* ------------------------------------------------------------------ */
 /* Cell list (Sec. 2, cell lists [45]; Sec. 3.6, cache-friendly         */
@@ -158,27 +166,42 @@ fpm_status fpm_reorder(int32_t n, int32_t elem_bytes, const uint32_t *perm, cons
 /* Verlet lists (Sec. 2, Verlet lists [46]; Sec. 4.1)                   */
 /* ------------------------------------------------------------------ */
 
+/* Bytes of the Verlet-list object for n particles, grid and capacity cap
+ * (entries per particle).  The object must be 256-byte aligned. */
+fpm_status fpm_verlet_list_bytes(int32_t n, const fpm_grid *grid, int32_t cap, size_t *bytes);
+
 /* Full Verlet list of n particles sorted by fpm_celllist_build on a grid
- * made with r_cell >= r_list: for every i, every j != i of the 27 (or fewer)
- * neighbouring cells with r2 < (T)(r_list^2), where per periodic dimension
- * d = x_i - x_j, replaced by (x_i - L) - x_j if d > L/2 and by
- * x_i - (x_j - L) if d < -L/2 (the exact image shift first, then one rounded
- * subtraction), and r2 = fma(dz,dz, fma(dy,dy, dx*dx)), all in the
- * positions' precision.
- * pos     : [n] sorted, wrapped positions.   cell_start : [ncell+1].
- * cap     : entries reserved per particle; nbr : [cap * fpm_nbr_ld(n)] uint32
- *           (ELL, entry k of i at nbr[k*ld + i]); nn : [n] uint32, the number
- *           of stored entries (min(count, cap)).  A count above cap latches
- *           FPM_FLAG_CAPACITY; d_status->max_nn receives the largest count.
+ * made with r_cell >= r_list, positions unchanged since: for every i, every
+ * j != i of the 27 (or fewer) neighbouring cells with r2 < (T)(r_list^2),
+ * where per periodic dimension d = x_i - x_j, replaced by (x_i - L) - x_j
+ * when j is seen through the upper wall and by x_i - (x_j - L) through the
+ * lower wall (the exact image shift first, then one rounded subtraction),
+ * and r2 = fma(dz,dz, fma(dy,dy, dx*dx)), all in the positions' precision.
+ * (The image is chosen by the cell stencil; for every pair inside r_list it
+ * is the minimum image.)
+ * pos     : [n] sorted positions.     cell_start : [ncell+1].
+ * cap     : entries reserved per particle.
+ * list    : fpm_verlet_list_bytes() bytes, written.  nn : [n] uint32, the
+ *           number of stored entries (min(count, cap)).  A count above cap
+ *           latches FPM_FLAG_CAPACITY (so does a tile neighbourhood of more
+ *           than 65535 particles, whose particles then get nn = 0);
+ *           d_status->max_nn receives the largest count.
  * pos_ref : [n] (same type as pos) receives pos, the reference positions of
  *           the displacement test (may be NULL).
  * d_gate  : as in fpm_celllist_build.  After a gated build the gate word is
  *           cleared and d_status->nrebuild incremented.
- * The order of entries within a list is not part of the contract; the set is. */
+ * Until the next build the positions may move but must not be wrapped: the
+ * image of every listed pair is fixed by the build. */
 fpm_status fpm_verlet_build(const fpm_box *box, const fpm_grid *grid, int32_t n, fpm_prec prec,
                             const void *pos, const uint32_t *cell_start, double r_list, int32_t cap,
-                            uint32_t *nbr, uint32_t *nn, void *pos_ref,
+                            void *list, size_t list_bytes, uint32_t *nn, void *pos_ref,
                             fpm_dev_status *d_status, uint32_t *d_gate, fpm_stream stream);
+
+/* Particle indices of a Verlet list: out[k*ld + i] = j for k < nn[i]
+ * (out : [cap * fpm_nbr_ld(n)] uint32; other slots untouched).  The order of
+ * entries within a list is not part of the contract; the set is. */
+fpm_status fpm_verlet_decode(const fpm_grid *grid, int32_t n, int32_t cap, const void *list,
+                             const uint32_t *nn, uint32_t *out, fpm_stream stream);
 
 /* Verlet rebuild test: sets d_status->rebuild = 1 when some particle moved
  * (minimum image) by more than skin/2 since pos_ref, judged in the
@@ -194,26 +217,32 @@ fpm_status fpm_verlet_check(const fpm_box *box, int32_t n, fpm_prec prec, const 
 /* Listing 4.1, truncated at r_cut, applied over the Verlet list)          */
 /* ------------------------------------------------------------------ */
 
-/* Bytes of workspace for fpm_lj_forces / fpm_kinetic (partial sums and a
- * completion counter).  The workspace must be ZERO-FILLED once before its
- * first use; every call leaves its counter at zero again. */
-fpm_status fpm_reduce_workspace(int32_t n, size_t *bytes);
+/* Bytes of workspace for the FP64 reductions of fpm_lj_forces and
+ * fpm_kinetic (partial sums and a completion counter) for n particles on
+ * grid (grid may be NULL for fpm_kinetic alone).  The workspace must be
+ * ZERO-FILLED once before its first use; every call leaves its counter at
+ * zero again. */
+fpm_status fpm_reduce_workspace(int32_t n, const fpm_grid *grid, size_t *bytes);
 
 /* Forces of the truncated (unshifted) LJ potential over the full Verlet
  * list: F_i = sum_j 24 eps (2 s^12/r^14 - s^6/r^8) (x_i - x_j) over entries
- * with r2 < (T)(rc^2) (r2 as in fpm_verlet_build).  Pair arithmetic and the
- * per-particle accumulation run in the positions' precision.
+ * with r2 < (T)(rc^2) (separation and r2 as in fpm_verlet_build).  Pair
+ * arithmetic and the per-particle accumulation run in the positions'
+ * precision.  box, grid, cap, list and nn as given to fpm_verlet_build.
  * force     : [n] float4|double4; w = 1/2 sum_j V(r_ij), the particle's share
  *             of the potential energy.
  * d_energy  : [3] double: U = sum_{i<j} V, W = sum_{i<j} r_ij . F_ij and
  *             the number of interacting pairs.  Reduced in FP64 in a fixed
  *             order (bit-reproducible).  May be NULL (no reduction).
- * workspace : fpm_reduce_workspace() bytes (zero-filled once).            */
-fpm_status fpm_lj_forces(const fpm_box *box, int32_t n, fpm_prec prec, const void *pos,
-                         const uint32_t *nbr, const uint32_t *nn, int32_t cap,
+ * workspace : fpm_reduce_workspace() bytes (zero-filled once).
+ * d_status  : device status block or NULL; FPM_FLAG_TIMEOUT is latched if a
+ *             tile's bulk copy into shared memory did not complete within
+ *             about 2 s (its particles' forces are then not written). */
+fpm_status fpm_lj_forces(const fpm_box *box, const fpm_grid *grid, int32_t n, fpm_prec prec, const void *pos,
+                         const void *list, const uint32_t *nn, int32_t cap,
                          double eps, double sigma, double rc,
                          void *force, double *d_energy, void *workspace, size_t workspace_bytes,
-                         fpm_stream stream);
+                         fpm_dev_status *d_status, fpm_stream stream);
 
 /* fpm_lj_forces without a workspace argument, for callers that cannot
  * allocate device memory at all: a host program whose device memory is owned
@@ -223,8 +252,8 @@ fpm_status fpm_lj_forces(const fpm_box *box, int32_t n, fpm_prec prec, const voi
  * Same arguments and results as fpm_lj_forces.  The energy reduction uses a
  * scratch array compiled into the library (4 MiB + 256 B of device memory on
  * every GPU that loads it, held until the process exits), which limits n to
- * 2^24 = 16,777,216 particles; larger n returns FPM_ERR_INVALID.  The call
- * allocates and frees nothing.
+ * 2^24 = 16,777,216 particles and the grid to 65,536 tiles; larger sizes
+ * return FPM_ERR_INVALID.  The call allocates and frees nothing.
  * - The first call on each device looks the scratch address up (with that
  *   device current); make that first call before any stream capture.
  * - Every call clears the scratch's completion counter on `stream` before
@@ -232,20 +261,28 @@ fpm_status fpm_lj_forces(const fpm_box *box, int32_t n, fpm_prec prec, const voi
  *   run at the same time on the GPU (different streams, or concurrently
  *   replayed graphs) race and give wrong energies.  Serialise them.
  * - With d_energy == NULL the scratch is not touched. */
-fpm_status fpm_lj_forces_noalloc(const fpm_box *box, int32_t n, fpm_prec prec, const void *pos,
-                                 const uint32_t *nbr, const uint32_t *nn, int32_t cap,
+fpm_status fpm_lj_forces_noalloc(const fpm_box *box, const fpm_grid *grid, int32_t n, fpm_prec prec,
+                                 const void *pos, const void *list, const uint32_t *nn, int32_t cap,
                                  double eps, double sigma, double rc,
-                                 void *force, double *d_energy, fpm_stream stream);
+                                 void *force, double *d_energy, fpm_dev_status *d_status, fpm_stream stream);
 
 /* ------------------------------------------------------------------ */
 /* Velocity Verlet (Listing 4.1 time loop: v += dt/2 F; x += dt v; ...;   */
 /* v += dt/2 F), unit mass                                                */
 /* ------------------------------------------------------------------ */
 
-/* half = 0: v += dt/2 F; x += dt v; wrap periodic coordinates into [0,L).
+/* half = 0: v += dt/2 F; x += dt v.  Positions are not wrapped here (a
+ * Verlet list fixes the periodic image of each pair until the next build);
+ * fpm_celllist_build wraps them.
  * half = 1: v += dt/2 F.  pos is untouched when half = 1 (may be NULL). */
 fpm_status fpm_vv_step(const fpm_box *box, int32_t n, fpm_prec prec, int32_t half, double dt,
                        void *pos, void *vel, const void *force, fpm_stream stream);
+
+/* fpm_vv_step(half = 0) followed by fpm_verlet_check on the new positions,
+ * in one pass over the particles (same results as the two calls). */
+fpm_status fpm_vv_drift_check(const fpm_box *box, int32_t n, fpm_prec prec, double dt, void *pos, void *vel,
+                              const void *force, const void *pos_ref, double skin, fpm_dev_status *d_status,
+                              fpm_stream stream);
 
 /* Kinetic energy and momentum in FP64 (fixed-order, bit-reproducible):
  * d_out[0] = 1/2 sum |v|^2, d_out[1..3] = sum v. */

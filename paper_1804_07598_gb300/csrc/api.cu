@@ -55,7 +55,7 @@ extern "C" int64_t fpm_nbr_ld(int32_t n)
     return ((int64_t)n + 31) / 32 * 32;
 }
 
-extern "C" fpm_status fpm_grid_make(const fpm_box *box, double r_cell, fpm_grid *out)
+extern "C" fpm_status fpm_grid_make(const fpm_box *box, double r_cell, int32_t n_hint, fpm_grid *out)
 {
     if (!box || !out) return fpm_fail(FPM_ERR_INVALID, "fpm_grid_make: null pointer");
     if (!(r_cell > 0.0) || !std::isfinite(r_cell))
@@ -80,15 +80,28 @@ extern "C" fpm_status fpm_grid_make(const fpm_box *box, double r_cell, fpm_grid 
     if (total > (int64_t)(1u << 24))
         return fpm_fail(FPM_ERR_INVALID, "fpm_grid_make: %lld cells exceed the 2^24 limit", (long long)total);
     g.ncell = (int32_t)total;
+    // tile width along x: about 170 particles per tile, at most 14 cells
+    const double per_cell = n_hint > 0 ? (double)n_hint / (double)total : 16.0;
+    int w = (int)std::lround(170.0 / (per_cell > 1e-9 ? per_cell : 1e-9));
+    if (w < 1) w = 1;
+    if (w > 14) w = 14;
+    int tiles = (g.nc[0] + w - 1) / w;
+    if (tiles < 1) tiles = 1;
+    g.tiles_x = tiles;
     *out = g;
     return FPM_OK;
 }
 
-extern "C" fpm_status fpm_reduce_workspace(int32_t n, size_t *bytes)
+extern "C" fpm_status fpm_reduce_workspace(int32_t n, const fpm_grid *grid, size_t *bytes)
 {
     if (!bytes || n < 0) return fpm_fail(FPM_ERR_INVALID, "fpm_reduce_workspace: bad argument");
-    // counter (256 B) + 8 doubles per block of 256 particles (at least one block)
+    // counter (256 B) + 8 doubles per block: blocks of 256 particles, or one
+    // block per cell tile for the pair sweeps
     size_t blocks = ((size_t)n + 255) / 256;
+    if (grid) {
+        const size_t tiles = (size_t)(grid->tiles_x > 0 ? grid->tiles_x : 1) * (size_t)grid->nc[1] * (size_t)grid->nc[2];
+        if (tiles > blocks) blocks = tiles;
+    }
     if (blocks < 1) blocks = 1;
     *bytes = 256 + blocks * 8 * sizeof(double);
     return FPM_OK;

@@ -62,6 +62,13 @@ __device__ __forceinline__ double4_32a ldg4(const double4_32a *p)
     return r;
 }
 
+// Small integer flags carried in the unused w component of a staged 4-vector.
+template <typename T> __device__ __forceinline__ T flags_as(int f);
+template <> __device__ __forceinline__ float flags_as<float>(int f) { return __int_as_float(f); }
+template <> __device__ __forceinline__ double flags_as<double>(int f) { return __longlong_as_double((long long)f); }
+__device__ __forceinline__ int flags_of(float w) { return __float_as_int(w); }
+__device__ __forceinline__ int flags_of(double w) { return (int)__double_as_longlong(w); }
+
 // Explicitly rounded arithmetic so that no contraction changes a decision the
 // oracle takes with the same operations.
 __device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
@@ -142,29 +149,58 @@ __device__ __forceinline__ void latch_flag(fpm_dev_status *st, uint32_t flag)
     if (st) atomicOr(&st->flags, flag);
 }
 
-// Warp-level double sum with a fixed shuffle tree (deterministic).
-__device__ __forceinline__ double warp_sum(double v)
+// Reports a block's rebuild decision: the flag word is set if any thread saw
+// a displacement above the threshold, and max_disp2 raised to the block's
+// largest squared displacement (float bits; one atomic per block, skipped
+// when it cannot raise the value).  All threads of the block must call it.
+__device__ __forceinline__ void disp_report(bool over, float d2, fpm_dev_status *st)
+{
+    __shared__ unsigned s_any, s_max;
+    if (threadIdx.x == 0) {
+        s_any = 0u;
+        s_max = 0u;
+    }
+    __syncthreads();
+    const unsigned any = __ballot_sync(kFull, over);
+    const unsigned m = __reduce_max_sync(kFull, __float_as_uint(d2));
+    if ((threadIdx.x & 31) == 0) {
+        if (any) atomicOr(&s_any, 1u);
+        if (m) atomicMax(&s_max, m);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_any) st->rebuild = 1u;
+        if (s_max > *(volatile unsigned *)&st->max_disp2) atomicMax(&st->max_disp2, s_max);
+    }
+}
+
+// Warp-level sum with a fixed shuffle tree (deterministic: lane 0's result
+// depends only on the 32 inputs).
+template <typename TV> __device__ __forceinline__ TV warp_sum(TV v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     return v;
 }
 
-// Deterministic FP64 reduction of NV values per thread across the grid.
-// Every block writes its partial sums to part[blockIdx][NV]; the last block
-// to finish (completion counter) sums the partials in index order and writes
+// Deterministic reduction of NV values per thread across the grid: within a
+// warp in TV (the caller's accumulation type), from there on in FP64.  Every
+// block writes its partial sums to part[blockIdx][NV]; the last block to
+// finish (completion counter) sums the partials in index order and writes
 // out[0..NV); it then resets the counter.  blockDim must be a multiple of 32
-// and <= 1024.  All threads of the block must call it.
-template <int NV>
-__device__ void grid_reduce(double (&v)[NV], double *part, unsigned *counter, double *out)
+// and <= 1024.  All threads of the block must call it.  (FP64 arithmetic
+// runs at a small fraction of the FP32 rate on this GPU, so the per-thread
+// values are not widened before the warp stage.)
+template <int NV, typename TV>
+__device__ void grid_reduce(TV (&v)[NV], double *part, unsigned *counter, double *out)
 {
     __shared__ double sh[32][NV];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-        double s = warp_sum(v[k]);
-        if (lane == 0) sh[warp][k] = s;
+        const TV s = warp_sum(v[k]);
+        if (lane == 0) sh[warp][k] = (double)s;
     }
     __syncthreads();
     if (warp == 0) {
@@ -212,3 +248,4 @@ __device__ void grid_reduce(double (&v)[NV], double *part, unsigned *counter, do
 // Host-side error plumbing (api.cu).
 fpm_status fpm_fail(fpm_status s, const char *fmt, ...);
 fpm_status fpm_check_launch(const char *what);
+fpm_status fpm_check_grid(const fpm_box *box, const fpm_grid *grid, const char *who);

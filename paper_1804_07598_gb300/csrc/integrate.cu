@@ -1,0 +1,153 @@
+// integrate.cu -- the two halves of velocity Verlet (the time loop of
+// Listing 4.1, Sec. 4.1: v += dt/2 F; x += dt v; ...; v += dt/2 F; unit mass)
+// and the FP64 kinetic-energy / momentum reduction.
+#include "reduce.cuh"
+
+namespace fpm {
+
+// v += dt/2 F; x += dt v.  No wrap: a Verlet list fixes the image of each
+// pair until the next build, which wraps.
+template <typename T>
+__global__ void k_vv_kick_drift(int n, T hdt, T dt, V4<T> *__restrict__ pos, V4<T> *__restrict__ vel,
+                                const V4<T> *__restrict__ force)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    V4<T> x = pos[i], v = vel[i];
+    const V4<T> f = force[i];
+    v.x += hdt * f.x;
+    v.y += hdt * f.y;
+    v.z += hdt * f.z;
+    x.x += dt * v.x;
+    x.y += dt * v.y;
+    x.z += dt * v.z;
+    pos[i] = x;
+    vel[i] = v;
+}
+
+// The same step fused with the Verlet rebuild test on the new positions
+// (fpm_verlet_check), saving a second pass over positions.
+template <typename T>
+__global__ void k_vv_drift_check(BoxT<T> box, int n, T hdt, T dt, V4<T> *__restrict__ pos, V4<T> *__restrict__ vel,
+                                 const V4<T> *__restrict__ force, const V4<T> *__restrict__ ref, T th,
+                                 fpm_dev_status *st)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool over = false;
+    float d2f = 0.0f;
+    if (i < n) {
+        V4<T> x = pos[i], v = vel[i];
+        const V4<T> f = force[i];
+        v.x += hdt * f.x;
+        v.y += hdt * f.y;
+        v.z += hdt * f.z;
+        x.x += dt * v.x;
+        x.y += dt * v.y;
+        x.z += dt * v.z;
+        pos[i] = x;
+        vel[i] = v;
+        T dx, dy, dz;
+        const T d2 = separation(x, ref[i], box, dx, dy, dz);
+        over = d2 > th;
+        d2f = (float)d2;
+    }
+    disp_report(over, d2f, st);
+}
+
+template <typename T>
+__global__ void k_vv_kick(int n, T hdt, V4<T> *__restrict__ vel, const V4<T> *__restrict__ force)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    V4<T> v = vel[i];
+    const V4<T> f = force[i];
+    v.x += hdt * f.x;
+    v.y += hdt * f.y;
+    v.z += hdt * f.z;
+    vel[i] = v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_kinetic(int n, const V4<T> *__restrict__ vel, double *part,
+                                                 unsigned *counter, double *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (i < n) {
+        const V4<T> u = vel[i];
+        const double x = u.x, y = u.y, z = u.z;
+        v[0] = 0.5 * (x * x + y * y + z * z);
+        v[1] = x;
+        v[2] = y;
+        v[3] = z;
+    }
+    grid_reduce<4>(v, part, counter, out);
+}
+
+}  // namespace fpm
+
+using namespace fpm;
+
+extern "C" fpm_status fpm_vv_step(const fpm_box *box, int32_t n, fpm_prec prec, int32_t half, double dt, void *pos,
+                                  void *vel, const void *force, fpm_stream stream)
+{
+    if (!box || n < 0 || (half != 0 && half != 1) || (n > 0 && (!vel || !force || (half == 0 && !pos))))
+        return fpm_fail(FPM_ERR_INVALID, "fpm_vv_step: null pointer or bad argument");
+    if (prec != FPM_F32 && prec != FPM_F64) return fpm_fail(FPM_ERR_INVALID, "fpm_vv_step: bad precision");
+    if (n == 0) return FPM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    if (prec == FPM_F32) {
+        if (half == 0)
+            k_vv_kick_drift<float><<<blocks, 256, 0, st>>>(n, (float)(0.5 * dt), (float)dt, (float4 *)pos,
+                                                           (float4 *)vel, (const float4 *)force);
+        else
+            k_vv_kick<float><<<blocks, 256, 0, st>>>(n, (float)(0.5 * dt), (float4 *)vel, (const float4 *)force);
+    } else {
+        if (half == 0)
+            k_vv_kick_drift<double><<<blocks, 256, 0, st>>>(n, 0.5 * dt, dt, (double4_32a *)pos, (double4_32a *)vel,
+                                                            (const double4_32a *)force);
+        else
+            k_vv_kick<double><<<blocks, 256, 0, st>>>(n, 0.5 * dt, (double4_32a *)vel, (const double4_32a *)force);
+    }
+    return fpm_check_launch("fpm_vv_step");
+}
+
+extern "C" fpm_status fpm_vv_drift_check(const fpm_box *box, int32_t n, fpm_prec prec, double dt, void *pos,
+                                         void *vel, const void *force, const void *pos_ref, double skin,
+                                         fpm_dev_status *d_status, fpm_stream stream)
+{
+    if (!box || n < 0 || !d_status || !(skin >= 0.0) || (n > 0 && (!pos || !vel || !force || !pos_ref)))
+        return fpm_fail(FPM_ERR_INVALID, "fpm_vv_drift_check: null pointer or bad argument");
+    if (prec != FPM_F32 && prec != FPM_F64) return fpm_fail(FPM_ERR_INVALID, "fpm_vv_drift_check: bad precision");
+    if (n == 0) return FPM_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    if (prec == FPM_F32)
+        k_vv_drift_check<float><<<blocks, 256, 0, st>>>(make_box<float>(*box), n, (float)(0.5 * dt), (float)dt,
+                                                        (float4 *)pos, (float4 *)vel, (const float4 *)force,
+                                                        (const float4 *)pos_ref, (float)(0.25 * skin * skin),
+                                                        d_status);
+    else
+        k_vv_drift_check<double><<<blocks, 256, 0, st>>>(make_box<double>(*box), n, 0.5 * dt, dt, (double4_32a *)pos,
+                                                         (double4_32a *)vel, (const double4_32a *)force,
+                                                         (const double4_32a *)pos_ref, 0.25 * skin * skin, d_status);
+    return fpm_check_launch("fpm_vv_drift_check");
+}
+
+extern "C" fpm_status fpm_kinetic(int32_t n, fpm_prec prec, const void *vel, double *d_out, void *workspace,
+                                  size_t workspace_bytes, fpm_stream stream)
+{
+    if (n < 0 || !d_out || (n > 0 && !vel)) return fpm_fail(FPM_ERR_INVALID, "fpm_kinetic: bad argument");
+    if (prec != FPM_F32 && prec != FPM_F64) return fpm_fail(FPM_ERR_INVALID, "fpm_kinetic: bad precision");
+    RedWs r;
+    fpm_status s = red_ws(n, nullptr, workspace, workspace_bytes, "fpm_kinetic", r);
+    if (s != FPM_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int blocks = n > 0 ? (n + 255) / 256 : 1;
+    if (prec == FPM_F32)
+        k_kinetic<float><<<blocks, 256, 0, st>>>(n, (const float4 *)vel, r.part, r.counter, d_out);
+    else
+        k_kinetic<double><<<blocks, 256, 0, st>>>(n, (const double4_32a *)vel, r.part, r.counter, d_out);
+    return fpm_check_launch("fpm_kinetic");
+}

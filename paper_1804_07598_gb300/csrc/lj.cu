@@ -1,212 +1,207 @@
-// lj.cu -- Lennard-Jones pair sweep over the Verlet list (Sec. 4.1: the LJ
-// potential V(r) = 4 eps [(s/r)^12 - (s/r)^6] and the pair force
+// lj.cu -- Lennard-Jones pair sweep over the tiled Verlet list (Sec. 4.1:
+// V(r) = 4 eps [(s/r)^12 - (s/r)^6] and the pair force
 // 24 eps (2 s^12/r^14 - s^6/r^8)(x_p - x_q) of Listing 4.1, truncated at
-// r_cut), the two halves of velocity Verlet (Listing 4.1 time loop) and the
-// FP64 kinetic-energy / momentum reduction.
+// r_cut).
 //
-// The force sweep walks the FULL list (every pair twice, once from each
-// side): no atomics, so forces are bit-reproducible run to run and the sum
-// of forces is the only place Newton's third law is checked.
-#include "fpm_common.cuh"
+// One block per cell tile: the tile's neighbourhood positions are staged in
+// shared memory (tiles.cuh), then one thread per home particle walks its
+// 16-bit list entries, two per 32-bit word, reading neighbours from shared
+// memory.  The sweep covers the FULL list (each pair from both sides): no
+// atomics, bit-reproducible forces.  Energy, virial and the pair count are
+// reduced per block in FP64 and then in a fixed order across blocks.
+#include <mutex>
+
+#include "reduce.cuh"
+#include "tiles.cuh"
 
 namespace fpm {
 
-__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+// 1/x for the pair sweep.  Single precision: the hardware approximation
+// refined by one Newton-Raphson step, y <- y + y (1 - x y) (the classical
+// iteration for the reciprocal); inputs are squared distances (positive,
+// normal).  Double precision: the correctly rounded reciprocal.
+__device__ __forceinline__ float recip(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    const float e = __fmaf_rn(-x, y, 1.0f);
+    return __fmaf_rn(y, e, y);
+}
 __device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_lj_forces(BoxT<T> box, int n, const V4<T> *__restrict__ pos,
-                                                   const uint32_t *__restrict__ nbr, const uint32_t *__restrict__ nn,
-                                                   int64_t ld, T eps24, T eps4, T sig2, T rc2,
-                                                   V4<T> *__restrict__ force, double *part, unsigned *counter,
-                                                   double *out)
+template <typename T> struct LJParams {
+    T eps24, eps4, sig2, rc2;
+};
+
+// One list entry, masked (not branched) by the cutoff test.  With
+// s6 = (sigma^2/r^2)^3 and a = 2 s6^2 - s6, the pair force is
+// 24 eps a / r^2 (x_i - x_j), its virial 24 eps a and its energy
+// 4 eps (s6^2 - s6); the constant factors 24 eps and 4 eps are applied once
+// per particle by the caller, so the sums here are of a/r^2 * d, a, and
+// s6^2 - s6.
+template <typename T, bool FAST, bool SMEM>
+__device__ __forceinline__ void lj_pair(const TileCfg &cfg, const BoxT<T> &box, const TileDesc &d,
+                                        const V4<T> *__restrict__ pos, const V4<T> *__restrict__ st, const V4<T> &pi,
+                                        int s, const LJParams<T> &P, T &fx, T &fy, T &fz, T &u, T &w, uint32_t &np)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    T fx = 0, fy = 0, fz = 0, u = 0, w = 0;
-    uint32_t np = 0;
-    if (i < n) {
+    const V4<T> pj = SMEM ? st[s] : staged_global(d, box, pos, s);
+    T dx, dy, dz;
+    const T r2 = tile_sep<FAST>(pi, pj, box, cfg, dx, dy, dz);
+    const bool in = r2 < P.rc2;
+    const T ir2 = recip(r2);
+    const T s2 = P.sig2 * ir2;
+    const T s6 = s2 * s2 * s2;
+    const T s12 = s6 * s6;
+    const T a = in ? (T)2 * s12 - s6 : (T)0;
+    const T g = a * ir2;
+    fx += g * dx;
+    fy += g * dy;
+    fz += g * dz;
+    w += a;
+    u += in ? s12 - s6 : (T)0;
+    np += in ? 1u : 0u;
+}
+
+template <typename T, bool FAST, bool SMEM>
+__device__ __forceinline__ void lj_sweep(const TileCfg &cfg, const BoxT<T> &box, const TileDesc &d,
+                                         const V4<T> *__restrict__ pos, const V4<T> *__restrict__ st,
+                                         const V4<T> &pi, uint32_t m, const uint32_t *__restrict__ col, int64_t ld,
+                                         const LJParams<T> &P, T &fx, T &fy, T &fz, T &u, T &w, uint32_t &np)
+{
+    // list words are loaded kChunk at a time, one chunk ahead of their use;
+    // full chunks run without per-entry guards
+    constexpr uint32_t kChunk = 4;
+    const uint32_t nw = (m + 1u) >> 1;
+    const uint32_t nfull = (m >> 1) / kChunk * kChunk;  // words whose both entries exist, in whole chunks
+    uint32_t cur[kChunk], nxt[kChunk];
+    const uint32_t *p = col;  // next word to load
+#pragma unroll
+    for (uint32_t q = 0; q < kChunk; ++q) {
+        cur[q] = q < nfull ? __ldcs(p) : 0u;
+        p += ld;
+    }
+    for (uint32_t w0 = 0; w0 < nfull; w0 += kChunk) {
+        const bool more = w0 + kChunk < nfull;
+#pragma unroll
+        for (uint32_t q = 0; q < kChunk; ++q) {
+            nxt[q] = more ? __ldcs(p) : 0u;
+            p += ld;
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < kChunk; ++q) {
+            lj_pair<T, FAST, SMEM>(cfg, box, d, pos, st, pi, (int)(cur[q] & 0xffffu), P, fx, fy, fz, u, w, np);
+            lj_pair<T, FAST, SMEM>(cfg, box, d, pos, st, pi, (int)(cur[q] >> 16), P, fx, fy, fz, u, w, np);
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < kChunk; ++q) cur[q] = nxt[q];
+    }
+    for (uint32_t wi = nfull; wi < nw; ++wi) {
+        const uint32_t wv = __ldcs(col + (int64_t)wi * ld);
+        lj_pair<T, FAST, SMEM>(cfg, box, d, pos, st, pi, (int)(wv & 0xffffu), P, fx, fy, fz, u, w, np);
+        if (2u * wi + 1u < m)
+            lj_pair<T, FAST, SMEM>(cfg, box, d, pos, st, pi, (int)(wv >> 16), P, fx, fy, fz, u, w, np);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads)
+    k_lj_tiles(TileCfg cfg, BoxT<T> box, const V4<T> *__restrict__ pos, const TileDesc *__restrict__ descs,
+               const uint32_t *__restrict__ words, const uint32_t *__restrict__ nn, int64_t ld, int stage_cap,
+               LJParams<T> P, V4<T> *__restrict__ force, double *part, unsigned *counter, double *out,
+               fpm_dev_status *status)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    V4<T> *sp = (V4<T> *)smem_raw;
+    __shared__ TileDesc d;
+    __shared__ __align__(8) uint64_t bar;
+    load_desc(descs + blockIdx.x, d);
+    const bool in_smem = d.M <= stage_cap;
+    const bool staged = in_smem ? stage_positions(d, box, pos, sp, &bar, status) : true;
+    T usum = 0, wsum = 0;
+    uint32_t npsum = 0;
+    for (uint32_t i = d.h0 + threadIdx.x; staged && i < d.h1; i += blockDim.x) {
         const V4<T> pi = pos[i];
         const uint32_t m = nn[i];
-        const uint32_t *col = nbr + i;
-        for (uint32_t k = 0; k < m; ++k) {
-            const uint32_t j = __ldcs(col + (int64_t)k * ld);
-            const V4<T> pj = ldg4(pos + j);
-            T dx, dy, dz;
-            const T r2 = separation(pi, pj, box, dx, dy, dz);
-            if (r2 < rc2) {
-                const T ir2 = recip(r2);
-                const T s2 = sig2 * ir2;
-                const T s6 = s2 * s2 * s2;
-                const T fr = eps24 * ir2 * s6 * ((T)2 * s6 - (T)1);
-                fx += fr * dx;
-                fy += fr * dy;
-                fz += fr * dz;
-                u += eps4 * s6 * (s6 - (T)1);
-                w += fr * r2;
-                ++np;
-            }
+        T fx = 0, fy = 0, fz = 0, u = 0, w = 0;
+        uint32_t np = 0;
+        if (in_smem) {
+            if (d.slow) lj_sweep<T, false, true>(cfg, box, d, pos, sp, pi, m, words + i, ld, P, fx, fy, fz, u, w, np);
+            else lj_sweep<T, true, true>(cfg, box, d, pos, sp, pi, m, words + i, ld, P, fx, fy, fz, u, w, np);
+        } else {
+            lj_sweep<T, false, false>(cfg, box, d, pos, sp, pi, m, words + i, ld, P, fx, fy, fz, u, w, np);
         }
         V4<T> f;
-        f.x = fx;
-        f.y = fy;
-        f.z = fz;
-        f.w = (T)0.5 * u;
+        f.x = P.eps24 * fx;
+        f.y = P.eps24 * fy;
+        f.z = P.eps24 * fz;
+        f.w = (T)0.5 * P.eps4 * u;
         force[i] = f;
+        usum += P.eps4 * u;
+        wsum += P.eps24 * w;
+        npsum += np;
     }
     if (out) {
-        double v[3] = {0.5 * (double)u, 0.5 * (double)w, 0.5 * (double)np};
+        T v[3] = {(T)0.5 * usum, (T)0.5 * wsum, (T)0.5 * (T)npsum};
         grid_reduce<3>(v, part, counter, out);
     }
 }
 
 template <typename T>
-__global__ void k_vv_kick_drift(BoxT<T> box, int n, T hdt, T dt, V4<T> *__restrict__ pos, V4<T> *__restrict__ vel,
-                                const V4<T> *__restrict__ force)
+static fpm_status lj_launch(const fpm_box &b, const fpm_grid &g, int n, const void *pos, const void *list,
+                            const uint32_t *nn, int cap, double eps, double sigma, double rc, void *force,
+                            double *d_energy, const RedWs &r, fpm_dev_status *status, cudaStream_t stream)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    V4<T> x = pos[i], v = vel[i];
-    const V4<T> f = force[i];
-    v.x += hdt * f.x;
-    v.y += hdt * f.y;
-    v.z += hdt * f.z;
-    x.x += dt * v.x;
-    x.y += dt * v.y;
-    x.z += dt * v.z;
-    if (box.per[0]) x.x = wrap1(x.x, box.L[0]);
-    if (box.per[1]) x.y = wrap1(x.y, box.L[1]);
-    if (box.per[2]) x.z = wrap1(x.z, box.L[2]);
-    pos[i] = x;
-    vel[i] = v;
-}
-
-template <typename T>
-__global__ void k_vv_kick(int n, T hdt, V4<T> *__restrict__ vel, const V4<T> *__restrict__ force)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    V4<T> v = vel[i];
-    const V4<T> f = force[i];
-    v.x += hdt * f.x;
-    v.y += hdt * f.y;
-    v.z += hdt * f.z;
-    vel[i] = v;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_kinetic(int n, const V4<T> *__restrict__ vel, double *part,
-                                                 unsigned *counter, double *out)
-{
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
-    if (i < n) {
-        const V4<T> u = vel[i];
-        const double x = u.x, y = u.y, z = u.z;
-        v[0] = 0.5 * (x * x + y * y + z * z);
-        v[1] = x;
-        v[2] = y;
-        v[3] = z;
-    }
-    grid_reduce<4>(v, part, counter, out);
-}
-
-// Reduction workspace: counter at offset 0, partials from byte 256.
-struct RedWs {
-    unsigned *counter;
-    double *part;
-};
-
-static fpm_status red_ws(int n, void *ws, size_t bytes, const char *who, RedWs &r)
-{
-    size_t need = 0;
-    fpm_reduce_workspace(n, &need);
-    if (!ws || bytes < need) return fpm_fail(FPM_ERR_WORKSPACE, "%s: workspace %zu < %zu bytes", who, bytes, need);
-    if (((uintptr_t)ws & 15u) != 0) return fpm_fail(FPM_ERR_WORKSPACE, "%s: workspace not 16-B aligned", who);
-    r.counter = (unsigned *)ws;
-    r.part = (double *)((char *)ws + 256);
-    return FPM_OK;
-}
-
-template <typename T>
-static fpm_status lj_launch(const fpm_box &b, int n, const void *pos, const uint32_t *nbr, const uint32_t *nn,
-                            double eps, double sigma, double rc, void *force, double *d_energy, const RedWs &r,
-                            cudaStream_t stream)
-{
+    const TileCfg cfg = make_tile_cfg(b, g);
+    const ListLayout L = list_layout(n, cfg, cap);
     const BoxT<T> box = make_box<T>(b);
-    const T rc2 = (T)(rc * rc);
-    const T sig2 = (T)(sigma * sigma);
-    const int blocks = n > 0 ? (n + 255) / 256 : 1;
-    k_lj_forces<T><<<blocks, 256, 0, stream>>>(box, n, (const V4<T> *)pos, nbr, nn, fpm_nbr_ld(n), (T)(24.0 * eps),
-                                               (T)(4.0 * eps), sig2, rc2, (V4<T> *)force, r.part, r.counter,
-                                               d_energy);
+    LJParams<T> P;
+    P.eps24 = (T)(24.0 * eps);
+    P.eps4 = (T)(4.0 * eps);
+    P.sig2 = (T)(sigma * sigma);
+    P.rc2 = (T)(rc * rc);
+    const int sc = stage_capacity(n, g, sizeof(V4<T>));
+    smem_opt_in((const void *)k_lj_tiles<T>);
+    k_lj_tiles<T><<<cfg.ntiles, kTileThreads, sc * sizeof(V4<T>), stream>>>(
+        cfg, box, (const V4<T> *)pos, (const TileDesc *)((const char *)list + L.off_tiles),
+        (const uint32_t *)((const char *)list + L.off_words), nn, L.ld, sc, P, (V4<T> *)force, r.part, r.counter,
+        d_energy, status);
     return fpm_check_launch("fpm_lj_forces");
+}
+
+static fpm_status lj_args(const fpm_box *box, const fpm_grid *grid, int32_t n, fpm_prec prec, const void *pos,
+                          const void *list, const uint32_t *nn, int32_t cap, double sigma, double rc, void *force,
+                          const char *who)
+{
+    fpm_status s = fpm_check_grid(box, grid, who);
+    if (s != FPM_OK) return s;
+    if (n < 0 || cap < 1 || !(rc > 0.0) || !(sigma > 0.0) || (n > 0 && (!pos || !list || !nn || !force)))
+        return fpm_fail(FPM_ERR_INVALID, "%s: null pointer or bad size", who);
+    if (prec != FPM_F32 && prec != FPM_F64) return fpm_fail(FPM_ERR_INVALID, "%s: bad precision", who);
+    if (((uintptr_t)list & 255u) != 0) return fpm_fail(FPM_ERR_INVALID, "%s: list not 256-B aligned", who);
+    return FPM_OK;
 }
 
 }  // namespace fpm
 
 using namespace fpm;
 
-extern "C" fpm_status fpm_lj_forces(const fpm_box *box, int32_t n, fpm_prec prec, const void *pos,
-                                    const uint32_t *nbr, const uint32_t *nn, int32_t cap, double eps, double sigma,
-                                    double rc, void *force, double *d_energy, void *workspace,
-                                    size_t workspace_bytes, fpm_stream stream)
+extern "C" fpm_status fpm_lj_forces(const fpm_box *box, const fpm_grid *grid, int32_t n, fpm_prec prec,
+                                    const void *pos, const void *list, const uint32_t *nn, int32_t cap, double eps,
+                                    double sigma, double rc, void *force, double *d_energy, void *workspace,
+                                    size_t workspace_bytes, fpm_dev_status *d_status, fpm_stream stream)
 {
-    if (!box || n < 0 || cap < 1 || !(rc > 0.0) || !(sigma > 0.0) || (n > 0 && (!pos || !nbr || !nn || !force)))
-        return fpm_fail(FPM_ERR_INVALID, "fpm_lj_forces: null pointer or bad size");
-    if (prec != FPM_F32 && prec != FPM_F64) return fpm_fail(FPM_ERR_INVALID, "fpm_lj_forces: bad precision");
-    if (n == 0 && !d_energy) return FPM_OK;
+    fpm_status s = lj_args(box, grid, n, prec, pos, list, nn, cap, sigma, rc, force, "fpm_lj_forces");
+    if (s != FPM_OK) return s;
+    if (n == 0) return FPM_OK;
     RedWs r{nullptr, nullptr};
     if (d_energy) {
-        fpm_status s = red_ws(n, workspace, workspace_bytes, "fpm_lj_forces", r);
+        s = red_ws(n, grid, workspace, workspace_bytes, "fpm_lj_forces", r);
         if (s != FPM_OK) return s;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    if (prec == FPM_F32) return lj_launch<float>(*box, n, pos, nbr, nn, eps, sigma, rc, force, d_energy, r, st);
-    return lj_launch<double>(*box, n, pos, nbr, nn, eps, sigma, rc, force, d_energy, r, st);
-}
-
-extern "C" fpm_status fpm_vv_step(const fpm_box *box, int32_t n, fpm_prec prec, int32_t half, double dt, void *pos,
-                                  void *vel, const void *force, fpm_stream stream)
-{
-    if (!box || n < 0 || (half != 0 && half != 1) || (n > 0 && (!vel || !force || (half == 0 && !pos))))
-        return fpm_fail(FPM_ERR_INVALID, "fpm_vv_step: null pointer or bad argument");
-    if (prec != FPM_F32 && prec != FPM_F64) return fpm_fail(FPM_ERR_INVALID, "fpm_vv_step: bad precision");
-    if (n == 0) return FPM_OK;
-    cudaStream_t st = (cudaStream_t)stream;
-    const unsigned blocks = (unsigned)((n + 255) / 256);
-    if (prec == FPM_F32) {
-        const BoxT<float> b = make_box<float>(*box);
-        if (half == 0)
-            k_vv_kick_drift<float><<<blocks, 256, 0, st>>>(b, n, (float)(0.5 * dt), (float)dt, (float4 *)pos,
-                                                           (float4 *)vel, (const float4 *)force);
-        else
-            k_vv_kick<float><<<blocks, 256, 0, st>>>(n, (float)(0.5 * dt), (float4 *)vel, (const float4 *)force);
-    } else {
-        const BoxT<double> b = make_box<double>(*box);
-        if (half == 0)
-            k_vv_kick_drift<double><<<blocks, 256, 0, st>>>(b, n, 0.5 * dt, dt, (double4_32a *)pos,
-                                                            (double4_32a *)vel, (const double4_32a *)force);
-        else
-            k_vv_kick<double><<<blocks, 256, 0, st>>>(n, 0.5 * dt, (double4_32a *)vel, (const double4_32a *)force);
-    }
-    return fpm_check_launch("fpm_vv_step");
-}
-
-extern "C" fpm_status fpm_kinetic(int32_t n, fpm_prec prec, const void *vel, double *d_out, void *workspace,
-                                  size_t workspace_bytes, fpm_stream stream)
-{
-    if (n < 0 || !d_out || (n > 0 && !vel)) return fpm_fail(FPM_ERR_INVALID, "fpm_kinetic: bad argument");
-    if (prec != FPM_F32 && prec != FPM_F64) return fpm_fail(FPM_ERR_INVALID, "fpm_kinetic: bad precision");
-    RedWs r;
-    fpm_status s = red_ws(n, workspace, workspace_bytes, "fpm_kinetic", r);
-    if (s != FPM_OK) return s;
-    cudaStream_t st = (cudaStream_t)stream;
-    const int blocks = n > 0 ? (n + 255) / 256 : 1;
     if (prec == FPM_F32)
-        k_kinetic<float><<<blocks, 256, 0, st>>>(n, (const float4 *)vel, r.part, r.counter, d_out);
-    else
-        k_kinetic<double><<<blocks, 256, 0, st>>>(n, (const double4_32a *)vel, r.part, r.counter, d_out);
-    return fpm_check_launch("fpm_kinetic");
+        return lj_launch<float>(*box, *grid, n, pos, list, nn, cap, eps, sigma, rc, force, d_energy, r, d_status, st);
+    return lj_launch<double>(*box, *grid, n, pos, list, nn, cap, eps, sigma, rc, force, d_energy, r, d_status, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -215,12 +210,11 @@ extern "C" fpm_status fpm_kinetic(int32_t n, fpm_prec prec, const void *vel, dou
 // Its scratch (the per-block partial sums and the completion counter) is a
 // file-scope device array, present on every GPU that loads this library.
 // ---------------------------------------------------------------------------
-#include <mutex>
-
 namespace {
 
-constexpr int kNoAllocMaxN = 1 << 24;  // particles per call
-constexpr size_t kNoAllocBytes = 256 + (size_t)((kNoAllocMaxN + 255) / 256) * 8 * sizeof(double);  // 4 MiB + 256 B
+constexpr int kNoAllocMaxN = 1 << 24;       // particles per call
+constexpr int kNoAllocMaxBlocks = 1 << 16;  // tiles (blocks) per call
+constexpr size_t kNoAllocBytes = 256 + (size_t)kNoAllocMaxBlocks * 8 * sizeof(double);  // 4 MiB + 256 B
 
 static __device__ __align__(256) unsigned char g_lj_scratch[kNoAllocBytes];
 
@@ -250,23 +244,25 @@ fpm_status scratch_for_current_device(void **out)
 
 }  // namespace
 
-extern "C" fpm_status fpm_lj_forces_noalloc(const fpm_box *box, int32_t n, fpm_prec prec, const void *pos,
-                                            const uint32_t *nbr, const uint32_t *nn, int32_t cap, double eps,
-                                            double sigma, double rc, void *force, double *d_energy,
-                                            fpm_stream stream)
+extern "C" fpm_status fpm_lj_forces_noalloc(const fpm_box *box, const fpm_grid *grid, int32_t n, fpm_prec prec,
+                                            const void *pos, const void *list, const uint32_t *nn, int32_t cap,
+                                            double eps, double sigma, double rc, void *force, double *d_energy,
+                                            fpm_dev_status *d_status, fpm_stream stream)
 {
     if (n > kNoAllocMaxN)
         return fpm_fail(FPM_ERR_INVALID, "fpm_lj_forces_noalloc: n=%d exceeds the built-in scratch limit of %d particles",
                         n, kNoAllocMaxN);
-    if (!box || n < 0 || cap < 1 || !(rc > 0.0) || !(sigma > 0.0) || (n > 0 && (!pos || !nbr || !nn || !force)))
-        return fpm_fail(FPM_ERR_INVALID, "fpm_lj_forces_noalloc: null pointer or bad size");
-    if (prec != FPM_F32 && prec != FPM_F64) return fpm_fail(FPM_ERR_INVALID, "fpm_lj_forces_noalloc: bad precision");
-    if (n == 0 && !d_energy) return FPM_OK;
+    fpm_status s = lj_args(box, grid, n, prec, pos, list, nn, cap, sigma, rc, force, "fpm_lj_forces_noalloc");
+    if (s != FPM_OK) return s;
+    if ((int64_t)grid->tiles_x * grid->nc[1] * grid->nc[2] > kNoAllocMaxBlocks)
+        return fpm_fail(FPM_ERR_INVALID, "fpm_lj_forces_noalloc: more than %d tiles exceed the built-in scratch limit",
+                        kNoAllocMaxBlocks);
+    if (n == 0) return FPM_OK;
     RedWs r{nullptr, nullptr};
     cudaStream_t st = (cudaStream_t)stream;
     if (d_energy) {
         void *scratch = nullptr;
-        fpm_status s = scratch_for_current_device(&scratch);
+        s = scratch_for_current_device(&scratch);
         if (s != FPM_OK) return s;
         // the completion counter must start at zero; the array keeps whatever
         // the previous call left there
@@ -276,6 +272,7 @@ extern "C" fpm_status fpm_lj_forces_noalloc(const fpm_box *box, int32_t n, fpm_p
         r.counter = (unsigned *)scratch;
         r.part = (double *)((char *)scratch + 256);
     }
-    if (prec == FPM_F32) return lj_launch<float>(*box, n, pos, nbr, nn, eps, sigma, rc, force, d_energy, r, st);
-    return lj_launch<double>(*box, n, pos, nbr, nn, eps, sigma, rc, force, d_energy, r, st);
+    if (prec == FPM_F32)
+        return lj_launch<float>(*box, *grid, n, pos, list, nn, cap, eps, sigma, rc, force, d_energy, r, d_status, st);
+    return lj_launch<double>(*box, *grid, n, pos, list, nn, cap, eps, sigma, rc, force, d_energy, r, d_status, st);
 }

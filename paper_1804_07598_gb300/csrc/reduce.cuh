@@ -1,0 +1,26 @@
+// reduce.cuh -- the caller-provided workspace of the fixed-order FP64
+// reductions (grid_reduce in fpm_common.cuh): a completion counter at offset
+// 0 and per-block partial sums from byte 256.
+#pragma once
+
+#include "fpm_common.cuh"
+
+namespace fpm {
+
+struct RedWs {
+    unsigned *counter;
+    double *part;
+};
+
+inline fpm_status red_ws(int n, const fpm_grid *grid, void *ws, size_t bytes, const char *who, RedWs &r)
+{
+    size_t need = 0;
+    fpm_reduce_workspace(n, grid, &need);
+    if (!ws || bytes < need) return fpm_fail(FPM_ERR_WORKSPACE, "%s: workspace %zu < %zu bytes", who, bytes, need);
+    if (((uintptr_t)ws & 15u) != 0) return fpm_fail(FPM_ERR_WORKSPACE, "%s: workspace not 16-B aligned", who);
+    r.counter = (unsigned *)ws;
+    r.part = (double *)((char *)ws + 256);
+    return FPM_OK;
+}
+
+}  // namespace fpm

@@ -1,0 +1,406 @@
+// tiles.cuh -- cell tiles shared by the Verlet build and the pair sweeps.
+//
+// A tile is a run of consecutive cells [a, b) along x in one (cy, cz) row of
+// the cell grid.  Its "neighbourhood" is every cell of the 27-cell stencils of
+// its cells: for each of the (up to) 9 stencil rows (dz, dy), the x cells
+// a-1 .. b.  Because particles are sorted by cell, each stencil row is one to
+// three contiguous index ranges ("pieces": the cell below x = 0 seen through
+// the periodic wall, the interior run, the cell above ncx-1 seen through the
+// wall).  A block stages the neighbourhood's positions into shared memory in
+// that fixed order, and the Verlet list stores 16-bit indices into it.
+//
+// Periodic images are resolved by the stencil geometry, never by comparing
+// coordinates.  In every periodic dimension with nc >= 3 ("wrap" mode) a
+// neighbour reached through the lower wall is staged as x_j - L, and one
+// reached through the upper wall keeps x_j but carries a flag telling the
+// pair code to use x_i - L for the home particle.  Both shifts are exact (the
+// shifted coordinate lies within a factor 2 of L), so the separation is
+//     x_i - (x_j - L)   or   (x_i - L) - x_j
+// with one rounding: the minimum-image separation as the oracle defines it.
+// A periodic dimension with nc == 1 ("all" mode) holds every particle in the
+// one cell and the pair code chooses the image by comparing with L/2.
+//
+// Positions must not be wrapped between a Verlet build and the sweeps that
+// use its list (the drift of fpm_vv_step does not wrap; the cell-list build
+// does): the image choice is frozen at build time.
+#pragma once
+
+#include "fpm_common.cuh"
+
+namespace fpm {
+
+enum : int { kModeOpen = 0, kModeWrap = 1, kModeAll = 2 };
+
+constexpr int kTileThreads = 192;          // threads per tile block
+constexpr int kMaxTileCells = 14;          // home cells per tile along x
+constexpr int kMaxSeq = kMaxTileCells + 2; // staged cells per stencil row
+constexpr int kMaxRows = 9;
+constexpr int kPiecesPerRow = 3;
+constexpr int kMaxPieces = kMaxRows * kPiecesPerRow;
+constexpr int kMaxStaged = 65535;          // 16-bit list entries
+constexpr int kSmemBudget = 200 * 1024;    // dynamic shared memory per tile block
+
+// flags of a staged particle / piece (stored in the staged w component)
+constexpr int kUpX = 1, kUpY = 2, kUpZ = 4;        // home uses x_i - L in that dim
+constexpr int kLoX = 8, kLoY = 16, kLoZ = 32;      // staged as x_j - L in that dim
+
+struct TileCfg {
+    int nc[3];
+    int mode[3];
+    int tiles_x;
+    int ntiles;
+};
+
+inline TileCfg make_tile_cfg(const fpm_box &b, const fpm_grid &g)
+{
+    TileCfg c{};
+    for (int d = 0; d < 3; ++d) {
+        c.nc[d] = g.nc[d];
+        c.mode[d] = !b.periodic[d] ? kModeOpen : (g.nc[d] == 1 ? kModeAll : kModeWrap);
+    }
+    c.tiles_x = g.tiles_x;
+    c.ntiles = g.tiles_x * g.nc[1] * g.nc[2];
+    return c;
+}
+
+// One piece of a tile's neighbourhood: staged slots [soff, soff+len) hold
+// particles [gstart, gstart+len) of the sorted arrays.
+struct Piece {
+    int soff;
+    int len;
+    uint32_t gstart;
+    int flags;
+};
+
+// Per-tile descriptor written by the Verlet build and read by the sweeps.
+struct TileDesc {
+    uint32_t h0, h1;  // home particles [h0, h1)
+    int M;            // staged particles
+    int slow;         // 1 if any piece has kUp* flags or a dimension is in "all" mode
+    Piece piece[kMaxPieces];
+};
+
+// Layout of a Verlet-list object in caller memory:
+//   [0, 256)                       reserved
+//   [256, 256 + ntiles*sizeof(TileDesc))  tile descriptors
+//   then the ELL words: entry k of particle i is the 16-bit half (k & 1) of
+//   word (k >> 1) * ld + i.
+struct ListLayout {
+    size_t off_tiles, off_words, total;
+    int64_t ld;
+    int words_per_particle;
+};
+
+inline ListLayout list_layout(int n, const TileCfg &c, int cap)
+{
+    ListLayout L{};
+    L.ld = fpm_nbr_ld(n);
+    L.words_per_particle = (cap + 1) / 2;
+    L.off_tiles = 256;
+    size_t t = L.off_tiles + (size_t)c.ntiles * sizeof(TileDesc);
+    L.off_words = (t + 255) & ~(size_t)255;
+    L.total = L.off_words + (size_t)L.words_per_particle * (size_t)L.ld * 4;
+    return L;
+}
+
+// Stencil offsets of one row dimension: cell index and wrap class (-1: seen
+// through the lower wall, +1: through the upper wall, 0: direct).  Returns the
+// count and the index of the zero offset in *mid.
+__device__ __forceinline__ int stencil_rows(int c, int nc, int mode, int cell[3], int wrap[3], int *mid)
+{
+    if (mode == kModeAll) {
+        cell[0] = 0;
+        wrap[0] = 0;
+        *mid = 0;
+        return 1;
+    }
+    int k = 0;
+    for (int o = -1; o <= 1; ++o) {
+        int cc = c + o, w = 0;
+        if (mode == kModeWrap) {
+            if (cc < 0) { cc += nc; w = -1; }
+            else if (cc >= nc) { cc -= nc; w = 1; }
+        } else if (cc < 0 || cc >= nc) {
+            continue;
+        }
+        if (o == 0) *mid = k;
+        cell[k] = cc;
+        wrap[k] = w;
+        ++k;
+    }
+    return k;
+}
+
+// Full tile geometry, built in shared memory by the Verlet build.
+struct TileGeom {
+    int nrows, nseq, seq_start, a, b, mid_row, M;
+    int row_cy[kMaxRows], row_cz[kMaxRows], row_wy[kMaxRows], row_wz[kMaxRows];
+    uint32_t start[kMaxRows][kMaxSeq];  // first sorted index of each staged cell
+    int cnt[kMaxRows][kMaxSeq];
+    int off[kMaxRows][kMaxSeq + 1];     // staged offset of each staged cell
+};
+
+__device__ __forceinline__ int seq_cell_x(int x, int ncx, int mode, int *wrap)
+{
+    *wrap = 0;
+    if (mode == kModeWrap) {
+        if (x < 0) { *wrap = -1; return x + ncx; }
+        if (x >= ncx) { *wrap = 1; return x - ncx; }
+    }
+    return x;
+}
+
+// Computes the geometry of `tile` and its descriptor (in shared memory).  All
+// threads of the block must call it.
+__device__ inline void tile_geometry(const TileCfg &cfg, int tile, const uint32_t *__restrict__ cs, TileGeom &g,
+                              TileDesc &d)
+{
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        const int tx = tile % cfg.tiles_x, row = tile / cfg.tiles_x;
+        const int cy = row % cfg.nc[1], cz = row / cfg.nc[1];
+        const int ncx = cfg.nc[0];
+        const int a = (int)((int64_t)tx * ncx / cfg.tiles_x), b = (int)((int64_t)(tx + 1) * ncx / cfg.tiles_x);
+        g.a = a;
+        g.b = b;
+        if (cfg.mode[0] == kModeAll) {
+            g.seq_start = 0;
+            g.nseq = 1;
+        } else if (cfg.mode[0] == kModeWrap) {
+            g.seq_start = a - 1;
+            g.nseq = b - a + 2;
+        } else {
+            const int s = a > 0 ? a - 1 : 0, e = b < ncx ? b + 1 : ncx;
+            g.seq_start = s;
+            g.nseq = e - s;
+        }
+        int zc[3], zw[3], yc[3], yw[3], zmid = 0, ymid = 0;
+        const int kz = stencil_rows(cz, cfg.nc[2], cfg.mode[2], zc, zw, &zmid);
+        const int ky = stencil_rows(cy, cfg.nc[1], cfg.mode[1], yc, yw, &ymid);
+        int r = 0;
+        for (int i = 0; i < kz; ++i)
+            for (int j = 0; j < ky; ++j) {
+                g.row_cy[r] = yc[j];
+                g.row_cz[r] = zc[i];
+                g.row_wy[r] = yw[j];
+                g.row_wz[r] = zw[i];
+                if (i == zmid && j == ymid) g.mid_row = r;
+                ++r;
+            }
+        g.nrows = r;
+    }
+    __syncthreads();
+    const int tot = g.nrows * g.nseq;
+    for (int k = tid; k < tot; k += blockDim.x) {
+        const int r = k / g.nseq, t = k - r * g.nseq;
+        int w;
+        const int x = seq_cell_x(g.seq_start + t, cfg.nc[0], cfg.mode[0], &w);
+        const uint32_t c = (uint32_t)(((int64_t)g.row_cz[r] * cfg.nc[1] + g.row_cy[r]) * cfg.nc[0] + x);
+        const uint32_t s0 = cs[c], s1 = cs[c + 1];
+        g.start[r][t] = s0;
+        g.cnt[r][t] = (int)(s1 - s0);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int o = 0;
+        for (int r = 0; r < g.nrows; ++r) {
+            for (int t = 0; t < g.nseq; ++t) {
+                g.off[r][t] = o;
+                o += g.cnt[r][t];
+            }
+            g.off[r][g.nseq] = o;
+        }
+        g.M = o;
+        d.M = o;
+        // home particles: cells a .. b-1 of the middle row
+        const int ta = g.a - g.seq_start, tb = g.b - 1 - g.seq_start;
+        d.h0 = g.start[g.mid_row][ta];
+        d.h1 = g.start[g.mid_row][tb] + (uint32_t)g.cnt[g.mid_row][tb];
+        int slow = (cfg.mode[0] == kModeAll || cfg.mode[1] == kModeAll || cfg.mode[2] == kModeAll) ? 1 : 0;
+        for (int r = 0; r < kMaxRows; ++r)
+            for (int p = 0; p < kPiecesPerRow; ++p) d.piece[r * kPiecesPerRow + p] = Piece{0, 0, 0u, 0};
+        for (int r = 0; r < g.nrows; ++r) {
+            int p = 0, t = 0;
+            const int rowflags = (g.row_wy[r] > 0 ? kUpY : 0) | (g.row_wz[r] > 0 ? kUpZ : 0) |
+                                 (g.row_wy[r] < 0 ? kLoY : 0) | (g.row_wz[r] < 0 ? kLoZ : 0);
+            while (t < g.nseq) {
+                int w0;
+                seq_cell_x(g.seq_start + t, cfg.nc[0], cfg.mode[0], &w0);
+                int t1 = t;
+                while (t1 + 1 < g.nseq) {
+                    int w1;
+                    seq_cell_x(g.seq_start + t1 + 1, cfg.nc[0], cfg.mode[0], &w1);
+                    if (w1 != w0) break;
+                    ++t1;
+                }
+                const int f = rowflags | (w0 > 0 ? kUpX : 0) | (w0 < 0 ? kLoX : 0);
+                if (f & (kUpX | kUpY | kUpZ)) slow = 1;
+                d.piece[r * kPiecesPerRow + p] = Piece{g.off[r][t], g.off[r][t1 + 1] - g.off[r][t], g.start[r][t], f};
+                ++p;
+                t = t1 + 1;
+            }
+        }
+        d.slow = slow;
+    }
+    __syncthreads();
+}
+
+// Loads a tile descriptor from global memory into shared memory.
+__device__ __forceinline__ void load_desc(const TileDesc *__restrict__ src, TileDesc &dst)
+{
+    const int words = (int)(sizeof(TileDesc) / 4);
+    const uint32_t *s = (const uint32_t *)src;
+    uint32_t *o = (uint32_t *)&dst;
+    for (int k = threadIdx.x; k < words; k += blockDim.x) o[k] = __ldg(s + k);
+    __syncthreads();
+}
+
+// ---- TMA bulk staging -------------------------------------------------------
+// Every piece is a contiguous run of 16-byte (float4) or 32-byte (double4)
+// records in the sorted position array, so one cp.async.bulk per piece copies
+// it into shared memory; all copies complete on one mbarrier.  Waits are
+// bounded (kWaitCycles); on expiry FPM_FLAG_TIMEOUT is latched.
+
+constexpr long long kWaitCycles = 4000000000LL;  // about 2 s of SM clock
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long budget)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > budget) return false;
+    }
+}
+
+// Stages the neighbourhood positions of a tile into shared memory: slot s of
+// piece p holds pos[gstart + (s - soff)] with the lower-wall shifts applied
+// and (in tiles that need them) the piece flags in w.  Returns false, the same
+// in every thread, if the copies did not complete within the wait budget.
+template <typename T>
+__device__ bool stage_positions(const TileDesc &d, const BoxT<T> &box, const V4<T> *__restrict__ pos,
+                                V4<T> *__restrict__ st, uint64_t *bar, fpm_dev_status *status)
+{
+    const uint32_t b = smem_u32(bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t bytes = (uint32_t)d.M * (uint32_t)sizeof(V4<T>);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+        for (int p = 0; p < kMaxPieces; ++p) {
+            const Piece pc = d.piece[p];
+            if (pc.len == 0) continue;
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    smem_u32(st + pc.soff)),
+                "l"(pos + pc.gstart), "r"((uint32_t)pc.len * (uint32_t)sizeof(V4<T>)), "r"(b)
+                : "memory");
+        }
+    }
+    bool ok = mbar_wait(b, 0u, kWaitCycles);
+    if (!ok) {
+        latch_flag(status, FPM_FLAG_TIMEOUT);
+        ok = mbar_wait(b, 0u, kWaitCycles);  // let copies in flight land before leaving
+    }
+    if (!__syncthreads_and(ok)) return false;
+    for (int p = 0; p < kMaxPieces; ++p) {
+        const Piece pc = d.piece[p];
+        if (pc.len == 0 || (pc.flags == 0 && !d.slow)) continue;
+        const T sx = (pc.flags & kLoX) ? box.L[0] : (T)0;
+        const T sy = (pc.flags & kLoY) ? box.L[1] : (T)0;
+        const T sz = (pc.flags & kLoZ) ? box.L[2] : (T)0;
+        for (int e = threadIdx.x; e < pc.len; e += blockDim.x) {
+            V4<T> q = st[pc.soff + e];
+            q.x = rsub(q.x, sx);
+            q.y = rsub(q.y, sy);
+            q.z = rsub(q.z, sz);
+            q.w = flags_as<T>(pc.flags);
+            st[pc.soff + e] = q;
+        }
+    }
+    __syncthreads();
+    return true;
+}
+
+// Position of staged slot s read straight from global memory (used when the
+// neighbourhood does not fit in shared memory).
+template <typename T>
+__device__ __forceinline__ V4<T> staged_global(const TileDesc &d, const BoxT<T> &box, const V4<T> *__restrict__ pos,
+                                               int s)
+{
+    int p = 0;
+    for (int k = 0; k < kMaxPieces; ++k) {
+        const Piece pc = d.piece[k];
+        if (pc.len > 0 && s >= pc.soff && s < pc.soff + pc.len) {
+            p = k;
+            break;
+        }
+    }
+    const Piece pc = d.piece[p];
+    V4<T> q = ldg4(pos + pc.gstart + (s - pc.soff));
+    if (pc.flags & kLoX) q.x = rsub(q.x, box.L[0]);
+    if (pc.flags & kLoY) q.y = rsub(q.y, box.L[1]);
+    if (pc.flags & kLoZ) q.z = rsub(q.z, box.L[2]);
+    q.w = flags_as<T>(pc.flags);
+    return q;
+}
+
+// Separation x_i - x_j for a staged neighbour (see the file comment).  FAST:
+// the tile has no kUp flags and no "all"-mode dimension.
+template <bool FAST, typename T>
+__device__ __forceinline__ T tile_sep(const V4<T> &pi, const V4<T> &pj, const BoxT<T> &box, const TileCfg &cfg, T &dx,
+                                      T &dy, T &dz)
+{
+    if (FAST) {
+        dx = rsub(pi.x, pj.x);
+        dy = rsub(pi.y, pj.y);
+        dz = rsub(pi.z, pj.z);
+    } else {
+        const int f = flags_of(pj.w);
+        dx = cfg.mode[0] == kModeAll ? sep1(pi.x, pj.x, box.L[0], box.h[0])
+                                     : rsub((f & kUpX) ? rsub(pi.x, box.L[0]) : pi.x, pj.x);
+        dy = cfg.mode[1] == kModeAll ? sep1(pi.y, pj.y, box.L[1], box.h[1])
+                                     : rsub((f & kUpY) ? rsub(pi.y, box.L[1]) : pi.y, pj.y);
+        dz = cfg.mode[2] == kModeAll ? sep1(pi.z, pj.z, box.L[2], box.h[2])
+                                     : rsub((f & kUpZ) ? rsub(pi.z, box.L[2]) : pi.z, pj.z);
+    }
+    return rfma(dz, dz, rfma(dy, dy, rmul(dx, dx)));
+}
+
+// Shared-memory budget for staged positions: 1.4x the mean neighbourhood of
+// a tile plus slack, capped by what one block may use.
+inline int stage_capacity(int n, const fpm_grid &g, size_t elem_bytes)
+{
+    const double rho_c = g.ncell > 0 ? (double)n / g.ncell : 0.0;
+    const int wx = (g.nc[0] + g.tiles_x - 1) / g.tiles_x;
+    const int seq = g.nc[0] == 1 ? 1 : wx + 2;
+    const int rows = (g.nc[1] >= 3 ? 3 : g.nc[1]) * (g.nc[2] >= 3 ? 3 : g.nc[2]);
+    const double want = 1.2 * rows * seq * rho_c + 96.0;
+    const int maxe = (int)((size_t)kSmemBudget / elem_bytes);
+    int e = want > maxe ? maxe : (int)want;
+    e = (e + 31) / 32 * 32;
+    if (e > maxe) e = maxe / 32 * 32;
+    return e < 256 ? 256 : e;
+}
+
+// Lets a kernel use the full dynamic shared-memory budget (a host call, not a
+// stream operation; safe during graph capture).
+inline void smem_opt_in(const void *kernel)
+{
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
+}
+
+}  // namespace fpm

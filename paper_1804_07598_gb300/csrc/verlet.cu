@@ -1,99 +1,119 @@
-// verlet.cu -- Verlet-list build over the sorted cell list and the
-// displacement test that decides when to rebuild it (Verlet lists [46] of
-// Sec. 2, used for the MD benchmark of Sec. 4.1; skin and rebuild rule: half
-// the skin, the textbook criterion).
+// verlet.cu -- Verlet-list build over cell tiles, list decoding, and the
+// displacement test that decides when to rebuild (Verlet lists [46] of
+// Sec. 2, used for the MD benchmark of Sec. 4.1; rebuild when a particle has
+// moved more than half the skin).
 //
-// Thread per particle i (sorted order).  For each of the 9 (dz,dy) rows of
-// the 27-cell stencil the three x-cells cx-1..cx+1 are consecutive in the
-// sorted arrays, so a row is one index range (two when it wraps around the
-// periodic x boundary); candidates are streamed from those ranges.
-#include "fpm_common.cuh"
+// One block per tile (tiles.cuh): the tile's neighbourhood is staged in
+// shared memory, one thread per home particle scans the three staged cells
+// around its own cell in each of the up-to-9 stencil rows, and writes the
+// staged index of every neighbour inside r_list as a 16-bit entry.
+#include "tiles.cuh"
 
 namespace fpm {
 
-// Offsets of one dimension of the stencil: {c-1,c,c+1} (wrapped or clipped),
-// or {c} when the dimension has one cell.  Returns how many.
-__device__ __forceinline__ int stencil_dim(int c, int nc, int per, int out[3])
+template <bool FAST, bool SMEM, typename T>
+__device__ __forceinline__ uint32_t scan_candidates(const TileCfg &cfg, const BoxT<T> &box, const TileGeom &g,
+                                                    const TileDesc &d, const V4<T> *__restrict__ pos,
+                                                    const V4<T> *__restrict__ st, const V4<T> &pi, int self,
+                                                    int t0, int t1, T rl2, int cap, int64_t ld, uint32_t i,
+                                                    uint32_t *__restrict__ words)
 {
-    if (nc == 1) {
-        out[0] = 0;
-        return 1;
+    uint32_t cnt = 0, pending = 0;
+    for (int r = 0; r < g.nrows; ++r) {
+        const int s0 = g.off[r][t0], s1 = g.off[r][t1 + 1];
+        for (int s = s0; s < s1; ++s) {
+            if (s == self) continue;
+            const V4<T> pj = SMEM ? st[s] : staged_global(d, box, pos, s);
+            T dx, dy, dz;
+            const T r2 = tile_sep<FAST>(pi, pj, box, cfg, dx, dy, dz);
+            if (r2 < rl2) {
+                if (cnt < (uint32_t)cap) {
+                    if (cnt & 1u) words[(int64_t)(cnt >> 1) * ld + i] = pending | ((uint32_t)s << 16);
+                    else pending = (uint32_t)s;
+                }
+                ++cnt;
+            }
+        }
     }
-    int k = 0;
-#pragma unroll
-    for (int o = -1; o <= 1; ++o) {
-        int cc = c + o;
-        if (per) cc = cc < 0 ? cc + nc : (cc >= nc ? cc - nc : cc);
-        else if (cc < 0 || cc >= nc) continue;
-        out[k++] = cc;
-    }
-    return k;
+    const uint32_t stored = cnt < (uint32_t)cap ? cnt : (uint32_t)cap;
+    if (stored & 1u) words[(int64_t)(stored >> 1) * ld + i] = pending;
+    return cnt;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_verlet_build(BoxT<T> box, GridD grid, int n, const V4<T> *__restrict__ pos,
-                                                      const uint32_t *__restrict__ cs, T rl2, int cap, int64_t ld,
-                                                      uint32_t *__restrict__ nbr, uint32_t *__restrict__ nn,
-                                                      V4<T> *__restrict__ pos_ref, fpm_dev_status *st,
-                                                      const uint32_t *gate)
+__global__ void __launch_bounds__(kTileThreads)
+    k_verlet_tiles(TileCfg cfg, BoxT<T> box, const V4<T> *__restrict__ pos, const uint32_t *__restrict__ cs, T rl2,
+                   int cap, int64_t ld, int stage_cap, TileDesc *__restrict__ descs, uint32_t *__restrict__ words,
+                   uint32_t *__restrict__ nn, V4<T> *__restrict__ pos_ref, fpm_dev_status *st, const uint32_t *gate)
 {
     if (gated_off(gate)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t cnt = 0;
-    if (i < n) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    V4<T> *sp = (V4<T> *)smem_raw;
+    __shared__ TileGeom g;
+    __shared__ TileDesc d;
+    tile_geometry(cfg, blockIdx.x, cs, g, d);
+    {  // publish the descriptor for the sweeps
+        const int nw = (int)(sizeof(TileDesc) / 4);
+        uint32_t *o = (uint32_t *)(descs + blockIdx.x);
+        const uint32_t *s = (const uint32_t *)&d;
+        for (int k = threadIdx.x; k < nw; k += blockDim.x) o[k] = s[k];
+    }
+    uint32_t maxc = 0;
+    if (d.M > kMaxStaged) {  // 16-bit entries cannot address this neighbourhood
+        for (uint32_t i = d.h0 + threadIdx.x; i < d.h1; i += blockDim.x) nn[i] = 0u;
+        if (threadIdx.x == 0) latch_flag(st, FPM_FLAG_CAPACITY);
+        return;
+    }
+    __shared__ __align__(8) uint64_t bar;
+    const bool in_smem = d.M <= stage_cap;
+    if (in_smem && !stage_positions(d, box, pos, sp, &bar, st)) {
+        for (uint32_t i = d.h0 + threadIdx.x; i < d.h1; i += blockDim.x) nn[i] = 0u;
+        return;
+    }
+    for (uint32_t i = d.h0 + threadIdx.x; i < d.h1; i += blockDim.x) {
         const V4<T> pi = pos[i];
         if (pos_ref) pos_ref[i] = pi;
-        bool bad = false;
-        int c[3];
-        cell_of(pi, box, grid, c, bad);
-        int oz[3], oy[3];
-        const int kz = stencil_dim(c[2], grid.nc[2], box.per[2], oz);
-        const int ky = stencil_dim(c[1], grid.nc[1], box.per[1], oy);
-        const int ncx = grid.nc[0];
-        // x range(s) of the row, as cell offsets [x0, x1] (inclusive) pieces
-        int xa0, xa1, xb0 = 1, xb1 = 0;  // second piece empty unless wrapping
-        if (ncx == 1) {
-            xa0 = 0;
-            xa1 = 0;
-        } else if (box.per[0]) {
-            if (c[0] == 0) {
-                xa0 = 0; xa1 = 1; xb0 = ncx - 1; xb1 = ncx - 1;
-            } else if (c[0] == ncx - 1) {
-                xa0 = ncx - 2; xa1 = ncx - 1; xb0 = 0; xb1 = 0;
-            } else {
-                xa0 = c[0] - 1; xa1 = c[0] + 1;
-            }
+        // the home cell: the staged cell of the middle row holding i
+        int th = g.a - g.seq_start;
+        for (int t = g.a - g.seq_start; t < g.b - g.seq_start; ++t)
+            if (i >= g.start[g.mid_row][t] && i < g.start[g.mid_row][t] + (uint32_t)g.cnt[g.mid_row][t]) th = t;
+        const int self = g.off[g.mid_row][th] + (int)(i - g.start[g.mid_row][th]);
+        const int t0 = th > 0 ? th - 1 : 0;
+        const int t1 = th + 1 < g.nseq ? th + 1 : g.nseq - 1;
+        uint32_t c;
+        if (in_smem) {
+            c = d.slow ? scan_candidates<false, true>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld, i, words)
+                       : scan_candidates<true, true>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld, i, words);
         } else {
-            xa0 = c[0] > 0 ? c[0] - 1 : 0;
-            xa1 = c[0] < ncx - 1 ? c[0] + 1 : ncx - 1;
+            c = scan_candidates<false, false>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld, i, words);
         }
-        for (int a = 0; a < kz; ++a) {
-            for (int b = 0; b < ky; ++b) {
-                const uint32_t row = linear_cell(0, oy[b], oz[a], grid);
-#pragma unroll 1
-                for (int piece = 0; piece < 2; ++piece) {
-                    const int x0 = piece ? xb0 : xa0, x1 = piece ? xb1 : xa1;
-                    if (x0 > x1) continue;
-                    const uint32_t j0 = cs[row + x0], j1 = cs[row + x1 + 1];
-                    for (uint32_t j = j0; j < j1; ++j) {
-                        if (j == (uint32_t)i) continue;
-                        const V4<T> pj = pos[j];
-                        T dx, dy, dz;
-                        const T r2 = separation(pi, pj, box, dx, dy, dz);
-                        if (r2 < rl2) {
-                            if (cnt < (uint32_t)cap) nbr[(int64_t)cnt * ld + i] = j;
-                            ++cnt;
-                        }
-                    }
-                }
-            }
-        }
-        nn[i] = cnt < (uint32_t)cap ? cnt : (uint32_t)cap;
-        if (cnt > (uint32_t)cap) latch_flag(st, FPM_FLAG_CAPACITY);
+        nn[i] = c < (uint32_t)cap ? c : (uint32_t)cap;
+        if (c > (uint32_t)cap) latch_flag(st, FPM_FLAG_CAPACITY);
+        maxc = c > maxc ? c : maxc;
     }
-    // one atomic max per warp
-    uint32_t m = __reduce_max_sync(kFull, cnt);
+    const uint32_t m = __reduce_max_sync(kFull, maxc);
     if ((threadIdx.x & 31) == 0 && st && m > 0) atomicMax(&st->max_nn, m);
+}
+
+__global__ void __launch_bounds__(kTileThreads)
+    k_verlet_decode(const TileDesc *__restrict__ descs, const uint32_t *__restrict__ words,
+                    const uint32_t *__restrict__ nn, int64_t ld, uint32_t *__restrict__ out)
+{
+    __shared__ TileDesc d;
+    load_desc(descs + blockIdx.x, d);
+    for (uint32_t i = d.h0 + threadIdx.x; i < d.h1; i += blockDim.x) {
+        const uint32_t m = nn[i];
+        for (uint32_t k = 0; k < m; ++k) {
+            const uint32_t w = words[(int64_t)(k >> 1) * ld + i];
+            const int s = (int)((k & 1u) ? (w >> 16) : (w & 0xffffu));
+            uint32_t j = 0xffffffffu;
+            for (int p = 0; p < kMaxPieces; ++p) {
+                const Piece pc = d.piece[p];
+                if (pc.len > 0 && s >= pc.soff && s < pc.soff + pc.len) j = pc.gstart + (uint32_t)(s - pc.soff);
+            }
+            out[(int64_t)k * ld + i] = j;
+        }
+    }
 }
 
 __global__ void k_gate_done(uint32_t *gate, fpm_dev_status *st)
@@ -117,25 +137,25 @@ __global__ void k_verlet_check(BoxT<T> box, int n, const V4<T> *__restrict__ pos
         over = d2 > th;
         d2f = (float)d2;
     }
-    const unsigned any = __ballot_sync(kFull, over);
-    const uint32_t m = __reduce_max_sync(kFull, __float_as_uint(d2f));
-    if ((threadIdx.x & 31) == 0) {
-        if (any) st->rebuild = 1u;
-        if (m) atomicMax(&st->max_disp2, m);
-    }
+    disp_report(over, d2f, st);
 }
 
 template <typename T>
 static fpm_status verlet_launch(const fpm_box &b, const fpm_grid &g, int n, const void *pos, const uint32_t *cs,
-                                double r_list, int cap, uint32_t *nbr, uint32_t *nn, void *pos_ref,
-                                fpm_dev_status *st, uint32_t *gate, cudaStream_t stream)
+                                double r_list, int cap, void *list, uint32_t *nn, void *pos_ref, fpm_dev_status *st,
+                                uint32_t *gate, cudaStream_t stream)
 {
+    const TileCfg cfg = make_tile_cfg(b, g);
+    const ListLayout L = list_layout(n, cfg, cap);
     const BoxT<T> box = make_box<T>(b);
-    const GridD grid = make_grid(g);
     const T rl2 = (T)(r_list * r_list);
-    if (n > 0)
-        k_verlet_build<T><<<(n + 255) / 256, 256, 0, stream>>>(box, grid, n, (const V4<T> *)pos, cs, rl2, cap,
-                                                               fpm_nbr_ld(n), nbr, nn, (V4<T> *)pos_ref, st, gate);
+    const int sc = stage_capacity(n, g, sizeof(V4<T>));
+    if (n > 0) {
+        smem_opt_in((const void *)k_verlet_tiles<T>);
+        k_verlet_tiles<T><<<cfg.ntiles, kTileThreads, sc * sizeof(V4<T>), stream>>>(
+            cfg, box, (const V4<T> *)pos, cs, rl2, cap, L.ld, sc, (TileDesc *)((char *)list + L.off_tiles),
+            (uint32_t *)((char *)list + L.off_words), nn, (V4<T> *)pos_ref, st, gate);
+    }
     if (gate) k_gate_done<<<1, 1, 0, stream>>>(gate, st);
     return fpm_check_launch("fpm_verlet_build");
 }
@@ -164,30 +184,75 @@ static bool box_ok(const fpm_box *b)
     return true;
 }
 
+// Checks shared by every call taking a grid and a list.
+fpm_status fpm_check_grid(const fpm_box *box, const fpm_grid *grid, const char *who)
+{
+    if (!box_ok(box) || !grid) return fpm_fail(FPM_ERR_INVALID, "%s: null box or grid", who);
+    for (int d = 0; d < 3; ++d)
+        if (grid->nc[d] < 1) return fpm_fail(FPM_ERR_INVALID, "%s: bad grid", who);
+    if ((int64_t)grid->nc[0] * grid->nc[1] * grid->nc[2] != grid->ncell)
+        return fpm_fail(FPM_ERR_INVALID, "%s: grid->ncell inconsistent with nc", who);
+    if (grid->tiles_x < 1 || grid->tiles_x > grid->nc[0] ||
+        (grid->nc[0] + grid->tiles_x - 1) / grid->tiles_x > kMaxTileCells)
+        return fpm_fail(FPM_ERR_INVALID, "%s: grid->tiles_x inconsistent with nc[0]", who);
+    for (int d = 0; d < 3; ++d)
+        if (box->periodic[d] && grid->nc[d] == 2)
+            return fpm_fail(FPM_ERR_INVALID, "%s: a periodic dimension cannot have 2 cells", who);
+    return FPM_OK;
+}
+
+extern "C" fpm_status fpm_verlet_list_bytes(int32_t n, const fpm_grid *grid, int32_t cap, size_t *bytes)
+{
+    if (!grid || !bytes || n < 0 || cap < 1 || grid->tiles_x < 1)
+        return fpm_fail(FPM_ERR_INVALID, "fpm_verlet_list_bytes: bad argument");
+    TileCfg c{};
+    c.ntiles = grid->tiles_x * grid->nc[1] * grid->nc[2];
+    *bytes = list_layout(n, c, cap).total;
+    return FPM_OK;
+}
+
 extern "C" fpm_status fpm_verlet_build(const fpm_box *box, const fpm_grid *grid, int32_t n, fpm_prec prec,
                                        const void *pos, const uint32_t *cell_start, double r_list, int32_t cap,
-                                       uint32_t *nbr, uint32_t *nn, void *pos_ref, fpm_dev_status *d_status,
-                                       uint32_t *d_gate, fpm_stream stream)
+                                       void *list, size_t list_bytes, uint32_t *nn, void *pos_ref,
+                                       fpm_dev_status *d_status, uint32_t *d_gate, fpm_stream stream)
 {
-    if (!box_ok(box) || !grid || n < 0 || cap < 1 || !(r_list > 0.0) || !cell_start ||
-        (n > 0 && (!pos || !nbr || !nn)))
+    fpm_status s = fpm_check_grid(box, grid, "fpm_verlet_build");
+    if (s != FPM_OK) return s;
+    if (n < 0 || cap < 1 || !(r_list > 0.0) || !cell_start || (n > 0 && (!pos || !list || !nn)))
         return fpm_fail(FPM_ERR_INVALID, "fpm_verlet_build: null pointer or bad size");
     if (prec != FPM_F32 && prec != FPM_F64) return fpm_fail(FPM_ERR_INVALID, "fpm_verlet_build: bad precision");
     for (int d = 0; d < 3; ++d) {
-        if (grid->nc[d] < 1) return fpm_fail(FPM_ERR_INVALID, "fpm_verlet_build: bad grid");
-        // every cell must be at least r_list wide, and a periodic box must hold the sphere
         if (grid->nc[d] > 1 && box->L[d] / grid->nc[d] < r_list)
             return fpm_fail(FPM_ERR_INVALID, "fpm_verlet_build: cells narrower than r_list in dim %d", d);
         if (box->periodic[d] && !(box->L[d] > 2.0 * r_list * (1.0 + 1.0 / 1024.0)))
             return fpm_fail(FPM_ERR_INVALID, "fpm_verlet_build: periodic L[%d] must exceed 2 r_list", d);
-        if (box->periodic[d] && grid->nc[d] == 2)
-            return fpm_fail(FPM_ERR_INVALID, "fpm_verlet_build: a periodic dim cannot have 2 cells");
     }
+    size_t need = 0;
+    fpm_verlet_list_bytes(n, grid, cap, &need);
+    if (n > 0 && list_bytes < need)
+        return fpm_fail(FPM_ERR_WORKSPACE, "fpm_verlet_build: list object %zu < %zu bytes", list_bytes, need);
+    if (((uintptr_t)list & 255u) != 0) return fpm_fail(FPM_ERR_INVALID, "fpm_verlet_build: list not 256-B aligned");
     cudaStream_t st = (cudaStream_t)stream;
     if (prec == FPM_F32)
-        return verlet_launch<float>(*box, *grid, n, pos, cell_start, r_list, cap, nbr, nn, pos_ref, d_status, d_gate,
+        return verlet_launch<float>(*box, *grid, n, pos, cell_start, r_list, cap, list, nn, pos_ref, d_status, d_gate,
                                     st);
-    return verlet_launch<double>(*box, *grid, n, pos, cell_start, r_list, cap, nbr, nn, pos_ref, d_status, d_gate, st);
+    return verlet_launch<double>(*box, *grid, n, pos, cell_start, r_list, cap, list, nn, pos_ref, d_status, d_gate,
+                                 st);
+}
+
+extern "C" fpm_status fpm_verlet_decode(const fpm_grid *grid, int32_t n, int32_t cap, const void *list,
+                                        const uint32_t *nn, uint32_t *out, fpm_stream stream)
+{
+    if (!grid || n < 0 || cap < 1 || (n > 0 && (!list || !nn || !out)) || grid->tiles_x < 1)
+        return fpm_fail(FPM_ERR_INVALID, "fpm_verlet_decode: bad argument");
+    if (n == 0) return FPM_OK;
+    TileCfg c{};
+    c.ntiles = grid->tiles_x * grid->nc[1] * grid->nc[2];
+    const ListLayout L = list_layout(n, c, cap);
+    k_verlet_decode<<<c.ntiles, kTileThreads, 0, (cudaStream_t)stream>>>(
+        (const TileDesc *)((const char *)list + L.off_tiles), (const uint32_t *)((const char *)list + L.off_words),
+        nn, L.ld, out);
+    return fpm_check_launch("fpm_verlet_decode");
 }
 
 extern "C" fpm_status fpm_verlet_check(const fpm_box *box, int32_t n, fpm_prec prec, const void *pos,

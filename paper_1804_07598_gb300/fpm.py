@@ -37,7 +37,7 @@ class fpm_box(_c.Structure):
 
 
 class fpm_grid(_c.Structure):
-    _fields_ = [("nc", _c.c_int32 * 3), ("ncell", _c.c_int32), ("inv", _c.c_float * 3), ("pad", _c.c_float)]
+    _fields_ = [("nc", _c.c_int32 * 3), ("ncell", _c.c_int32), ("inv", _c.c_float * 3), ("tiles_x", _c.c_int32)]
 
     @property
     def shape(self):
@@ -68,21 +68,26 @@ _SIG = {
     "fpm_last_error": (_c.c_char_p, []),
     "fpm_status_from_device": (_c.c_int, [_c.POINTER(fpm_dev_status)]),
     "fpm_nbr_ld": (_c.c_int64, [_c.c_int32]),
-    "fpm_grid_make": (_c.c_int, [_c.POINTER(fpm_box), _c.c_double, _c.POINTER(fpm_grid)]),
+    "fpm_grid_make": (_c.c_int, [_c.POINTER(fpm_box), _c.c_double, _c.c_int32, _c.POINTER(fpm_grid)]),
     "fpm_celllist_workspace": (_c.c_int, [_c.c_int32, _c.POINTER(fpm_grid), _c.c_int, _c.POINTER(_c.c_size_t)]),
     "fpm_celllist_build": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _c.c_int,
                                       _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _c.c_size_t, _VP, _VP, _VP]),
     "fpm_reorder": (_c.c_int, [_c.c_int32, _c.c_int32, _VP, _VP, _VP, _VP, _VP]),
+    "fpm_verlet_list_bytes": (_c.c_int, [_c.c_int32, _c.POINTER(fpm_grid), _c.c_int32, _c.POINTER(_c.c_size_t)]),
     "fpm_verlet_build": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _c.c_int, _VP, _VP,
-                                    _c.c_double, _c.c_int32, _VP, _VP, _VP, _VP, _VP, _VP]),
+                                    _c.c_double, _c.c_int32, _VP, _c.c_size_t, _VP, _VP, _VP, _VP, _VP]),
+    "fpm_verlet_decode": (_c.c_int, [_c.POINTER(fpm_grid), _c.c_int32, _c.c_int32, _VP, _VP, _VP, _VP]),
     "fpm_verlet_check": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.c_int, _VP, _VP, _c.c_double, _VP, _VP]),
-    "fpm_reduce_workspace": (_c.c_int, [_c.c_int32, _c.POINTER(_c.c_size_t)]),
-    "fpm_lj_forces": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.c_int, _VP, _VP, _VP, _c.c_int32,
-                                 _c.c_double, _c.c_double, _c.c_double, _VP, _VP, _VP, _c.c_size_t, _VP]),
-    "fpm_lj_forces_noalloc": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.c_int, _VP, _VP, _VP, _c.c_int32,
-                                         _c.c_double, _c.c_double, _c.c_double, _VP, _VP, _VP]),
+    "fpm_reduce_workspace": (_c.c_int, [_c.c_int32, _c.POINTER(fpm_grid), _c.POINTER(_c.c_size_t)]),
+    "fpm_lj_forces": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _c.c_int, _VP, _VP, _VP,
+                                 _c.c_int32, _c.c_double, _c.c_double, _c.c_double, _VP, _VP, _VP, _c.c_size_t, _VP,
+                                 _VP]),
+    "fpm_lj_forces_noalloc": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _c.c_int, _VP, _VP,
+                                         _VP, _c.c_int32, _c.c_double, _c.c_double, _c.c_double, _VP, _VP, _VP, _VP]),
     "fpm_vv_step": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.c_int, _c.c_int32, _c.c_double, _VP, _VP, _VP,
                                _VP]),
+    "fpm_vv_drift_check": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.c_int, _c.c_double, _VP, _VP, _VP, _VP,
+                                      _c.c_double, _VP, _VP]),
     "fpm_kinetic": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _VP, _VP, _c.c_size_t, _VP]),
 }
 
@@ -172,10 +177,16 @@ def fpm_nbr_ld(n: int) -> int:
     return int(lib().fpm_nbr_ld(int(n)))
 
 
-def fpm_grid_make(box: fpm_box, r_cell: float) -> fpm_grid:
+def fpm_grid_make(box: fpm_box, r_cell: float, n_hint: int = 0) -> fpm_grid:
     g = fpm_grid()
-    _check(lib().fpm_grid_make(_c.byref(box), float(r_cell), _c.byref(g)))
+    _check(lib().fpm_grid_make(_c.byref(box), float(r_cell), int(n_hint), _c.byref(g)))
     return g
+
+
+def fpm_verlet_list_bytes(n: int, grid: fpm_grid, cap: int) -> int:
+    b = _c.c_size_t(0)
+    _check(lib().fpm_verlet_list_bytes(int(n), _c.byref(grid), int(cap), _c.byref(b)))
+    return b.value
 
 
 def fpm_celllist_workspace(n: int, grid: fpm_grid, prec: int) -> int:
@@ -184,9 +195,9 @@ def fpm_celllist_workspace(n: int, grid: fpm_grid, prec: int) -> int:
     return b.value
 
 
-def fpm_reduce_workspace(n: int) -> int:
+def fpm_reduce_workspace(n: int, grid: fpm_grid = None) -> int:
     b = _c.c_size_t(0)
-    _check(lib().fpm_reduce_workspace(int(n), _c.byref(b)))
+    _check(lib().fpm_reduce_workspace(int(n), _c.byref(grid) if grid is not None else None, _c.byref(b)))
     return b.value
 
 
@@ -215,12 +226,18 @@ def fpm_reorder(n, elem_bytes, perm, src, dst, d_gate=None, stream=None):
     _count(1 if n > 0 else 0)
 
 
-def fpm_verlet_build(box, grid, n, prec, pos, cell_start, r_list, cap, nbr, nn, pos_ref=None, d_status=None,
+def fpm_verlet_build(box, grid, n, prec, pos, cell_start, r_list, cap, list_obj, nn, pos_ref=None, d_status=None,
                      d_gate=None, stream=None):
     _check(lib().fpm_verlet_build(_c.byref(box), _c.byref(grid), int(n), int(prec), _ptr(pos), _ptr(cell_start),
-                                  float(r_list), int(cap), _ptr(nbr), _ptr(nn), _ptr(pos_ref), _ptr(d_status),
-                                  _ptr(d_gate), _stream(stream)))
+                                  float(r_list), int(cap), _ptr(list_obj), _nbytes(list_obj), _ptr(nn),
+                                  _ptr(pos_ref), _ptr(d_status), _ptr(d_gate), _stream(stream)))
     _count((1 if n > 0 else 0) + (1 if d_gate is not None else 0))
+
+
+def fpm_verlet_decode(grid, n, cap, list_obj, nn, out, stream=None):
+    _check(lib().fpm_verlet_decode(_c.byref(grid), int(n), int(cap), _ptr(list_obj), _ptr(nn), _ptr(out),
+                                   _stream(stream)))
+    _count(1 if n > 0 else 0)
 
 
 def fpm_verlet_check(box, n, prec, pos, pos_ref, skin, d_status, stream=None):
@@ -229,27 +246,34 @@ def fpm_verlet_check(box, n, prec, pos, pos_ref, skin, d_status, stream=None):
     _count(1 if n > 0 else 0)
 
 
-def fpm_lj_forces(box, n, prec, pos, nbr, nn, cap, eps, sigma, rc, force, d_energy=None, workspace=None,
-                  stream=None):
-    _check(lib().fpm_lj_forces(_c.byref(box), int(n), int(prec), _ptr(pos), _ptr(nbr), _ptr(nn), int(cap),
-                               float(eps), float(sigma), float(rc), _ptr(force), _ptr(d_energy), _ptr(workspace),
-                               _nbytes(workspace), _stream(stream)))
-    _count(1 if (n > 0 or d_energy is not None) else 0)
+def fpm_lj_forces(box, grid, n, prec, pos, list_obj, nn, cap, eps, sigma, rc, force, d_energy=None,
+                  workspace=None, d_status=None, stream=None):
+    _check(lib().fpm_lj_forces(_c.byref(box), _c.byref(grid), int(n), int(prec), _ptr(pos), _ptr(list_obj), _ptr(nn),
+                               int(cap), float(eps), float(sigma), float(rc), _ptr(force), _ptr(d_energy),
+                               _ptr(workspace), _nbytes(workspace), _ptr(d_status), _stream(stream)))
+    _count(1 if n > 0 else 0)
 
 
-def fpm_lj_forces_noalloc(box, n, prec, pos, nbr, nn, cap, eps, sigma, rc, force, d_energy=None, stream=None):
+def fpm_lj_forces_noalloc(box, grid, n, prec, pos, list_obj, nn, cap, eps, sigma, rc, force, d_energy=None,
+                          d_status=None, stream=None):
     """fpm_lj_forces for callers that cannot allocate device memory: the
     reduction scratch is built into the library (n <= 2^24); concurrent calls
     on one device must be serialised by the caller."""
-    _check(lib().fpm_lj_forces_noalloc(_c.byref(box), int(n), int(prec), _ptr(pos), _ptr(nbr), _ptr(nn), int(cap),
-                                       float(eps), float(sigma), float(rc), _ptr(force), _ptr(d_energy),
-                                       _stream(stream)))
-    _count((1 if (n > 0 or d_energy is not None) else 0) + (1 if d_energy is not None else 0))
+    _check(lib().fpm_lj_forces_noalloc(_c.byref(box), _c.byref(grid), int(n), int(prec), _ptr(pos), _ptr(list_obj),
+                                       _ptr(nn), int(cap), float(eps), float(sigma), float(rc), _ptr(force),
+                                       _ptr(d_energy), _ptr(d_status), _stream(stream)))
+    _count(1 if n > 0 else 0)
 
 
 def fpm_vv_step(box, n, prec, half, dt, pos, vel, force, stream=None):
     _check(lib().fpm_vv_step(_c.byref(box), int(n), int(prec), int(half), float(dt), _ptr(pos), _ptr(vel),
                              _ptr(force), _stream(stream)))
+    _count(1 if n > 0 else 0)
+
+
+def fpm_vv_drift_check(box, n, prec, dt, pos, vel, force, pos_ref, skin, d_status, stream=None):
+    _check(lib().fpm_vv_drift_check(_c.byref(box), int(n), int(prec), float(dt), _ptr(pos), _ptr(vel), _ptr(force),
+                                    _ptr(pos_ref), float(skin), _ptr(d_status), _stream(stream)))
     _count(1 if n > 0 else 0)
 
 

@@ -3,9 +3,9 @@ Listing 4.1): state buffers in device memory, the velocity-Verlet step with a
 device-gated Verlet rebuild, and CUDA-graph capture of whole steps.
 
 One step (all on the current stream, no host synchronisation):
-    fpm_vv_step(half=0)         v += dt/2 F; x += dt v; wrap
-    fpm_verlet_check            rebuild flag := max |x - x_ref| > skin/2
-    fpm_celllist_build [gated]  re-bin and reorder in place
+    fpm_vv_drift_check          v += dt/2 F; x += dt v (no wrap until the rebuild);
+                                rebuild flag := max |x - x_ref| > skin/2
+    fpm_celllist_build [gated]  wrap, re-bin and reorder in place
     fpm_verlet_build   [gated]  new list, x_ref := x, flag cleared
     fpm_lj_forces               F, U, W, pairs
     fpm_vv_step(half=1)         v += dt/2 F
@@ -42,7 +42,7 @@ class LJSystem:
         self.eps, self.sigma, self.rc, self.skin, self.dt = float(eps), float(sigma), float(rc), float(skin), float(dt)
         self.r_list = self.rc + self.skin
         self.box = fpm.make_box(self.L, self.periodic)
-        self.grid = fpm.fpm_grid_make(self.box, self.r_list)
+        self.grid = fpm.fpm_grid_make(self.box, self.r_list, n)
         vol = float(np.prod(self.L))
         self.cap = int(cap) if cap else default_cap(max(n, 1) / vol, self.r_list)
         self.ld = fpm.fpm_nbr_ld(n)
@@ -58,11 +58,11 @@ class LJSystem:
         self.ids = torch.arange(n, dtype=torch.int32, device=dev)
         self.perm = torch.zeros(max(n, 1), dtype=torch.int32, device=dev)
         self.cell_start = torch.zeros(self.grid.ncell + 1, dtype=torch.int32, device=dev)
-        self.nbr = torch.zeros(max(1, self.cap * self.ld), dtype=torch.int32, device=dev)
+        self.nbr = torch.zeros(fpm.fpm_verlet_list_bytes(n, self.grid, self.cap), dtype=torch.uint8, device=dev)
         self.nn = torch.zeros(max(n, 1), dtype=torch.int32, device=dev)
         self.status = torch.zeros(fpm.STATUS_BYTES // 4, dtype=torch.int32, device=dev)
         self.ws_cell = torch.zeros(fpm.fpm_celllist_workspace(n, self.grid, self.prec), dtype=torch.uint8, device=dev)
-        self.ws_red = torch.zeros(fpm.fpm_reduce_workspace(n), dtype=torch.uint8, device=dev)
+        self.ws_red = torch.zeros(fpm.fpm_reduce_workspace(n, self.grid), dtype=torch.uint8, device=dev)
         self.energy = torch.zeros(3, dtype=torch.float64, device=dev)
         self.kin = torch.zeros(4, dtype=torch.float64, device=dev)
         self._graph = None
@@ -82,12 +82,12 @@ class LJSystem:
                              self.cap, self.nbr, self.nn, self.pos_ref, self.status, gate)
 
     def compute_forces(self):
-        fpm.fpm_lj_forces(self.box, self.n, self.prec, self.pos, self.nbr, self.nn, self.cap, self.eps, self.sigma,
-                          self.rc, self.force, self.energy, self.ws_red)
+        fpm.fpm_lj_forces(self.box, self.grid, self.n, self.prec, self.pos, self.nbr, self.nn, self.cap, self.eps,
+                          self.sigma, self.rc, self.force, self.energy, self.ws_red, self.status)
 
     def _step(self):
-        fpm.fpm_vv_step(self.box, self.n, self.prec, 0, self.dt, self.pos, self.vel, self.force)
-        fpm.fpm_verlet_check(self.box, self.n, self.prec, self.pos, self.pos_ref, self.skin, self.status)
+        fpm.fpm_vv_drift_check(self.box, self.n, self.prec, self.dt, self.pos, self.vel, self.force, self.pos_ref,
+                               self.skin, self.status)
         self.rebuild(gated=True)
         self.compute_forces()
         fpm.fpm_vv_step(self.box, self.n, self.prec, 1, self.dt, None, self.vel, self.force)
@@ -140,6 +140,13 @@ class LJSystem:
         if code != fpm.FPM_OK:
             raise fpm.FpmError(code, f"device status flags={st.flags} max_nn={st.max_nn} cap={self.cap}")
         return st
+
+    def neighbor_lists(self):
+        """The Verlet list as particle indices: (nbr [cap, ld] uint32, nn [n])."""
+        out = torch.full((self.cap * self.ld,), -1, dtype=torch.int32, device=self.device)
+        fpm.fpm_verlet_decode(self.grid, self.n, self.cap, self.nbr, self.nn, out)
+        return (out.cpu().numpy().view(np.uint32).reshape(self.cap, self.ld),
+                self.nn[: self.n].cpu().numpy().view(np.uint32))
 
     def state_numpy(self):
         """(pos, vel, ids) in the current (sorted) order, as numpy."""

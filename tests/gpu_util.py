@@ -35,7 +35,7 @@ def gpu_celllist(pos4, L, periodic, r_cell, prec, vel4=None, ids=None, inplace=F
     n = pos4.shape[0]
     td = tdtype(prec)
     box = fpm.make_box(L, periodic)
-    grid = fpm.fpm_grid_make(box, r_cell)
+    grid = fpm.fpm_grid_make(box, r_cell, n)
     p_in = dev(pos4, td)
     v_in = dev(vel4, td) if vel4 is not None else None
     i_in = dev(np.asarray(ids, np.uint32).view(np.int32), torch.int32) if ids is not None else None
@@ -61,20 +61,23 @@ def gpu_celllist(pos4, L, periodic, r_cell, prec, vel4=None, ids=None, inplace=F
 
 
 def gpu_verlet(res, r_list, prec, cap=None, gate=None):
-    """Run fpm_verlet_build on the sorted output of gpu_celllist."""
+    """Run fpm_verlet_build on the sorted output of gpu_celllist and decode the
+    list into particle indices."""
     n = res["pos"].shape[0]
     cap = cap or 160
     ld = fpm.fpm_nbr_ld(n)
-    nbr = torch.full((max(1, cap * ld),), -1, dtype=torch.int32, device="cuda")
+    lst = torch.full((fpm.fpm_verlet_list_bytes(n, res["grid"], cap),), 0xA5, dtype=torch.uint8, device="cuda")
     nn = torch.full((max(n, 1),), -1, dtype=torch.int32, device="cuda")
     ref = torch.zeros_like(res["dev"]["pos"])
     st = status_tensor()
     fpm.fpm_verlet_build(res["box"], res["grid"], n, fprec(prec), res["dev"]["pos"], res["dev"]["cs"], r_list, cap,
-                         nbr, nn, ref, st, gate)
+                         lst, nn, ref, st, gate)
+    nbr = torch.full((max(1, cap * ld),), -1, dtype=torch.int32, device="cuda")
+    fpm.fpm_verlet_decode(res["grid"], n, cap, lst, nn, nbr)
     torch.cuda.synchronize()
     return dict(nbr=u32(nbr)[:cap * ld].reshape(cap, ld) if n else np.zeros((cap, 0), np.uint32),
                 nn=u32(nn)[:n], ref=ref, status=fpm.read_status(st), cap=cap, ld=ld,
-                dev=dict(nbr=nbr, nn=nn))
+                dev=dict(list=lst, nn=nn))
 
 
 def ell_sets(v, n):

@@ -25,7 +25,7 @@ def test_grid_rule(fpm_lib):
     for L, per, r in [((16.79596, 16.79596, 16.79596), (1, 1, 1), 2.8), ((105.81456,) * 3, (1, 1, 1), 2.8),
                       ((6.46, 6.46, 6.46), (1, 1, 1), 2.8), ((1.6, 0.67, 0.4), (0, 0, 0), 0.0098),
                       ((9.0, 12.0, 5.7), (1, 1, 1), 2.8), ((6.0, 6.0, 6.0), (0, 0, 0), 2.8)]:
-        g = fpm.fpm_grid_make(fpm.make_box(L, per), r)
+        g = fpm.fpm_grid_make(fpm.make_box(L, per), r, 1000)
         nc, inv = oracle.cell_grid(L, per, r)
         assert tuple(g.nc) == tuple(int(x) for x in nc)
         assert np.array_equal(np.array(g.inv, np.float32), inv)
@@ -44,8 +44,8 @@ def test_invalid_arguments_rejected(fpm_lib):
     assert fpm_lib.fpm_celllist_build(ctypes.byref(fpm.make_box((10.0,) * 3)), ctypes.byref(g), 10, 0, None, None,
                                       None, None, None, None, None, None, None, 0, None, None, None) \
         == fpm.FPM_ERR_INVALID
-    assert fpm_lib.fpm_lj_forces(ctypes.byref(fpm.make_box((10.0,) * 3)), 10, 0, None, None, None, 0, 1.0, 1.0, 2.5,
-                                 None, None, None, 0, None) == fpm.FPM_ERR_INVALID
+    assert fpm_lib.fpm_lj_forces(ctypes.byref(fpm.make_box((10.0,) * 3)), ctypes.byref(g), 10, 0, None, None, None, 0,
+                                 1.0, 1.0, 2.5, None, None, None, 0, None, None) == fpm.FPM_ERR_INVALID
     assert fpm_lib.fpm_vv_step(ctypes.byref(fpm.make_box((10.0,) * 3)), 10, 0, 2, 0.005, None, None, None, None) \
         == fpm.FPM_ERR_INVALID
     assert fpm.fpm_status_string(fpm.FPM_ERR_CAPACITY).startswith("neighbour")
@@ -67,4 +67,20 @@ def test_workspace_sizes(fpm_lib):
     b64 = fpm.fpm_celllist_workspace(1000188, g, fpm.FPM_F64)
     assert b64 > b32 > 1000188 * 16
     assert fpm.fpm_reduce_workspace(1000188) >= 256 + (1000188 // 256) * 24
+    g = fpm.fpm_grid_make(fpm.make_box((105.81456,) * 3), 2.8, 1000188)
+    ntiles = g.tiles_x * g.nc[1] * g.nc[2]
+    assert fpm.fpm_reduce_workspace(1000188, g) >= 256 + ntiles * 24
+    assert fpm.fpm_verlet_list_bytes(1000188, g, 120) >= 60 * fpm.fpm_nbr_ld(1000188) * 4
+
+
+def test_tile_width_rule(fpm_lib):
+    """About 170 particles per tile, at most 14 cells wide; every tile at
+    least one cell."""
+    for L, n in [((105.81456,) * 3, 1000188), ((16.79596,) * 3, 4000), ((6.46,) * 3, 256), ((60.0,) * 3, 1000)]:
+        g = fpm.fpm_grid_make(fpm.make_box(L), 2.8, n)
+        width = -(-g.nc[0] // g.tiles_x)
+        assert 1 <= g.tiles_x <= g.nc[0] and width <= 14
+        if g.nc[0] > 1:
+            per_tile = n / (g.nc[1] * g.nc[2] * g.tiles_x)
+            assert per_tile < 2 * 170 + 2 * n / g.ncell
     assert fpm.fpm_nbr_ld(1000188) % 32 == 0 and fpm.fpm_nbr_ld(1000188) >= 1000188

@@ -78,7 +78,7 @@ def test_verlet_gate(cuda, prec):
     gate = st.data_ptr() + 8
     n = 800
     cap = 128
-    nbr = torch.full((cap * fpm.fpm_nbr_ld(n),), -1, dtype=torch.int32, device="cuda")
+    nbr = torch.zeros((fpm.fpm_verlet_list_bytes(n, g["grid"], cap),), dtype=torch.uint8, device="cuda")
     nn = torch.full((n,), -1, dtype=torch.int32, device="cuda")
     fpm.fpm_verlet_build(g["box"], g["grid"], n, fprec(prec), g["dev"]["pos"], g["dev"]["cs"], 2.8, cap, nbr, nn,
                          None, st, gate)

@@ -33,7 +33,7 @@ def test_noalloc_matches_workspace_version(cuda, prec):
     for call in range(2):  # two calls in a row share the scratch array
         f = torch.full_like(s.force, float("nan"))
         e = torch.full((3,), float("nan"), dtype=torch.float64, device="cuda")
-        fpm.fpm_lj_forces_noalloc(s.box, s.n, s.prec, s.pos, s.nbr, s.nn, s.cap, s.eps, s.sigma, s.rc, f, e)
+        fpm.fpm_lj_forces_noalloc(s.box, s.grid, s.n, s.prec, s.pos, s.nbr, s.nn, s.cap, s.eps, s.sigma, s.rc, f, e)
         torch.cuda.synchronize()
         fn = f.cpu().numpy().astype(np.float64)
         en = e.cpu().numpy()
@@ -45,7 +45,8 @@ def test_noalloc_matches_workspace_version(cuda, prec):
 
 def test_noalloc_rejects_oversize(fpm_lib):
     box = fpm.make_box((10.0, 10.0, 10.0))
+    grid = fpm.fpm_grid_make(box, 2.8, 1000)
     with pytest.raises(fpm.FpmError) as e:
-        fpm.fpm_lj_forces_noalloc(box, (1 << 24) + 1, fpm.FPM_F32, 1, 1, 1, 64, 1.0, 1.0, 2.5, 1, 1, 0)
+        fpm.fpm_lj_forces_noalloc(box, grid, (1 << 24) + 1, fpm.FPM_F32, 1, 256, 1, 64, 1.0, 1.0, 2.5, 1, 1, None, 0)
     assert e.value.status == fpm.FPM_ERR_INVALID
     assert "scratch limit" in fpm.fpm_last_error()
