@@ -36,7 +36,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic per launch of the force kernel from one ncu capture, valid only
 # while the kernel source hashes to the recorded value (else reported null).
 # Filled from the ncu summary under profiles/ (see the design doc).
-NCU_TRAFFIC = {"lj.cu": {"sha": None, "bytes_per_launch": None}}
+NCU_TRAFFIC = {"lj.cu": {"sha": "a7ecc8bd38425de0", "bytes_per_launch": 184805120}}
 
 
 def parse():
@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--profile", default=None, choices=["forces", "step"],
+                    help="profiling target for ncu: build the 1M-atom system, then run --steps force sweeps "
+                         "or eager steps (no timing, no JSON line)")
     ap.add_argument("--fp64-steps", type=int, default=100)
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--kernel-reps", type=int, default=50)
@@ -340,8 +343,31 @@ def run_ours(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_target(args):
+    """A small, self-contained launch sequence for ncu captures."""
+    import torch
+    from paper_1804_07598_gb300 import build as fbuild
+    from paper_1804_07598_gb300 import inputs
+    from paper_1804_07598_gb300.md import LJSystem
+    fbuild.build()
+    wl = inputs.WORKLOADS[WORKLOAD]
+    pos, vel, L = inputs.lj_state(wl)
+    s = LJSystem(pos, vel, L, eps=wl.eps, sigma=wl.sigma, rc=wl.rc, skin=wl.skin, dt=wl.dt, precision="f32")
+    for _ in range(args.steps):
+        if args.profile == "forces":
+            s.compute_forces()
+        else:
+            s.step(1)
+    torch.cuda.synchronize()
+    s.check_status()
+    print(f"profile target done: {args.profile} x{args.steps}, n={s.n}", flush=True)
+
+
 def main():
     args = parse()
+    if args.profile:
+        run_profile_target(args)
+        return
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)
