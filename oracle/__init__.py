@@ -4,8 +4,9 @@ TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
 package.  The product library (``paper_1804_07598_gb300``) never imports it and
 shares no code with it: the arithmetic lives in ``fpm_oracle.c`` (plain C,
-compiled by gcc with ``-ffp-contract=off``) and in ``sph.py`` / ``adjoint.py``
-of this package; this module only marshals numpy arrays.
+compiled by gcc with ``-ffp-contract=off``); this module marshals numpy
+arrays and, for the adjoint, applies the reverse of velocity Verlet step by
+step in plain numpy on top of the C force and Hessian-vector routines.
 
 Every function cites the passage of the paper it follows; the conventions the
 paper leaves open are listed at the top of ``fpm_oracle.c``.
@@ -270,3 +271,76 @@ def lj_nve(pos, vel, L, periodic, eps, sigma, rc, dt, nsteps, record=True):
                         ptr):
         raise ValueError("box too small for the cutoff")
     return p, v, e
+
+
+# --------------------------------------------------------------------------
+# Adjoint of the LJ force and of velocity Verlet (the differentiable workload;
+# the paper has no adjoint: these are the chain rule applied to Sec. 4.1's
+# force and Listing 4.1's integrator)
+# --------------------------------------------------------------------------
+
+def lj_hvp(pos, a, L, periodic, eps, sigma, rc, mask_f32=False):
+    """(J a) with J = dF/dx (symmetric), a.dF/d(eps, sigma) and dU/d(eps, sigma).
+    Returns (Ja [n,4], dtheta[2], dU[2])."""
+    lib_ = lib()
+    if not hasattr(lib_.orc_lj_hvp, "_set"):
+        lib_.orc_lj_hvp.restype = ctypes.c_int
+        lib_.orc_lj_hvp.argtypes = [ctypes.c_int, _P(np.float64), _P(np.float64), _P(np.int32), ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_double, ctypes.c_int, _P(np.float64), _P(np.float64),
+                                    _P(np.float64), _P(np.float64)]
+        lib_.orc_lj_hvp._set = True
+    p, av = _pos4(pos, np.float64), _pos4(a, np.float64)
+    Lb, pb = _box(L, periodic)
+    out = np.zeros_like(p)
+    dth = np.zeros(2)
+    dU = np.zeros(2)
+    if lib_.orc_lj_hvp(p.shape[0], p, Lb, pb, float(eps), float(sigma), float(rc), int(bool(mask_f32)), av, out,
+                       dth, dU):
+        raise ValueError("box too small for the cutoff")
+    return out, dth, dU
+
+
+def lj_rollout_loss(pos, vel, L, periodic, eps, sigma, rc, dt, nsteps):
+    """Loss of the differentiable workload: run nsteps of NVE velocity Verlet
+    from (pos, vel) in FP64, then L = U(x_T) + sum_i |F_i(x_T)|^2."""
+    p, v, _ = lj_nve(pos, vel, L, periodic, eps, sigma, rc, dt, nsteps, record=False)
+    f, U, _, _ = lj_forces(p, L, periodic, eps, sigma, rc)
+    return U + float(np.sum(f[:, :3] ** 2))
+
+
+def lj_rollout_grad(pos, vel, L, periodic, eps, sigma, rc, dt, nsteps):
+    """Gradient of lj_rollout_loss w.r.t. the initial positions, the initial
+    velocities, eps and sigma, by the reverse of velocity Verlet:
+      seed   xbar = -F_T + 2 J(x_T) F_T, vbar = 0,
+             thbar = dU/dth + 2 F_T . dF/dth;
+      step n+1 -> n:
+             xbar += J(x_{n+1}) (dt/2 vbar); thbar += (dt/2 vbar) . dF/dth(x_{n+1})
+             vbar += dt xbar
+             xbar += J(x_n) (dt/2 vbar);     thbar += (dt/2 vbar) . dF/dth(x_n)
+    Returns (loss, xbar0 [n,3], vbar0 [n,3], thbar [2])."""
+    p = _pos4(pos, np.float64)
+    v = _pos4(vel, np.float64)
+    xs = [p.copy()]
+    for _ in range(nsteps):
+        p, v, _ = lj_nve(p, v, L, periodic, eps, sigma, rc, dt, 1, record=False)
+        xs.append(p.copy())
+    fT, U, _, _ = lj_forces(xs[-1], L, periodic, eps, sigma, rc)
+    loss = U + float(np.sum(fT[:, :3] ** 2))
+    fT[:, 3] = 0.0
+    JF, dth, dU = lj_hvp(xs[-1], fT, L, periodic, eps, sigma, rc)
+    xbar = -fT[:, :3] + 2.0 * JF[:, :3]
+    vbar = np.zeros_like(xbar)
+    thbar = dU + 2.0 * dth
+    h = 0.5 * dt
+    for n in range(nsteps - 1, -1, -1):
+        a = np.zeros((xbar.shape[0], 4))
+        a[:, :3] = h * vbar
+        Ja, dth, _ = lj_hvp(xs[n + 1], a, L, periodic, eps, sigma, rc)
+        xbar = xbar + Ja[:, :3]
+        thbar = thbar + dth
+        vbar = vbar + dt * xbar
+        a[:, :3] = h * vbar
+        Ja, dth, _ = lj_hvp(xs[n], a, L, periodic, eps, sigma, rc)
+        xbar = xbar + Ja[:, :3]
+        thbar = thbar + dth
+    return loss, xbar, vbar, thbar

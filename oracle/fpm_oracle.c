@@ -562,3 +562,65 @@ int orc_lj_nve(int n, double *pos4, double *vel4, const double L[3], const int p
     free(f);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint of the LJ force (not in the paper; the differentiable workload)  */
+/* ------------------------------------------------------------------------ */
+
+/* Hessian-vector product of the LJ force field and parameter derivatives.
+ * With s = r^2, phi(s) = 24 eps (2 sigma^12 s^-7 - sigma^6 s^-4) the pair
+ * force factor (F_i = sum_j phi r_ij, r_ij = x_i - x_j) and
+ * dphi/ds = 24 eps (-14 sigma^12 s^-8 + 4 sigma^6 s^-5):
+ *   out_i  += sum_j [phi (a_i - a_j) + 2 dphi/ds (r_ij . (a_i - a_j)) r_ij]
+ *             = (J a)_i with J = dF/dx (symmetric),
+ *   dth[0] += sum_i a_i . dF_i/d eps   = sum_pairs (a_i - a_j) . r_ij phi / eps,
+ *   dth[1] += sum_i a_i . dF_i/d sigma = sum_pairs (a_i - a_j) . r_ij
+ *             24 eps (24 sigma^11 s^-7 - 6 sigma^5 s^-4),
+ *   dU[0]  += dU/d eps   = sum_pairs 4 (sigma^12 s^-6 - sigma^6 s^-3),
+ *   dU[1]  += dU/d sigma = sum_pairs 4 eps (12 sigma^11 s^-6 - 6 sigma^5 s^-3).
+ * Pairs inside rc exactly as in orc_lj_forces (mask_f32 likewise).  out4 is
+ * [n][4] and is overwritten (w = 0). Returns 0 or 1 (box too small). */
+int orc_lj_hvp(int n, const double *pos4, const double L[3], const int periodic[3],
+               double eps, double sigma, double rc, int mask_f32, const double *a4,
+               double *out4, double dth[2], double dU[2])
+{
+    orc_cells cl;
+    double r_cell = mask_f32 ? rc * (1.0 + 1.0 / 65536.0) : rc;
+    if (cells_build(&cl, n, NULL, pos4, L, periodic, r_cell)) return 1;
+    memset(out4, 0, sizeof(double) * 4 * (size_t)n);
+    dth[0] = dth[1] = dU[0] = dU[1] = 0.0;
+    double s2 = sigma * sigma, s6 = s2 * s2 * s2, s12 = s6 * s6;
+    double s5 = s6 / sigma, s11 = s12 / sigma;
+    uint32_t *cand = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) {
+        const double *xi = pos4 + 4 * (size_t)i;
+        int m = stencil_candidates(&cl, periodic, cl.cell[i], cand);
+        for (int t = 0; t < m; ++t) {
+            uint32_t j = cand[t];
+            if (j <= (uint32_t)i) continue;
+            double r[3];
+            if (!pair_inside(xi, pos4 + 4 * (size_t)j, L, periodic, rc, mask_f32, r)) continue;
+            double s = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+            double s3 = s * s * s, s4 = s3 * s, s5p = s4 * s, s6p = s3 * s3, s7 = s6p * s, s8 = s7 * s;
+            double phi = 24.0 * eps * (2.0 * s12 / s7 - s6 / s4);
+            double dphi = 24.0 * eps * (-14.0 * s12 / s8 + 4.0 * s6 / s5p);
+            double da[3], rda = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                da[d] = a4[4 * (size_t)i + d] - a4[4 * (size_t)j + d];
+                rda += r[d] * da[d];
+            }
+            for (int d = 0; d < 3; ++d) {
+                double h = phi * da[d] + 2.0 * dphi * rda * r[d];
+                out4[4 * (size_t)i + d] += h;
+                out4[4 * (size_t)j + d] -= h;
+            }
+            dth[0] += rda * phi / eps;
+            dth[1] += rda * 24.0 * eps * (24.0 * s11 / s7 - 6.0 * s5 / s4);
+            dU[0] += 4.0 * (s12 / s6p - s6 / s3);
+            dU[1] += 4.0 * eps * (12.0 * s11 / s6p - 6.0 * s5 / s3);
+        }
+    }
+    free(cand);
+    cells_free(&cl);
+    return 0;
+}
