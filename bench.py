@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--kernel-reps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--adjoint-steps", type=int, default=200)
     return ap.parse_args()
 
 
@@ -310,6 +311,28 @@ def run_ours(args, ws, rank, local):
     d2h = h2d + he.numel() * he.element_size()
     s.check_status()
 
+    # adjoint / forward cost on the differentiable workload (32,768 particles,
+    # 200 NVE steps, checkpoints every 20, FP32 forward, FP64 adjoint state)
+    adj = None
+    if args.adjoint_steps > 0:
+        from paper_1804_07598_gb300.adjoint import LJAdjointRunner
+        wla = inputs.WORKLOADS["lj_adjoint"]
+        xa, va, La = inputs.lj_state(wla)
+        runner = LJAdjointRunner(xa, va, La, nsteps=args.adjoint_steps, every=20, precision="f32", dt=wla.dt)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        runner.forward()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        runner.backward()
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        adj = {"workload": f"lj_adjoint: {wla.n} particles, FCC 16x16x32, {args.adjoint_steps} steps, "
+                           f"checkpoints every 20, loss U + sum|F|^2",
+               "forward_s": t1 - t0, "backward_s": t2 - t1, "adjoint_over_forward": (t2 - t1) / (t1 - t0),
+               "note": "both passes issue eager launches; backward = segment recomputation + reverse sweeps"}
+        del runner
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline(args.cpu_steps)
@@ -336,6 +359,7 @@ def run_ours(args, ws, rank, local):
                      "alg_bytes_per_launch": alg_bytes, "launch_us": force_us},
         "e2e": {"value": ws * args.e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
+        "adjoint": adj,
         "gpu_launches": per_step_launches * args.steps,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,

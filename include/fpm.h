@@ -289,6 +289,47 @@ fpm_status fpm_vv_drift_check(const fpm_box *box, int32_t n, fpm_prec prec, doub
 fpm_status fpm_kinetic(int32_t n, fpm_prec prec, const void *vel, double *d_out,
                        void *workspace, size_t workspace_bytes, fpm_stream stream);
 
+/* ------------------------------------------------------------------ */
+/* Adjoint of the LJ force and of velocity Verlet (not in the paper:     */
+/* the chain rule applied to the force of Sec. 4.1 and the integrator    */
+/* of Listing 4.1, for gradients w.r.t. positions, eps and sigma)        */
+/* ------------------------------------------------------------------ */
+
+/* Backward sweep of the LJ force over a Verlet list (same box, grid, list,
+ * nn, cap and cutoff as fpm_lj_forces).  With J = dF/dx (symmetric):
+ *   adj_pos[i].xyz += scale * (J a)_i                       (FP64, double4 [n])
+ *   d_params[0]    += scale * sum_i a_i . dF_i/d eps
+ *   d_params[1]    += scale * sum_i a_i . dF_i/d sigma
+ *   d_params[2]    += dU/d eps,  d_params[3] += dU/d sigma    (U as in fpm_lj_forces)
+ * a : [n] float4|double4 in the positions' precision (w ignored).  Pair
+ * arithmetic in the positions' precision; adj_pos and d_params accumulate in
+ * FP64 (d_params in a fixed order, bit-reproducible).  d_params may be NULL
+ * (then no workspace is needed).  workspace : fpm_reduce_workspace(n, grid).
+ * adj_pos 32-byte aligned. */
+fpm_status fpm_lj_backward(const fpm_box *box, const fpm_grid *grid, int32_t n, fpm_prec prec, const void *pos,
+                           const void *list, const uint32_t *nn, int32_t cap,
+                           double eps, double sigma, double rc,
+                           const void *a, double scale, double *adj_pos, double *d_params,
+                           void *workspace, size_t workspace_bytes, fpm_dev_status *d_status, fpm_stream stream);
+
+/* One reverse velocity-Verlet update of the FP64 adjoint state (xbar, vbar:
+ * double4 [n]).  For every k, with j = perm[k] (perm from the cell-list build
+ * that reordered the particles during this step) or j = k (perm NULL):
+ *   xbar_out[j] = xbar_in[k];  vbar_out[j] = vbar_in[k] + dt * xbar_in[k];
+ *   a_out[j] = (T)(c * vbar_out[j])   (float4|double4, the vector for the next
+ *                                      fpm_lj_backward).
+ * With perm, inputs and outputs must be distinct arrays; without, they may
+ * alias. */
+fpm_status fpm_vv_adjoint(int32_t n, fpm_prec prec, const uint32_t *perm, double dt, double c,
+                          const double *xbar_in, const double *vbar_in, double *xbar_out, double *vbar_out,
+                          void *a_out, fpm_stream stream);
+
+/* Seed of the loss L = U(x_T) + sum_i |F_i(x_T)|^2: xbar = -F, vbar = 0,
+ * a_out = F (so that fpm_lj_backward(a_out, scale = 2) adds 2 J F and
+ * 2 F . dF/d(eps, sigma), and its d_params[2..3] add dU/d(eps, sigma)). */
+fpm_status fpm_adjoint_seed(int32_t n, fpm_prec prec, const void *force, double *xbar, double *vbar,
+                            void *a_out, fpm_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -192,7 +192,8 @@ template <typename TV> __device__ __forceinline__ TV warp_sum(TV v)
 // runs at a small fraction of the FP32 rate on this GPU, so the per-thread
 // values are not widened before the warp stage.)
 template <int NV, typename TV>
-__device__ void grid_reduce(TV (&v)[NV], double *part, unsigned *counter, double *out)
+__device__ void grid_reduce(TV (&v)[NV], double *part, unsigned *counter, double *out, bool accumulate = false,
+                            const double *scale = nullptr)
 {
     __shared__ double sh[32][NV];
     __shared__ bool last;
@@ -237,7 +238,8 @@ __device__ void grid_reduce(TV (&v)[NV], double *part, unsigned *counter, double
         for (int k = 0; k < NV; ++k) {
             double s = lane < nw ? sh[lane][k] : 0.0;
             s = warp_sum(s);
-            if (lane == 0 && out) out[k] = s;
+            const double val = scale ? scale[k] * s : s;
+            if (lane == 0 && out) out[k] = accumulate ? out[k] + val : val;
         }
         if (lane == 0) *counter = 0u;
     }

@@ -284,11 +284,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
 
 // Stages the neighbourhood positions of a tile into shared memory: slot s of
 // piece p holds pos[gstart + (s - soff)] with the lower-wall shifts applied
-// and (in tiles that need them) the piece flags in w.  Returns false, the same
-// in every thread, if the copies did not complete within the wait budget.
+// and (in tiles that need them) the piece flags in w.  When aux is given, the
+// same slots of a second per-particle array (an adjoint vector) are copied
+// unchanged into aux_st on the same barrier.  Returns false, the same in every
+// thread, if the copies did not complete within the wait budget.
 template <typename T>
 __device__ bool stage_positions(const TileDesc &d, const BoxT<T> &box, const V4<T> *__restrict__ pos,
-                                V4<T> *__restrict__ st, uint64_t *bar, fpm_dev_status *status)
+                                V4<T> *__restrict__ st, uint64_t *bar, fpm_dev_status *status,
+                                const V4<T> *__restrict__ aux = nullptr, V4<T> *__restrict__ aux_st = nullptr)
 {
     const uint32_t b = smem_u32(bar);
     if (threadIdx.x == 0) {
@@ -298,16 +301,23 @@ __device__ bool stage_positions(const TileDesc &d, const BoxT<T> &box, const V4<
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        const uint32_t bytes = (uint32_t)d.M * (uint32_t)sizeof(V4<T>);
+        const uint32_t bytes = (uint32_t)d.M * (uint32_t)sizeof(V4<T>) * (aux ? 2u : 1u);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
         for (int p = 0; p < kMaxPieces; ++p) {
             const Piece pc = d.piece[p];
             if (pc.len == 0) continue;
+            const uint32_t nb = (uint32_t)pc.len * (uint32_t)sizeof(V4<T>);
             asm volatile(
                 "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                     smem_u32(st + pc.soff)),
-                "l"(pos + pc.gstart), "r"((uint32_t)pc.len * (uint32_t)sizeof(V4<T>)), "r"(b)
+                "l"(pos + pc.gstart), "r"(nb), "r"(b)
                 : "memory");
+            if (aux)
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_u32(aux_st + pc.soff)),
+                    "l"(aux + pc.gstart), "r"(nb), "r"(b)
+                    : "memory");
         }
     }
     bool ok = mbar_wait(b, 0u, kWaitCycles);
@@ -333,6 +343,17 @@ __device__ bool stage_positions(const TileDesc &d, const BoxT<T> &box, const V4<
     }
     __syncthreads();
     return true;
+}
+
+// Sorted particle index held by staged slot s.
+__device__ __forceinline__ uint32_t staged_index(const TileDesc &d, int s)
+{
+    uint32_t j = 0;
+    for (int k = 0; k < kMaxPieces; ++k) {
+        const Piece pc = d.piece[k];
+        if (pc.len > 0 && s >= pc.soff && s < pc.soff + pc.len) j = pc.gstart + (uint32_t)(s - pc.soff);
+    }
+    return j;
 }
 
 // Position of staged slot s read straight from global memory (used when the

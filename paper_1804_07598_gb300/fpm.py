@@ -88,6 +88,12 @@ _SIG = {
                                _VP]),
     "fpm_vv_drift_check": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.c_int, _c.c_double, _VP, _VP, _VP, _VP,
                                       _c.c_double, _VP, _VP]),
+    "fpm_lj_backward": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _c.c_int, _VP, _VP, _VP,
+                                   _c.c_int32, _c.c_double, _c.c_double, _c.c_double, _VP, _c.c_double, _VP, _VP,
+                                   _VP, _c.c_size_t, _VP, _VP]),
+    "fpm_vv_adjoint": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _c.c_double, _c.c_double, _VP, _VP, _VP, _VP, _VP,
+                                  _VP]),
+    "fpm_adjoint_seed": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _VP, _VP, _VP, _VP]),
     "fpm_kinetic": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _VP, _VP, _c.c_size_t, _VP]),
 }
 
@@ -281,3 +287,24 @@ def fpm_kinetic(n, prec, vel, d_out, workspace, stream=None):
     _check(lib().fpm_kinetic(int(n), int(prec), _ptr(vel), _ptr(d_out), _ptr(workspace), _nbytes(workspace),
                              _stream(stream)))
     _count(1)
+
+
+def fpm_lj_backward(box, grid, n, prec, pos, list_obj, nn, cap, eps, sigma, rc, a, scale, adj_pos, d_params=None,
+                    workspace=None, d_status=None, stream=None):
+    _check(lib().fpm_lj_backward(_c.byref(box), _c.byref(grid), int(n), int(prec), _ptr(pos), _ptr(list_obj),
+                                 _ptr(nn), int(cap), float(eps), float(sigma), float(rc), _ptr(a), float(scale),
+                                 _ptr(adj_pos), _ptr(d_params), _ptr(workspace), _nbytes(workspace), _ptr(d_status),
+                                 _stream(stream)))
+    _count(1 if n > 0 else 0)
+
+
+def fpm_vv_adjoint(n, prec, perm, dt, c, xbar_in, vbar_in, xbar_out, vbar_out, a_out, stream=None):
+    _check(lib().fpm_vv_adjoint(int(n), int(prec), _ptr(perm), float(dt), float(c), _ptr(xbar_in), _ptr(vbar_in),
+                                _ptr(xbar_out), _ptr(vbar_out), _ptr(a_out), _stream(stream)))
+    _count(1 if n > 0 else 0)
+
+
+def fpm_adjoint_seed(n, prec, force, xbar, vbar, a_out, stream=None):
+    _check(lib().fpm_adjoint_seed(int(n), int(prec), _ptr(force), _ptr(xbar), _ptr(vbar), _ptr(a_out),
+                                  _stream(stream)))
+    _count(1 if n > 0 else 0)
