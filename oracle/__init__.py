@@ -344,3 +344,110 @@ def lj_rollout_grad(pos, vel, L, periodic, eps, sigma, rc, dt, nsteps):
         xbar = xbar + Ja[:, :3]
         thbar = thbar + dth
     return loss, xbar, vbar, thbar
+
+
+# --------------------------------------------------------------------------
+# Weakly compressible SPH (Sec. 4.2, Eqs. 1-5)
+# --------------------------------------------------------------------------
+
+class _SphParams(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_double), ("m", ctypes.c_double), ("rho0", ctypes.c_double), ("c0", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("alpha", ctypes.c_double), ("eta2", ctypes.c_double),
+                ("g", ctypes.c_double * 3), ("kernel", ctypes.c_int)]
+
+
+def sph_params(h, m, rho0=1000.0, c0=None, gamma=7.0, alpha=0.1, g=(0.0, 0.0, -9.81), kernel="wendland",
+               h_swl=0.3):
+    """SPH parameter block.  c0 defaults to 20 sqrt(|g| h_swl) (the reading of
+    Eq. 4's c_sound = 20); eta^2 = 0.01 h^2."""
+    if c0 is None:
+        c0 = 20.0 * float(np.sqrt(np.linalg.norm(g) * h_swl))
+    p = _SphParams()
+    p.h, p.m, p.rho0, p.c0, p.gamma, p.alpha, p.eta2 = h, m, rho0, c0, gamma, alpha, 0.01 * h * h
+    for d in range(3):
+        p.g[d] = g[d]
+    p.kernel = 0 if kernel == "wendland" else 1
+    return p
+
+
+def _sph_sig():
+    L_ = lib()
+    if getattr(L_, "_sph_set", False):
+        return L_
+    PP = ctypes.POINTER(_SphParams)
+    f64 = ctypes.c_double
+    for name, res, args in [
+        ("orc_sph_kernel", None, [ctypes.c_int, f64, f64, ctypes.POINTER(f64), ctypes.POINTER(f64)]),
+        ("orc_sph_eos", f64, [PP, f64]),
+        ("orc_sph_density_sum", ctypes.c_int, [ctypes.c_int, _P(np.float64), _P(np.float64), _P(np.int32), PP,
+                                               _P(np.float64)]),
+        ("orc_sph_rates", ctypes.c_int, [ctypes.c_int, _P(np.float64), _P(np.float64), _P(np.float64),
+                                         _P(np.float64), _P(np.int32), PP, ctypes.c_int, _P(np.float64),
+                                         _P(np.float64), _P(np.float64)]),
+        ("orc_sph_dt", f64, [PP, _P(np.float64), f64]),
+        ("orc_sph_step", f64, [ctypes.c_int, _P(np.float64), _P(np.float64), _P(np.float64), _P(np.float64),
+                               _P(np.int32), PP, f64]),
+    ]:
+        fn = getattr(L_, name)
+        fn.restype = res
+        fn.argtypes = args
+    L_._sph_set = True
+    return L_
+
+
+def sph_kernel(p, r):
+    """(W(r), dW/dr(r)) for an array of distances."""
+    L_ = _sph_sig()
+    r = np.atleast_1d(np.asarray(r, np.float64))
+    W, D = np.zeros_like(r), np.zeros_like(r)
+    w, d = ctypes.c_double(), ctypes.c_double()
+    for k, x in enumerate(r):
+        L_.orc_sph_kernel(p.kernel, p.h, float(x), ctypes.byref(w), ctypes.byref(d))
+        W[k], D[k] = w.value, d.value
+    return W, D
+
+
+def sph_eos(p, rho):
+    L_ = _sph_sig()
+    return np.array([L_.orc_sph_eos(ctypes.byref(p), float(x)) for x in np.atleast_1d(rho)])
+
+
+def sph_density_sum(pos, L, periodic, p):
+    L_ = _sph_sig()
+    x = _pos4(pos, np.float64)
+    Lb, pb = _box(L, periodic)
+    rho = np.zeros(x.shape[0])
+    if L_.orc_sph_density_sum(x.shape[0], x, Lb, pb, ctypes.byref(p), rho):
+        raise ValueError("box too small for the support")
+    return rho
+
+
+def sph_rates(pos, vel, rho, L, periodic, p, mask_f32=False):
+    """Eqs. 1-2 rates: (acc [n,4], drho [n], (max|a| fluid, max|mu|)).
+    pos[:,3] is the particle type (0 fluid, 1 fixed boundary)."""
+    L_ = _sph_sig()
+    x, v = _pos4(pos, np.float64), _pos4(vel, np.float64)
+    r = np.ascontiguousarray(rho, np.float64)
+    Lb, pb = _box(L, periodic)
+    acc = np.zeros_like(x)
+    dr = np.zeros(x.shape[0])
+    dtc = np.zeros(2)
+    if L_.orc_sph_rates(x.shape[0], x, v, r, Lb, pb, ctypes.byref(p), int(bool(mask_f32)), acc, dr, dtc):
+        raise ValueError("box too small for the support")
+    return acc, dr, dtc
+
+
+def sph_dt(p, dtc, cfl=0.2):
+    return float(_sph_sig().orc_sph_dt(ctypes.byref(p), np.ascontiguousarray(dtc, np.float64), float(cfl)))
+
+
+def sph_step(pos, vel, rho, L, periodic, p, cfl=0.2):
+    """One symplectic step; returns (pos, vel, rho, dt)."""
+    L_ = _sph_sig()
+    x, v = _pos4(pos, np.float64), _pos4(vel, np.float64)
+    r = np.array(rho, np.float64)
+    Lb, pb = _box(L, periodic)
+    dt = L_.orc_sph_step(x.shape[0], x, v, r, Lb, pb, ctypes.byref(p), float(cfl))
+    if dt < 0:
+        raise ValueError("box too small for the support")
+    return x, v, r, dt

@@ -624,3 +624,210 @@ int orc_lj_hvp(int n, const double *pos4, const double L[3], const int periodic[
     cells_free(&cl);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Weakly compressible SPH (Sec. 4.2, Eqs. 1-5)                              */
+/* ------------------------------------------------------------------------ */
+
+/* Parameters.  kernel 0: Wendland C2, W = a (1 - q/2)^4 (2q + 1),
+ * a = 21 / (16 pi h^3), q = r/h in [0, 2]; kernel 1: cubic spline,
+ * W = s [1 - 1.5 q^2 + 0.75 q^3] (q < 1), s 0.25 (2 - q)^3 (1 <= q < 2),
+ * s = 1 / (pi h^3).  Both have support 2h. */
+typedef struct {
+    double h, m, rho0, c0, gamma, alpha, eta2, g[3];
+    int kernel;
+} orc_sph_params;
+
+/* W(r) and dW/dr for one distance r >= 0. */
+void orc_sph_kernel(int kernel, double h, double r, double *W, double *dWdr)
+{
+    const double pi = 3.14159265358979323846;
+    double q = r / h;
+    *W = 0.0;
+    *dWdr = 0.0;
+    if (q >= 2.0) return;
+    if (kernel == 0) {
+        double a = 21.0 / (16.0 * pi * h * h * h);
+        double t = 1.0 - 0.5 * q;
+        *W = a * t * t * t * t * (2.0 * q + 1.0);
+        *dWdr = a / h * (-2.0 * t * t * t * (2.0 * q + 1.0) + 2.0 * t * t * t * t);
+    } else {
+        double s = 1.0 / (pi * h * h * h);
+        if (q < 1.0) {
+            *W = s * (1.0 - 1.5 * q * q + 0.75 * q * q * q);
+            *dWdr = s / h * (-3.0 * q + 2.25 * q * q);
+        } else {
+            double t = 2.0 - q;
+            *W = s * 0.25 * t * t * t;
+            *dWdr = s / h * (-0.75 * t * t);
+        }
+    }
+}
+
+/* Tait equation of state (Eqs. 3-4): P = b [(rho/rho0)^gamma - 1],
+ * b = c0^2 rho0 / gamma. */
+double orc_sph_eos(const orc_sph_params *p, double rho)
+{
+    double b = p->c0 * p->c0 * p->rho0 / p->gamma;
+    return b * (pow(rho / p->rho0, p->gamma) - 1.0);
+}
+
+/* Density by summation, sum_j m W(|x_i - x_j|) including j = i. */
+int orc_sph_density_sum(int n, const double *pos4, const double L[3], const int periodic[3],
+                        const orc_sph_params *p, double *rho)
+{
+    orc_cells cl;
+    double rcut = 2.0 * p->h;
+    if (cells_build(&cl, n, NULL, pos4, L, periodic, rcut)) return 1;
+    uint32_t *cand = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) {
+        double W, dW;
+        orc_sph_kernel(p->kernel, p->h, 0.0, &W, &dW);
+        double s = p->m * W;
+        int m = stencil_candidates(&cl, periodic, cl.cell[i], cand);
+        for (int t = 0; t < m; ++t) {
+            uint32_t j = cand[t];
+            if (j == (uint32_t)i) continue;
+            double r[3];
+            double r2 = sep_f64(pos4 + 4 * (size_t)i, pos4 + 4 * (size_t)j, L, periodic, r);
+            if (!(r2 < rcut * rcut)) continue;
+            orc_sph_kernel(p->kernel, p->h, sqrt(r2), &W, &dW);
+            s += p->m * W;
+        }
+        rho[i] = s;
+    }
+    free(cand);
+    cells_free(&cl);
+    return 0;
+}
+
+/* Rates of Eqs. 1-2 for every particle.  pos4 w holds the type: 0 fluid,
+ * 1 fixed boundary particle.  For each pair p<q inside the support 2h (the
+ * test r^2 < (2h)^2 in single precision when mask_f32):
+ *   grad_p W = (dW/dr) (x_p - x_q) / r,  v_pq = v_p - v_q,
+ *   drho_p += m v_pq . grad_p W,   drho_q += the same,
+ *   Pi = -alpha c0 mu / rhobar with mu = h v_pq.(x_p - x_q) / (r^2 + eta^2),
+ *        rhobar = (rho_p + rho_q)/2, when v_pq.(x_p - x_q) < 0, else 0,
+ *   acc_p += -m ((P_p + P_q)/(rho_p rho_q) + Pi) grad_p W,  acc_q -= the same;
+ * then acc += g for fluid particles and acc = 0 for boundary particles.
+ * dtc[0] = max |acc| over fluid particles, dtc[1] = max |mu| over pairs. */
+int orc_sph_rates(int n, const double *pos4, const double *vel4, const double *rho, const double L[3],
+                  const int periodic[3], const orc_sph_params *p, int mask_f32, double *acc4, double *drho,
+                  double dtc[2])
+{
+    orc_cells cl;
+    double rcut = 2.0 * p->h;
+    double r_cell = mask_f32 ? rcut * (1.0 + 1.0 / 65536.0) : rcut;
+    if (cells_build(&cl, n, NULL, pos4, L, periodic, r_cell)) return 1;
+    memset(acc4, 0, sizeof(double) * 4 * (size_t)n);
+    memset(drho, 0, sizeof(double) * (size_t)n);
+    double *P = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) P[i] = orc_sph_eos(p, rho[i]);
+    double mumax = 0.0;
+    uint32_t *cand = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) {
+        const double *xi = pos4 + 4 * (size_t)i;
+        int m = stencil_candidates(&cl, periodic, cl.cell[i], cand);
+        for (int t = 0; t < m; ++t) {
+            uint32_t j = cand[t];
+            if (j <= (uint32_t)i) continue;
+            const double *xj = pos4 + 4 * (size_t)j;
+            double r[3];
+            if (!pair_inside(xi, xj, L, periodic, rcut, mask_f32, r)) continue;
+            double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+            double rr = sqrt(r2);
+            double W, dW;
+            orc_sph_kernel(p->kernel, p->h, rr, &W, &dW);
+            double gw[3], vr = 0.0, vdg = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                gw[d] = rr > 0.0 ? dW * r[d] / rr : 0.0;
+                double v = vel4[4 * (size_t)i + d] - vel4[4 * (size_t)j + d];
+                vr += v * r[d];
+                vdg += v * gw[d];
+            }
+            drho[i] += p->m * vdg;
+            drho[j] += p->m * vdg;
+            double mu = p->h * vr / (r2 + p->eta2);
+            if (fabs(mu) > mumax) mumax = fabs(mu);
+            double Pi = 0.0;
+            if (vr < 0.0) Pi = -p->alpha * p->c0 * mu / (0.5 * (rho[i] + rho[j]));
+            double c = -p->m * ((P[i] + P[j]) / (rho[i] * rho[j]) + Pi);
+            for (int d = 0; d < 3; ++d) {
+                acc4[4 * (size_t)i + d] += c * gw[d];
+                acc4[4 * (size_t)j + d] -= c * gw[d];
+            }
+        }
+    }
+    double amax = 0.0;
+    for (int i = 0; i < n; ++i) {
+        if (pos4[4 * (size_t)i + 3] != 0.0) {
+            acc4[4 * (size_t)i] = acc4[4 * (size_t)i + 1] = acc4[4 * (size_t)i + 2] = 0.0;
+            continue;
+        }
+        double a2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            acc4[4 * (size_t)i + d] += p->g[d];
+            a2 += acc4[4 * (size_t)i + d] * acc4[4 * (size_t)i + d];
+        }
+        if (sqrt(a2) > amax) amax = sqrt(a2);
+    }
+    dtc[0] = amax;
+    dtc[1] = mumax;
+    free(cand);
+    free(P);
+    cells_free(&cl);
+    return 0;
+}
+
+/* Time step from the constraints: dt = cfl min(sqrt(h / max|a|), h / (c0 + max|mu|)). */
+double orc_sph_dt(const orc_sph_params *p, const double dtc[2], double cfl)
+{
+    double dtf = dtc[0] > 0.0 ? sqrt(p->h / dtc[0]) : 1e300;
+    double dtv = p->h / (p->c0 + dtc[1]);
+    return cfl * (dtf < dtv ? dtf : dtv);
+}
+
+/* One symplectic step (predictor-corrector, the time stepping of Sec. 4.2):
+ *   dt from the constraints of the rates at t^n;
+ *   half: x += dt/2 v, v += dt/2 a, rho += dt/2 Drho (boundary: rho only);
+ *   rates at the half step;
+ *   v1 = v0 + dt a, x1 = x0 + dt (v1 + v0)/2 (fluid only),
+ *   rho1 = rho0 (2 - e)/(2 + e), e = -(Drho / rho_half) dt (all particles).
+ * Returns the dt used (negative on error). */
+double orc_sph_step(int n, double *pos4, double *vel4, double *rho, const double L[3], const int periodic[3],
+                    const orc_sph_params *p, double cfl)
+{
+    size_t m4 = 4 * (size_t)(n > 0 ? n : 1), m1 = (size_t)(n > 0 ? n : 1);
+    double *acc = (double *)malloc(sizeof(double) * m4), *dr = (double *)malloc(sizeof(double) * m1);
+    double *ph = (double *)malloc(sizeof(double) * m4), *vh = (double *)malloc(sizeof(double) * m4);
+    double *rh = (double *)malloc(sizeof(double) * m1);
+    double dtc[2];
+    double dt = -1.0;
+    if (orc_sph_rates(n, pos4, vel4, rho, L, periodic, p, 0, acc, dr, dtc)) goto done;
+    dt = orc_sph_dt(p, dtc, cfl);
+    memcpy(ph, pos4, sizeof(double) * 4 * (size_t)n);
+    memcpy(vh, vel4, sizeof(double) * 4 * (size_t)n);
+    for (int i = 0; i < n; ++i) {
+        rh[i] = rho[i] + 0.5 * dt * dr[i];
+        if (pos4[4 * (size_t)i + 3] != 0.0) continue;
+        for (int d = 0; d < 3; ++d) {
+            ph[4 * (size_t)i + d] = pos4[4 * (size_t)i + d] + 0.5 * dt * vel4[4 * (size_t)i + d];
+            vh[4 * (size_t)i + d] = vel4[4 * (size_t)i + d] + 0.5 * dt * acc[4 * (size_t)i + d];
+        }
+    }
+    if (orc_sph_rates(n, ph, vh, rh, L, periodic, p, 0, acc, dr, dtc)) { dt = -1.0; goto done; }
+    for (int i = 0; i < n; ++i) {
+        double e = -(dr[i] / rh[i]) * dt;
+        rho[i] = rho[i] * (2.0 - e) / (2.0 + e);
+        if (pos4[4 * (size_t)i + 3] != 0.0) continue;
+        for (int d = 0; d < 3; ++d) {
+            double v0 = vel4[4 * (size_t)i + d];
+            double v1 = v0 + dt * acc[4 * (size_t)i + d];
+            vel4[4 * (size_t)i + d] = v1;
+            pos4[4 * (size_t)i + d] += dt * 0.5 * (v1 + v0);
+        }
+    }
+done:
+    free(acc); free(dr); free(ph); free(vh); free(rh);
+    return dt;
+}
