@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--adjoint-steps", type=int, default=200)
+    ap.add_argument("--sph-steps", type=int, default=500)
     return ap.parse_args()
 
 
@@ -333,6 +334,33 @@ def run_ours(args, ws, rank, local):
                "note": "both passes issue eager launches; backward = segment recomputation + reverse sweeps"}
         del runner
 
+    # SPH dam break (2.13M particles: 1.51M fluid + 0.62M boundary), symplectic
+    # steps with dynamic dt, replayed from a CUDA graph
+    sph = None
+    if args.sph_steps > 0:
+        from paper_1804_07598_gb300.sph import SPHSystem
+        dd = inputs.dam_break(inputs.SPH_DP)
+        ss = SPHSystem(dd["pos"], dd["vel"], dd["rho"], dd["L"], dd["h"], dd["m"], c0=dd["c0"])
+        ss.step(3)
+        gs = ss.capture(steps_per_graph=1)
+        for _ in range(3):
+            gs.replay()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.sph_steps):
+            gs.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ss.check_status()
+        sms = e0.elapsed_time(e1)
+        nlist = int(ss.nn[: ss.n].sum().item())
+        sph = {"workload": f"dam break, dp {inputs.SPH_DP}, {dd['n_fluid']} fluid + {dd['n_boundary']} boundary "
+                           f"particles, Wendland C2 h = 1.3 dp, CFL 0.2, two rate evaluations per step",
+               "steps_per_s": args.sph_steps / (sms / 1e3), "ms_per_step": sms / args.sph_steps,
+               "particle_steps_per_s": ss.n * args.sph_steps / (sms / 1e3), "list_slots": nlist,
+               "simulated_time_s": float(ss.dt.cpu().numpy()[0]) * args.sph_steps}
+        del ss, gs
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         cpu = cpu_baseline(args.cpu_steps)
@@ -360,6 +388,7 @@ def run_ours(args, ws, rank, local):
         "e2e": {"value": ws * args.e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "adjoint": adj,
+        "sph": sph,
         "gpu_launches": per_step_launches * args.steps,
         "clocks": clk.summary(),
         "cpu_baseline": cpu,

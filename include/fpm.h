@@ -290,6 +290,61 @@ fpm_status fpm_kinetic(int32_t n, fpm_prec prec, const void *vel, double *d_out,
                        void *workspace, size_t workspace_bytes, fpm_stream stream);
 
 /* ------------------------------------------------------------------ */
+/* Weakly compressible SPH (Sec. 4.2, Eqs. 1-5), single precision        */
+/* ------------------------------------------------------------------ */
+
+/* SPH constants.  kernel 0: Wendland C2, W = a (1-q/2)^4 (2q+1),
+ * a = 21/(16 pi h^3); kernel 1: cubic spline, s [1 - 1.5q^2 + 0.75q^3] for
+ * q < 1, s 0.25 (2-q)^3 for q < 2, s = 1/(pi h^3); q = r/h, support 2h.
+ * Tait EOS P = b[(rho/rho0)^gamma - 1], b = c0^2 rho0 / gamma (Eqs. 3-4;
+ * gamma an integer in [1,8]); artificial viscosity alpha, eta2 (Eq. 5);
+ * gravity g. */
+typedef struct {
+    double h, mass, rho0, c0, gamma, alpha, eta2, g[3];
+    int32_t kernel;
+} fpm_sph_params;
+
+/* Rates of Eqs. 1-2 over a Verlet list built with r_list >= 2h (same box,
+ * grid, list, nn, cap conventions as fpm_lj_forces):
+ *   pos : [n] float4 (x, y, z, type), type 0 fluid, 1 fixed boundary particle;
+ *   vr  : [n] float4 (vx, vy, vz, rho - rho0);
+ *   acc : [n] float4 (ax, ay, az, Drho/Dt): for each pair inside 2h,
+ *         grad_p W = (dW/dr)(x_p - x_q)/r, Drho_p += m (v_p - v_q).grad_p W,
+ *         a_p += -m [(P_p+P_q)/(rho_p rho_q) + Pi_pq] grad_p W with
+ *         Pi_pq = -alpha c0 mu / ((rho_p+rho_q)/2) when (v_p-v_q).(x_p-x_q) < 0,
+ *         mu = h (v_p-v_q).(x_p-x_q) / (r^2 + eta2); fluid: a += g;
+ *         boundary: a = 0 (Drho still computed).
+ *   d_dtcons : [2] float, raised (atomic max) to max |a| over fluid particles
+ *         and max |mu| over pairs; must hold 0 (or smaller values) on entry
+ *         (fpm_sph_predict / fpm_sph_correct clear the buffers they consume).
+ * The pressure is evaluated from rho - rho0 by the binomial expansion of
+ * (1+x)^gamma - 1 (no cancellation in single precision). */
+fpm_status fpm_sph_forces(const fpm_box *box, const fpm_grid *grid, int32_t n, const void *pos, const void *vr,
+                          const void *list, const uint32_t *nn, int32_t cap, const fpm_sph_params *params,
+                          void *acc, float *d_dtcons, fpm_dev_status *d_status, fpm_stream stream);
+
+/* Symplectic predictor (the "Verlet time-stepping with dynamic step size" of
+ * Sec. 4.2, read as the predictor-corrector of the DualSPHysics scheme):
+ *   dt = cfl min( sqrt(h / max|a|), h / (c0 + max|mu|) ) from d_dtcons (the
+ *   rates at t^n), written to d_dt[0];
+ *   pos_h = pos + dt/2 v, vr_h.xyz = v + dt/2 a (fluid; boundary unchanged),
+ *   vr_h.w = (rho - rho0) + dt/2 Drho (all);  d_dtcons_h[0..1] = 0.
+ * With pos_ref, the displacement test of fpm_verlet_check runs on pos_h. */
+fpm_status fpm_sph_predict(const fpm_box *box, int32_t n, const fpm_sph_params *params, double cfl,
+                           const void *pos, const void *vr, const void *acc, const float *d_dtcons,
+                           void *pos_h, void *vr_h, float *d_dt, float *d_dtcons_h,
+                           const void *pos_ref, double skin, fpm_dev_status *d_status, fpm_stream stream);
+
+/* Symplectic corrector with the rates at the half step (acc_h):
+ *   v1 = v0 + dt a, x1 = x0 + dt (v0 + v1)/2 (fluid only),
+ *   rho1 = rho0 (2 - e)/(2 + e) with e = -(Drho / rho_half) dt (all), in place
+ *   on pos, vr; d_dtcons[0..1] = 0.  With pos_ref, sets d_status->rebuild when
+ *   |x1 - x_ref| + dt |v1| > skin/2 (room for the next half step). */
+fpm_status fpm_sph_correct(const fpm_box *box, int32_t n, const fpm_sph_params *params, void *pos, void *vr,
+                           const void *vr_h, const void *acc_h, const float *d_dt, float *d_dtcons,
+                           const void *pos_ref, double skin, fpm_dev_status *d_status, fpm_stream stream);
+
+/* ------------------------------------------------------------------ */
 /* Adjoint of the LJ force and of velocity Verlet (not in the paper:     */
 /* the chain rule applied to the force of Sec. 4.1 and the integrator    */
 /* of Listing 4.1, for gradients w.r.t. positions, eps and sigma)        */

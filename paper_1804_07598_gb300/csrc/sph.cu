@@ -1,0 +1,372 @@
+// sph.cu -- weakly compressible SPH rates (Sec. 4.2, Eqs. 1-5) over the tiled
+// Verlet list, and the symplectic predictor / corrector.
+//
+// State per particle (sorted order): pos = (x, y, z, type) with type 0 for
+// fluid and 1 for a fixed boundary particle; vr = (vx, vy, vz, drho) where
+// drho = rho - rho0 (carrying the density deviation keeps the Tait pressure,
+// a difference of nearly equal numbers, accurate in single precision).
+// Rates: acc = (ax, ay, az, Drho/Dt).
+//
+// For each pair inside the kernel support 2h (the list is built with
+// r_list = 2h + skin):
+//   grad_p W = F (x_p - x_q),  F = (dW/dr)/r,
+//   Drho_p  += m (v_p - v_q) . grad_p W                               (Eq. 2)
+//   a_p     += -m [(P_p + P_q)/(rho_p rho_q) + Pi_pq] grad_p W         (Eq. 1)
+//   Pi_pq    = -alpha c0 mu / rhobar when (v_p - v_q).(x_p - x_q) < 0, else 0,
+//   mu       = h (v_p - v_q).(x_p - x_q) / (r^2 + eta^2)               (Eq. 5)
+//   P        = b [(rho/rho0)^gamma - 1],  b = c0^2 rho0 / gamma       (Eqs. 3-4)
+// with a_p += g for fluid and a_p = 0 for boundary particles.  The pressure is
+// evaluated as b * sum_{k=1..gamma} C(gamma,k) x^k, x = drho/rho0 (the
+// binomial expansion, no cancellation), which needs an integer gamma (<= 8).
+#include "reduce.cuh"
+#include "tiles.cuh"
+
+namespace fpm {
+
+struct SphK {
+    float h, m, rho0, inv_rho0, c0, alpha, eta2, b, g[3];
+    float two_h2;    // (2h)^2, the support test
+    float wcoef;     // Wendland: F = wcoef (1 - q/2)^3;  cubic: s/h^2
+    float inv_h;
+    float binom[8];  // C(gamma, k), k = 1..gamma (0 beyond)
+    int gamma;
+    int kernel;      // 0 Wendland C2, 1 cubic spline
+};
+
+__device__ __forceinline__ float sph_rcp(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    const float e = __fmaf_rn(-x, y, 1.0f);
+    return __fmaf_rn(y, e, y);
+}
+
+// b * ((1 + x)^gamma - 1) by Horner on the binomial coefficients.
+__device__ __forceinline__ float tait(const SphK &K, float drho)
+{
+    const float x = drho * K.inv_rho0;
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 7; k >= 0; --k) s = __fmaf_rn(s, x, K.binom[k]);
+    return K.b * (s * x);
+}
+
+// (dW/dr)/r for r2 inside the support.
+__device__ __forceinline__ float grad_factor(const SphK &K, float r2)
+{
+    const float ir = rsqrtf(r2);
+    const float q = r2 * ir * K.inv_h;
+    if (K.kernel == 0) {
+        const float t = 1.0f - 0.5f * q;
+        return K.wcoef * t * t * t;
+    }
+    // cubic spline: s/h^2 (-3 + 2.25 q) for q < 1; -0.75 s/h^2 (2-q)^2 / q for q >= 1
+    const float t = 2.0f - q;
+    return q < 1.0f ? K.wcoef * (-3.0f + 2.25f * q) : -0.75f * K.wcoef * t * t * sph_rcp(q);
+}
+
+template <bool FAST, bool SMEM>
+__device__ __forceinline__ void sph_pair(const TileCfg &cfg, const BoxT<float> &box, const TileDesc &d,
+                                         const float4 *__restrict__ pos, const float4 *__restrict__ vr,
+                                         const float4 *__restrict__ st, const float4 *__restrict__ sv,
+                                         const float4 &pi, const float4 &vi, float rho_i, float Pi_over, int s,
+                                         const SphK &K, float &ax, float &ay, float &az, float &dr, float &mumax)
+{
+    float4 pj, vj;
+    if (SMEM) {
+        pj = st[s];
+        vj = sv[s];
+    } else {
+        pj = staged_global(d, box, pos, s);
+        vj = ldg4(vr + staged_index(d, s));
+    }
+    float dx, dy, dz;
+    const float r2 = tile_sep<FAST>(pi, pj, box, cfg, dx, dy, dz);
+    const bool in = r2 < K.two_h2 && r2 > 0.0f;
+    const float F = in ? grad_factor(K, r2) : 0.0f;
+    const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
+    const float vdr = vx * dx + vy * dy + vz * dz;
+    dr += K.m * F * vdr;
+    const float rho_j = K.rho0 + vj.w;
+    const float Pj = tait(K, vj.w);
+    const float inv_rr = sph_rcp(rho_i * rho_j);
+    const float mu = K.h * vdr * sph_rcp(r2 + K.eta2);
+    const float visc = vdr < 0.0f ? -K.alpha * K.c0 * mu * 2.0f * sph_rcp(rho_i + rho_j) : 0.0f;
+    const float c = -K.m * ((Pi_over + Pj) * inv_rr + visc) * F;
+    ax += c * dx;
+    ay += c * dy;
+    az += c * dz;
+    if (in) mumax = fmaxf(mumax, fabsf(mu));
+}
+
+template <bool FAST, bool SMEM>
+__device__ __forceinline__ void sph_sweep(const TileCfg &cfg, const BoxT<float> &box, const TileDesc &d,
+                                          const float4 *__restrict__ pos, const float4 *__restrict__ vr,
+                                          const float4 *__restrict__ st, const float4 *__restrict__ sv,
+                                          const float4 &pi, const float4 &vi, float rho_i, float Pi, uint32_t m,
+                                          const uint32_t *__restrict__ col, int64_t ld, const SphK &K, float &ax,
+                                          float &ay, float &az, float &dr, float &mumax)
+{
+    for (uint32_t wi = 0; wi < (m + 1u) >> 1; ++wi) {
+        const uint32_t wv = __ldcs(col + (int64_t)wi * ld);
+        sph_pair<FAST, SMEM>(cfg, box, d, pos, vr, st, sv, pi, vi, rho_i, Pi, (int)(wv & 0xffffu), K, ax, ay, az, dr,
+                             mumax);
+        if (2u * wi + 1u < m)
+            sph_pair<FAST, SMEM>(cfg, box, d, pos, vr, st, sv, pi, vi, rho_i, Pi, (int)(wv >> 16), K, ax, ay, az,
+                                 dr, mumax);
+    }
+}
+
+__global__ void __launch_bounds__(kTileThreads)
+    k_sph_tiles(TileCfg cfg, BoxT<float> box, const float4 *__restrict__ pos, const float4 *__restrict__ vr,
+                const TileDesc *__restrict__ descs, const uint32_t *__restrict__ words,
+                const uint32_t *__restrict__ nn, int64_t ld, int stage_cap, SphK K, float4 *__restrict__ acc,
+                float *dtcons, fpm_dev_status *status)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float4 *sp = (float4 *)smem_raw;
+    float4 *sv = sp + stage_cap;
+    __shared__ TileDesc d;
+    __shared__ __align__(8) uint64_t bar;
+    load_desc(descs + blockIdx.x, d);
+    const bool in_smem = d.M <= stage_cap;
+    const bool staged = in_smem ? stage_positions(d, box, pos, sp, &bar, status, vr, sv) : true;
+    float amax = 0.0f, mumax = 0.0f;
+    for (uint32_t i = d.h0 + threadIdx.x; staged && i < d.h1; i += blockDim.x) {
+        const float4 pi = pos[i];
+        const float4 vi = vr[i];
+        const uint32_t m = nn[i];
+        const float rho_i = K.rho0 + vi.w;
+        const float P_i = tait(K, vi.w);
+        float ax = 0.0f, ay = 0.0f, az = 0.0f, dr = 0.0f;
+        if (in_smem) {
+            if (d.slow)
+                sph_sweep<false, true>(cfg, box, d, pos, vr, sp, sv, pi, vi, rho_i, P_i, m, words + i, ld, K, ax, ay,
+                                       az, dr, mumax);
+            else
+                sph_sweep<true, true>(cfg, box, d, pos, vr, sp, sv, pi, vi, rho_i, P_i, m, words + i, ld, K, ax, ay,
+                                      az, dr, mumax);
+        } else {
+            sph_sweep<false, false>(cfg, box, d, pos, vr, sp, sv, pi, vi, rho_i, P_i, m, words + i, ld, K, ax, ay, az,
+                                    dr, mumax);
+        }
+        float4 a;
+        if (pi.w == 0.0f) {
+            a.x = ax + K.g[0];
+            a.y = ay + K.g[1];
+            a.z = az + K.g[2];
+            amax = fmaxf(amax, sqrtf(a.x * a.x + a.y * a.y + a.z * a.z));
+        } else {
+            a.x = a.y = a.z = 0.0f;
+        }
+        a.w = dr;
+        acc[i] = a;
+    }
+    // one atomic max per warp on the (non-negative) float bits
+    const unsigned ma = __reduce_max_sync(kFull, __float_as_uint(amax));
+    const unsigned mm = __reduce_max_sync(kFull, __float_as_uint(mumax));
+    if ((threadIdx.x & 31) == 0 && dtcons) {
+        if (ma) atomicMax((unsigned *)dtcons, ma);
+        if (mm) atomicMax((unsigned *)dtcons + 1, mm);
+    }
+}
+
+__device__ __forceinline__ float sph_dt(const float *dtcons, float h, float c0, float cfl)
+{
+    const float amax = dtcons[0], mumax = dtcons[1];
+    const float dtf = amax > 0.0f ? sqrtf(h / amax) : 3.0e38f;
+    const float dtv = h / (c0 + mumax);
+    return cfl * fminf(dtf, dtv);
+}
+
+// Symplectic predictor: dt from the constraints of the rates at t^n; half
+// step x += dt/2 v, v += dt/2 a (fluid), drho += dt/2 Drho (all).  Also runs
+// the Verlet rebuild test on the half-step positions.
+__global__ void k_sph_predict(int n, BoxT<float> box, const float4 *__restrict__ pos, const float4 *__restrict__ vr,
+                              const float4 *__restrict__ acc, const float *__restrict__ dtcons, float h, float c0,
+                              float cfl, float4 *__restrict__ pos_h, float4 *__restrict__ vr_h, float *d_dt,
+                              float *dtcons_h, const float4 *__restrict__ ref, float th, fpm_dev_status *st)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const float dt = sph_dt(dtcons, h, c0, cfl);
+    if (i == 0) {
+        *d_dt = dt;
+        dtcons_h[0] = 0.0f;
+        dtcons_h[1] = 0.0f;
+    }
+    bool over = false;
+    float d2 = 0.0f;
+    if (i < n) {
+        float4 p = pos[i], v = vr[i];
+        const float4 a = acc[i];
+        if (p.w == 0.0f) {
+            p.x += 0.5f * dt * v.x;
+            p.y += 0.5f * dt * v.y;
+            p.z += 0.5f * dt * v.z;
+            v.x += 0.5f * dt * a.x;
+            v.y += 0.5f * dt * a.y;
+            v.z += 0.5f * dt * a.z;
+        }
+        v.w += 0.5f * dt * a.w;
+        pos_h[i] = p;
+        vr_h[i] = v;
+        if (ref) {
+            float dx, dy, dz;
+            d2 = separation(p, ref[i], box, dx, dy, dz);
+            over = d2 > th;
+        }
+    }
+    if (ref) disp_report(over, d2, st);
+}
+
+// Symplectic corrector with the rates at the half step:
+//   v1 = v0 + dt a;  x1 = x0 + dt (v0 + v1)/2 (fluid only);
+//   rho1 = rho0 (2 - e)/(2 + e), e = -(Drho/rho_half) dt, written as
+//   drho1 = (drho0 (2 - e) - 2 rho0 e) / (2 + e).
+// Then the rebuild test on x1 with a margin for the next half step:
+// |x1 - x_ref| + dt |v1| > skin/2.  Clears the constraint buffer of t^n.
+__global__ void k_sph_correct(int n, BoxT<float> box, float4 *__restrict__ pos, float4 *__restrict__ vr,
+                              const float4 *__restrict__ vr_h, const float4 *__restrict__ acc_h,
+                              const float *__restrict__ d_dt, float rho0, float *dtcons,
+                              const float4 *__restrict__ ref, float half_skin, fpm_dev_status *st)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const float dt = *d_dt;
+    bool over = false;
+    float d2 = 0.0f;
+    if (i < n) {
+        float4 p = pos[i], v = vr[i];
+        const float4 a = acc_h[i];
+        const float4 vh = vr_h[i];
+        const float rho_h = rho0 + vh.w;
+        const float e = -(a.w / rho_h) * dt;
+        v.w = (v.w * (2.0f - e) - 2.0f * rho0 * e) / (2.0f + e);
+        if (p.w == 0.0f) {
+            const float v0x = v.x, v0y = v.y, v0z = v.z;
+            v.x = v0x + dt * a.x;
+            v.y = v0y + dt * a.y;
+            v.z = v0z + dt * a.z;
+            p.x += dt * 0.5f * (v0x + v.x);
+            p.y += dt * 0.5f * (v0y + v.y);
+            p.z += dt * 0.5f * (v0z + v.z);
+        }
+        pos[i] = p;
+        vr[i] = v;
+        if (ref) {
+            float dx, dy, dz;
+            d2 = separation(p, ref[i], box, dx, dy, dz);
+            const float reach = sqrtf(d2) + dt * sqrtf(v.x * v.x + v.y * v.y + v.z * v.z);
+            over = reach > half_skin;
+        }
+    }
+    if (i == 0) {
+        dtcons[0] = 0.0f;
+        dtcons[1] = 0.0f;
+    }
+    if (ref) disp_report(over, d2, st);
+}
+
+static SphK make_sph(const fpm_sph_params &p)
+{
+    SphK K{};
+    const double pi = 3.14159265358979323846;
+    K.h = (float)p.h;
+    K.m = (float)p.mass;
+    K.rho0 = (float)p.rho0;
+    K.inv_rho0 = (float)(1.0 / p.rho0);
+    K.c0 = (float)p.c0;
+    K.alpha = (float)p.alpha;
+    K.eta2 = (float)p.eta2;
+    K.gamma = (int)p.gamma;
+    K.b = (float)(p.c0 * p.c0 * p.rho0 / p.gamma);
+    for (int d = 0; d < 3; ++d) K.g[d] = (float)p.g[d];
+    K.two_h2 = (float)(4.0 * p.h * p.h);
+    K.inv_h = (float)(1.0 / p.h);
+    K.kernel = p.kernel;
+    if (p.kernel == 0) {
+        const double a = 21.0 / (16.0 * pi * p.h * p.h * p.h);
+        K.wcoef = (float)(-5.0 * a / (p.h * p.h));
+    } else {
+        K.wcoef = (float)(1.0 / (pi * p.h * p.h * p.h) / (p.h * p.h));
+    }
+    // C(gamma, k) for k = 1..gamma in binom[k-1], Horner from the highest
+    double c = 1.0;
+    for (int k = 1; k <= 8; ++k) {
+        c = c * (double)(K.gamma - k + 1) / (double)k;
+        K.binom[k - 1] = k <= K.gamma ? (float)c : 0.0f;
+    }
+    return K;
+}
+
+}  // namespace fpm
+
+using namespace fpm;
+
+static fpm_status sph_params_ok(const fpm_sph_params *p, const char *who)
+{
+    if (!p || !(p->h > 0.0) || !(p->mass > 0.0) || !(p->rho0 > 0.0) || !(p->c0 > 0.0) || !(p->eta2 >= 0.0))
+        return fpm_fail(FPM_ERR_INVALID, "%s: bad SPH parameters", who);
+    if (p->gamma != (double)(int)p->gamma || p->gamma < 1.0 || p->gamma > 8.0)
+        return fpm_fail(FPM_ERR_INVALID, "%s: gamma must be an integer in [1, 8]", who);
+    if (p->kernel != 0 && p->kernel != 1) return fpm_fail(FPM_ERR_INVALID, "%s: kernel must be 0 or 1", who);
+    return FPM_OK;
+}
+
+extern "C" fpm_status fpm_sph_forces(const fpm_box *box, const fpm_grid *grid, int32_t n, const void *pos,
+                                     const void *vr, const void *list, const uint32_t *nn, int32_t cap,
+                                     const fpm_sph_params *params, void *acc, float *d_dtcons,
+                                     fpm_dev_status *d_status, fpm_stream stream)
+{
+    fpm_status s = fpm_check_grid(box, grid, "fpm_sph_forces");
+    if (s != FPM_OK) return s;
+    s = sph_params_ok(params, "fpm_sph_forces");
+    if (s != FPM_OK) return s;
+    if (n < 0 || cap < 1 || (n > 0 && (!pos || !vr || !list || !nn || !acc)))
+        return fpm_fail(FPM_ERR_INVALID, "fpm_sph_forces: null pointer or bad size");
+    if (((uintptr_t)list & 255u) != 0) return fpm_fail(FPM_ERR_INVALID, "fpm_sph_forces: list not 256-B aligned");
+    if (n == 0) return FPM_OK;
+    const TileCfg cfg = make_tile_cfg(*box, *grid);
+    const ListLayout L = list_layout(n, cfg, cap);
+    const int sc = stage_capacity(n, *grid, 2 * sizeof(float4));
+    smem_opt_in((const void *)k_sph_tiles);
+    k_sph_tiles<<<cfg.ntiles, kTileThreads, 2 * (size_t)sc * sizeof(float4), (cudaStream_t)stream>>>(
+        cfg, make_box<float>(*box), (const float4 *)pos, (const float4 *)vr,
+        (const TileDesc *)((const char *)list + L.off_tiles), (const uint32_t *)((const char *)list + L.off_words), nn,
+        L.ld, sc, make_sph(*params), (float4 *)acc, d_dtcons, d_status);
+    return fpm_check_launch("fpm_sph_forces");
+}
+
+extern "C" fpm_status fpm_sph_predict(const fpm_box *box, int32_t n, const fpm_sph_params *params, double cfl,
+                                      const void *pos, const void *vr, const void *acc, const float *d_dtcons,
+                                      void *pos_h, void *vr_h, float *d_dt, float *d_dtcons_h, const void *pos_ref,
+                                      double skin, fpm_dev_status *d_status, fpm_stream stream)
+{
+    fpm_status s = sph_params_ok(params, "fpm_sph_predict");
+    if (s != FPM_OK) return s;
+    if (!box || n < 0 || !d_dtcons || !d_dt || !d_dtcons_h || (pos_ref && !d_status) ||
+        (n > 0 && (!pos || !vr || !acc || !pos_h || !vr_h)))
+        return fpm_fail(FPM_ERR_INVALID, "fpm_sph_predict: null pointer or bad size");
+    const int blocks = n > 0 ? (n + 255) / 256 : 1;
+    k_sph_predict<<<blocks, 256, 0, (cudaStream_t)stream>>>(
+        n, make_box<float>(*box), (const float4 *)pos, (const float4 *)vr, (const float4 *)acc, d_dtcons,
+        (float)params->h, (float)params->c0, (float)cfl, (float4 *)pos_h, (float4 *)vr_h, d_dt, d_dtcons_h,
+        (const float4 *)pos_ref, (float)(0.25 * skin * skin), d_status);
+    return fpm_check_launch("fpm_sph_predict");
+}
+
+extern "C" fpm_status fpm_sph_correct(const fpm_box *box, int32_t n, const fpm_sph_params *params, void *pos,
+                                      void *vr, const void *vr_h, const void *acc_h, const float *d_dt,
+                                      float *d_dtcons, const void *pos_ref, double skin, fpm_dev_status *d_status,
+                                      fpm_stream stream)
+{
+    fpm_status s = sph_params_ok(params, "fpm_sph_correct");
+    if (s != FPM_OK) return s;
+    if (!box || n < 0 || !d_dt || !d_dtcons || (pos_ref && !d_status) ||
+        (n > 0 && (!pos || !vr || !vr_h || !acc_h)))
+        return fpm_fail(FPM_ERR_INVALID, "fpm_sph_correct: null pointer or bad size");
+    const int blocks = n > 0 ? (n + 255) / 256 : 1;
+    k_sph_correct<<<blocks, 256, 0, (cudaStream_t)stream>>>(
+        n, make_box<float>(*box), (float4 *)pos, (float4 *)vr, (const float4 *)vr_h, (const float4 *)acc_h, d_dt,
+        (float)params->rho0, d_dtcons, (const float4 *)pos_ref, (float)(0.5 * skin), d_status);
+    return fpm_check_launch("fpm_sph_correct");
+}

@@ -50,6 +50,12 @@ class fpm_dev_status(_c.Structure):
                 ("reserved", _c.c_uint32 * 10)]
 
 
+class fpm_sph_params(_c.Structure):
+    _fields_ = [("h", _c.c_double), ("mass", _c.c_double), ("rho0", _c.c_double), ("c0", _c.c_double),
+                ("gamma", _c.c_double), ("alpha", _c.c_double), ("eta2", _c.c_double), ("g", _c.c_double * 3),
+                ("kernel", _c.c_int32)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -88,6 +94,12 @@ _SIG = {
                                _VP]),
     "fpm_vv_drift_check": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.c_int, _c.c_double, _VP, _VP, _VP, _VP,
                                       _c.c_double, _VP, _VP]),
+    "fpm_sph_forces": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _VP, _VP, _VP, _VP,
+                                  _c.c_int32, _c.POINTER(fpm_sph_params), _VP, _VP, _VP, _VP]),
+    "fpm_sph_predict": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.POINTER(fpm_sph_params), _c.c_double, _VP,
+                                   _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _c.c_double, _VP, _VP]),
+    "fpm_sph_correct": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.POINTER(fpm_sph_params), _VP, _VP, _VP, _VP,
+                                   _VP, _VP, _VP, _c.c_double, _VP, _VP]),
     "fpm_lj_backward": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _c.c_int, _VP, _VP, _VP,
                                    _c.c_int32, _c.c_double, _c.c_double, _c.c_double, _VP, _c.c_double, _VP, _VP,
                                    _VP, _c.c_size_t, _VP, _VP]),
@@ -308,3 +320,27 @@ def fpm_adjoint_seed(n, prec, force, xbar, vbar, a_out, stream=None):
     _check(lib().fpm_adjoint_seed(int(n), int(prec), _ptr(force), _ptr(xbar), _ptr(vbar), _ptr(a_out),
                                   _stream(stream)))
     _count(1 if n > 0 else 0)
+
+
+def fpm_sph_forces(box, grid, n, pos, vr, list_obj, nn, cap, params, acc, d_dtcons=None, d_status=None,
+                   stream=None):
+    _check(lib().fpm_sph_forces(_c.byref(box), _c.byref(grid), int(n), _ptr(pos), _ptr(vr), _ptr(list_obj),
+                                _ptr(nn), int(cap), _c.byref(params), _ptr(acc), _ptr(d_dtcons), _ptr(d_status),
+                                _stream(stream)))
+    _count(1 if n > 0 else 0)
+
+
+def fpm_sph_predict(box, n, params, cfl, pos, vr, acc, d_dtcons, pos_h, vr_h, d_dt, d_dtcons_h, pos_ref=None,
+                    skin=0.0, d_status=None, stream=None):
+    _check(lib().fpm_sph_predict(_c.byref(box), int(n), _c.byref(params), float(cfl), _ptr(pos), _ptr(vr), _ptr(acc),
+                                 _ptr(d_dtcons), _ptr(pos_h), _ptr(vr_h), _ptr(d_dt), _ptr(d_dtcons_h),
+                                 _ptr(pos_ref), float(skin), _ptr(d_status), _stream(stream)))
+    _count(1)
+
+
+def fpm_sph_correct(box, n, params, pos, vr, vr_h, acc_h, d_dt, d_dtcons, pos_ref=None, skin=0.0, d_status=None,
+                    stream=None):
+    _check(lib().fpm_sph_correct(_c.byref(box), int(n), _c.byref(params), _ptr(pos), _ptr(vr), _ptr(vr_h),
+                                 _ptr(acc_h), _ptr(d_dt), _ptr(d_dtcons), _ptr(pos_ref), float(skin), _ptr(d_status),
+                                 _stream(stream)))
+    _count(1)

@@ -140,3 +140,50 @@ def replica_state(N: int, rho: float, T: float, seed: int):
     x = fcc_lattice((m, m, m), a)[:N]
     v = maxwell_boltzmann(N, T, seed)
     return as4(x), as4(v), np.array([L, L, L])
+
+
+# ---------------------------------------------------------------------------
+# SPH dam break (Sec. 4.2 test case, the tank shape of the SPH workload)
+# ---------------------------------------------------------------------------
+
+def dam_break(dp: float, tank=(1.6, 0.67, 0.4), column=(0.4, 0.67, 0.3), layers: int = 3, lz: float = 1.0,
+              rho0: float = 1000.0, g: float = 9.81, gamma: float = 7.0, coef: float = 20.0):
+    """A fluid column at one end of an open-top tank with `layers` layers of
+    fixed boundary particles on the floor and the four walls, all on a cubic
+    lattice of spacing dp.  Coordinates start at 0 (the boundary layers fill
+    [0, layers*dp) on the low sides).  Returns a dict with pos [n,4] (w = type,
+    0 fluid / 1 boundary), vel [n,3] (zero), rho [n] (hydrostatic:
+    rho0 (1 + rho0 g depth / b)^(1/gamma), b = c0^2 rho0 / gamma,
+    c0 = coef sqrt(g h_swl)), the box L, and the SPH constants h = 1.3 dp,
+    m = rho0 dp^3."""
+    nb = int(layers)
+    nxt, nyt, nzt = (int(round(t / dp)) for t in tank)
+    nxf, nyf, nzf = (int(round(c / dp)) for c in column)
+    off = nb * dp
+
+    def grid(nx, ny, nz, x0, y0, z0):
+        iz, iy, ix = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        return np.stack([x0 + (ix.ravel() + 0.5) * dp, y0 + (iy.ravel() + 0.5) * dp, z0 + (iz.ravel() + 0.5) * dp], 1)
+
+    fluid = grid(nxf, nyf, nzf, off, off, off)
+    floor = grid(nxt + 2 * nb, nyt + 2 * nb, nb, 0.0, 0.0, 0.0)
+    xw = np.concatenate([grid(nb, nyt + 2 * nb, nzt, 0.0, 0.0, off),
+                         grid(nb, nyt + 2 * nb, nzt, off + nxt * dp, 0.0, off)])
+    yw = np.concatenate([grid(nxt, nb, nzt, off, 0.0, off), grid(nxt, nb, nzt, off, off + nyt * dp, off)])
+    bnd = np.concatenate([floor, xw, yw])
+    h_swl = column[2]  # the nominal fluid height of the paper's setup
+    c0 = coef * math.sqrt(g * h_swl)
+    b = c0 * c0 * rho0 / gamma
+    x = np.concatenate([fluid, bnd])
+    depth = np.maximum(h_swl - (x[:, 2] - off), 0.0)
+    rho = rho0 * (1.0 + rho0 * g * depth / b) ** (1.0 / gamma)
+    pos = np.zeros((x.shape[0], 4))
+    pos[:, :3] = x
+    pos[fluid.shape[0]:, 3] = 1.0
+    L = np.array([(nxt + 2 * nb) * dp, (nyt + 2 * nb) * dp, lz])
+    return dict(pos=pos, vel=np.zeros((x.shape[0], 3)), rho=rho, L=L, n_fluid=fluid.shape[0],
+                n_boundary=bnd.shape[0], h=1.3 * dp, m=rho0 * dp ** 3, c0=c0, b=b, rho0=rho0, dp=dp,
+                h_swl=h_swl)
+
+
+SPH_DP = 3.7704e-3  # dam break with ~1.51M fluid particles (106 x 178 x 80)

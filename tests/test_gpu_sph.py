@@ -1,0 +1,123 @@
+"""GPU parity of the SPH rates (Eqs. 1-5) and of the symplectic step against
+the oracle on identical states.
+
+Tolerances: acc of fluid particles within 1e-4 of RMS(a - g), Drho within
+1e-4 of RMS(Drho), the dt constraints within 1e-4 relative (FP32 pair
+arithmetic against FP64; the support test is taken in FP32 on both sides)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1804_07598_gb300 import fpm, inputs
+from paper_1804_07598_gb300.sph import SPHSystem
+
+pytestmark = pytest.mark.gpu
+
+
+def f32box(L):
+    return np.asarray(L, np.float64).astype(np.float32).astype(np.float64)
+
+
+def make(dp=0.02, kernel="wendland", perturb=True, seed=3):
+    d = inputs.dam_break(dp)
+    rng = np.random.default_rng(seed)
+    vel = d["vel"].copy()
+    rho = d["rho"].copy()
+    nf = d["n_fluid"]
+    if perturb:
+        vel[:nf] = rng.normal(0.0, 0.3, (nf, 3))
+        rho += rng.uniform(-2.0, 2.0, rho.shape[0])
+        pos = d["pos"].copy()
+        pos[:nf, :3] += rng.uniform(-0.1, 0.1, (nf, 3)) * dp
+    else:
+        pos = d["pos"]
+    s = SPHSystem(pos, vel, rho, d["L"], d["h"], d["m"], c0=d["c0"], kernel=kernel)
+    return d, s
+
+
+def oracle_params(d, kernel):
+    return oracle.sph_params(d["h"], d["m"], rho0=d["rho0"], c0=d["c0"], kernel=kernel)
+
+
+@pytest.mark.parametrize("kernel", ["wendland", "cubic"])
+def test_sph_rates_match_oracle(cuda, kernel):
+    d, s = make(kernel=kernel)
+    s.rates()
+    torch.cuda.synchronize()
+    s.check_status()
+    pos, vel, rho, _ = s.state_numpy()
+    acc = s.acc.cpu().numpy().astype(np.float64)
+    oacc, odr, odtc = oracle.sph_rates(pos.astype(np.float64), vel.astype(np.float64), rho, f32box(s.L), s.periodic,
+                                       oracle_params(d, kernel), mask_f32=True)
+    fluid = pos[:, 3] == 0
+    g = np.array([0.0, 0.0, -9.81])
+    ra = np.sqrt(np.mean(np.sum((oacc[fluid, :3] - g) ** 2, axis=1)))
+    ea = np.max(np.linalg.norm(acc[fluid, :3] - oacc[fluid, :3], axis=1)) / ra
+    rd = np.sqrt(np.mean(odr ** 2))
+    ed = np.max(np.abs(acc[:, 3] - odr)) / rd
+    assert ea <= 1e-4, ea
+    assert ed <= 1e-4, ed
+    assert np.all(acc[~fluid, :3] == 0.0)
+    dtc = s.dtcons.cpu().numpy()
+    assert abs(dtc[0] - odtc[0]) <= 1e-4 * odtc[0] and abs(dtc[1] - odtc[1]) <= 1e-4 * odtc[1]
+
+
+def test_sph_rest_lattice(cuda):
+    """Periodic lattice at rest with uniform density: Drho = 0, a = g."""
+    dp = 0.01
+    n = 12
+    gi = np.stack(np.meshgrid(*[np.arange(n)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    pos = np.zeros((gi.shape[0], 4))
+    pos[:, :3] = (gi + 0.5) * dp
+    s = SPHSystem(pos, np.zeros((gi.shape[0], 3)), np.full(gi.shape[0], 1002.0), [n * dp] * 3, 1.3 * dp,
+                  1000.0 * dp ** 3, periodic=(1, 1, 1))
+    s.rates()
+    a = s.acc.cpu().numpy()
+    assert np.max(np.abs(a[:, 3])) < 1e-3 * (1000.0 * 1.0)  # |Drho| << rho / s, FP32 sums of cancelling terms
+    assert np.max(np.abs(a[:, :3] - np.array([0, 0, -9.81]))) < 1e-3
+
+
+def test_sph_step_matches_oracle(cuda):
+    """One symplectic step (two rate evaluations, dynamic dt) on identical
+    states: dt, positions, velocities and densities against the oracle step
+    (rows matched through the particle ids, in case the step rebuilt)."""
+    d, s = make(perturb=True)
+    pos0, vel0, rho0, ids0 = s.state_numpy()
+    s.step(1)
+    torch.cuda.synchronize()
+    s.check_status()
+    dt = float(s.dt.cpu().numpy()[0])
+    op, ov, orho, odt = oracle.sph_step(pos0.astype(np.float64), vel0.astype(np.float64), rho0, f32box(s.L),
+                                        s.periodic, oracle_params(d, "wendland"))
+    assert abs(dt - odt) <= 1e-5 * odt
+    pos1, vel1, rho1, ids1 = s.state_numpy()
+    row = np.empty(ids0.shape[0], np.int64)
+    row[ids0] = np.arange(ids0.shape[0])
+    r = row[ids1]  # oracle row of each GPU slot
+    ulp = np.float32(1.0) * np.finfo(np.float32).eps
+    dx_o = op[r, :3] - pos0[r, :3]
+    err_x = np.abs(pos1[:, :3].astype(np.float64) - op[r, :3])
+    assert np.all(err_x <= 1e-4 * np.max(np.abs(dx_o)) + 2 * ulp * np.abs(op[r, :3]))
+    dv_o = ov[r, :3] - vel0[r, :3]
+    err_v = np.abs(vel1.astype(np.float64) - ov[r, :3])
+    assert np.all(err_v <= 1e-4 * np.max(np.abs(dv_o)) + 2 * ulp * np.abs(ov[r, :3]))
+    drho_o = orho[r] - rho0[r]
+    assert np.all(np.abs(rho1 - orho[r]) <= 1e-4 * np.max(np.abs(drho_o)) + 2 * ulp * 10.0)
+    assert np.array_equal(pos1[pos1[:, 3] == 1, :3], pos0[r][pos1[:, 3] == 1, :3])  # boundary fixed
+
+
+def test_sph_graph_equals_eager(cuda):
+    d = inputs.dam_break(0.02)
+    a = SPHSystem(d["pos"], d["vel"], d["rho"], d["L"], d["h"], d["m"], c0=d["c0"])
+    b = SPHSystem(d["pos"], d["vel"], d["rho"], d["L"], d["h"], d["m"], c0=d["c0"])
+    a.step(20)
+    b.capture(steps_per_graph=5)
+    b.run(20)
+    torch.cuda.synchronize()
+    assert torch.equal(a.pos, b.pos) and torch.equal(a.vr, b.vr)
+    a.check_status()
+    pos, vel, rho, _ = a.state_numpy()
+    bnd = pos[:, 3] == 1
+    assert np.all(vel[bnd] == 0.0)
+    assert np.all(np.isfinite(pos)) and np.all(np.isfinite(vel))
