@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--profile", default=None, choices=["forces", "step"],
+    ap.add_argument("--profile", default=None, choices=["forces", "step", "sph"],
                     help="profiling target for ncu: build the 1M-atom system, then run --steps force sweeps "
                          "or eager steps (no timing, no JSON line)")
     ap.add_argument("--fp64-steps", type=int, default=100)
@@ -403,6 +403,15 @@ def run_profile_target(args):
     from paper_1804_07598_gb300 import inputs
     from paper_1804_07598_gb300.md import LJSystem
     fbuild.build()
+    if args.profile == "sph":
+        from paper_1804_07598_gb300.sph import SPHSystem
+        dd = inputs.dam_break(inputs.SPH_DP)
+        ss = SPHSystem(dd["pos"], dd["vel"], dd["rho"], dd["L"], dd["h"], dd["m"], c0=dd["c0"])
+        ss.step(args.steps)
+        torch.cuda.synchronize()
+        ss.check_status()
+        print(f"profile target done: sph x{args.steps}, n={ss.n}", flush=True)
+        return
     wl = inputs.WORKLOADS[WORKLOAD]
     pos, vel, L = inputs.lj_state(wl)
     s = LJSystem(pos, vel, L, eps=wl.eps, sigma=wl.sigma, rc=wl.rc, skin=wl.skin, dt=wl.dt, precision="f32")

@@ -71,12 +71,18 @@ typedef struct {
  * dimension is then a candidate); inv[d] = (float)(nc[d] / L[d]).
  * tiles_x: the pair sweeps work on tiles of consecutive cells along x; each
  * row of nc[0] cells is split into tiles_x tiles of near-equal width (at most
- * 14 cells).  ntiles = tiles_x * nc[1] * nc[2]. */
+ * 14 cells).  ntiles = tiles_x * nc[1] * nc[2].
+ * stage_cap: particles of a tile's neighbourhood that a sweep stages in shared
+ * memory (0: estimated from the mean density).  A tile with a larger
+ * neighbourhood is still computed correctly, reading neighbours from global
+ * memory, and counted in fpm_dev_status.spilled; fpm_dev_status.max_staged
+ * after a Verlet build tells the caller what to set. */
 typedef struct {
     int32_t nc[3];
     int32_t ncell;
     float inv[3];
     int32_t tiles_x;
+    int32_t stage_cap;
 } fpm_grid;
 
 /* Device-side status block (caller-allocated in device memory, 64 bytes,
@@ -88,7 +94,9 @@ typedef struct {
     uint32_t nrebuild;     /* number of gated rebuilds performed                  */
     uint32_t max_disp2;    /* float bits of the largest squared displacement      */
     uint32_t bad_index;    /* a particle index that raised FPM_ERR_DOMAIN         */
-    uint32_t reserved[10];
+    uint32_t max_staged;   /* largest tile neighbourhood seen by a Verlet build   */
+    uint32_t spilled;      /* tile sweeps whose neighbourhood exceeded stage_cap  */
+    uint32_t reserved[8];
 } fpm_dev_status;
 
 #define FPM_FLAG_CAPACITY 1u
@@ -217,11 +225,12 @@ fpm_status fpm_verlet_check(const fpm_box *box, int32_t n, fpm_prec prec, const 
 /* Listing 4.1, truncated at r_cut, applied over the Verlet list)          */
 /* ------------------------------------------------------------------ */
 
-/* Bytes of workspace for the FP64 reductions of fpm_lj_forces and
- * fpm_kinetic (partial sums and a completion counter) for n particles on
- * grid (grid may be NULL for fpm_kinetic alone).  The workspace must be
- * ZERO-FILLED once before its first use; every call leaves its counter at
- * zero again. */
+/* Bytes of workspace for the tile sweeps (fpm_lj_forces, fpm_lj_backward,
+ * fpm_sph_forces: tile-scheduling counters and per-tile FP64 partial sums)
+ * and for fpm_kinetic (per-block partial sums), for n particles on grid (grid
+ * may be NULL for fpm_kinetic alone).  The workspace must be ZERO-FILLED once
+ * before its first use; every call leaves its counters at zero again.  Calls
+ * sharing a workspace must not run concurrently. */
 fpm_status fpm_reduce_workspace(int32_t n, const fpm_grid *grid, size_t *bytes);
 
 /* Forces of the truncated (unshifted) LJ potential over the full Verlet
@@ -234,7 +243,8 @@ fpm_status fpm_reduce_workspace(int32_t n, const fpm_grid *grid, size_t *bytes);
  * d_energy  : [3] double: U = sum_{i<j} V, W = sum_{i<j} r_ij . F_ij and
  *             the number of interacting pairs.  Reduced in FP64 in a fixed
  *             order (bit-reproducible).  May be NULL (no reduction).
- * workspace : fpm_reduce_workspace() bytes (zero-filled once).
+ * workspace : fpm_reduce_workspace(n, grid) bytes (zero-filled once; always
+ *             needed: it holds the sweep's tile-scheduling counters).
  * d_status  : device status block or NULL; FPM_FLAG_TIMEOUT is latched if a
  *             tile's bulk copy into shared memory did not complete within
  *             about 2 s (its particles' forces are then not written). */
@@ -318,10 +328,13 @@ typedef struct {
  *         and max |mu| over pairs; must hold 0 (or smaller values) on entry
  *         (fpm_sph_predict / fpm_sph_correct clear the buffers they consume).
  * The pressure is evaluated from rho - rho0 by the binomial expansion of
- * (1+x)^gamma - 1 (no cancellation in single precision). */
+ * (1+x)^gamma - 1 (no cancellation in single precision).
+ * workspace : fpm_reduce_workspace(n, grid) bytes, zero-filled once (it holds
+ *             the tile-scheduling counters of the sweep). */
 fpm_status fpm_sph_forces(const fpm_box *box, const fpm_grid *grid, int32_t n, const void *pos, const void *vr,
                           const void *list, const uint32_t *nn, int32_t cap, const fpm_sph_params *params,
-                          void *acc, float *d_dtcons, fpm_dev_status *d_status, fpm_stream stream);
+                          void *acc, float *d_dtcons, void *workspace, size_t workspace_bytes,
+                          fpm_dev_status *d_status, fpm_stream stream);
 
 /* Symplectic predictor (the "Verlet time-stepping with dynamic step size" of
  * Sec. 4.2, read as the predictor-corrector of the DualSPHysics scheme):
@@ -358,8 +371,8 @@ fpm_status fpm_sph_correct(const fpm_box *box, int32_t n, const fpm_sph_params *
  *   d_params[2]    += dU/d eps,  d_params[3] += dU/d sigma    (U as in fpm_lj_forces)
  * a : [n] float4|double4 in the positions' precision (w ignored).  Pair
  * arithmetic in the positions' precision; adj_pos and d_params accumulate in
- * FP64 (d_params in a fixed order, bit-reproducible).  d_params may be NULL
- * (then no workspace is needed).  workspace : fpm_reduce_workspace(n, grid).
+ * FP64 (d_params in a fixed order, bit-reproducible).  d_params may be NULL.
+ * workspace : fpm_reduce_workspace(n, grid) bytes (zero-filled once).
  * adj_pos 32-byte aligned. */
 fpm_status fpm_lj_backward(const fpm_box *box, const fpm_grid *grid, int32_t n, fpm_prec prec, const void *pos,
                            const void *list, const uint32_t *nn, int32_t cap,

@@ -95,23 +95,44 @@ __device__ __forceinline__ void hvp_sweep(const TileCfg &cfg, const BoxT<T> &box
     }
 }
 
+// The sweep of a tile whose neighbourhood did not fit in shared memory (rare;
+// out of line so that it does not add to the registers of the common path).
 template <typename T>
-__global__ void __launch_bounds__(kTileThreads)
+__device__ __noinline__ void hvp_sweep_spilled(const TileCfg &cfg, const BoxT<T> &box, const TileDesc &d,
+                                               const V4<T> *__restrict__ pos, const V4<T> *__restrict__ avec,
+                                               const V4<T> &pi, const V4<T> &ai, uint32_t m,
+                                               const uint32_t *__restrict__ col, int64_t ld, const HvpParams<T> &P,
+                                               HvpAcc<T> *A)
+{
+    HvpAcc<T> a{};
+    hvp_sweep<T, false, false>(cfg, box, d, pos, avec, nullptr, nullptr, pi, ai, m, col, ld, P, a);
+    *A = a;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads, 4)
     k_lj_hvp_tiles(TileCfg cfg, BoxT<T> box, const V4<T> *__restrict__ pos, const V4<T> *__restrict__ avec,
-                   const TileDesc *__restrict__ descs, const uint32_t *__restrict__ words,
-                   const uint32_t *__restrict__ nn, int64_t ld, int stage_cap, HvpParams<T> P, double hscale,
-                   double e24, double e24s, double eps4, double *__restrict__ adj_pos, double *part,
-                   unsigned *counter, double *out, fpm_dev_status *status)
+                   ListView lv, const uint32_t *__restrict__ nn, int64_t ld, int stage_cap, HvpParams<T> P,
+                   double hscale, double e24, double e24s, double eps4, double *__restrict__ adj_pos, Sched sched,
+                   double *part, double *out, fpm_dev_status *status)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     V4<T> *sp = (V4<T> *)smem_raw;
     V4<T> *sa = sp + stage_cap;
     __shared__ TileDesc d;
     __shared__ __align__(8) uint64_t bar;
-    load_desc(descs + blockIdx.x, d);
-    const bool in_smem = d.M <= stage_cap;
-    const bool staged = in_smem ? stage_positions(d, box, pos, sp, &bar, status, avec, sa) : true;
+    __shared__ uint32_t s_k;
+    __shared__ bool s_last;
+    stage_init(&bar);
+    uint32_t phase = 0;
+    const uint32_t *__restrict__ words = lv.words;
+    const uint32_t ntodo = *lv.count;
+    for (uint32_t k = next_ticket(sched, &s_k); k < ntodo; k = next_ticket(sched, &s_k)) {
     T de = 0, ds = 0, ue = 0, us = 0;
+    load_desc(lv.descs + lv.active[k], d);
+    const bool in_smem = d.M <= stage_cap;
+    if (!in_smem) note_spill(status);
+    const bool staged = in_smem ? stage_positions(d, box, pos, sp, &bar, phase, status, avec, sa) : true;
     for (uint32_t i = d.h0 + threadIdx.x; staged && i < d.h1; i += blockDim.x) {
         const V4<T> pi = pos[i];
         const V4<T> ai = avec[i];
@@ -121,7 +142,7 @@ __global__ void __launch_bounds__(kTileThreads)
             if (d.slow) hvp_sweep<T, false, true>(cfg, box, d, pos, avec, sp, sa, pi, ai, m, words + i, ld, P, A);
             else hvp_sweep<T, true, true>(cfg, box, d, pos, avec, sp, sa, pi, ai, m, words + i, ld, P, A);
         } else {
-            hvp_sweep<T, false, false>(cfg, box, d, pos, avec, sp, sa, pi, ai, m, words + i, ld, P, A);
+            hvp_sweep_spilled<T>(cfg, box, d, pos, avec, pi, ai, m, words + i, ld, P, &A);
         }
         // adj_pos += hscale * 24 eps * sum[...]  (FP64 accumulation of the adjoint state)
         double *o = adj_pos + 4 * (size_t)i;
@@ -135,17 +156,17 @@ __global__ void __launch_bounds__(kTileThreads)
         us += A.us;
     }
     if (out) {
+        const T v[4] = {de, ds, ue, us};
+        block_sum_store<4>(v, part + (size_t)k * 4);
+    }
+    __syncthreads();  // everyone done with d and the staged tile
+    }
+    if (sched_finish(sched, &s_last) && out) {
         // a.dF/deps = 24 sum a.(g r); a.dF/dsigma = (24 eps/sigma) sum a.(gs r);
         // dU/deps = 4 * 1/2 sum (s12 - s6); dU/dsigma = (24 eps/sigma) * 1/2 sum (2 s12 - s6)
-        T v[4] = {de, ds, ue, us};
-        __shared__ double scale4[4];
-        if (threadIdx.x == 0) {
-            scale4[0] = hscale * 24.0;
-            scale4[1] = hscale * e24s;
-            scale4[2] = 0.5 * 4.0;
-            scale4[3] = 0.5 * e24s;
-        }
-        grid_reduce<4>(v, part, counter, out, true, scale4);
+        const double scale4[4] = {hscale * 24.0, hscale * e24s, 0.5 * 4.0, 0.5 * e24s};
+        __threadfence();
+        sum_tile_partials<4>(part, ntodo, out, true, scale4);
     }
     (void)eps4;
 }
@@ -214,11 +235,13 @@ static fpm_status hvp_launch(const fpm_box &b, const fpm_grid &g, int n, const v
     P.rc2 = (T)(rc * rc);
     // two staged arrays share the shared-memory budget
     int sc = stage_capacity(n, g, 2 * sizeof(V4<T>));
+    const size_t smem = 2 * (size_t)sc * sizeof(V4<T>);
     smem_opt_in((const void *)k_lj_hvp_tiles<T>);
-    k_lj_hvp_tiles<T><<<cfg.ntiles, kTileThreads, 2 * (size_t)sc * sizeof(V4<T>), stream>>>(
-        cfg, box, (const V4<T> *)pos, (const V4<T> *)a, (const TileDesc *)((const char *)list + L.off_tiles),
-        (const uint32_t *)((const char *)list + L.off_words), nn, L.ld, sc, P, scale, 24.0 * eps, 24.0 * eps / sigma,
-        4.0 * eps, adj_pos, r.part, r.counter, d_params, st);
+    const int blocks = persistent_blocks((const void *)k_lj_hvp_tiles<T>, kTileThreads, smem, cfg.ntiles);
+    k_lj_hvp_tiles<T><<<blocks, kTileThreads, smem, stream>>>(cfg, box, (const V4<T> *)pos, (const V4<T> *)a,
+                                                              list_view(list, L), nn, L.ld, sc, P, scale, 24.0 * eps,
+                                                              24.0 * eps / sigma, 4.0 * eps, adj_pos,
+                                                              Sched{r.work, r.done}, r.part, d_params, st);
     return fpm_check_launch("fpm_lj_backward");
 }
 
@@ -241,11 +264,9 @@ extern "C" fpm_status fpm_lj_backward(const fpm_box *box, const fpm_grid *grid, 
     if (((uintptr_t)list & 255u) != 0 || ((uintptr_t)adj_pos & 31u) != 0)
         return fpm_fail(FPM_ERR_INVALID, "fpm_lj_backward: list must be 256-B and adj_pos 32-B aligned");
     if (n == 0) return FPM_OK;
-    RedWs r{nullptr, nullptr};
-    if (d_params) {
-        s = red_ws(n, grid, workspace, workspace_bytes, "fpm_lj_backward", r);
-        if (s != FPM_OK) return s;
-    }
+    RedWs r{};
+    s = red_ws(n, grid, workspace, workspace_bytes, "fpm_lj_backward", r);
+    if (s != FPM_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     if (prec == FPM_F32)
         return hvp_launch<float>(*box, *grid, n, pos, list, nn, cap, eps, sigma, rc, a, scale, adj_pos, d_params, r,

@@ -105,44 +105,59 @@ __device__ __forceinline__ void lj_sweep(const TileCfg &cfg, const BoxT<T> &box,
 
 template <typename T>
 __global__ void __launch_bounds__(kTileThreads)
-    k_lj_tiles(TileCfg cfg, BoxT<T> box, const V4<T> *__restrict__ pos, const TileDesc *__restrict__ descs,
-               const uint32_t *__restrict__ words, const uint32_t *__restrict__ nn, int64_t ld, int stage_cap,
-               LJParams<T> P, V4<T> *__restrict__ force, double *part, unsigned *counter, double *out,
-               fpm_dev_status *status)
+    k_lj_tiles(TileCfg cfg, BoxT<T> box, const V4<T> *__restrict__ pos, ListView lv, const uint32_t *__restrict__ nn,
+               int64_t ld, int stage_cap, LJParams<T> P, V4<T> *__restrict__ force, Sched sched, double *part,
+               double *out, fpm_dev_status *status)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     V4<T> *sp = (V4<T> *)smem_raw;
     __shared__ TileDesc d;
     __shared__ __align__(8) uint64_t bar;
-    load_desc(descs + blockIdx.x, d);
-    const bool in_smem = d.M <= stage_cap;
-    const bool staged = in_smem ? stage_positions(d, box, pos, sp, &bar, status) : true;
-    T usum = 0, wsum = 0;
-    uint32_t npsum = 0;
-    for (uint32_t i = d.h0 + threadIdx.x; staged && i < d.h1; i += blockDim.x) {
-        const V4<T> pi = pos[i];
-        const uint32_t m = nn[i];
-        T fx = 0, fy = 0, fz = 0, u = 0, w = 0;
-        uint32_t np = 0;
-        if (in_smem) {
-            if (d.slow) lj_sweep<T, false, true>(cfg, box, d, pos, sp, pi, m, words + i, ld, P, fx, fy, fz, u, w, np);
-            else lj_sweep<T, true, true>(cfg, box, d, pos, sp, pi, m, words + i, ld, P, fx, fy, fz, u, w, np);
-        } else {
-            lj_sweep<T, false, false>(cfg, box, d, pos, sp, pi, m, words + i, ld, P, fx, fy, fz, u, w, np);
+    __shared__ uint32_t s_k;
+    __shared__ bool s_last;
+    stage_init(&bar);
+    uint32_t phase = 0;
+    const uint32_t *__restrict__ words = lv.words;
+    const uint32_t ntodo = *lv.count;
+    for (uint32_t k = next_ticket(sched, &s_k); k < ntodo; k = next_ticket(sched, &s_k)) {
+        load_desc(lv.descs + lv.active[k], d);
+        const bool in_smem = d.M <= stage_cap;
+        if (!in_smem) note_spill(status);
+        const bool staged = in_smem ? stage_positions(d, box, pos, sp, &bar, phase, status) : true;
+        T usum = 0, wsum = 0;
+        uint32_t npsum = 0;
+        for (uint32_t i = d.h0 + threadIdx.x; staged && i < d.h1; i += blockDim.x) {
+            const V4<T> pi = pos[i];
+            const uint32_t m = nn[i];
+            T fx = 0, fy = 0, fz = 0, u = 0, w = 0;
+            uint32_t np = 0;
+            if (in_smem) {
+                if (d.slow)
+                    lj_sweep<T, false, true>(cfg, box, d, pos, sp, pi, m, words + i, ld, P, fx, fy, fz, u, w, np);
+                else
+                    lj_sweep<T, true, true>(cfg, box, d, pos, sp, pi, m, words + i, ld, P, fx, fy, fz, u, w, np);
+            } else {
+                lj_sweep<T, false, false>(cfg, box, d, pos, sp, pi, m, words + i, ld, P, fx, fy, fz, u, w, np);
+            }
+            V4<T> f;
+            f.x = P.eps24 * fx;
+            f.y = P.eps24 * fy;
+            f.z = P.eps24 * fz;
+            f.w = (T)0.5 * P.eps4 * u;
+            force[i] = f;
+            usum += P.eps4 * u;
+            wsum += P.eps24 * w;
+            npsum += np;
         }
-        V4<T> f;
-        f.x = P.eps24 * fx;
-        f.y = P.eps24 * fy;
-        f.z = P.eps24 * fz;
-        f.w = (T)0.5 * P.eps4 * u;
-        force[i] = f;
-        usum += P.eps4 * u;
-        wsum += P.eps24 * w;
-        npsum += np;
+        if (out) {  // this tile's U, W, pairs (halved: every pair is seen from both sides)
+            const T v[3] = {(T)0.5 * usum, (T)0.5 * wsum, (T)0.5 * (T)npsum};
+            block_sum_store<3>(v, part + (size_t)k * 3);
+        }
+        __syncthreads();  // everyone done with d and the staged tile
     }
-    if (out) {
-        T v[3] = {(T)0.5 * usum, (T)0.5 * wsum, (T)0.5 * (T)npsum};
-        grid_reduce<3>(v, part, counter, out);
+    if (sched_finish(sched, &s_last) && out) {
+        __threadfence();
+        sum_tile_partials<3>(part, ntodo, out, false, nullptr);
     }
 }
 
@@ -160,11 +175,12 @@ static fpm_status lj_launch(const fpm_box &b, const fpm_grid &g, int n, const vo
     P.sig2 = (T)(sigma * sigma);
     P.rc2 = (T)(rc * rc);
     const int sc = stage_capacity(n, g, sizeof(V4<T>));
+    const size_t smem = (size_t)sc * sizeof(V4<T>);
     smem_opt_in((const void *)k_lj_tiles<T>);
-    k_lj_tiles<T><<<cfg.ntiles, kTileThreads, sc * sizeof(V4<T>), stream>>>(
-        cfg, box, (const V4<T> *)pos, (const TileDesc *)((const char *)list + L.off_tiles),
-        (const uint32_t *)((const char *)list + L.off_words), nn, L.ld, sc, P, (V4<T> *)force, r.part, r.counter,
-        d_energy, status);
+    const int blocks = persistent_blocks((const void *)k_lj_tiles<T>, kTileThreads, smem, cfg.ntiles);
+    k_lj_tiles<T><<<blocks, kTileThreads, smem, stream>>>(cfg, box, (const V4<T> *)pos, list_view(list, L), nn, L.ld,
+                                                          sc, P, (V4<T> *)force, Sched{r.work, r.done}, r.part,
+                                                          d_energy, status);
     return fpm_check_launch("fpm_lj_forces");
 }
 
@@ -193,11 +209,9 @@ extern "C" fpm_status fpm_lj_forces(const fpm_box *box, const fpm_grid *grid, in
     fpm_status s = lj_args(box, grid, n, prec, pos, list, nn, cap, sigma, rc, force, "fpm_lj_forces");
     if (s != FPM_OK) return s;
     if (n == 0) return FPM_OK;
-    RedWs r{nullptr, nullptr};
-    if (d_energy) {
-        s = red_ws(n, grid, workspace, workspace_bytes, "fpm_lj_forces", r);
-        if (s != FPM_OK) return s;
-    }
+    RedWs r{};
+    s = red_ws(n, grid, workspace, workspace_bytes, "fpm_lj_forces", r);
+    if (s != FPM_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     if (prec == FPM_F32)
         return lj_launch<float>(*box, *grid, n, pos, list, nn, cap, eps, sigma, rc, force, d_energy, r, d_status, st);
@@ -258,18 +272,20 @@ extern "C" fpm_status fpm_lj_forces_noalloc(const fpm_box *box, const fpm_grid *
         return fpm_fail(FPM_ERR_INVALID, "fpm_lj_forces_noalloc: more than %d tiles exceed the built-in scratch limit",
                         kNoAllocMaxBlocks);
     if (n == 0) return FPM_OK;
-    RedWs r{nullptr, nullptr};
+    RedWs r{};
     cudaStream_t st = (cudaStream_t)stream;
-    if (d_energy) {
+    {
         void *scratch = nullptr;
         s = scratch_for_current_device(&scratch);
         if (s != FPM_OK) return s;
-        // the completion counter must start at zero; the array keeps whatever
+        // the scheduling counters must start at zero; the array keeps whatever
         // the previous call left there
-        cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(unsigned), st);
+        cudaError_t e = cudaMemsetAsync(scratch, 0, 64, st);
         if (e != cudaSuccess)
-            return fpm_fail(FPM_ERR_CUDA, "fpm_lj_forces_noalloc: clearing the counter: %s", cudaGetErrorString(e));
+            return fpm_fail(FPM_ERR_CUDA, "fpm_lj_forces_noalloc: clearing the counters: %s", cudaGetErrorString(e));
         r.counter = (unsigned *)scratch;
+        r.work = (unsigned *)((char *)scratch + 16);
+        r.done = (unsigned *)((char *)scratch + 32);
         r.part = (double *)((char *)scratch + 256);
     }
     if (prec == FPM_F32)

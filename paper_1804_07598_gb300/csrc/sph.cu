@@ -117,21 +117,46 @@ __device__ __forceinline__ void sph_sweep(const TileCfg &cfg, const BoxT<float> 
     }
 }
 
-__global__ void __launch_bounds__(kTileThreads)
+// The sweep of a tile whose neighbourhood did not fit in shared memory (rare;
+// out of line so that it does not add to the registers of the common path).
+__device__ __noinline__ void sph_sweep_spilled(const TileCfg &cfg, const BoxT<float> &box, const TileDesc &d,
+                                               const float4 *__restrict__ pos, const float4 *__restrict__ vr,
+                                               const float4 &pi, const float4 &vi, float rho_i, float P_i,
+                                               uint32_t m, const uint32_t *__restrict__ col, int64_t ld,
+                                               const SphK &K, float *out5)
+{
+    float ax = 0.0f, ay = 0.0f, az = 0.0f, dr = 0.0f, mumax = 0.0f;
+    sph_sweep<false, false>(cfg, box, d, pos, vr, nullptr, nullptr, pi, vi, rho_i, P_i, m, col, ld, K, ax, ay, az, dr,
+                            mumax);
+    out5[0] = ax;
+    out5[1] = ay;
+    out5[2] = az;
+    out5[3] = dr;
+    out5[4] = mumax;
+}
+
+__global__ void __launch_bounds__(kTileThreads, 4)
     k_sph_tiles(TileCfg cfg, BoxT<float> box, const float4 *__restrict__ pos, const float4 *__restrict__ vr,
-                const TileDesc *__restrict__ descs, const uint32_t *__restrict__ words,
-                const uint32_t *__restrict__ nn, int64_t ld, int stage_cap, SphK K, float4 *__restrict__ acc,
-                float *dtcons, fpm_dev_status *status)
+                ListView lv, const uint32_t *__restrict__ nn, int64_t ld, int stage_cap, SphK K,
+                float4 *__restrict__ acc, float *dtcons, Sched sched, fpm_dev_status *status)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float4 *sp = (float4 *)smem_raw;
     float4 *sv = sp + stage_cap;
     __shared__ TileDesc d;
     __shared__ __align__(8) uint64_t bar;
-    load_desc(descs + blockIdx.x, d);
-    const bool in_smem = d.M <= stage_cap;
-    const bool staged = in_smem ? stage_positions(d, box, pos, sp, &bar, status, vr, sv) : true;
+    __shared__ uint32_t s_k;
+    __shared__ bool s_last;
+    stage_init(&bar);
+    uint32_t phase = 0;
+    const uint32_t *__restrict__ words = lv.words;
     float amax = 0.0f, mumax = 0.0f;
+    const uint32_t ntodo = *lv.count;
+    for (uint32_t k = next_ticket(sched, &s_k); k < ntodo; k = next_ticket(sched, &s_k)) {
+    load_desc(lv.descs + lv.active[k], d);
+    const bool in_smem = d.M <= stage_cap;
+    if (!in_smem) note_spill(status);
+    const bool staged = in_smem ? stage_positions(d, box, pos, sp, &bar, phase, status, vr, sv) : true;
     for (uint32_t i = d.h0 + threadIdx.x; staged && i < d.h1; i += blockDim.x) {
         const float4 pi = pos[i];
         const float4 vi = vr[i];
@@ -147,8 +172,13 @@ __global__ void __launch_bounds__(kTileThreads)
                 sph_sweep<true, true>(cfg, box, d, pos, vr, sp, sv, pi, vi, rho_i, P_i, m, words + i, ld, K, ax, ay,
                                       az, dr, mumax);
         } else {
-            sph_sweep<false, false>(cfg, box, d, pos, vr, sp, sv, pi, vi, rho_i, P_i, m, words + i, ld, K, ax, ay, az,
-                                    dr, mumax);
+            float o5[5];
+            sph_sweep_spilled(cfg, box, d, pos, vr, pi, vi, rho_i, P_i, m, words + i, ld, K, o5);
+            ax = o5[0];
+            ay = o5[1];
+            az = o5[2];
+            dr = o5[3];
+            mumax = fmaxf(mumax, o5[4]);
         }
         float4 a;
         if (pi.w == 0.0f) {
@@ -162,6 +192,8 @@ __global__ void __launch_bounds__(kTileThreads)
         a.w = dr;
         acc[i] = a;
     }
+    __syncthreads();  // everyone done with d and the staged tile
+    }
     // one atomic max per warp on the (non-negative) float bits
     const unsigned ma = __reduce_max_sync(kFull, __float_as_uint(amax));
     const unsigned mm = __reduce_max_sync(kFull, __float_as_uint(mumax));
@@ -169,6 +201,7 @@ __global__ void __launch_bounds__(kTileThreads)
         if (ma) atomicMax((unsigned *)dtcons, ma);
         if (mm) atomicMax((unsigned *)dtcons + 1, mm);
     }
+    sched_finish(sched, &s_last);
 }
 
 __device__ __forceinline__ float sph_dt(const float *dtcons, float h, float c0, float cfl)
@@ -314,8 +347,8 @@ static fpm_status sph_params_ok(const fpm_sph_params *p, const char *who)
 
 extern "C" fpm_status fpm_sph_forces(const fpm_box *box, const fpm_grid *grid, int32_t n, const void *pos,
                                      const void *vr, const void *list, const uint32_t *nn, int32_t cap,
-                                     const fpm_sph_params *params, void *acc, float *d_dtcons,
-                                     fpm_dev_status *d_status, fpm_stream stream)
+                                     const fpm_sph_params *params, void *acc, float *d_dtcons, void *workspace,
+                                     size_t workspace_bytes, fpm_dev_status *d_status, fpm_stream stream)
 {
     fpm_status s = fpm_check_grid(box, grid, "fpm_sph_forces");
     if (s != FPM_OK) return s;
@@ -325,14 +358,18 @@ extern "C" fpm_status fpm_sph_forces(const fpm_box *box, const fpm_grid *grid, i
         return fpm_fail(FPM_ERR_INVALID, "fpm_sph_forces: null pointer or bad size");
     if (((uintptr_t)list & 255u) != 0) return fpm_fail(FPM_ERR_INVALID, "fpm_sph_forces: list not 256-B aligned");
     if (n == 0) return FPM_OK;
+    RedWs r{};
+    s = red_ws(n, grid, workspace, workspace_bytes, "fpm_sph_forces", r);
+    if (s != FPM_OK) return s;
     const TileCfg cfg = make_tile_cfg(*box, *grid);
     const ListLayout L = list_layout(n, cfg, cap);
     const int sc = stage_capacity(n, *grid, 2 * sizeof(float4));
+    const size_t smem = 2 * (size_t)sc * sizeof(float4);
     smem_opt_in((const void *)k_sph_tiles);
-    k_sph_tiles<<<cfg.ntiles, kTileThreads, 2 * (size_t)sc * sizeof(float4), (cudaStream_t)stream>>>(
-        cfg, make_box<float>(*box), (const float4 *)pos, (const float4 *)vr,
-        (const TileDesc *)((const char *)list + L.off_tiles), (const uint32_t *)((const char *)list + L.off_words), nn,
-        L.ld, sc, make_sph(*params), (float4 *)acc, d_dtcons, d_status);
+    const int blocks = persistent_blocks((const void *)k_sph_tiles, kTileThreads, smem, cfg.ntiles);
+    k_sph_tiles<<<blocks, kTileThreads, smem, (cudaStream_t)stream>>>(
+        cfg, make_box<float>(*box), (const float4 *)pos, (const float4 *)vr, list_view(list, L), nn, L.ld, sc,
+        make_sph(*params), (float4 *)acc, d_dtcons, Sched{r.work, r.done}, d_status);
     return fpm_check_launch("fpm_sph_forces");
 }
 

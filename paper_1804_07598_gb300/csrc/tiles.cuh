@@ -32,6 +32,7 @@ namespace fpm {
 enum : int { kModeOpen = 0, kModeWrap = 1, kModeAll = 2 };
 
 constexpr int kTileThreads = 192;          // threads per tile block
+constexpr int kTileTarget = 170;           // particles per tile the grid's tile width aims at
 constexpr int kMaxTileCells = 14;          // home cells per tile along x
 constexpr int kMaxSeq = kMaxTileCells + 2; // staged cells per stencil row
 constexpr int kMaxRows = 9;
@@ -81,12 +82,14 @@ struct TileDesc {
 };
 
 // Layout of a Verlet-list object in caller memory:
-//   [0, 256)                       reserved
+//   [0, 4)                          number of non-empty tiles
+//   [16, 24)                        scheduling counters of the Verlet scan
 //   [256, 256 + ntiles*sizeof(TileDesc))  tile descriptors
+//   then ntiles uint32: the non-empty tiles in increasing order
 //   then the ELL words: entry k of particle i is the 16-bit half (k & 1) of
 //   word (k >> 1) * ld + i.
 struct ListLayout {
-    size_t off_tiles, off_words, total;
+    size_t off_tiles, off_active, off_words, total;
     int64_t ld;
     int words_per_particle;
 };
@@ -98,9 +101,26 @@ inline ListLayout list_layout(int n, const TileCfg &c, int cap)
     L.words_per_particle = (cap + 1) / 2;
     L.off_tiles = 256;
     size_t t = L.off_tiles + (size_t)c.ntiles * sizeof(TileDesc);
+    L.off_active = (t + 255) & ~(size_t)255;
+    t = L.off_active + (size_t)c.ntiles * 4;
     L.off_words = (t + 255) & ~(size_t)255;
     L.total = L.off_words + (size_t)L.words_per_particle * (size_t)L.ld * 4;
     return L;
+}
+
+// Pointers into a list object.
+struct ListView {
+    const uint32_t *count;
+    const TileDesc *descs;
+    const uint32_t *active;
+    const uint32_t *words;
+};
+
+inline ListView list_view(const void *list, const ListLayout &L)
+{
+    const char *b = (const char *)list;
+    return ListView{(const uint32_t *)b, (const TileDesc *)(b + L.off_tiles), (const uint32_t *)(b + L.off_active),
+                    (const uint32_t *)(b + L.off_words)};
 }
 
 // Stencil offsets of one row dimension: cell index and wrap class (-1: seen
@@ -245,6 +265,12 @@ __device__ inline void tile_geometry(const TileCfg &cfg, int tile, const uint32_
     __syncthreads();
 }
 
+// Counts a tile whose neighbourhood does not fit the staging buffer.
+__device__ __forceinline__ void note_spill(fpm_dev_status *st)
+{
+    if (st && threadIdx.x == 0) atomicAdd(&st->spilled, 1u);
+}
+
 // Loads a tile descriptor from global memory into shared memory.
 __device__ __forceinline__ void load_desc(const TileDesc *__restrict__ src, TileDesc &dst)
 {
@@ -282,25 +308,33 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
     }
 }
 
+// One-time set-up of the staging barrier of a block.
+__device__ __forceinline__ void stage_init(uint64_t *bar)
+{
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+}
+
 // Stages the neighbourhood positions of a tile into shared memory: slot s of
 // piece p holds pos[gstart + (s - soff)] with the lower-wall shifts applied
 // and (in tiles that need them) the piece flags in w.  When aux is given, the
-// same slots of a second per-particle array (an adjoint vector) are copied
-// unchanged into aux_st on the same barrier.  Returns false, the same in every
-// thread, if the copies did not complete within the wait budget.
+// same slots of a second per-particle array are copied unchanged into aux_st
+// on the same barrier.  `phase` is the barrier's parity, flipped per use.
+// Every thread must have finished with the previous tile's staged data (a
+// __syncthreads) before the call.  Returns false, the same in every thread,
+// if the copies did not complete within the wait budget.
 template <typename T>
 __device__ bool stage_positions(const TileDesc &d, const BoxT<T> &box, const V4<T> *__restrict__ pos,
-                                V4<T> *__restrict__ st, uint64_t *bar, fpm_dev_status *status,
+                                V4<T> *__restrict__ st, uint64_t *bar, uint32_t &phase, fpm_dev_status *status,
                                 const V4<T> *__restrict__ aux = nullptr, V4<T> *__restrict__ aux_st = nullptr)
 {
     const uint32_t b = smem_u32(bar);
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        // order this block's earlier generic accesses of the buffers before the async copies
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
         const uint32_t bytes = (uint32_t)d.M * (uint32_t)sizeof(V4<T>) * (aux ? 2u : 1u);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
         for (int p = 0; p < kMaxPieces; ++p) {
@@ -320,11 +354,12 @@ __device__ bool stage_positions(const TileDesc &d, const BoxT<T> &box, const V4<
                     : "memory");
         }
     }
-    bool ok = mbar_wait(b, 0u, kWaitCycles);
+    bool ok = mbar_wait(b, phase, kWaitCycles);
     if (!ok) {
         latch_flag(status, FPM_FLAG_TIMEOUT);
-        ok = mbar_wait(b, 0u, kWaitCycles);  // let copies in flight land before leaving
+        ok = mbar_wait(b, phase, kWaitCycles);  // let copies in flight land before leaving
     }
+    phase ^= 1u;
     if (!__syncthreads_and(ok)) return false;
     for (int p = 0; p < kMaxPieces; ++p) {
         const Piece pc = d.piece[p];
@@ -403,10 +438,22 @@ __device__ __forceinline__ T tile_sep(const V4<T> &pi, const V4<T> &pj, const Bo
 
 // Shared-memory budget for staged positions: 1.4x the mean neighbourhood of
 // a tile plus slack, capped by what one block may use.
+// The particles per cell assumed are the larger of the mean (n / ncell) and
+// the occupancy the tile width was chosen for (kTileTarget particles per
+// tile), so that a grid whose tiles were sized for the dense part of a
+// non-uniform system (set by the caller through fpm_grid.tiles_x) stages its
+// dense tiles in shared memory.
 inline int stage_capacity(int n, const fpm_grid &g, size_t elem_bytes)
 {
-    const double rho_c = g.ncell > 0 ? (double)n / g.ncell : 0.0;
+    const int maxe0 = (int)((size_t)kSmemBudget / elem_bytes) / 32 * 32;
+    if (g.stage_cap > 0) {
+        const int e = (g.stage_cap + 31) / 32 * 32;
+        return e > maxe0 ? maxe0 : e;
+    }
     const int wx = (g.nc[0] + g.tiles_x - 1) / g.tiles_x;
+    const double mean = g.ncell > 0 ? (double)n / g.ncell : 0.0;
+    const double sized = (double)kTileTarget / (double)(wx + 1);
+    const double rho_c = mean > sized ? mean : sized;
     const int seq = g.nc[0] == 1 ? 1 : wx + 2;
     const int rows = (g.nc[1] >= 3 ? 3 : g.nc[1]) * (g.nc[2] >= 3 ? 3 : g.nc[2]);
     const double want = 1.2 * rows * seq * rho_c + 96.0;
@@ -422,6 +469,114 @@ inline int stage_capacity(int n, const fpm_grid &g, size_t elem_bytes)
 inline void smem_opt_in(const void *kernel)
 {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBudget);
+}
+
+// ---- dynamic tile scheduling of the persistent sweeps -----------------------
+// A sweep's blocks take tickets k = 0, 1, ... from a work counter; ticket k is
+// the k-th non-empty tile.  The last block to finish resets the counters, so
+// they are zero again for the next launch (the memory holding them must be
+// zero before the first launch).
+
+struct Sched {
+    unsigned *work;  // next ticket
+    unsigned *done;  // blocks finished
+};
+
+// The next ticket of this block (all threads get the same value).  Every
+// thread must be done with the previous tile's shared data before the call.
+__device__ __forceinline__ uint32_t next_ticket(const Sched &sc, uint32_t *s_k)
+{
+    if (threadIdx.x == 0) *s_k = atomicAdd(sc.work, 1u);
+    __syncthreads();
+    return *s_k;
+}
+
+// Called by every block after its last ticket; returns true in the last block
+// to finish (in all its threads), after resetting the counters.
+__device__ __forceinline__ bool sched_finish(const Sched &sc, bool *s_last)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(sc.done, 1u);
+        *s_last = (t == gridDim.x - 1);
+        if (*s_last) {
+            *sc.work = 0u;
+            *sc.done = 0u;
+        }
+    }
+    __syncthreads();
+    return *s_last;
+}
+
+// Sums NV per-thread values over the block (FP32 or FP64 within warps, FP64
+// across warps) and stores them, from thread 0, to dst[0..NV).  All threads
+// must call it.
+template <int NV, typename TV>
+__device__ __forceinline__ void block_sum_store(const TV (&v)[NV], double *dst)
+{
+    __shared__ double sh[32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const TV s = warp_sum(v[k]);
+        if (lane == 0) sh[warp][k] = (double)s;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = lane < nw ? sh[lane][k] : 0.0;
+            s = warp_sum(s);
+            if (lane == 0) dst[k] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// In the last block: out[k] (+)= scale[k] * sum over tickets j < count of
+// part[j*NV + k], in ticket order (bit-reproducible).
+template <int NV>
+__device__ __forceinline__ void sum_tile_partials(const double *part, uint32_t count, double *out, bool accumulate,
+                                                  const double *scale)
+{
+    double acc[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] = 0.0;
+    for (uint32_t j = threadIdx.x; j < count; j += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] += __ldcg(part + (size_t)j * NV + k);
+    __shared__ double sh[32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        const double s = warp_sum(acc[k]);
+        if (lane == 0) sh[warp][k] = s;
+    }
+    __syncthreads();
+    if (warp == 0 && out) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double s = lane < nw ? sh[lane][k] : 0.0;
+            s = warp_sum(s);
+            const double v = scale ? scale[k] * s : s;
+            if (lane == 0) out[k] = accumulate ? out[k] + v : v;
+        }
+    }
+}
+
+// Grid of a persistent tile sweep: as many blocks as fit on the GPU at once
+// (never more than there are tiles).  Each block walks the non-empty tiles
+// k = blockIdx.x, blockIdx.x + gridDim.x, ... of the list's active array.
+inline int persistent_blocks(const void *kernel, int threads, size_t smem, int ntiles)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    long long b = (long long)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    if (b > ntiles) b = ntiles;
+    return b < 1 ? 1 : (int)b;
 }
 
 }  // namespace fpm

@@ -40,59 +40,139 @@ __device__ __forceinline__ uint32_t scan_candidates(const TileCfg &cfg, const Bo
     return cnt;
 }
 
+// Phase 1, every tile: geometry and descriptor (no staging, little shared
+// memory, so the many empty tiles of a sparse box cost almost nothing).
+__global__ void __launch_bounds__(128)
+    k_tile_desc(TileCfg cfg, const uint32_t *__restrict__ cs, TileDesc *__restrict__ descs, fpm_dev_status *st,
+                const uint32_t *gate)
+{
+    if (gated_off(gate)) return;
+    __shared__ TileGeom g;
+    __shared__ TileDesc d;
+    tile_geometry(cfg, blockIdx.x, cs, g, d);
+    const int nw = (int)(sizeof(TileDesc) / 4);
+    uint32_t *o = (uint32_t *)(descs + blockIdx.x);
+    const uint32_t *s = (const uint32_t *)&d;
+    for (int k = threadIdx.x; k < nw; k += blockDim.x) o[k] = s[k];
+    if (threadIdx.x == 0 && st && d.h1 > d.h0) atomicMax(&st->max_staged, (uint32_t)d.M);
+}
+
+// Phase 2, one block: the non-empty tiles in increasing order (a block-wide
+// exclusive scan of the emptiness flags, 1024 x 4 tiles per pass).
+__global__ void __launch_bounds__(1024)
+    k_tile_compact(const TileDesc *__restrict__ descs, int ntiles, uint32_t *__restrict__ active,
+                   uint32_t *__restrict__ count, const uint32_t *gate)
+{
+    if (gated_off(gate)) return;
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c0 = 0; c0 < ntiles; c0 += 4 * (int)blockDim.x) {
+        uint32_t f[4], s = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int t = c0 + 4 * (int)threadIdx.x + q;
+            f[q] = (t < ntiles && descs[t].h1 > descs[t].h0) ? 1u : 0u;
+            s += f[q];
+        }
+        uint32_t incl = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, w, o);
+                if (lane >= o) w += y;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        uint32_t pos = base + incl - s + (warp > 0 ? wsum[warp - 1] : 0u);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (f[q]) active[pos++] = (uint32_t)(c0 + 4 * (int)threadIdx.x + q);
+        __syncthreads();
+        if (threadIdx.x == 0) base += wsum[(blockDim.x >> 5) - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *count = base;
+        count[4] = 0u;  // the scan's ticket and completion counters (list header bytes 16..23)
+        count[5] = 0u;
+    }
+}
+
+// Phase 3, persistent over the non-empty tiles: stage the neighbourhood and
+// scan each home particle's candidates.
 template <typename T>
 __global__ void __launch_bounds__(kTileThreads)
-    k_verlet_tiles(TileCfg cfg, BoxT<T> box, const V4<T> *__restrict__ pos, const uint32_t *__restrict__ cs, T rl2,
-                   int cap, int64_t ld, int stage_cap, TileDesc *__restrict__ descs, uint32_t *__restrict__ words,
-                   uint32_t *__restrict__ nn, V4<T> *__restrict__ pos_ref, fpm_dev_status *st, const uint32_t *gate)
+    k_verlet_scan(TileCfg cfg, BoxT<T> box, const V4<T> *__restrict__ pos, const uint32_t *__restrict__ cs, T rl2,
+                  int cap, int64_t ld, int stage_cap, const uint32_t *__restrict__ active,
+                  const uint32_t *__restrict__ count, Sched sched, uint32_t *__restrict__ words,
+                  uint32_t *__restrict__ nn, V4<T> *__restrict__ pos_ref, fpm_dev_status *st, const uint32_t *gate)
 {
     if (gated_off(gate)) return;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     V4<T> *sp = (V4<T> *)smem_raw;
     __shared__ TileGeom g;
     __shared__ TileDesc d;
-    tile_geometry(cfg, blockIdx.x, cs, g, d);
-    {  // publish the descriptor for the sweeps
-        const int nw = (int)(sizeof(TileDesc) / 4);
-        uint32_t *o = (uint32_t *)(descs + blockIdx.x);
-        const uint32_t *s = (const uint32_t *)&d;
-        for (int k = threadIdx.x; k < nw; k += blockDim.x) o[k] = s[k];
-    }
-    uint32_t maxc = 0;
-    if (d.M > kMaxStaged) {  // 16-bit entries cannot address this neighbourhood
-        for (uint32_t i = d.h0 + threadIdx.x; i < d.h1; i += blockDim.x) nn[i] = 0u;
-        if (threadIdx.x == 0) latch_flag(st, FPM_FLAG_CAPACITY);
-        return;
-    }
     __shared__ __align__(8) uint64_t bar;
-    const bool in_smem = d.M <= stage_cap;
-    if (in_smem && !stage_positions(d, box, pos, sp, &bar, st)) {
-        for (uint32_t i = d.h0 + threadIdx.x; i < d.h1; i += blockDim.x) nn[i] = 0u;
-        return;
-    }
-    for (uint32_t i = d.h0 + threadIdx.x; i < d.h1; i += blockDim.x) {
-        const V4<T> pi = pos[i];
-        if (pos_ref) pos_ref[i] = pi;
-        // the home cell: the staged cell of the middle row holding i
-        int th = g.a - g.seq_start;
-        for (int t = g.a - g.seq_start; t < g.b - g.seq_start; ++t)
-            if (i >= g.start[g.mid_row][t] && i < g.start[g.mid_row][t] + (uint32_t)g.cnt[g.mid_row][t]) th = t;
-        const int self = g.off[g.mid_row][th] + (int)(i - g.start[g.mid_row][th]);
-        const int t0 = th > 0 ? th - 1 : 0;
-        const int t1 = th + 1 < g.nseq ? th + 1 : g.nseq - 1;
-        uint32_t c;
-        if (in_smem) {
-            c = d.slow ? scan_candidates<false, true>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld, i, words)
-                       : scan_candidates<true, true>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld, i, words);
-        } else {
-            c = scan_candidates<false, false>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld, i, words);
+    __shared__ uint32_t s_k;
+    __shared__ bool s_last;
+    stage_init(&bar);
+    uint32_t phase = 0;
+    uint32_t maxc = 0;
+    const uint32_t ntodo = *count;
+    for (uint32_t k = next_ticket(sched, &s_k); k < ntodo; k = next_ticket(sched, &s_k)) {
+        tile_geometry(cfg, (int)active[k], cs, g, d);
+        if (d.M > kMaxStaged) {  // 16-bit entries cannot address this neighbourhood
+            for (uint32_t i = d.h0 + threadIdx.x; i < d.h1; i += blockDim.x) nn[i] = 0u;
+            if (threadIdx.x == 0) latch_flag(st, FPM_FLAG_CAPACITY);
+            __syncthreads();
+            continue;
         }
-        nn[i] = c < (uint32_t)cap ? c : (uint32_t)cap;
-        if (c > (uint32_t)cap) latch_flag(st, FPM_FLAG_CAPACITY);
-        maxc = c > maxc ? c : maxc;
+        const bool in_smem = d.M <= stage_cap;
+        if (!in_smem) note_spill(st);
+        if (in_smem && !stage_positions(d, box, pos, sp, &bar, phase, st)) {
+            for (uint32_t i = d.h0 + threadIdx.x; i < d.h1; i += blockDim.x) nn[i] = 0u;
+            __syncthreads();
+            continue;
+        }
+        for (uint32_t i = d.h0 + threadIdx.x; i < d.h1; i += blockDim.x) {
+            const V4<T> pi = pos[i];
+            if (pos_ref) pos_ref[i] = pi;
+            // the home cell: the staged cell of the middle row holding i
+            int th = g.a - g.seq_start;
+            for (int t = g.a - g.seq_start; t < g.b - g.seq_start; ++t)
+                if (i >= g.start[g.mid_row][t] && i < g.start[g.mid_row][t] + (uint32_t)g.cnt[g.mid_row][t]) th = t;
+            const int self = g.off[g.mid_row][th] + (int)(i - g.start[g.mid_row][th]);
+            const int t0 = th > 0 ? th - 1 : 0;
+            const int t1 = th + 1 < g.nseq ? th + 1 : g.nseq - 1;
+            uint32_t c;
+            if (in_smem) {
+                c = d.slow
+                        ? scan_candidates<false, true>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld, i, words)
+                        : scan_candidates<true, true>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld, i, words);
+            } else {
+                c = scan_candidates<false, false>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld, i, words);
+            }
+            nn[i] = c < (uint32_t)cap ? c : (uint32_t)cap;
+            if (c > (uint32_t)cap) latch_flag(st, FPM_FLAG_CAPACITY);
+            maxc = c > maxc ? c : maxc;
+        }
+        __syncthreads();  // everyone done with g, d and the staged tile
     }
     const uint32_t m = __reduce_max_sync(kFull, maxc);
     if ((threadIdx.x & 31) == 0 && st && m > 0) atomicMax(&st->max_nn, m);
+    sched_finish(sched, &s_last);
 }
 
 __global__ void __launch_bounds__(kTileThreads)
@@ -151,10 +231,20 @@ static fpm_status verlet_launch(const fpm_box &b, const fpm_grid &g, int n, cons
     const T rl2 = (T)(r_list * r_list);
     const int sc = stage_capacity(n, g, sizeof(V4<T>));
     if (n > 0) {
-        smem_opt_in((const void *)k_verlet_tiles<T>);
-        k_verlet_tiles<T><<<cfg.ntiles, kTileThreads, sc * sizeof(V4<T>), stream>>>(
-            cfg, box, (const V4<T> *)pos, cs, rl2, cap, L.ld, sc, (TileDesc *)((char *)list + L.off_tiles),
-            (uint32_t *)((char *)list + L.off_words), nn, (V4<T> *)pos_ref, st, gate);
+        char *lb = (char *)list;
+        TileDesc *descs = (TileDesc *)(lb + L.off_tiles);
+        uint32_t *active = (uint32_t *)(lb + L.off_active);
+        uint32_t *count = (uint32_t *)lb;
+        k_tile_desc<<<cfg.ntiles, 128, 0, stream>>>(cfg, cs, descs, st, gate);
+        k_tile_compact<<<1, 1024, 0, stream>>>(descs, cfg.ntiles, active, count, gate);
+        const size_t smem = (size_t)sc * sizeof(V4<T>);
+        smem_opt_in((const void *)k_verlet_scan<T>);
+        const int blocks = persistent_blocks((const void *)k_verlet_scan<T>, kTileThreads, smem, cfg.ntiles);
+        k_verlet_scan<T><<<blocks, kTileThreads, smem, stream>>>(cfg, box, (const V4<T> *)pos, cs, rl2, cap, L.ld, sc,
+                                                                 active, count,
+                                                                 Sched{(unsigned *)(lb + 16), (unsigned *)(lb + 20)},
+                                                                 (uint32_t *)(lb + L.off_words), nn, (V4<T> *)pos_ref, st,
+                                                                 gate);
     }
     if (gate) k_gate_done<<<1, 1, 0, stream>>>(gate, st);
     return fpm_check_launch("fpm_verlet_build");

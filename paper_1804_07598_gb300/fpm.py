@@ -37,7 +37,8 @@ class fpm_box(_c.Structure):
 
 
 class fpm_grid(_c.Structure):
-    _fields_ = [("nc", _c.c_int32 * 3), ("ncell", _c.c_int32), ("inv", _c.c_float * 3), ("tiles_x", _c.c_int32)]
+    _fields_ = [("nc", _c.c_int32 * 3), ("ncell", _c.c_int32), ("inv", _c.c_float * 3), ("tiles_x", _c.c_int32),
+                ("stage_cap", _c.c_int32)]
 
     @property
     def shape(self):
@@ -47,7 +48,7 @@ class fpm_grid(_c.Structure):
 class fpm_dev_status(_c.Structure):
     _fields_ = [("flags", _c.c_uint32), ("max_nn", _c.c_uint32), ("rebuild", _c.c_uint32),
                 ("nrebuild", _c.c_uint32), ("max_disp2", _c.c_uint32), ("bad_index", _c.c_uint32),
-                ("reserved", _c.c_uint32 * 10)]
+                ("max_staged", _c.c_uint32), ("spilled", _c.c_uint32), ("reserved", _c.c_uint32 * 8)]
 
 
 class fpm_sph_params(_c.Structure):
@@ -95,7 +96,7 @@ _SIG = {
     "fpm_vv_drift_check": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.c_int, _c.c_double, _VP, _VP, _VP, _VP,
                                       _c.c_double, _VP, _VP]),
     "fpm_sph_forces": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _VP, _VP, _VP, _VP,
-                                  _c.c_int32, _c.POINTER(fpm_sph_params), _VP, _VP, _VP, _VP]),
+                                  _c.c_int32, _c.POINTER(fpm_sph_params), _VP, _VP, _VP, _c.c_size_t, _VP, _VP]),
     "fpm_sph_predict": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.POINTER(fpm_sph_params), _c.c_double, _VP,
                                    _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _c.c_double, _VP, _VP]),
     "fpm_sph_correct": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.POINTER(fpm_sph_params), _VP, _VP, _VP, _VP,
@@ -249,7 +250,7 @@ def fpm_verlet_build(box, grid, n, prec, pos, cell_start, r_list, cap, list_obj,
     _check(lib().fpm_verlet_build(_c.byref(box), _c.byref(grid), int(n), int(prec), _ptr(pos), _ptr(cell_start),
                                   float(r_list), int(cap), _ptr(list_obj), _nbytes(list_obj), _ptr(nn),
                                   _ptr(pos_ref), _ptr(d_status), _ptr(d_gate), _stream(stream)))
-    _count((1 if n > 0 else 0) + (1 if d_gate is not None else 0))
+    _count((3 if n > 0 else 0) + (1 if d_gate is not None else 0))
 
 
 def fpm_verlet_decode(grid, n, cap, list_obj, nn, out, stream=None):
@@ -322,11 +323,11 @@ def fpm_adjoint_seed(n, prec, force, xbar, vbar, a_out, stream=None):
     _count(1 if n > 0 else 0)
 
 
-def fpm_sph_forces(box, grid, n, pos, vr, list_obj, nn, cap, params, acc, d_dtcons=None, d_status=None,
-                   stream=None):
+def fpm_sph_forces(box, grid, n, pos, vr, list_obj, nn, cap, params, acc, d_dtcons=None, workspace=None,
+                   d_status=None, stream=None):
     _check(lib().fpm_sph_forces(_c.byref(box), _c.byref(grid), int(n), _ptr(pos), _ptr(vr), _ptr(list_obj),
-                                _ptr(nn), int(cap), _c.byref(params), _ptr(acc), _ptr(d_dtcons), _ptr(d_status),
-                                _stream(stream)))
+                                _ptr(nn), int(cap), _c.byref(params), _ptr(acc), _ptr(d_dtcons), _ptr(workspace),
+                                _nbytes(workspace), _ptr(d_status), _stream(stream)))
     _count(1 if n > 0 else 0)
 
 

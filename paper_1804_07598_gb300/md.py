@@ -67,7 +67,14 @@ class LJSystem:
         self.kin = torch.zeros(4, dtype=torch.float64, device=dev)
         self._graph = None
         self.rebuild()
+        self.size_staging()
         self.compute_forces()
+
+    def size_staging(self, margin: float = 1.15):
+        """Set the grid's shared-memory staging capacity from the largest tile
+        neighbourhood the last Verlet build saw (synchronises)."""
+        st = fpm.read_status(self.status)
+        self.grid.stage_cap = int(math.ceil((margin * st.max_staged + 64) / 32.0)) * 32
 
     # -- pieces ---------------------------------------------------------
     @property

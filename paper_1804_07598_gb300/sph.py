@@ -42,6 +42,12 @@ class SPHSystem:
         self.skin = float(skin) if skin is not None else 0.25 * h
         self.r_list = 2.0 * h + self.skin
         self.grid = fpm.fpm_grid_make(self.box, self.r_list, n)
+        # tiles sized for the fluid's own density (the box is mostly empty):
+        # about 170 particles per tile at one particle per dp^3
+        dp = (m / rho0) ** (1.0 / 3.0)
+        per_cell = (self.L[0] / self.grid.nc[0]) * (self.L[1] / self.grid.nc[1]) * (self.L[2] / self.grid.nc[2]) / dp ** 3
+        width = int(min(14, max(1, round(170.0 / per_cell))))
+        self.grid.tiles_x = (self.grid.nc[0] + width - 1) // width
         self.cap = int(cap) if cap else max(32, int(math.ceil(1.6 * 4.0 / 3.0 * math.pi * (self.r_list / (m / rho0)
                                                                                            ** (1 / 3)) ** 3 / 8)) * 8)
         dev = self.device
@@ -67,8 +73,16 @@ class SPHSystem:
         self.dtcons = torch.zeros(2, dtype=f32, device=dev)
         self.dtcons_h = torch.zeros(2, dtype=f32, device=dev)
         self.dt = torch.zeros(1, dtype=f32, device=dev)
+        self.ws_red = torch.zeros(fpm.fpm_reduce_workspace(n, self.grid), dtype=torch.uint8, device=dev)
         self._graph = None
         self.rebuild()
+        self.size_staging()
+
+    def size_staging(self, margin: float = 1.15):
+        """Set the grid's shared-memory staging capacity from the largest tile
+        neighbourhood the last Verlet build saw (synchronises)."""
+        st = fpm.read_status(self.status)
+        self.grid.stage_cap = int(math.ceil((margin * st.max_staged + 64) / 32.0)) * 32
 
     @property
     def gate_ptr(self) -> int:
@@ -84,7 +98,8 @@ class SPHSystem:
     def rates(self, pos=None, vr=None, acc=None, dtcons=None):
         fpm.fpm_sph_forces(self.box, self.grid, self.n, self.pos if pos is None else pos,
                            self.vr if vr is None else vr, self.nbr, self.nn, self.cap, self.params,
-                           self.acc if acc is None else acc, self.dtcons if dtcons is None else dtcons, self.status)
+                           self.acc if acc is None else acc, self.dtcons if dtcons is None else dtcons, self.ws_red,
+                           self.status)
 
     def _step(self):
         self.rates()
