@@ -76,13 +76,18 @@ typedef struct {
  * memory (0: estimated from the mean density).  A tile with a larger
  * neighbourhood is still computed correctly, reading neighbours from global
  * memory, and counted in fpm_dev_status.spilled; fpm_dev_status.max_staged
- * after a Verlet build tells the caller what to set. */
+ * after a Verlet build tells the caller what to set.
+ * sweep_blocks: blocks of the tile sweeps (Verlet scan, LJ, SPH, adjoint),
+ * which take tiles by ticket: 0 = as many as fit on the GPU at once, > 0 =
+ * that many, -1 = one block per tile.  A launch-shape choice only: results
+ * do not depend on it. */
 typedef struct {
     int32_t nc[3];
     int32_t ncell;
     float inv[3];
     int32_t tiles_x;
     int32_t stage_cap;
+    int32_t sweep_blocks;
 } fpm_grid;
 
 /* Device-side status block (caller-allocated in device memory, 64 bytes,

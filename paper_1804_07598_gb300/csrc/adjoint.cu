@@ -127,7 +127,9 @@ __global__ void __launch_bounds__(kTileThreads, 4)
     uint32_t phase = 0;
     const uint32_t *__restrict__ words = lv.words;
     const uint32_t ntodo = *lv.count;
-    for (uint32_t k = next_ticket(sched, &s_k); k < ntodo; k = next_ticket(sched, &s_k)) {
+    uint32_t ahead = 0;
+    for (uint32_t k = blockIdx.x; k < ntodo; k = ticket_next(ahead, &s_k)) {
+        ahead = ticket_ahead(sched);
     T de = 0, ds = 0, ue = 0, us = 0;
     load_desc(lv.descs + lv.active[k], d);
     const bool in_smem = d.M <= stage_cap;
@@ -159,7 +161,6 @@ __global__ void __launch_bounds__(kTileThreads, 4)
         const T v[4] = {de, ds, ue, us};
         block_sum_store<4>(v, part + (size_t)k * 4);
     }
-    __syncthreads();  // everyone done with d and the staged tile
     }
     if (sched_finish(sched, &s_last) && out) {
         // a.dF/deps = 24 sum a.(g r); a.dF/dsigma = (24 eps/sigma) sum a.(gs r);
@@ -237,7 +238,7 @@ static fpm_status hvp_launch(const fpm_box &b, const fpm_grid &g, int n, const v
     int sc = stage_capacity(n, g, 2 * sizeof(V4<T>));
     const size_t smem = 2 * (size_t)sc * sizeof(V4<T>);
     smem_opt_in((const void *)k_lj_hvp_tiles<T>);
-    const int blocks = persistent_blocks((const void *)k_lj_hvp_tiles<T>, kTileThreads, smem, cfg.ntiles);
+    const int blocks = persistent_blocks((const void *)k_lj_hvp_tiles<T>, kTileThreads, smem, g, cfg.ntiles);
     k_lj_hvp_tiles<T><<<blocks, kTileThreads, smem, stream>>>(cfg, box, (const V4<T> *)pos, (const V4<T> *)a,
                                                               list_view(list, L), nn, L.ld, sc, P, scale, 24.0 * eps,
                                                               24.0 * eps / sigma, 4.0 * eps, adj_pos,

@@ -119,7 +119,9 @@ __global__ void __launch_bounds__(kTileThreads)
     uint32_t phase = 0;
     const uint32_t *__restrict__ words = lv.words;
     const uint32_t ntodo = *lv.count;
-    for (uint32_t k = next_ticket(sched, &s_k); k < ntodo; k = next_ticket(sched, &s_k)) {
+    uint32_t ahead = 0;
+    for (uint32_t k = blockIdx.x; k < ntodo; k = ticket_next(ahead, &s_k)) {
+        ahead = ticket_ahead(sched);
         load_desc(lv.descs + lv.active[k], d);
         const bool in_smem = d.M <= stage_cap;
         if (!in_smem) note_spill(status);
@@ -153,7 +155,6 @@ __global__ void __launch_bounds__(kTileThreads)
             const T v[3] = {(T)0.5 * usum, (T)0.5 * wsum, (T)0.5 * (T)npsum};
             block_sum_store<3>(v, part + (size_t)k * 3);
         }
-        __syncthreads();  // everyone done with d and the staged tile
     }
     if (sched_finish(sched, &s_last) && out) {
         __threadfence();
@@ -177,7 +178,7 @@ static fpm_status lj_launch(const fpm_box &b, const fpm_grid &g, int n, const vo
     const int sc = stage_capacity(n, g, sizeof(V4<T>));
     const size_t smem = (size_t)sc * sizeof(V4<T>);
     smem_opt_in((const void *)k_lj_tiles<T>);
-    const int blocks = persistent_blocks((const void *)k_lj_tiles<T>, kTileThreads, smem, cfg.ntiles);
+    const int blocks = persistent_blocks((const void *)k_lj_tiles<T>, kTileThreads, smem, g, cfg.ntiles);
     k_lj_tiles<T><<<blocks, kTileThreads, smem, stream>>>(cfg, box, (const V4<T> *)pos, list_view(list, L), nn, L.ld,
                                                           sc, P, (V4<T> *)force, Sched{r.work, r.done}, r.part,
                                                           d_energy, status);

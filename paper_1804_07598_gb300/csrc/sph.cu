@@ -152,7 +152,9 @@ __global__ void __launch_bounds__(kTileThreads, 4)
     const uint32_t *__restrict__ words = lv.words;
     float amax = 0.0f, mumax = 0.0f;
     const uint32_t ntodo = *lv.count;
-    for (uint32_t k = next_ticket(sched, &s_k); k < ntodo; k = next_ticket(sched, &s_k)) {
+    uint32_t ahead = 0;
+    for (uint32_t k = blockIdx.x; k < ntodo; k = ticket_next(ahead, &s_k)) {
+        ahead = ticket_ahead(sched);
     load_desc(lv.descs + lv.active[k], d);
     const bool in_smem = d.M <= stage_cap;
     if (!in_smem) note_spill(status);
@@ -192,7 +194,6 @@ __global__ void __launch_bounds__(kTileThreads, 4)
         a.w = dr;
         acc[i] = a;
     }
-    __syncthreads();  // everyone done with d and the staged tile
     }
     // one atomic max per warp on the (non-negative) float bits
     const unsigned ma = __reduce_max_sync(kFull, __float_as_uint(amax));
@@ -366,7 +367,7 @@ extern "C" fpm_status fpm_sph_forces(const fpm_box *box, const fpm_grid *grid, i
     const int sc = stage_capacity(n, *grid, 2 * sizeof(float4));
     const size_t smem = 2 * (size_t)sc * sizeof(float4);
     smem_opt_in((const void *)k_sph_tiles);
-    const int blocks = persistent_blocks((const void *)k_sph_tiles, kTileThreads, smem, cfg.ntiles);
+    const int blocks = persistent_blocks((const void *)k_sph_tiles, kTileThreads, smem, *grid, cfg.ntiles);
     k_sph_tiles<<<blocks, kTileThreads, smem, (cudaStream_t)stream>>>(
         cfg, make_box<float>(*box), (const float4 *)pos, (const float4 *)vr, list_view(list, L), nn, L.ld, sc,
         make_sph(*params), (float4 *)acc, d_dtcons, Sched{r.work, r.done}, d_status);

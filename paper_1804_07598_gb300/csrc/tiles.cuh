@@ -482,11 +482,22 @@ struct Sched {
     unsigned *done;  // blocks finished
 };
 
-// The next ticket of this block (all threads get the same value).  Every
-// thread must be done with the previous tile's shared data before the call.
-__device__ __forceinline__ uint32_t next_ticket(const Sched &sc, uint32_t *s_k)
+// Tile tickets.  A block's first ticket is its own index; each later one is
+// requested from the shared counter by thread 0 at the start of a tile
+// (ticket_ahead) and handed to the whole block at the tile's end
+// (ticket_next), so the atomic's latency hides behind the tile's work.
+// Tickets from gridDim.x on are handed out once each, in counter order.
+__device__ __forceinline__ uint32_t ticket_ahead(const Sched &sc)
 {
-    if (threadIdx.x == 0) *s_k = atomicAdd(sc.work, 1u);
+    return threadIdx.x == 0 ? gridDim.x + atomicAdd(sc.work, 1u) : 0u;
+}
+
+// The block's next ticket (all threads get the same value).  It begins with
+// a barrier, so the tile's shared data may be reused after it.
+__device__ __forceinline__ uint32_t ticket_next(uint32_t ahead, uint32_t *s_k)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) *s_k = ahead;
     __syncthreads();
     return *s_k;
 }
@@ -565,16 +576,23 @@ __device__ __forceinline__ void sum_tile_partials(const double *part, uint32_t c
     }
 }
 
-// Grid of a persistent tile sweep: as many blocks as fit on the GPU at once
-// (never more than there are tiles).  Each block walks the non-empty tiles
-// k = blockIdx.x, blockIdx.x + gridDim.x, ... of the list's active array.
-inline int persistent_blocks(const void *kernel, int threads, size_t smem, int ntiles)
+// Grid of a tile sweep (tiles are taken by ticket, see ticket_ahead):
+// g.sweep_blocks > 0 blocks, or one per tile (-1), or by default as many as
+// fit on the GPU at once; never more than there are tiles.
+inline int persistent_blocks(const void *kernel, int threads, size_t smem, const fpm_grid &g, int ntiles)
 {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
-    long long b = (long long)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    long long b;
+    if (g.sweep_blocks > 0) {
+        b = g.sweep_blocks;
+    } else if (g.sweep_blocks < 0) {
+        b = ntiles;
+    } else {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+        b = (long long)(sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    }
     if (b > ntiles) b = ntiles;
     return b < 1 ? 1 : (int)b;
 }

@@ -131,7 +131,9 @@ __global__ void __launch_bounds__(kTileThreads)
     uint32_t phase = 0;
     uint32_t maxc = 0;
     const uint32_t ntodo = *count;
-    for (uint32_t k = next_ticket(sched, &s_k); k < ntodo; k = next_ticket(sched, &s_k)) {
+    uint32_t ahead = 0;
+    for (uint32_t k = blockIdx.x; k < ntodo; k = ticket_next(ahead, &s_k)) {
+        ahead = ticket_ahead(sched);
         tile_geometry(cfg, (int)active[k], cs, g, d);
         if (d.M > kMaxStaged) {  // 16-bit entries cannot address this neighbourhood
             for (uint32_t i = d.h0 + threadIdx.x; i < d.h1; i += blockDim.x) nn[i] = 0u;
@@ -168,7 +170,6 @@ __global__ void __launch_bounds__(kTileThreads)
             if (c > (uint32_t)cap) latch_flag(st, FPM_FLAG_CAPACITY);
             maxc = c > maxc ? c : maxc;
         }
-        __syncthreads();  // everyone done with g, d and the staged tile
     }
     const uint32_t m = __reduce_max_sync(kFull, maxc);
     if ((threadIdx.x & 31) == 0 && st && m > 0) atomicMax(&st->max_nn, m);
@@ -239,7 +240,7 @@ static fpm_status verlet_launch(const fpm_box &b, const fpm_grid &g, int n, cons
         k_tile_compact<<<1, 1024, 0, stream>>>(descs, cfg.ntiles, active, count, gate);
         const size_t smem = (size_t)sc * sizeof(V4<T>);
         smem_opt_in((const void *)k_verlet_scan<T>);
-        const int blocks = persistent_blocks((const void *)k_verlet_scan<T>, kTileThreads, smem, cfg.ntiles);
+        const int blocks = persistent_blocks((const void *)k_verlet_scan<T>, kTileThreads, smem, g, cfg.ntiles);
         k_verlet_scan<T><<<blocks, kTileThreads, smem, stream>>>(cfg, box, (const V4<T> *)pos, cs, rl2, cap, L.ld, sc,
                                                                  active, count,
                                                                  Sched{(unsigned *)(lb + 16), (unsigned *)(lb + 20)},

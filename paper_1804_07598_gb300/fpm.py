@@ -38,7 +38,7 @@ class fpm_box(_c.Structure):
 
 class fpm_grid(_c.Structure):
     _fields_ = [("nc", _c.c_int32 * 3), ("ncell", _c.c_int32), ("inv", _c.c_float * 3), ("tiles_x", _c.c_int32),
-                ("stage_cap", _c.c_int32)]
+                ("stage_cap", _c.c_int32), ("sweep_blocks", _c.c_int32)]
 
     @property
     def shape(self):
