@@ -31,6 +31,10 @@ sys.path.insert(0, ROOT)
 METRIC = "LJ steps/s & pair-interactions/s at 1M atoms (FP32 vs FP64) ; adjoint/forward cost"
 UNIT = "steps/s"
 WORKLOAD = "lj_1m"
+# FP32 arithmetic of the LJ pair term per Verlet-list entry, an FMA counted as
+# two: separation 3, r^2 5, 1/r^2 1, s2 1, s6 2, s12 1, a = 2 s12 - s6 2,
+# a/r^2 1, force accumulation 6, virial 1, energy 2.
+FLOP_PER_SLOT = 25
 FALLBACK_HBM_GBS = 6800.0
 
 # DRAM traffic per launch of the force kernel from one ncu capture, valid only
@@ -55,6 +59,7 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--sph-steps", type=int, default=500)
+    ap.add_argument("--batch-steps", type=int, default=300)
     return ap.parse_args()
 
 
@@ -94,15 +99,18 @@ def max_over_ranks(x: float, ws: int) -> float:
 # ---------------------------------------------------------------- clocks ---
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms while active."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while the
+    sampler is open; summary() keeps the samples taken inside the timed
+    windows marked with window()."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
         self.f = None
+        self.windows = []
 
     def __enter__(self):
         try:
@@ -122,19 +130,41 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
+    class _Window:
+        def __init__(self, owner):
+            self.owner = owner
+
+        def __enter__(self):
+            self.t0 = time.time()
+
+        def __exit__(self, *a):
+            self.owner.windows.append((self.t0, time.time()))
+
+    def window(self):
+        """Context manager marking a timed region (host wall time)."""
+        return ClockSampler._Window(self)
+
     def summary(self):
         if self.proc is None or self.f is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        import datetime
         self.f.flush()
         rows = []
         with open(self.f.name) as fh:
             for line in fh:
                 p = [x.strip() for x in line.split(",")]
-                if len(p) >= 9:
-                    rows.append(p)
+                if len(p) < 10:
+                    continue
+                try:
+                    t = datetime.datetime.strptime(p[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                except ValueError:
+                    continue
+                # a sample describes the 200 ms before it: keep it if that overlaps a window
+                if any(t >= a and t - 0.2 <= b for a, b in self.windows):
+                    rows.append(p[1:])
         os.unlink(self.f.name)
         if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -240,7 +270,8 @@ def run_ours(args, ws, rank, local):
     st0 = s.device_status().nrebuild
 
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
+    clk = ClockSampler(local).__enter__()
+    with clk.window():
         barrier(ws)
         torch.cuda.synchronize()
         e0.record()
@@ -273,6 +304,11 @@ def run_ours(args, ws, rank, local):
     alg_bytes = 2 * nn_sum + 4 * s.n + 16 * s.n + 16 * s.n
     peak, peak_kind = hbm_peak()
     achieved = alg_bytes / (force_us * 1e-6) / 1e9
+    # FP32 arithmetic of one sweep: FLOP_PER_SLOT per list entry (every entry
+    # is evaluated and masked at rc); peak = SMs x 128 FP32 lanes x 2 x clock
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    alg_flop = FLOP_PER_SLOT * nn_sum
+    tflops = alg_flop / (force_us * 1e-6) / 1e12
 
     # FP64 path, same workload
     s64 = LJSystem(pos, vel, L, eps=wl.eps, sigma=wl.sigma, rc=wl.rc, skin=wl.skin, dt=wl.dt, precision="f64")
@@ -346,11 +382,12 @@ def run_ours(args, ws, rank, local):
         for _ in range(3):
             gs.replay()
         torch.cuda.synchronize()
-        e0.record()
-        for _ in range(args.sph_steps):
-            gs.replay()
-        e1.record()
-        torch.cuda.synchronize()
+        with clk.window():
+            e0.record()
+            for _ in range(args.sph_steps):
+                gs.replay()
+            e1.record()
+            torch.cuda.synchronize()
         ss.check_status()
         sms = e0.elapsed_time(e1)
         nlist = int(ss.nn[: ss.n].sum().item())
@@ -360,6 +397,50 @@ def run_ours(args, ws, rank, local):
                "particle_steps_per_s": ss.n * args.sph_steps / (sms / 1e3), "list_slots": nlist,
                "simulated_time_s": float(ss.dt.cpu().numpy()[0]) * args.sph_steps}
         del ss, gs
+
+    # batched ensemble: 512 periodic replicas of 256..16384 particles, one
+    # launch per operation, replayed from a CUDA graph, launch shapes autotuned
+    batch = None
+    if args.batch_steps > 0:
+        from paper_1804_07598_gb300 import autotune
+        from paper_1804_07598_gb300.batch import LJBatch
+        reps, N, rho, T = inputs.ensemble()
+        bb = LJBatch(reps)
+        tuned = autotune.tune_batch(bb)
+        bb.step(3)
+        gb = bb.capture(steps_per_graph=1)
+        for _ in range(3):
+            gb.replay()
+        torch.cuda.synchronize()
+        nr0 = fpm.read_status(bb.status).nrebuild
+        with clk.window():
+            e0.record()
+            for _ in range(args.batch_steps):
+                gb.replay()
+            e1.record()
+            torch.cuda.synchronize()
+        bst = bb.check_status()
+        bms = e0.elapsed_time(e1)
+        bpairs = float(bb.energies()[:, 2].sum())
+        bslots = int(bb.nn[: bb.n].sum().item())
+        bps = args.batch_steps / (bms / 1e3)
+        batch = {"workload": f"{bb.R} periodic LJ replicas, N log-uniform in [256, 16384] (seeded, {bb.n} total), "
+                             f"rho U[0.70, 0.95], T* U[0.6, 1.5], rc 2.5, skin 0.3, dt 0.005, FP32",
+                 "steps_per_s": bps, "ms_per_step": bms / args.batch_steps,
+                 "replica_steps_per_s": bb.R * bps, "particle_steps_per_s": bb.n * bps,
+                 "pair_interactions_per_s": bpairs * bps, "list_slots": bslots,
+                 "replica_rebuilds_per_step": (bst.nrebuild - nr0) / args.batch_steps,
+                 "launches_per_step": 7,
+                 "particle_steps_over_fp64_single": bb.n * bps / (fp64_steps_per_s * s.n),
+                 "autotune": {"config": tuned["config"], "ms_per_step": tuned["ms"],
+                              "candidates": len(tuned.get("trials", [])), "seconds": tuned["seconds"],
+                              "cached": tuned["cached"]}}
+        del bb, gb
+
+    clk.__exit__()
+    clocks = clk.summary()
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
@@ -381,16 +462,20 @@ def run_ours(args, ws, rank, local):
         "rebuilds_in_timed_region": int(rebuilds),
         "fp64_steps_per_s": fp64_steps_per_s * ws,
         "fp32_over_fp64": steps_per_s / (fp64_steps_per_s * ws),
-        "roofline": {"kernel": "k_lj_forces<float>", "bound": "hbm", "achieved": achieved, "peak": peak,
-                     "peak_kind": f"{peak_kind} (burst, kernel timed alone)", "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic_for("lj.cu"),
-                     "alg_bytes_per_launch": alg_bytes, "launch_us": force_us},
+        "roofline": {"kernel": "k_lj_tiles<float>", "bound": "alu", "achieved": tflops, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": tflops / fp32_peak, "traffic": traffic_for("lj.cu"),
+                     "peak_kind": f"FP32 CUDA cores: {n_sm} SMs x 128 lanes x 2 FLOP x {sm_mhz:.0f} MHz (median "
+                                  f"SM clock sampled under load)",
+                     "alg_flop_per_launch": alg_flop, "flop_per_list_slot": FLOP_PER_SLOT, "launch_us": force_us,
+                     "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                             "peak_kind": f"{peak_kind} (burst)", "alg_bytes_per_launch": alg_bytes}},
         "e2e": {"value": ws * args.e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "adjoint": adj,
         "sph": sph,
+        "batch": batch,
         "gpu_launches": per_step_launches * args.steps,
-        "clocks": clk.summary(),
+        "clocks": clocks,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

@@ -403,6 +403,107 @@ fpm_status fpm_vv_adjoint(int32_t n, fpm_prec prec, const uint32_t *perm, double
 fpm_status fpm_adjoint_seed(int32_t n, fpm_prec prec, const void *force, double *xbar, double *vbar,
                             void *a_out, fpm_stream stream);
 
+/* ------------------------------------------------------------------ */
+/* Batched replicas: R independent periodic LJ systems of uneven size    */
+/* advanced together (an ensemble of the MD system of Sec. 4.1; the      */
+/* paper runs one system per process), single precision                  */
+/* ------------------------------------------------------------------ */
+
+/* One replica of a batch.  Its particles are [p0, p0 + n) of the batch's
+ * concatenated arrays; its cells are entries [c0, c0 + grid.ncell] of the
+ * batch's cell_start (whose values are indices into the concatenated
+ * arrays); its tiles are [t0, t0 + grid.tiles_x * grid.nc[1] * grid.nc[2])
+ * of the batch's Verlet-list object.  Written by fpm_batch_plan; the calls
+ * below read a DEVICE copy of the array (d_reps), which the caller makes. */
+typedef struct {
+    fpm_box box;
+    fpm_grid grid;
+    int32_t p0, n;
+    int32_t c0, t0;
+} fpm_replica;
+
+/* Sizes of a batch (host struct, passed by pointer to every batched call).
+ * stage_cap and sweep_blocks act as in fpm_grid, for every replica; the
+ * plan sets stage_cap to an estimate and sweep_blocks to 0, and the caller
+ * may change both between calls (launch-shape choices: results do not
+ * depend on them, except that a tile whose neighbourhood exceeds stage_cap
+ * reads it from global memory and is counted in d_status->spilled). */
+typedef struct {
+    int32_t R;
+    int32_t n_total;
+    int32_t ncell_total;   /* cell_start has ncell_total + 1 entries */
+    int32_t ntiles_total;
+    int32_t max_n;
+    int32_t max_ncell;
+    int32_t stage_cap;
+    int32_t sweep_blocks;
+} fpm_batch;
+
+/* Plans a batch of R replicas (host only): replica r has counts[r]
+ * particles in boxes[r] (every dimension periodic, L > 2 r_cell (1 + 2^-10)),
+ * a cell grid made as by fpm_grid_make(boxes[r], r_cell, counts[r]) but with
+ * tile widths aimed at tile_target particles per tile (0: 170), and the
+ * offsets p0, c0, t0 in replica order.  reps : [R] host array, written.
+ * Limits: R <= 65535, max_ncell <= 32768 cells per replica. */
+fpm_status fpm_batch_plan(int32_t R, const fpm_box *boxes, const int32_t *counts, double r_cell,
+                          int32_t tile_target, fpm_replica *reps, fpm_batch *batch);
+
+/* v += dt/2 F; x += dt v (no wrap) for all particles of the batch, then the
+ * rebuild test of each replica: d_rep_flag[r] |= 1 when a particle of
+ * replica r moved by more than skin/2 since pos_ref (d2 > (float)(skin^2/4),
+ * d = x - x_ref per component).  d_rep_flag : [R] uint32. */
+fpm_status fpm_batch_drift_check(const fpm_batch *batch, const fpm_replica *d_reps, double dt, void *pos,
+                                 void *vel, const void *force, const void *pos_ref, double skin,
+                                 uint32_t *d_rep_flag, fpm_stream stream);
+
+/* Bytes of device workspace of fpm_batch_celllist_build. */
+fpm_status fpm_batch_celllist_workspace(const fpm_batch *batch, size_t *bytes);
+
+/* Cell lists of the replicas whose d_rep_flag is set (all replicas when
+ * d_rep_flag is NULL), each as fpm_celllist_build on its own box and grid:
+ * wrap, cell index, the stable counting sort by (cell, index), and the
+ * in-place reorder of pos, vel (float4 [n_total]) and ids (uint32, may be
+ * NULL), within the replica's range.  cell_start : [ncell_total + 1];
+ * perm[k] = the index before the reorder of the particle now at k (entries
+ * of replicas not rebuilt are untouched).  One block per replica.  A
+ * particle outside its box (a non-finite coordinate) latches
+ * FPM_FLAG_DOMAIN. */
+fpm_status fpm_batch_celllist_build(const fpm_batch *batch, const fpm_replica *d_reps, void *pos, void *vel,
+                                    uint32_t *ids, uint32_t *cell_start, uint32_t *perm, void *workspace,
+                                    size_t workspace_bytes, const uint32_t *d_rep_flag,
+                                    fpm_dev_status *d_status, fpm_stream stream);
+
+/* Bytes of the batch's Verlet-list object for capacity cap (256-B aligned). */
+fpm_status fpm_batch_list_bytes(const fpm_batch *batch, int32_t cap, size_t *bytes);
+
+/* Verlet lists (as fpm_verlet_build, per replica) of the replicas whose
+ * d_rep_flag is set (all when NULL), then clears every d_rep_flag and adds
+ * the number of rebuilt replicas to d_status->nrebuild.  pos_ref receives
+ * the positions of the rebuilt replicas.  The list object must have been
+ * built for all replicas once (d_rep_flag NULL) before a gated build. */
+fpm_status fpm_batch_verlet_build(const fpm_batch *batch, const fpm_replica *d_reps, const void *pos,
+                                  const uint32_t *cell_start, double r_list, int32_t cap, void *list,
+                                  size_t list_bytes, uint32_t *nn, void *pos_ref, uint32_t *d_rep_flag,
+                                  fpm_dev_status *d_status, fpm_stream stream);
+
+/* As fpm_verlet_decode, for the batch's list (indices into the concatenated
+ * arrays; out : [cap * fpm_nbr_ld(n_total)]). */
+fpm_status fpm_batch_verlet_decode(const fpm_batch *batch, int32_t cap, const void *list, const uint32_t *nn,
+                                   uint32_t *out, fpm_stream stream);
+
+/* Bytes of workspace of fpm_batch_lj_forces (zero-filled once before first
+ * use; every call leaves its counters at zero again). */
+fpm_status fpm_batch_workspace(const fpm_batch *batch, size_t *bytes);
+
+/* LJ forces of every replica (as fpm_lj_forces on its own box, single
+ * precision) in one persistent launch over all tiles of the batch.
+ * d_energy : [R][3] double (U, W, pairs of each replica, FP64, fixed order)
+ * or NULL. */
+fpm_status fpm_batch_lj_forces(const fpm_batch *batch, const fpm_replica *d_reps, const void *pos,
+                               const void *list, const uint32_t *nn, int32_t cap, double eps, double sigma,
+                               double rc, void *force, double *d_energy, void *workspace,
+                               size_t workspace_bytes, fpm_dev_status *d_status, fpm_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,712 @@
+// batch.cu -- R independent periodic Lennard-Jones replicas of uneven size
+// advanced together: the MD system of Sec. 4.1 (cell lists and Verlet lists
+// of Sec. 2, the pair force of Listing 4.1, velocity Verlet) run as an
+// ensemble.  The paper runs one system per process; here every operation is
+// one launch over the whole batch.
+//
+// Layout.  Replica r owns particles [p0, p0+n) of the concatenated arrays,
+// cells [c0, c0+ncell) of one concatenated cell_start (whose values index the
+// concatenated arrays), and tiles [t0, t0+ntiles) of one Verlet-list object.
+// Tiles, staging and the pair code are those of the single-system path
+// (tiles.cuh, lj_pair.cuh); a block looks up the replica of its tile by
+// binary search over t0 and takes that replica's box and grid.
+//
+// Rebuilds are per replica: the drift kernel flags a replica when one of its
+// particles moved more than skin/2, and only flagged replicas are re-binned
+// (one block per replica: the counting sort runs in shared memory) and get
+// new tile descriptors and lists (a persistent scan over their tiles).
+#include <algorithm>
+#include <cmath>
+
+#include "lj_pair.cuh"
+#include "reduce.cuh"
+
+namespace fpm {
+
+constexpr int kBatchCellThreads = 512;
+constexpr int kBatchMaxCells = 32768;   // cells of one replica (shared-memory counters)
+constexpr int kBatchMaxReplicas = 65535;
+constexpr int kBatchDescBlocks = 2048;  // grid of the descriptor kernel (grid-stride over tiles)
+
+__host__ __device__ inline int rep_ntiles(const fpm_grid &g) { return g.tiles_x * g.nc[1] * g.nc[2]; }
+
+// The replica holding particle i / tile t: the last r whose p0 / t0 is <= i.
+__device__ __forceinline__ int replica_of_particle(const fpm_replica *__restrict__ reps, int R, uint32_t i)
+{
+    int lo = 0, hi = R - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((uint32_t)__ldg(&reps[mid].p0) <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int replica_of_tile(const fpm_replica *__restrict__ reps, int R, uint32_t t)
+{
+    int lo = 0, hi = R - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((uint32_t)__ldg(&reps[mid].t0) <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---- drift + per-replica rebuild test ---------------------------------------
+
+__global__ void __launch_bounds__(256)
+    k_bdrift_check(int n, int R, const fpm_replica *__restrict__ reps, float hdt, float dt, float4 *__restrict__ pos,
+                   float4 *__restrict__ vel, const float4 *__restrict__ force, const float4 *__restrict__ ref,
+                   float th, uint32_t *__restrict__ flag)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool over = false;
+    if (i < n) {
+        float4 x = pos[i], v = vel[i];
+        const float4 f = force[i];
+        v.x += hdt * f.x;
+        v.y += hdt * f.y;
+        v.z += hdt * f.z;
+        x.x += dt * v.x;
+        x.y += dt * v.y;
+        x.z += dt * v.z;
+        pos[i] = x;
+        vel[i] = v;
+        const float4 r0 = ref[i];
+        const float dx = x.x - r0.x, dy = x.y - r0.y, dz = x.z - r0.z;
+        over = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx))) > th;
+    }
+    const unsigned m = __ballot_sync(kFull, over);
+    if (!over) return;
+    const int r = replica_of_particle(reps, R, (uint32_t)i);
+    const unsigned peers = __match_any_sync(m, r);
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicOr(&flag[r], 1u);
+}
+
+// ---- cell lists, one block per flagged replica ------------------------------
+
+// In-place exclusive scan of a[0..m) in shared memory by the whole block
+// (blockDim a multiple of 32); a[m] receives the total.
+__device__ void smem_exclusive_scan(uint32_t *a, int m, uint32_t *wsum)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t carry = 0;
+    for (int base = 0; base < m; base += blockDim.x) {
+        const int k = base + threadIdx.x;
+        const uint32_t v = k < m ? a[k] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = lane < nw ? wsum[lane] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, w, o);
+                if (lane >= o) w += y;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        if (k < m) a[k] = carry + x - v + (warp > 0 ? wsum[warp - 1] : 0u);
+        carry += wsum[nw - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) a[m] = carry;
+    __syncthreads();
+}
+
+// Ascending bitonic sort of one value per lane across a full warp.
+__device__ __forceinline__ uint32_t bwarp_sort32(uint32_t v)
+{
+    const unsigned lane = threadIdx.x & 31;
+#pragma unroll
+    for (unsigned k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (unsigned j = k >> 1; j > 0; j >>= 1) {
+            const uint32_t o = __shfl_xor_sync(kFull, v, j);
+            const bool up = (lane & k) == 0;
+            const bool low = (lane & j) == 0;
+            v = (low == up) ? min(v, o) : max(v, o);
+        }
+    }
+    return v;
+}
+
+struct BCellWs {
+    float4 *spos, *svel;
+    uint32_t *sid, *cell, *rank, *tmp;
+};
+
+// Per replica: wrap and bin into shared-memory counters (the atomic gives an
+// arrival rank), exclusive scan -> cell_start, scatter of indices by (cell,
+// rank), then one warp per cell sorts its slice by particle index (the
+// stable order) and gathers pos / vel / ids into place.
+__global__ void __launch_bounds__(kBatchCellThreads)
+    k_bcell(int R, const fpm_replica *__restrict__ reps, float4 *__restrict__ pos, float4 *__restrict__ vel,
+            uint32_t *__restrict__ ids, uint32_t *__restrict__ cell_start, uint32_t *__restrict__ perm, BCellWs w,
+            const uint32_t *__restrict__ flag, fpm_dev_status *st)
+{
+    extern __shared__ uint32_t cnt[];  // [ncell + 1]
+    __shared__ uint32_t wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int r = blockIdx.x; r < R; r += gridDim.x) {
+        if (flag && flag[r] == 0u) continue;
+        const fpm_replica rp = reps[r];
+        const BoxT<float> box = make_box<float>(rp.box);
+        const GridD g = make_grid(rp.grid);
+        const int ncell = rp.grid.ncell;
+        const uint32_t p0 = (uint32_t)rp.p0, n = (uint32_t)rp.n;
+        for (int c = threadIdx.x; c <= ncell; c += blockDim.x) cnt[c] = 0u;
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < n; k += blockDim.x) {
+            const uint32_t i = p0 + k;
+            float4 p = pos[i];
+            p.x = wrap1(p.x, box.L[0]);
+            p.y = wrap1(p.y, box.L[1]);
+            p.z = wrap1(p.z, box.L[2]);
+            bool bad = false;
+            int cc[3];
+            cell_of(p, box, g, cc, bad);
+            if (bad) {
+                latch_flag(st, FPM_FLAG_DOMAIN);
+                if (st) atomicExch(&st->bad_index, i);
+            }
+            const uint32_t c = linear_cell(cc[0], cc[1], cc[2], g);
+            w.spos[i] = p;
+            if (vel) w.svel[i] = vel[i];
+            w.sid[i] = ids ? ids[i] : i;
+            w.cell[i] = c;
+            w.rank[i] = atomicAdd(&cnt[c], 1u);
+        }
+        __syncthreads();
+        smem_exclusive_scan(cnt, ncell, wsum);
+        for (int c = threadIdx.x; c <= ncell; c += blockDim.x) cell_start[rp.c0 + c] = p0 + cnt[c];
+        for (uint32_t k = threadIdx.x; k < n; k += blockDim.x) {
+            const uint32_t i = p0 + k;
+            w.tmp[p0 + cnt[w.cell[i]] + w.rank[i]] = i;
+        }
+        __syncthreads();
+        for (int c = warp; c < ncell; c += nw) {
+            const uint32_t s = p0 + cnt[c], e = p0 + cnt[c + 1];
+            const uint32_t m = e - s;
+            if (m == 0) continue;
+            if (m <= 32) {
+                uint32_t v = (uint32_t)lane < m ? w.tmp[s + lane] : 0xffffffffu;
+                v = bwarp_sort32(v);
+                if ((uint32_t)lane < m) {
+                    const uint32_t slot = s + lane;
+                    pos[slot] = w.spos[v];
+                    if (vel) vel[slot] = w.svel[v];
+                    if (ids) ids[slot] = w.sid[v];
+                    if (perm) perm[slot] = v;
+                }
+                continue;
+            }
+            // larger cells: rank of each element = number of smaller indices
+            for (uint32_t e0 = 0; e0 < m; e0 += 32) {
+                const bool mine = e0 + lane < m;
+                const uint32_t v = mine ? w.tmp[s + e0 + lane] : 0xffffffffu;
+                uint32_t rk = 0;
+                for (uint32_t m0 = 0; m0 < m; m0 += 32) {
+                    const uint32_t u = (m0 + lane < m) ? w.tmp[s + m0 + lane] : 0xffffffffu;
+#pragma unroll 8
+                    for (int t = 0; t < 32; ++t) rk += (__shfl_sync(kFull, u, t) < v) ? 1u : 0u;
+                }
+                if (mine) {
+                    const uint32_t slot = s + rk;
+                    pos[slot] = w.spos[v];
+                    if (vel) vel[slot] = w.svel[v];
+                    if (ids) ids[slot] = w.sid[v];
+                    if (perm) perm[slot] = v;
+                }
+            }
+        }
+        __syncthreads();  // cnt is reused by the next replica of this block
+    }
+}
+
+// ---- Verlet lists of the flagged replicas -----------------------------------
+
+// Descriptors of every tile of a flagged replica (grid-stride over tiles).
+__global__ void __launch_bounds__(128)
+    k_btile_desc(int R, int ntiles, const fpm_replica *__restrict__ reps, const uint32_t *__restrict__ cs,
+                 TileDesc *__restrict__ descs, const uint32_t *__restrict__ flag, fpm_dev_status *st)
+{
+    __shared__ TileGeom g;
+    __shared__ TileDesc d;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int r = replica_of_tile(reps, R, (uint32_t)tile);
+        if (flag && flag[r] == 0u) continue;
+        const fpm_replica rp = reps[r];
+        const TileCfg cfg = make_tile_cfg(rp.box, rp.grid);
+        tile_geometry(cfg, tile - rp.t0, cs + rp.c0, g, d);
+        const int nwd = (int)(sizeof(TileDesc) / 4);
+        uint32_t *o = (uint32_t *)(descs + tile);
+        const uint32_t *s = (const uint32_t *)&d;
+        for (int k = threadIdx.x; k < nwd; k += blockDim.x) o[k] = s[k];
+        if (threadIdx.x == 0 && st && d.h1 > d.h0) atomicMax(&st->max_staged, (uint32_t)d.M);
+        __syncthreads();  // d and g are rewritten for the next tile
+    }
+}
+
+// One block: the work list of the scan (every tile of every flagged replica,
+// in replica order), the scan's scheduling counters, and the flags cleared.
+__global__ void __launch_bounds__(1024)
+    k_bwork(int R, const fpm_replica *__restrict__ reps, uint32_t *__restrict__ flag, uint32_t *__restrict__ work,
+            uint32_t *__restrict__ header, fpm_dev_status *st)
+{
+    __shared__ uint32_t wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t carry = 0, nflag = 0;
+    for (int base = 0; base < R; base += blockDim.x) {
+        const int r = base + threadIdx.x;
+        bool f = false;
+        uint32_t nt = 0, t0 = 0;
+        if (r < R) {
+            f = !flag || flag[r] != 0u;
+            if (flag) flag[r] = 0u;
+            if (f) {
+                nt = (uint32_t)rep_ntiles(reps[r].grid);
+                t0 = (uint32_t)reps[r].t0;
+            }
+        }
+        nflag += (uint32_t)__syncthreads_count(f);
+        uint32_t x = nt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t v = lane < nw ? wsum[lane] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(kFull, v, o);
+                if (lane >= o) v += y;
+            }
+            wsum[lane] = v;
+        }
+        __syncthreads();
+        const uint32_t off = carry + x - nt + (warp > 0 ? wsum[warp - 1] : 0u);
+        for (uint32_t j = 0; j < nt; ++j) work[off + j] = t0 + j;
+        carry += wsum[nw - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        header[0] = carry;
+        header[4] = 0u;  // the scan's ticket and completion counters (list header bytes 16..23)
+        header[5] = 0u;
+        if (st) st->nrebuild += nflag;
+    }
+}
+
+__global__ void __launch_bounds__(kTileThreads)
+    k_bverlet_scan(int R, const fpm_replica *__restrict__ reps, const float4 *__restrict__ pos,
+                   const uint32_t *__restrict__ cs, float rl2, int cap, int64_t ld, int stage_cap,
+                   const uint32_t *__restrict__ work, const uint32_t *__restrict__ count, Sched sched,
+                   uint32_t *__restrict__ words, uint32_t *__restrict__ nn, float4 *__restrict__ pos_ref,
+                   fpm_dev_status *st)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float4 *sp = (float4 *)smem_raw;
+    __shared__ TileGeom g;
+    __shared__ TileDesc d;
+    __shared__ TileCfg s_cfg;
+    __shared__ BoxT<float> s_box;
+    __shared__ int s_tile, s_c0;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t s_k;
+    __shared__ bool s_last;
+    stage_init(&bar);
+    uint32_t phase = 0, maxc = 0, ahead = 0;
+    const uint32_t ntodo = *count;
+    for (uint32_t k = blockIdx.x; k < ntodo; k = ticket_next(ahead, &s_k)) {
+        ahead = ticket_ahead(sched);
+        if (threadIdx.x == 0) {
+            const uint32_t tile = work[k];
+            const int r = replica_of_tile(reps, R, tile);
+            const fpm_replica rp = reps[r];
+            s_cfg = make_tile_cfg(rp.box, rp.grid);
+            s_box = make_box<float>(rp.box);
+            s_tile = (int)tile - rp.t0;
+            s_c0 = rp.c0;
+        }
+        __syncthreads();
+        const TileCfg cfg = s_cfg;
+        const BoxT<float> box = s_box;
+        const uint32_t c = verlet_tile<float>(cfg, box, s_tile, cs + s_c0, pos, rl2, cap, ld, stage_cap, g, d, sp,
+                                              &bar, phase, words, nn, pos_ref, st);
+        maxc = c > maxc ? c : maxc;
+    }
+    const uint32_t m = __reduce_max_sync(kFull, maxc);
+    if ((threadIdx.x & 31) == 0 && st && m > 0) atomicMax(&st->max_nn, m);
+    sched_finish(sched, &s_last);
+}
+
+// ---- LJ forces over every tile of the batch ---------------------------------
+
+__global__ void __launch_bounds__(kTileThreads)
+    k_blj_tiles(int R, int ntiles, const fpm_replica *__restrict__ reps, const float4 *__restrict__ pos,
+                ListView lv, const uint32_t *__restrict__ nn, int64_t ld, int stage_cap, LJParams<float> P,
+                float4 *__restrict__ force, Sched sched, double *part, uint32_t *rep_done, double *out,
+                fpm_dev_status *status)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float4 *sp = (float4 *)smem_raw;
+    __shared__ TileDesc d;
+    __shared__ TileCfg s_cfg;
+    __shared__ BoxT<float> s_box;
+    __shared__ int s_r, s_t0, s_nt;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t s_k;
+    __shared__ bool s_last, s_rep_last;
+    stage_init(&bar);
+    uint32_t phase = 0, ahead = 0;
+    const uint32_t *__restrict__ words = lv.words;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t k = blockIdx.x; k < (uint32_t)ntiles; k = ticket_next(ahead, &s_k)) {
+        ahead = ticket_ahead(sched);
+        if (threadIdx.x == 0) {
+            const int r = replica_of_tile(reps, R, k);
+            const fpm_replica rp = reps[r];
+            s_cfg = make_tile_cfg(rp.box, rp.grid);
+            s_box = make_box<float>(rp.box);
+            s_r = r;
+            s_t0 = rp.t0;
+            s_nt = rep_ntiles(rp.grid);
+        }
+        load_desc(lv.descs + k, d);  // ends with a barrier: s_* are visible
+        const TileCfg cfg = s_cfg;
+        const BoxT<float> box = s_box;
+        float usum = 0.0f, wsum = 0.0f;
+        uint32_t npsum = 0;
+        if (d.h1 > d.h0) {
+            const bool in_smem = d.M <= stage_cap;
+            if (!in_smem) note_spill(status);
+            const bool staged = in_smem ? stage_positions(d, box, pos, sp, &bar, phase, status) : true;
+            for (uint32_t i = d.h0 + threadIdx.x; staged && i < d.h1; i += blockDim.x) {
+                const float4 pi = pos[i];
+                const uint32_t m = nn[i];
+                float fx = 0.0f, fy = 0.0f, fz = 0.0f, u = 0.0f, w = 0.0f;
+                uint32_t np = 0;
+                if (in_smem) {
+                    if (d.slow)
+                        lj_sweep<float, false, true>(cfg, box, d, pos, sp, pi, m, words + i, ld, P, fx, fy, fz, u, w,
+                                                     np);
+                    else
+                        lj_sweep<float, true, true>(cfg, box, d, pos, sp, pi, m, words + i, ld, P, fx, fy, fz, u, w,
+                                                    np);
+                } else {
+                    lj_sweep<float, false, false>(cfg, box, d, pos, sp, pi, m, words + i, ld, P, fx, fy, fz, u, w,
+                                                  np);
+                }
+                float4 f;
+                f.x = P.eps24 * fx;
+                f.y = P.eps24 * fy;
+                f.z = P.eps24 * fz;
+                f.w = 0.5f * P.eps4 * u;
+                force[i] = f;
+                usum += P.eps4 * u;
+                wsum += P.eps24 * w;
+                npsum += np;
+            }
+        }
+        if (out) {
+            // this tile's U, W, pairs (halved: every pair is seen from both sides)
+            const float v[3] = {0.5f * usum, 0.5f * wsum, 0.5f * (float)npsum};
+            block_sum_store<3>(v, part + (size_t)k * 3);
+            if (threadIdx.x == 0) {
+                __threadfence();
+                const uint32_t t = atomicAdd(&rep_done[s_r], 1u);
+                s_rep_last = (t == (uint32_t)s_nt - 1u);
+            }
+            __syncthreads();
+            if (s_rep_last) {  // the replica's last tile: its sums, in tile order
+                __threadfence();
+                if (warp == 0) {
+                    double acc[3] = {0.0, 0.0, 0.0};
+                    for (int j = lane; j < s_nt; j += 32)
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) acc[q] += __ldcg(part + (size_t)(s_t0 + j) * 3 + q);
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        const double s = warp_sum(acc[q]);
+                        if (lane == 0) out[(size_t)s_r * 3 + q] = s;
+                    }
+                    if (lane == 0) rep_done[s_r] = 0u;
+                }
+            }
+        }
+    }
+    sched_finish(sched, &s_last);
+}
+
+// ---- host side -------------------------------------------------------------
+
+struct BatchWs {
+    Sched sched;
+    double *part;
+    uint32_t *rep_done;
+};
+
+static size_t bws_layout(const fpm_batch &b, size_t *off_done)
+{
+    size_t o = 256 + (size_t)b.ntiles_total * 3 * sizeof(double);
+    o = (o + 255) & ~(size_t)255;
+    if (off_done) *off_done = o;
+    return o + (size_t)b.R * sizeof(uint32_t);
+}
+
+static size_t bcell_layout(const fpm_batch &b, size_t off[6])
+{
+    const size_t n = (size_t)b.n_total;
+    size_t o = 0;
+    const size_t sz[6] = {n * 16, n * 16, n * 4, n * 4, n * 4, n * 4};
+    for (int k = 0; k < 6; ++k) {
+        off[k] = o;
+        o = (o + sz[k] + 255) & ~(size_t)255;
+    }
+    return o;
+}
+
+static fpm_status batch_ok(const fpm_batch *b, const fpm_replica *d_reps, const char *who)
+{
+    if (!b || !d_reps || b->R < 1 || b->R > kBatchMaxReplicas || b->n_total < 0 || b->ncell_total < b->R ||
+        b->ntiles_total < b->R || b->max_ncell < 1 || b->max_ncell > kBatchMaxCells)
+        return fpm_fail(FPM_ERR_INVALID, "%s: bad batch", who);
+    return FPM_OK;
+}
+
+static int batch_stage_cap(const fpm_batch &b)
+{
+    const int maxe = (int)((size_t)kSmemBudget / sizeof(float4)) / 32 * 32;
+    int e = b.stage_cap > 0 ? (b.stage_cap + 31) / 32 * 32 : maxe;
+    return e > maxe ? maxe : e;
+}
+
+}  // namespace fpm
+
+using namespace fpm;
+
+extern "C" fpm_status fpm_batch_plan(int32_t R, const fpm_box *boxes, const int32_t *counts, double r_cell,
+                                     int32_t tile_target, fpm_replica *reps, fpm_batch *batch)
+{
+    if (R < 1 || R > kBatchMaxReplicas || !boxes || !counts || !reps || !batch || !(r_cell > 0.0) ||
+        tile_target < 0)
+        return fpm_fail(FPM_ERR_INVALID, "fpm_batch_plan: bad argument");
+    const double target = tile_target > 0 ? (double)tile_target : (double)kTileTarget;
+    int64_t p0 = 0, c0 = 0, t0 = 0;
+    int max_n = 0, max_ncell = 0, stage = 0;
+    for (int r = 0; r < R; ++r) {
+        const fpm_box &b = boxes[r];
+        if (!b.periodic[0] || !b.periodic[1] || !b.periodic[2])
+            return fpm_fail(FPM_ERR_INVALID, "fpm_batch_plan: replica %d is not periodic in every dimension", r);
+        if (counts[r] < 0) return fpm_fail(FPM_ERR_INVALID, "fpm_batch_plan: counts[%d] < 0", r);
+        fpm_grid g{};
+        const fpm_status s = fpm_grid_make(&b, r_cell, counts[r], &g);
+        if (s != FPM_OK) return s;
+        if (g.ncell > kBatchMaxCells)
+            return fpm_fail(FPM_ERR_INVALID, "fpm_batch_plan: replica %d has %d cells (limit %d)", r, g.ncell,
+                            kBatchMaxCells);
+        // tile width along x: about `target` particles per tile, at most 14 cells
+        const double per_cell = counts[r] > 0 ? (double)counts[r] / (double)g.ncell : 1.0;
+        int w = (int)std::lround(target / per_cell);
+        w = std::max(1, std::min(kMaxTileCells, w));
+        g.tiles_x = std::max(1, (g.nc[0] + w - 1) / w);
+        g.stage_cap = 0;
+        g.sweep_blocks = 0;
+        reps[r].box = b;
+        reps[r].grid = g;
+        reps[r].p0 = (int32_t)p0;
+        reps[r].n = counts[r];
+        reps[r].c0 = (int32_t)c0;
+        reps[r].t0 = (int32_t)t0;
+        p0 += counts[r];
+        c0 += g.ncell;
+        t0 += rep_ntiles(g);
+        if (p0 > (int64_t)INT32_MAX / 2 || c0 >= (int64_t)INT32_MAX / 2 || t0 >= (int64_t)INT32_MAX / 2)
+            return fpm_fail(FPM_ERR_INVALID, "fpm_batch_plan: batch too large");
+        max_n = std::max(max_n, counts[r]);
+        max_ncell = std::max(max_ncell, g.ncell);
+        stage = std::max(stage, stage_capacity(counts[r], g, sizeof(float4)));
+    }
+    batch->R = R;
+    batch->n_total = (int32_t)p0;
+    batch->ncell_total = (int32_t)c0;
+    batch->ntiles_total = (int32_t)t0;
+    batch->max_n = max_n;
+    batch->max_ncell = max_ncell;
+    batch->stage_cap = stage;
+    batch->sweep_blocks = 0;
+    return FPM_OK;
+}
+
+extern "C" fpm_status fpm_batch_drift_check(const fpm_batch *batch, const fpm_replica *d_reps, double dt, void *pos,
+                                            void *vel, const void *force, const void *pos_ref, double skin,
+                                            uint32_t *d_rep_flag, fpm_stream stream)
+{
+    fpm_status s = batch_ok(batch, d_reps, "fpm_batch_drift_check");
+    if (s != FPM_OK) return s;
+    const int n = batch->n_total;
+    if (!d_rep_flag || !(skin >= 0.0) || (n > 0 && (!pos || !vel || !force || !pos_ref)))
+        return fpm_fail(FPM_ERR_INVALID, "fpm_batch_drift_check: null pointer or bad argument");
+    if (n == 0) return FPM_OK;
+    k_bdrift_check<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
+        n, batch->R, d_reps, (float)(0.5 * dt), (float)dt, (float4 *)pos, (float4 *)vel, (const float4 *)force,
+        (const float4 *)pos_ref, (float)(0.25 * skin * skin), d_rep_flag);
+    return fpm_check_launch("fpm_batch_drift_check");
+}
+
+extern "C" fpm_status fpm_batch_celllist_workspace(const fpm_batch *batch, size_t *bytes)
+{
+    if (!batch || !bytes || batch->n_total < 0) return fpm_fail(FPM_ERR_INVALID, "fpm_batch_celllist_workspace");
+    size_t off[6];
+    *bytes = bcell_layout(*batch, off);
+    return FPM_OK;
+}
+
+extern "C" fpm_status fpm_batch_celllist_build(const fpm_batch *batch, const fpm_replica *d_reps, void *pos,
+                                               void *vel, uint32_t *ids, uint32_t *cell_start, uint32_t *perm,
+                                               void *workspace, size_t workspace_bytes, const uint32_t *d_rep_flag,
+                                               fpm_dev_status *d_status, fpm_stream stream)
+{
+    fpm_status s = batch_ok(batch, d_reps, "fpm_batch_celllist_build");
+    if (s != FPM_OK) return s;
+    if (!cell_start || (batch->n_total > 0 && !pos))
+        return fpm_fail(FPM_ERR_INVALID, "fpm_batch_celllist_build: null pointer");
+    size_t off[6];
+    const size_t need = bcell_layout(*batch, off);
+    if (!workspace || workspace_bytes < need)
+        return fpm_fail(FPM_ERR_WORKSPACE, "fpm_batch_celllist_build: workspace %zu < %zu bytes", workspace_bytes,
+                        need);
+    if (((uintptr_t)workspace & 15u) != 0)
+        return fpm_fail(FPM_ERR_WORKSPACE, "fpm_batch_celllist_build: workspace not 16-B aligned");
+    char *w = (char *)workspace;
+    BCellWs ws{(float4 *)(w + off[0]), (float4 *)(w + off[1]), (uint32_t *)(w + off[2]),
+               (uint32_t *)(w + off[3]), (uint32_t *)(w + off[4]), (uint32_t *)(w + off[5])};
+    const size_t smem = ((size_t)batch->max_ncell + 1) * sizeof(uint32_t);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute((const void *)k_bcell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_bcell<<<batch->R, kBatchCellThreads, smem, (cudaStream_t)stream>>>(batch->R, d_reps, (float4 *)pos,
+                                                                         (float4 *)vel, ids, cell_start, perm, ws,
+                                                                         d_rep_flag, d_status);
+    return fpm_check_launch("fpm_batch_celllist_build");
+}
+
+static ListLayout batch_list_layout(const fpm_batch &b, int cap)
+{
+    TileCfg c{};
+    c.ntiles = b.ntiles_total;
+    return list_layout(b.n_total, c, cap);
+}
+
+extern "C" fpm_status fpm_batch_list_bytes(const fpm_batch *batch, int32_t cap, size_t *bytes)
+{
+    if (!batch || !bytes || cap < 1 || batch->ntiles_total < 1)
+        return fpm_fail(FPM_ERR_INVALID, "fpm_batch_list_bytes: bad argument");
+    *bytes = batch_list_layout(*batch, cap).total;
+    return FPM_OK;
+}
+
+extern "C" fpm_status fpm_batch_verlet_build(const fpm_batch *batch, const fpm_replica *d_reps, const void *pos,
+                                             const uint32_t *cell_start, double r_list, int32_t cap, void *list,
+                                             size_t list_bytes, uint32_t *nn, void *pos_ref, uint32_t *d_rep_flag,
+                                             fpm_dev_status *d_status, fpm_stream stream)
+{
+    fpm_status s = batch_ok(batch, d_reps, "fpm_batch_verlet_build");
+    if (s != FPM_OK) return s;
+    if (cap < 1 || !(r_list > 0.0) || !cell_start || !list || (batch->n_total > 0 && (!pos || !nn)))
+        return fpm_fail(FPM_ERR_INVALID, "fpm_batch_verlet_build: null pointer or bad size");
+    const ListLayout L = batch_list_layout(*batch, cap);
+    if (list_bytes < L.total)
+        return fpm_fail(FPM_ERR_WORKSPACE, "fpm_batch_verlet_build: list object %zu < %zu bytes", list_bytes,
+                        L.total);
+    if (((uintptr_t)list & 255u) != 0)
+        return fpm_fail(FPM_ERR_INVALID, "fpm_batch_verlet_build: list not 256-B aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    char *lb = (char *)list;
+    TileDesc *descs = (TileDesc *)(lb + L.off_tiles);
+    uint32_t *work = (uint32_t *)(lb + L.off_active);
+    uint32_t *header = (uint32_t *)lb;
+    const int R = batch->R;
+    const int nt = batch->ntiles_total;
+    k_btile_desc<<<std::min(nt, kBatchDescBlocks), 128, 0, st>>>(R, nt, d_reps, cell_start, descs, d_rep_flag,
+                                                                d_status);
+    k_bwork<<<1, 1024, 0, st>>>(R, d_reps, d_rep_flag, work, header, d_status);
+    const int sc = batch_stage_cap(*batch);
+    const size_t smem = (size_t)sc * sizeof(float4);
+    smem_opt_in((const void *)k_bverlet_scan);
+    fpm_grid gg{};
+    gg.sweep_blocks = batch->sweep_blocks;
+    const int blocks = persistent_blocks((const void *)k_bverlet_scan, kTileThreads, smem, gg, nt);
+    k_bverlet_scan<<<blocks, kTileThreads, smem, st>>>(R, d_reps, (const float4 *)pos, cell_start,
+                                                       (float)(r_list * r_list), cap, L.ld, sc, work, header,
+                                                       Sched{(unsigned *)(lb + 16), (unsigned *)(lb + 20)},
+                                                       (uint32_t *)(lb + L.off_words), nn, (float4 *)pos_ref,
+                                                       d_status);
+    return fpm_check_launch("fpm_batch_verlet_build");
+}
+
+extern "C" fpm_status fpm_batch_verlet_decode(const fpm_batch *batch, int32_t cap, const void *list,
+                                              const uint32_t *nn, uint32_t *out, fpm_stream stream)
+{
+    if (!batch || cap < 1 || !list || !nn || !out || batch->ntiles_total < 1)
+        return fpm_fail(FPM_ERR_INVALID, "fpm_batch_verlet_decode: bad argument");
+    const ListLayout L = batch_list_layout(*batch, cap);
+    return verlet_decode_launch((const TileDesc *)((const char *)list + L.off_tiles),
+                                (const uint32_t *)((const char *)list + L.off_words), nn, L.ld, out,
+                                batch->ntiles_total, (cudaStream_t)stream);
+}
+
+extern "C" fpm_status fpm_batch_workspace(const fpm_batch *batch, size_t *bytes)
+{
+    if (!batch || !bytes || batch->R < 1 || batch->ntiles_total < 1)
+        return fpm_fail(FPM_ERR_INVALID, "fpm_batch_workspace: bad argument");
+    *bytes = bws_layout(*batch, nullptr);
+    return FPM_OK;
+}
+
+extern "C" fpm_status fpm_batch_lj_forces(const fpm_batch *batch, const fpm_replica *d_reps, const void *pos,
+                                          const void *list, const uint32_t *nn, int32_t cap, double eps,
+                                          double sigma, double rc, void *force, double *d_energy, void *workspace,
+                                          size_t workspace_bytes, fpm_dev_status *d_status, fpm_stream stream)
+{
+    fpm_status s = batch_ok(batch, d_reps, "fpm_batch_lj_forces");
+    if (s != FPM_OK) return s;
+    if (cap < 1 || !(rc > 0.0) || !(sigma > 0.0) || !list || (batch->n_total > 0 && (!pos || !nn || !force)))
+        return fpm_fail(FPM_ERR_INVALID, "fpm_batch_lj_forces: null pointer or bad size");
+    if (((uintptr_t)list & 255u) != 0) return fpm_fail(FPM_ERR_INVALID, "fpm_batch_lj_forces: list not aligned");
+    size_t off_done = 0;
+    const size_t need = bws_layout(*batch, &off_done);
+    if (!workspace || workspace_bytes < need)
+        return fpm_fail(FPM_ERR_WORKSPACE, "fpm_batch_lj_forces: workspace %zu < %zu bytes", workspace_bytes, need);
+    if (((uintptr_t)workspace & 15u) != 0)
+        return fpm_fail(FPM_ERR_WORKSPACE, "fpm_batch_lj_forces: workspace not 16-B aligned");
+    char *w = (char *)workspace;
+    const ListLayout L = batch_list_layout(*batch, cap);
+    LJParams<float> P;
+    P.eps24 = (float)(24.0 * eps);
+    P.eps4 = (float)(4.0 * eps);
+    P.sig2 = (float)(sigma * sigma);
+    P.rc2 = (float)(rc * rc);
+    const int sc = batch_stage_cap(*batch);
+    const size_t smem = (size_t)sc * sizeof(float4);
+    smem_opt_in((const void *)k_blj_tiles);
+    fpm_grid gg{};
+    gg.sweep_blocks = batch->sweep_blocks;
+    const int nt = batch->ntiles_total;
+    const int blocks = persistent_blocks((const void *)k_blj_tiles, kTileThreads, smem, gg, nt);
+    k_blj_tiles<<<blocks, kTileThreads, smem, (cudaStream_t)stream>>>(
+        batch->R, nt, d_reps, (const float4 *)pos, list_view(list, L), nn, L.ld, sc, P, (float4 *)force,
+        Sched{(unsigned *)(w + 16), (unsigned *)(w + 32)}, (double *)(w + 256), (uint32_t *)(w + off_done),
+        d_energy, d_status);
+    return fpm_check_launch("fpm_batch_lj_forces");
+}

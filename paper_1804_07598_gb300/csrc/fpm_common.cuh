@@ -23,7 +23,7 @@ template <typename T> struct BoxT {
     int per[3];
 };
 
-template <typename T> inline BoxT<T> make_box(const fpm_box &b)
+template <typename T> __host__ __device__ inline BoxT<T> make_box(const fpm_box &b)
 {
     BoxT<T> o;
     for (int d = 0; d < 3; ++d) {
@@ -39,7 +39,7 @@ struct GridD {
     float inv[3];
 };
 
-inline GridD make_grid(const fpm_grid &g)
+__host__ __device__ inline GridD make_grid(const fpm_grid &g)
 {
     GridD o;
     for (int d = 0; d < 3; ++d) {

@@ -1,0 +1,98 @@
+// lj_pair.cuh -- the Lennard-Jones pair term and the walk over one
+// particle's 16-bit Verlet-list entries, shared by the single-system sweep
+// (lj.cu) and the batched sweep (batch.cu).  Pair law of Sec. 4.1:
+// V(r) = 4 eps [(s/r)^12 - (s/r)^6], force 24 eps (2 s^12/r^14 - s^6/r^8) r_ij.
+#pragma once
+
+#include "tiles.cuh"
+
+namespace fpm {
+
+// 1/x for the pair sweep.  Single precision: the hardware approximation
+// refined by one Newton-Raphson step, y <- y + y (1 - x y) (the classical
+// iteration for the reciprocal); inputs are squared distances (positive,
+// normal).  Double precision: the correctly rounded reciprocal.
+__device__ __forceinline__ float recip(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    const float e = __fmaf_rn(-x, y, 1.0f);
+    return __fmaf_rn(y, e, y);
+}
+__device__ __forceinline__ double recip(double x) { return __drcp_rn(x); }
+
+template <typename T> struct LJParams {
+    T eps24, eps4, sig2, rc2;
+};
+
+// One list entry, masked (not branched) by the cutoff test.  With
+// s6 = (sigma^2/r^2)^3 and a = 2 s6^2 - s6, the pair force is
+// 24 eps a / r^2 (x_i - x_j), its virial 24 eps a and its energy
+// 4 eps (s6^2 - s6); the constant factors 24 eps and 4 eps are applied once
+// per particle by the caller, so the sums here are of a/r^2 * d, a, and
+// s6^2 - s6.
+template <typename T, bool FAST, bool SMEM>
+__device__ __forceinline__ void lj_pair(const TileCfg &cfg, const BoxT<T> &box, const TileDesc &d,
+                                        const V4<T> *__restrict__ pos, const V4<T> *__restrict__ st, const V4<T> &pi,
+                                        int s, const LJParams<T> &P, T &fx, T &fy, T &fz, T &u, T &w, uint32_t &np)
+{
+    const V4<T> pj = SMEM ? st[s] : staged_global(d, box, pos, s);
+    T dx, dy, dz;
+    const T r2 = tile_sep<FAST>(pi, pj, box, cfg, dx, dy, dz);
+    const bool in = r2 < P.rc2;
+    const T ir2 = recip(r2);
+    const T s2 = P.sig2 * ir2;
+    const T s6 = s2 * s2 * s2;
+    const T s12 = s6 * s6;
+    const T a = in ? (T)2 * s12 - s6 : (T)0;
+    const T g = a * ir2;
+    fx += g * dx;
+    fy += g * dy;
+    fz += g * dz;
+    w += a;
+    u += in ? s12 - s6 : (T)0;
+    np += in ? 1u : 0u;
+}
+
+template <typename T, bool FAST, bool SMEM>
+__device__ __forceinline__ void lj_sweep(const TileCfg &cfg, const BoxT<T> &box, const TileDesc &d,
+                                         const V4<T> *__restrict__ pos, const V4<T> *__restrict__ st,
+                                         const V4<T> &pi, uint32_t m, const uint32_t *__restrict__ col, int64_t ld,
+                                         const LJParams<T> &P, T &fx, T &fy, T &fz, T &u, T &w, uint32_t &np)
+{
+    // list words are loaded kChunk at a time, one chunk ahead of their use;
+    // full chunks run without per-entry guards
+    constexpr uint32_t kChunk = 4;
+    const uint32_t nw = (m + 1u) >> 1;
+    const uint32_t nfull = (m >> 1) / kChunk * kChunk;  // words whose both entries exist, in whole chunks
+    uint32_t cur[kChunk], nxt[kChunk];
+    const uint32_t *p = col;  // next word to load
+#pragma unroll
+    for (uint32_t q = 0; q < kChunk; ++q) {
+        cur[q] = q < nfull ? __ldcs(p) : 0u;
+        p += ld;
+    }
+    for (uint32_t w0 = 0; w0 < nfull; w0 += kChunk) {
+        const bool more = w0 + kChunk < nfull;
+#pragma unroll
+        for (uint32_t q = 0; q < kChunk; ++q) {
+            nxt[q] = more ? __ldcs(p) : 0u;
+            p += ld;
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < kChunk; ++q) {
+            lj_pair<T, FAST, SMEM>(cfg, box, d, pos, st, pi, (int)(cur[q] & 0xffffu), P, fx, fy, fz, u, w, np);
+            lj_pair<T, FAST, SMEM>(cfg, box, d, pos, st, pi, (int)(cur[q] >> 16), P, fx, fy, fz, u, w, np);
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < kChunk; ++q) cur[q] = nxt[q];
+    }
+    for (uint32_t wi = nfull; wi < nw; ++wi) {
+        const uint32_t wv = __ldcs(col + (int64_t)wi * ld);
+        lj_pair<T, FAST, SMEM>(cfg, box, d, pos, st, pi, (int)(wv & 0xffffu), P, fx, fy, fz, u, w, np);
+        if (2u * wi + 1u < m)
+            lj_pair<T, FAST, SMEM>(cfg, box, d, pos, st, pi, (int)(wv >> 16), P, fx, fy, fz, u, w, np);
+    }
+}
+
+}  // namespace fpm

@@ -52,7 +52,7 @@ struct TileCfg {
     int ntiles;
 };
 
-inline TileCfg make_tile_cfg(const fpm_box &b, const fpm_grid &g)
+__host__ __device__ inline TileCfg make_tile_cfg(const fpm_box &b, const fpm_grid &g)
 {
     TileCfg c{};
     for (int d = 0; d < 3; ++d) {
@@ -435,6 +435,93 @@ __device__ __forceinline__ T tile_sep(const V4<T> &pi, const V4<T> &pj, const Bo
     }
     return rfma(dz, dz, rfma(dy, dy, rmul(dx, dx)));
 }
+
+// Verlet-list scan of one home particle i (staged slot `self`): the staged
+// cells t0..t1 of every stencil row, candidates inside r_list written as
+// 16-bit staged indices, two per word (entry k in half k & 1 of word
+// (k >> 1) * ld + i).  Returns the candidate count (entries beyond cap are
+// counted, not stored).
+template <bool FAST, bool SMEM, typename T>
+__device__ __forceinline__ uint32_t scan_candidates(const TileCfg &cfg, const BoxT<T> &box, const TileGeom &g,
+                                                    const TileDesc &d, const V4<T> *__restrict__ pos,
+                                                    const V4<T> *__restrict__ st, const V4<T> &pi, int self,
+                                                    int t0, int t1, T rl2, int cap, int64_t ld, uint32_t i,
+                                                    uint32_t *__restrict__ words)
+{
+    uint32_t cnt = 0, pending = 0;
+    for (int r = 0; r < g.nrows; ++r) {
+        const int s0 = g.off[r][t0], s1 = g.off[r][t1 + 1];
+        for (int s = s0; s < s1; ++s) {
+            if (s == self) continue;
+            const V4<T> pj = SMEM ? st[s] : staged_global(d, box, pos, s);
+            T dx, dy, dz;
+            const T r2 = tile_sep<FAST>(pi, pj, box, cfg, dx, dy, dz);
+            if (r2 < rl2) {
+                if (cnt < (uint32_t)cap) {
+                    if (cnt & 1u) words[(int64_t)(cnt >> 1) * ld + i] = pending | ((uint32_t)s << 16);
+                    else pending = (uint32_t)s;
+                }
+                ++cnt;
+            }
+        }
+    }
+    const uint32_t stored = cnt < (uint32_t)cap ? cnt : (uint32_t)cap;
+    if (stored & 1u) words[(int64_t)(stored >> 1) * ld + i] = pending;
+    return cnt;
+}
+
+// One tile of the Verlet build (all threads of the block call it): its
+// geometry and descriptor, the staging of its neighbourhood, and the scan of
+// every home particle (pos_ref[i] := pos[i] when pos_ref is given).  Returns
+// the largest candidate count this thread saw.
+template <typename T>
+__device__ __forceinline__ uint32_t verlet_tile(const TileCfg &cfg, const BoxT<T> &box, int tile,
+                                                const uint32_t *__restrict__ cs, const V4<T> *__restrict__ pos,
+                                                T rl2, int cap, int64_t ld, int stage_cap, TileGeom &g, TileDesc &d,
+                                                V4<T> *sp, uint64_t *bar, uint32_t &phase,
+                                                uint32_t *__restrict__ words, uint32_t *__restrict__ nn,
+                                                V4<T> *__restrict__ pos_ref, fpm_dev_status *st)
+{
+    tile_geometry(cfg, tile, cs, g, d);
+    if (d.M > kMaxStaged) {  // 16-bit entries cannot address this neighbourhood
+        for (uint32_t i = d.h0 + threadIdx.x; i < d.h1; i += blockDim.x) nn[i] = 0u;
+        if (threadIdx.x == 0) latch_flag(st, FPM_FLAG_CAPACITY);
+        return 0u;
+    }
+    const bool in_smem = d.M <= stage_cap;
+    if (!in_smem) note_spill(st);
+    if (in_smem && !stage_positions(d, box, pos, sp, bar, phase, st)) {
+        for (uint32_t i = d.h0 + threadIdx.x; i < d.h1; i += blockDim.x) nn[i] = 0u;
+        return 0u;
+    }
+    uint32_t maxc = 0;
+    for (uint32_t i = d.h0 + threadIdx.x; i < d.h1; i += blockDim.x) {
+        const V4<T> pi = pos[i];
+        if (pos_ref) pos_ref[i] = pi;
+        // the home cell: the staged cell of the middle row holding i
+        int th = g.a - g.seq_start;
+        for (int t = g.a - g.seq_start; t < g.b - g.seq_start; ++t)
+            if (i >= g.start[g.mid_row][t] && i < g.start[g.mid_row][t] + (uint32_t)g.cnt[g.mid_row][t]) th = t;
+        const int self = g.off[g.mid_row][th] + (int)(i - g.start[g.mid_row][th]);
+        const int t0 = th > 0 ? th - 1 : 0;
+        const int t1 = th + 1 < g.nseq ? th + 1 : g.nseq - 1;
+        uint32_t c;
+        if (in_smem) {
+            c = d.slow ? scan_candidates<false, true>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld, i, words)
+                       : scan_candidates<true, true>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld, i, words);
+        } else {
+            c = scan_candidates<false, false>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld, i, words);
+        }
+        nn[i] = c < (uint32_t)cap ? c : (uint32_t)cap;
+        if (c > (uint32_t)cap) latch_flag(st, FPM_FLAG_CAPACITY);
+        maxc = c > maxc ? c : maxc;
+    }
+    return maxc;
+}
+
+// Launches the list decoder (verlet.cu) over ntiles tile descriptors.
+fpm_status verlet_decode_launch(const TileDesc *descs, const uint32_t *words, const uint32_t *nn, int64_t ld,
+                                uint32_t *out, int ntiles, cudaStream_t stream);
 
 // Shared-memory budget for staged positions: 1.4x the mean neighbourhood of
 // a tile plus slack, capped by what one block may use.

@@ -11,35 +11,6 @@
 
 namespace fpm {
 
-template <bool FAST, bool SMEM, typename T>
-__device__ __forceinline__ uint32_t scan_candidates(const TileCfg &cfg, const BoxT<T> &box, const TileGeom &g,
-                                                    const TileDesc &d, const V4<T> *__restrict__ pos,
-                                                    const V4<T> *__restrict__ st, const V4<T> &pi, int self,
-                                                    int t0, int t1, T rl2, int cap, int64_t ld, uint32_t i,
-                                                    uint32_t *__restrict__ words)
-{
-    uint32_t cnt = 0, pending = 0;
-    for (int r = 0; r < g.nrows; ++r) {
-        const int s0 = g.off[r][t0], s1 = g.off[r][t1 + 1];
-        for (int s = s0; s < s1; ++s) {
-            if (s == self) continue;
-            const V4<T> pj = SMEM ? st[s] : staged_global(d, box, pos, s);
-            T dx, dy, dz;
-            const T r2 = tile_sep<FAST>(pi, pj, box, cfg, dx, dy, dz);
-            if (r2 < rl2) {
-                if (cnt < (uint32_t)cap) {
-                    if (cnt & 1u) words[(int64_t)(cnt >> 1) * ld + i] = pending | ((uint32_t)s << 16);
-                    else pending = (uint32_t)s;
-                }
-                ++cnt;
-            }
-        }
-    }
-    const uint32_t stored = cnt < (uint32_t)cap ? cnt : (uint32_t)cap;
-    if (stored & 1u) words[(int64_t)(stored >> 1) * ld + i] = pending;
-    return cnt;
-}
-
 // Phase 1, every tile: geometry and descriptor (no staging, little shared
 // memory, so the many empty tiles of a sparse box cost almost nothing).
 __global__ void __launch_bounds__(128)
@@ -134,42 +105,9 @@ __global__ void __launch_bounds__(kTileThreads)
     uint32_t ahead = 0;
     for (uint32_t k = blockIdx.x; k < ntodo; k = ticket_next(ahead, &s_k)) {
         ahead = ticket_ahead(sched);
-        tile_geometry(cfg, (int)active[k], cs, g, d);
-        if (d.M > kMaxStaged) {  // 16-bit entries cannot address this neighbourhood
-            for (uint32_t i = d.h0 + threadIdx.x; i < d.h1; i += blockDim.x) nn[i] = 0u;
-            if (threadIdx.x == 0) latch_flag(st, FPM_FLAG_CAPACITY);
-            __syncthreads();
-            continue;
-        }
-        const bool in_smem = d.M <= stage_cap;
-        if (!in_smem) note_spill(st);
-        if (in_smem && !stage_positions(d, box, pos, sp, &bar, phase, st)) {
-            for (uint32_t i = d.h0 + threadIdx.x; i < d.h1; i += blockDim.x) nn[i] = 0u;
-            __syncthreads();
-            continue;
-        }
-        for (uint32_t i = d.h0 + threadIdx.x; i < d.h1; i += blockDim.x) {
-            const V4<T> pi = pos[i];
-            if (pos_ref) pos_ref[i] = pi;
-            // the home cell: the staged cell of the middle row holding i
-            int th = g.a - g.seq_start;
-            for (int t = g.a - g.seq_start; t < g.b - g.seq_start; ++t)
-                if (i >= g.start[g.mid_row][t] && i < g.start[g.mid_row][t] + (uint32_t)g.cnt[g.mid_row][t]) th = t;
-            const int self = g.off[g.mid_row][th] + (int)(i - g.start[g.mid_row][th]);
-            const int t0 = th > 0 ? th - 1 : 0;
-            const int t1 = th + 1 < g.nseq ? th + 1 : g.nseq - 1;
-            uint32_t c;
-            if (in_smem) {
-                c = d.slow
-                        ? scan_candidates<false, true>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld, i, words)
-                        : scan_candidates<true, true>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld, i, words);
-            } else {
-                c = scan_candidates<false, false>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld, i, words);
-            }
-            nn[i] = c < (uint32_t)cap ? c : (uint32_t)cap;
-            if (c > (uint32_t)cap) latch_flag(st, FPM_FLAG_CAPACITY);
-            maxc = c > maxc ? c : maxc;
-        }
+        const uint32_t c = verlet_tile<T>(cfg, box, (int)active[k], cs, pos, rl2, cap, ld, stage_cap, g, d, sp, &bar,
+                                          phase, words, nn, pos_ref, st);
+        maxc = c > maxc ? c : maxc;
     }
     const uint32_t m = __reduce_max_sync(kFull, maxc);
     if ((threadIdx.x & 31) == 0 && st && m > 0) atomicMax(&st->max_nn, m);
@@ -195,6 +133,13 @@ __global__ void __launch_bounds__(kTileThreads)
             out[(int64_t)k * ld + i] = j;
         }
     }
+}
+
+fpm_status verlet_decode_launch(const TileDesc *descs, const uint32_t *words, const uint32_t *nn, int64_t ld,
+                                uint32_t *out, int ntiles, cudaStream_t stream)
+{
+    if (ntiles > 0) k_verlet_decode<<<ntiles, kTileThreads, 0, stream>>>(descs, words, nn, ld, out);
+    return fpm_check_launch("fpm_verlet_decode");
 }
 
 __global__ void k_gate_done(uint32_t *gate, fpm_dev_status *st)
@@ -340,10 +285,9 @@ extern "C" fpm_status fpm_verlet_decode(const fpm_grid *grid, int32_t n, int32_t
     TileCfg c{};
     c.ntiles = grid->tiles_x * grid->nc[1] * grid->nc[2];
     const ListLayout L = list_layout(n, c, cap);
-    k_verlet_decode<<<c.ntiles, kTileThreads, 0, (cudaStream_t)stream>>>(
-        (const TileDesc *)((const char *)list + L.off_tiles), (const uint32_t *)((const char *)list + L.off_words),
-        nn, L.ld, out);
-    return fpm_check_launch("fpm_verlet_decode");
+    return verlet_decode_launch((const TileDesc *)((const char *)list + L.off_tiles),
+                                (const uint32_t *)((const char *)list + L.off_words), nn, L.ld, out, c.ntiles,
+                                (cudaStream_t)stream);
 }
 
 extern "C" fpm_status fpm_verlet_check(const fpm_box *box, int32_t n, fpm_prec prec, const void *pos,

@@ -45,6 +45,17 @@ class fpm_grid(_c.Structure):
         return tuple(self.nc)
 
 
+class fpm_replica(_c.Structure):
+    _fields_ = [("box", fpm_box), ("grid", fpm_grid), ("p0", _c.c_int32), ("n", _c.c_int32), ("c0", _c.c_int32),
+                ("t0", _c.c_int32)]
+
+
+class fpm_batch(_c.Structure):
+    _fields_ = [("R", _c.c_int32), ("n_total", _c.c_int32), ("ncell_total", _c.c_int32),
+                ("ntiles_total", _c.c_int32), ("max_n", _c.c_int32), ("max_ncell", _c.c_int32),
+                ("stage_cap", _c.c_int32), ("sweep_blocks", _c.c_int32)]
+
+
 class fpm_dev_status(_c.Structure):
     _fields_ = [("flags", _c.c_uint32), ("max_nn", _c.c_uint32), ("rebuild", _c.c_uint32),
                 ("nrebuild", _c.c_uint32), ("max_disp2", _c.c_uint32), ("bad_index", _c.c_uint32),
@@ -108,6 +119,20 @@ _SIG = {
                                   _VP]),
     "fpm_adjoint_seed": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _VP, _VP, _VP, _VP]),
     "fpm_kinetic": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _VP, _VP, _c.c_size_t, _VP]),
+    "fpm_batch_plan": (_c.c_int, [_c.c_int32, _c.POINTER(fpm_box), _c.POINTER(_c.c_int32), _c.c_double, _c.c_int32,
+                                  _c.POINTER(fpm_replica), _c.POINTER(fpm_batch)]),
+    "fpm_batch_drift_check": (_c.c_int, [_c.POINTER(fpm_batch), _VP, _c.c_double, _VP, _VP, _VP, _VP, _c.c_double,
+                                         _VP, _VP]),
+    "fpm_batch_celllist_workspace": (_c.c_int, [_c.POINTER(fpm_batch), _c.POINTER(_c.c_size_t)]),
+    "fpm_batch_celllist_build": (_c.c_int, [_c.POINTER(fpm_batch), _VP, _VP, _VP, _VP, _VP, _VP, _VP, _c.c_size_t,
+                                            _VP, _VP, _VP]),
+    "fpm_batch_list_bytes": (_c.c_int, [_c.POINTER(fpm_batch), _c.c_int32, _c.POINTER(_c.c_size_t)]),
+    "fpm_batch_verlet_build": (_c.c_int, [_c.POINTER(fpm_batch), _VP, _VP, _VP, _c.c_double, _c.c_int32, _VP,
+                                          _c.c_size_t, _VP, _VP, _VP, _VP, _VP]),
+    "fpm_batch_verlet_decode": (_c.c_int, [_c.POINTER(fpm_batch), _c.c_int32, _VP, _VP, _VP, _VP]),
+    "fpm_batch_workspace": (_c.c_int, [_c.POINTER(fpm_batch), _c.POINTER(_c.c_size_t)]),
+    "fpm_batch_lj_forces": (_c.c_int, [_c.POINTER(fpm_batch), _VP, _VP, _VP, _VP, _c.c_int32, _c.c_double,
+                                       _c.c_double, _c.c_double, _VP, _VP, _VP, _c.c_size_t, _VP, _VP]),
 }
 
 
@@ -344,4 +369,72 @@ def fpm_sph_correct(box, n, params, pos, vr, vr_h, acc_h, d_dt, d_dtcons, pos_re
     _check(lib().fpm_sph_correct(_c.byref(box), int(n), _c.byref(params), _ptr(pos), _ptr(vr), _ptr(vr_h),
                                  _ptr(acc_h), _ptr(d_dt), _ptr(d_dtcons), _ptr(pos_ref), float(skin), _ptr(d_status),
                                  _stream(stream)))
+    _count(1)
+
+
+# ------------------------------------------------------------------ batched replicas
+
+def fpm_batch_plan(boxes, counts, r_cell: float, tile_target: int = 0):
+    """(reps: ctypes array of fpm_replica [R], batch: fpm_batch) for replicas
+    with the given fpm_box list and particle counts."""
+    R = len(boxes)
+    barr = (fpm_box * R)(*boxes)
+    carr = (_c.c_int32 * R)(*[int(c) for c in counts])
+    reps = (fpm_replica * R)()
+    b = fpm_batch()
+    _check(lib().fpm_batch_plan(int(R), barr, carr, float(r_cell), int(tile_target), reps, _c.byref(b)))
+    return reps, b
+
+
+def fpm_batch_drift_check(batch, d_reps, dt, pos, vel, force, pos_ref, skin, d_rep_flag, stream=None):
+    _check(lib().fpm_batch_drift_check(_c.byref(batch), _ptr(d_reps), float(dt), _ptr(pos), _ptr(vel), _ptr(force),
+                                       _ptr(pos_ref), float(skin), _ptr(d_rep_flag), _stream(stream)))
+    _count(1 if batch.n_total > 0 else 0)
+
+
+def fpm_batch_celllist_workspace(batch) -> int:
+    n = _c.c_size_t()
+    _check(lib().fpm_batch_celllist_workspace(_c.byref(batch), _c.byref(n)))
+    return n.value
+
+
+def fpm_batch_celllist_build(batch, d_reps, pos, vel, ids, cell_start, perm, workspace, d_rep_flag=None,
+                             d_status=None, stream=None):
+    _check(lib().fpm_batch_celllist_build(_c.byref(batch), _ptr(d_reps), _ptr(pos), _ptr(vel), _ptr(ids),
+                                          _ptr(cell_start), _ptr(perm), _ptr(workspace), _nbytes(workspace),
+                                          _ptr(d_rep_flag), _ptr(d_status), _stream(stream)))
+    _count(1)
+
+
+def fpm_batch_list_bytes(batch, cap: int) -> int:
+    n = _c.c_size_t()
+    _check(lib().fpm_batch_list_bytes(_c.byref(batch), int(cap), _c.byref(n)))
+    return n.value
+
+
+def fpm_batch_verlet_build(batch, d_reps, pos, cell_start, r_list, cap, list_obj, nn, pos_ref=None,
+                           d_rep_flag=None, d_status=None, stream=None):
+    _check(lib().fpm_batch_verlet_build(_c.byref(batch), _ptr(d_reps), _ptr(pos), _ptr(cell_start), float(r_list),
+                                        int(cap), _ptr(list_obj), _nbytes(list_obj), _ptr(nn), _ptr(pos_ref),
+                                        _ptr(d_rep_flag), _ptr(d_status), _stream(stream)))
+    _count(3)
+
+
+def fpm_batch_verlet_decode(batch, cap, list_obj, nn, out, stream=None):
+    _check(lib().fpm_batch_verlet_decode(_c.byref(batch), int(cap), _ptr(list_obj), _ptr(nn), _ptr(out),
+                                         _stream(stream)))
+    _count(1)
+
+
+def fpm_batch_workspace(batch) -> int:
+    n = _c.c_size_t()
+    _check(lib().fpm_batch_workspace(_c.byref(batch), _c.byref(n)))
+    return n.value
+
+
+def fpm_batch_lj_forces(batch, d_reps, pos, list_obj, nn, cap, eps, sigma, rc, force, d_energy=None,
+                        workspace=None, d_status=None, stream=None):
+    _check(lib().fpm_batch_lj_forces(_c.byref(batch), _ptr(d_reps), _ptr(pos), _ptr(list_obj), _ptr(nn), int(cap),
+                                     float(eps), float(sigma), float(rc), _ptr(force), _ptr(d_energy),
+                                     _ptr(workspace), _nbytes(workspace), _ptr(d_status), _stream(stream)))
     _count(1)

@@ -131,15 +131,32 @@ def batched_replicas(count: int = 512, seed: int = 2024, nmin: int = 256, nmax: 
     return N, rho, T
 
 
-def replica_state(N: int, rho: float, T: float, seed: int):
-    """A cubic FCC-like fill of one replica: ceil((N/4)^(1/3)) cells per side,
-    first N sites; box side from the density."""
+def replica_state(N: int, rho: float, T: float, seed: int, jitter: float = 0.06):
+    """One replica of the ensemble: a cubic box of side (N/rho)^(1/3) with N
+    sites drawn without replacement (seeded) from an FCC lattice of
+    m = ceil((N/4)^(1/3)) cells per side (so the density is rho on average,
+    with vacancies spread uniformly), each moved by a uniform jitter of
+    +-jitter*a off the lattice, and Maxwell-Boltzmann velocities at T."""
     m = int(math.ceil((N / 4.0) ** (1.0 / 3.0) - 1e-9))
     L = (N / rho) ** (1.0 / 3.0)
     a = L / m
-    x = fcc_lattice((m, m, m), a)[:N]
-    v = maxwell_boltzmann(N, T, seed)
+    sites = fcc_lattice((m, m, m), a)
+    rng = np.random.default_rng(seed)
+    keep = np.sort(rng.choice(sites.shape[0], size=N, replace=False))
+    x = sites[keep]
+    if jitter > 0:
+        x = np.mod(x + rng.uniform(-jitter * a, jitter * a, size=x.shape), L)
+    v = maxwell_boltzmann(N, T, seed + 1)
     return as4(x), as4(v), np.array([L, L, L])
+
+
+def ensemble(count: int = 512, seed: int = 2024, nmin: int = 256, nmax: int = 16384):
+    """The batched LJ ensemble: `count` replicas from batched_replicas, each
+    filled by replica_state with its own seed.  Returns (list of
+    (pos [N,4], vel [N,4], L [3]), N, rho, T)."""
+    N, rho, T = batched_replicas(count, seed, nmin, nmax)
+    reps = [replica_state(int(N[r]), float(rho[r]), float(T[r]), seed * 1000 + r) for r in range(count)]
+    return reps, N, rho, T
 
 
 # ---------------------------------------------------------------------------

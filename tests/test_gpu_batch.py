@@ -1,0 +1,215 @@
+"""GPU parity of the batched replicas (R periodic LJ systems of uneven size
+advanced together) against the oracle run replica by replica, on identical
+positions.
+
+Bit-exact: each replica's cell_start segment, sort permutation, sorted
+positions and neighbour sets.  Forces: max_i |F_i - F_i^ref| / RMS(F^ref)
+<= 1e-5; U relative <= 1e-6; pair counts exact (FP32 path, the oracle
+taking the FP32 box).  The virial W of a small replica is a strongly
+cancelling sum (|W| can be a few hundredths of sum |r_ij . F_ij|), and the
+rounding of a sum of FP32 pair terms scales with the sum of their magnitudes
+(the classical bound for recursive summation), so W is held to
+|dW| <= 1e-6 * sum_{i<j} |r_ij . F_ij|."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1804_07598_gb300 import autotune, fpm, inputs
+from paper_1804_07598_gb300.batch import LJBatch
+
+pytestmark = pytest.mark.gpu
+
+TOL_F, TOL_E = 1e-5, 1e-6
+PER = (1, 1, 1)
+
+
+def u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def small_ensemble(seed=5, extra=5):
+    """Replicas covering one cell per dimension (all-pairs: N=256 at 0.95, N=300
+    at 0.70), 3, 3 and 4 cells per dimension, plus log-uniform draws."""
+    specs = [(256, 0.95, 0.8), (300, 0.70, 1.2), (700, 0.80, 0.9), (1000, 0.85, 1.4), (1500, 0.75, 0.6)]
+    N, rho, T = inputs.batched_replicas(extra, seed, 256, 4000)
+    specs += [(int(N[k]), float(rho[k]), float(T[k])) for k in range(extra)]
+    return [inputs.replica_state(n, r, t, seed * 100 + k) for k, (n, r, t) in enumerate(specs)]
+
+
+def fbox(L):
+    return np.asarray(L, np.float64).astype(np.float32).astype(np.float64)
+
+
+def force_error(f, fref):
+    rms = np.sqrt(np.mean(np.sum(fref[:, :3] ** 2, axis=1)))
+    return np.max(np.linalg.norm(f[:, :3] - fref[:, :3], axis=1)) / rms
+
+
+def replica_sets(nbr, nn, p0, p1):
+    return [np.sort(nbr[:nn[i], i].astype(np.int64) - p0) for i in range(p0, p1)]
+
+
+def check_lists(b, r, pos_ref, nbr, nn):
+    """Replica r's Verlet lists equal the oracle's neighbour sets of the
+    positions they were built from."""
+    p0, p1 = b.replica_range(r)
+    offs, onbr = oracle.neighbors(pos_ref[p0:p1], b.L[r], PER, b.r_list)
+    assert np.array_equal(nn[p0:p1].astype(np.int64), np.diff(offs)), r
+    got = replica_sets(nbr, nn, p0, p1)
+    for i in range(p1 - p0):
+        assert np.array_equal(got[i], np.sort(onbr[offs[i]:offs[i + 1]].astype(np.int64))), (r, i)
+
+
+def abs_virial(x, L, rc):
+    """sum_{i<j, r<rc} |r_ij . F_ij| for sigma = eps = 1 (the scale of the
+    virial's rounding error), from the oracle's neighbour sets."""
+    offs, nbr = oracle.neighbors(x, L, PER, rc)
+    i = np.repeat(np.arange(x.shape[0]), np.diff(offs))
+    d = x[i, :3].astype(np.float64) - x[nbr.astype(np.int64), :3]
+    d -= L * np.rint(d / L)
+    ir6 = 1.0 / np.sum(d * d, axis=1) ** 3
+    return 0.5 * np.sum(np.abs(24.0 * (2.0 * ir6 * ir6 - ir6)))
+
+
+def check_forces(b, r, pos, force, energy):
+    p0, p1 = b.replica_range(r)
+    fref, U, W, pairs = oracle.lj_forces(pos[p0:p1].astype(np.float64), fbox(b.L[r]), PER, b.eps, b.sigma, b.rc,
+                                         mask_f32=True)
+    err = force_error(force[p0:p1].astype(np.float64), fref)
+    assert err <= TOL_F, (r, err)
+    assert abs(energy[r, 0] - U) <= TOL_E * abs(U), (r, energy[r, 0], U)
+    wscale = abs_virial(pos[p0:p1], fbox(b.L[r]), b.rc)
+    assert abs(energy[r, 1] - W) <= TOL_E * wscale, (r, energy[r, 1], W, wscale)
+    assert int(round(energy[r, 2])) == pairs, r
+    return err
+
+
+@pytest.mark.parametrize("tile_target,sweep_blocks", [(0, 0), (96, -1), (256, 0), (128, 300)])
+def test_batch_build_and_forces_match_oracle(cuda, tile_target, sweep_blocks):
+    reps = small_ensemble()
+    b = LJBatch(reps, tile_target=tile_target)
+    b.set_sweep_blocks(sweep_blocks)
+    b.compute_forces()
+    torch.cuda.synchronize()
+    b.check_status()
+    pos, _, ids = b.state_numpy()
+    cs, perm = u32(b.cell_start), u32(b.perm)
+    nbr, nn = b.neighbor_lists()
+    force, energy = b.force.cpu().numpy(), b.energies()
+    modes = set()
+    for r, (x, v, L) in enumerate(reps):
+        p0, p1 = b.replica_range(r)
+        o = oracle.celllist_build(x.astype(np.float32), L, PER, b.r_list)
+        c0, ncell = b.reps[r].c0, b.reps[r].grid.ncell
+        assert ncell == int(np.prod(o["nc"]))
+        modes.add(int(o["nc"][0]))
+        assert np.array_equal(cs[c0:c0 + ncell + 1].astype(np.int64) - p0, o["cell_start"].astype(np.int64)), r
+        assert np.array_equal(perm[p0:p1].astype(np.int64) - p0, o["perm"].astype(np.int64)), r
+        assert np.array_equal(ids[p0:p1].astype(np.int64) - p0, o["perm"].astype(np.int64)), r
+        assert np.array_equal(pos[p0:p1, :3], o["pos"][:, :3]), r
+        check_lists(b, r, pos, nbr, nn)
+        check_forces(b, r, pos, force, energy)
+    assert 1 in modes and 3 in modes  # all-pairs and stencil replicas both covered
+
+
+def test_batch_forces_deterministic(cuda):
+    b = LJBatch(small_ensemble(seed=9))
+    f1, e1 = b.force.clone(), b.energy.clone()
+    b.compute_forces()
+    assert torch.equal(f1, b.force) and torch.equal(e1, b.energy)
+
+
+def test_batch_gated_rebuild_touches_only_flagged_replicas(cuda):
+    reps = small_ensemble(seed=7)
+    b = LJBatch(reps)
+    R = b.R
+    flagged = [1, 3, R - 1]
+    # move the flagged replicas' particles so that their cells change
+    for r in flagged:
+        p0, p1 = b.replica_range(r)
+        b.pos[p0:p1, 0] += 0.9
+    torch.cuda.synchronize()
+    cs0, pos0 = u32(b.cell_start).copy(), b.pos.cpu().numpy().copy()
+    nbr0, nn0 = b.neighbor_lists()
+    nr0 = fpm.read_status(b.status).nrebuild
+    f = torch.zeros(R, dtype=torch.int32, device="cuda")
+    f[flagged] = 1
+    b.flags.copy_(f)
+    b.rebuild(gated=True)
+    b.compute_forces()
+    torch.cuda.synchronize()
+    st = b.check_status()
+    assert st.nrebuild - nr0 == len(flagged)
+    assert int(b.flags.abs().sum().item()) == 0
+    cs, pos = u32(b.cell_start), b.pos.cpu().numpy()
+    nbr, nn = b.neighbor_lists()
+    pref = b.pos_ref.cpu().numpy()
+    force, energy = b.force.cpu().numpy(), b.energies()
+    for r in range(R):
+        p0, p1 = b.replica_range(r)
+        c0, ncell = b.reps[r].c0, b.reps[r].grid.ncell
+        if r in flagged:
+            o = oracle.celllist_build(pos0[p0:p1], b.L[r], PER, b.r_list)
+            assert np.array_equal(cs[c0:c0 + ncell + 1].astype(np.int64) - p0, o["cell_start"].astype(np.int64))
+            assert np.array_equal(pos[p0:p1, :3], o["pos"][:, :3])
+            assert np.array_equal(pref[p0:p1], pos[p0:p1])
+        else:
+            assert np.array_equal(cs[c0:c0 + ncell + 1], cs0[c0:c0 + ncell + 1]), r
+            assert np.array_equal(pos[p0:p1], pos0[p0:p1]), r
+            assert np.array_equal(nn[p0:p1], nn0[p0:p1]), r
+            assert np.array_equal(nbr[:, p0:p1], nbr0[:, p0:p1]), r  # the list entries are untouched
+        check_lists(b, r, pref, nbr, nn)
+        check_forces(b, r, pos, force, energy)
+
+
+def test_batch_steps_keep_lists_valid(cuda):
+    """Steps under a CUDA graph: replicas rebuild on their own schedule; after
+    the run every replica's list equals the oracle's sets at its reference
+    positions and the forces equal the oracle's at the current positions."""
+    b = LJBatch(small_ensemble(seed=11))
+    b.step(3)
+    b.capture(steps_per_graph=2)
+    nr0 = fpm.read_status(b.status).nrebuild
+    b.run(60)
+    torch.cuda.synchronize()
+    st = b.check_status()
+    assert st.nrebuild > nr0  # some replicas were rebuilt
+    assert int(b.flags.abs().sum().item()) == 0
+    pos, vel, _ = b.state_numpy()
+    pref = b.pos_ref.cpu().numpy()
+    nbr, nn = b.neighbor_lists()
+    force, energy = b.force.cpu().numpy(), b.energies()
+    for r in range(b.R):
+        p0, p1 = b.replica_range(r)
+        # every particle within skin/2 of its reference (else it would have been rebuilt)
+        d = pos[p0:p1, :3].astype(np.float64) - pref[p0:p1, :3]
+        assert np.max(np.sum(d * d, axis=1)) <= (0.5 * b.skin) ** 2 * (1 + 1e-5)
+        check_lists(b, r, pref, nbr, nn)
+        check_forces(b, r, pos, force, energy)
+        # momentum of each replica stays ~0 (pairwise forces, zero initial momentum)
+        assert np.max(np.abs(vel[p0:p1, :3].astype(np.float64).sum(0))) < 1e-3 * (p1 - p0) ** 0.5
+
+
+def test_batch_full_ensemble_sampled(cuda):
+    """The 512-replica ensemble (about 1.9M particles) in the autotuned
+    launch configuration and under a CUDA graph: sampled replicas (smallest,
+    largest and three random) against the oracle after 20 steps."""
+    reps, N, rho, T = inputs.ensemble()
+    b = LJBatch(reps)
+    res = autotune.tune_batch(b, steps=6, warmup=2, tile_targets=(128, 170), sweep_blocks=(0, -1), use_cache=False)
+    assert res["config"]["tile_target"] in (128, 170)
+    b.step(2)
+    b.capture(steps_per_graph=1)
+    b.run(20)
+    torch.cuda.synchronize()
+    b.check_status()
+    pos, _, _ = b.state_numpy()
+    pref = b.pos_ref.cpu().numpy()
+    nbr, nn = b.neighbor_lists()
+    force, energy = b.force.cpu().numpy(), b.energies()
+    rng = np.random.default_rng(3)
+    sample = sorted({int(np.argmin(N)), int(np.argmax(N)), *rng.choice(b.R, 3, replace=False).tolist()})
+    for r in sample:
+        check_lists(b, r, pref, nbr, nn)
+        check_forces(b, r, pos, force, energy)
