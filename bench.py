@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--profile", default=None, choices=["forces", "step", "sph"],
+    ap.add_argument("--profile", default=None, choices=["forces", "step", "sph", "verlet", "batch"],
                     help="profiling target for ncu: build the 1M-atom system, then run --steps force sweeps "
                          "or eager steps (no timing, no JSON line)")
     ap.add_argument("--fp64-steps", type=int, default=100)
@@ -497,12 +497,23 @@ def run_profile_target(args):
         ss.check_status()
         print(f"profile target done: sph x{args.steps}, n={ss.n}", flush=True)
         return
+    if args.profile == "batch":
+        from paper_1804_07598_gb300.batch import LJBatch
+        reps, _, _, _ = inputs.ensemble()
+        bb = LJBatch(reps)
+        bb.step(args.steps)
+        torch.cuda.synchronize()
+        bb.check_status()
+        print(f"profile target done: batch x{args.steps}, n={bb.n}", flush=True)
+        return
     wl = inputs.WORKLOADS[WORKLOAD]
     pos, vel, L = inputs.lj_state(wl)
     s = LJSystem(pos, vel, L, eps=wl.eps, sigma=wl.sigma, rc=wl.rc, skin=wl.skin, dt=wl.dt, precision="f32")
     for _ in range(args.steps):
         if args.profile == "forces":
             s.compute_forces()
+        elif args.profile == "verlet":
+            s.rebuild()
         else:
             s.step(1)
     torch.cuda.synchronize()

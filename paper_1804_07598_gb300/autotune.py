@@ -119,16 +119,38 @@ def tune_batch(system, steps: int = 20, warmup: int = 5, tile_targets=(96, 128, 
     return tune(key, space, apply, measure, use_cache)
 
 
-def tune_system(system, steps: int = 20, warmup: int = 5, sweep_blocks=None, use_cache: bool = True) -> dict:
-    """Tunes the sweep blocks of an LJSystem (its tiles stay as planned)."""
-    if sweep_blocks is None:
-        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
-        sweep_blocks = (0, -1, 4 * sms, 6 * sms)
-    space = {"sweep_blocks": list(sweep_blocks)}
+def tune_system(system, steps: int = 20, warmup: int = 5, cells_per_tile=(6, 8, 10, 13), sweep_blocks=(0, -1),
+                use_cache: bool = True) -> dict:
+    """Tunes an LJSystem: cells per tile along x (re-tiles and rebuilds) x
+    sweep blocks, timing whole steps."""
+    nc0 = int(system.grid.nc[0])
+    tiles = sorted({max(1, -(-nc0 // int(w))) for w in cells_per_tile})
+    space = {"tiles_x": tiles, "sweep_blocks": list(sweep_blocks)}
     key = "lj_system:" + signature({"n": system.n, "L": [float(x) for x in system.L], "r_list": system.r_list,
                                     "prec": system.prec})
 
     def apply(cfg):
+        if cfg["tiles_x"] != system.grid.tiles_x:
+            system.retile(cfg["tiles_x"], cfg["sweep_blocks"])
+        system.grid.sweep_blocks = int(cfg["sweep_blocks"])
+        system._graph = None
+
+    def measure():
+        return time_steps(system._step, steps, warmup)
+
+    return tune(key, space, apply, measure, use_cache)
+
+
+def tune_sph(system, steps: int = 6, warmup: int = 2, tile_targets=(60, 90, 130, 170), sweep_blocks=(0, -1),
+             use_cache: bool = True) -> dict:
+    """Tunes an SPHSystem: particles per tile (re-tiles and rebuilds) x sweep
+    blocks, timing whole steps."""
+    space = {"tile_target": list(tile_targets), "sweep_blocks": list(sweep_blocks)}
+    key = "sph:" + signature({"n": system.n, "L": [float(x) for x in system.L], "r_list": system.r_list})
+
+    def apply(cfg):
+        if cfg["tile_target"] != system.tile_target:
+            system.retile(cfg["tile_target"], cfg["sweep_blocks"])
         system.grid.sweep_blocks = int(cfg["sweep_blocks"])
         system._graph = None
 

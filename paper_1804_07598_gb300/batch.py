@@ -74,6 +74,7 @@ class LJBatch:
         self.ws_cell = torch.zeros(fpm.fpm_batch_celllist_workspace(b), dtype=torch.uint8, device=dev)
         self.ws_red = torch.zeros(fpm.fpm_batch_workspace(b), dtype=torch.uint8, device=dev)
         self._graph = None
+        self.status[fpm.STATUS_MAX_STAGED] = 0  # the staging size follows the new tiles
         self.rebuild()
         self.size_staging()
         self.compute_forces()

@@ -88,11 +88,8 @@ __device__ __forceinline__ void hvp_sweep(const TileCfg &cfg, const BoxT<T> &box
                                           const uint32_t *__restrict__ col, int64_t ld, const HvpParams<T> &P,
                                           HvpAcc<T> &A)
 {
-    for (uint32_t wi = 0; wi < (m + 1u) >> 1; ++wi) {
-        const uint32_t wv = __ldcs(col + (int64_t)wi * ld);
-        hvp_pair<T, FAST, SMEM>(cfg, box, d, pos, avec, st, sa, pi, ai, (int)(wv & 0xffffu), P, A);
-        if (2u * wi + 1u < m) hvp_pair<T, FAST, SMEM>(cfg, box, d, pos, avec, st, sa, pi, ai, (int)(wv >> 16), P, A);
-    }
+    for_each_entry<4>(m, col, ld,
+                      [&](int s) { hvp_pair<T, FAST, SMEM>(cfg, box, d, pos, avec, st, sa, pi, ai, s, P, A); });
 }
 
 // The sweep of a tile whose neighbourhood did not fit in shared memory (rare;

@@ -92,6 +92,19 @@ extern "C" fpm_status fpm_grid_make(const fpm_box *box, double r_cell, int32_t n
     return FPM_OK;
 }
 
+int grid_cap(long long want)
+{
+    static int cap = 0;
+    if (cap == 0) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cap = 8 * (sms > 0 ? sms : 1);
+    }
+    if (want < 1) return 1;
+    return want < cap ? (int)want : cap;
+}
+
 extern "C" fpm_status fpm_reduce_workspace(int32_t n, const fpm_grid *grid, size_t *bytes)
 {
     if (!bytes || n < 0) return fpm_fail(FPM_ERR_INVALID, "fpm_reduce_workspace: bad argument");

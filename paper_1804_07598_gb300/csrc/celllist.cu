@@ -58,38 +58,43 @@ __global__ void k_bin(BoxT<T> box, GridD grid, int n, const V4<T> *__restrict__ 
                       uint32_t *__restrict__ rank, uint32_t *count, fpm_dev_status *st, const uint32_t *gate)
 {
     if (gated_off(gate)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool live = i < n;
-    uint32_t c = UINT_MAX;
-    if (live) {
-        V4<T> p = pos_in[i];
-        if (box.per[0]) p.x = wrap1(p.x, box.L[0]);
-        if (box.per[1]) p.y = wrap1(p.y, box.L[1]);
-        if (box.per[2]) p.z = wrap1(p.z, box.L[2]);
-        bool bad = false;
-        int cc[3];
-        cell_of(p, box, grid, cc, bad);
-        if (bad) {
-            latch_flag(st, FPM_FLAG_DOMAIN);
-            if (st) atomicExch(&st->bad_index, (uint32_t)i);
+    // grid-stride; the loop bound is uniform per block, so whole warps
+    // iterate together (the aggregated atomic below needs that)
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(base + threadIdx.x);
+        const bool live = i < n;
+        uint32_t c = UINT_MAX;
+        if (live) {
+            V4<T> p = pos_in[i];
+            if (box.per[0]) p.x = wrap1(p.x, box.L[0]);
+            if (box.per[1]) p.y = wrap1(p.y, box.L[1]);
+            if (box.per[2]) p.z = wrap1(p.z, box.L[2]);
+            bool bad = false;
+            int cc[3];
+            cell_of(p, box, grid, cc, bad);
+            if (bad) {
+                latch_flag(st, FPM_FLAG_DOMAIN);
+                if (st) atomicExch(&st->bad_index, (uint32_t)i);
+            }
+            c = linear_cell(cc[0], cc[1], cc[2], grid);
+            cell[i] = c;
+            if (stage_pos) stage_pos[i] = p;
+            if (stage_vel) stage_vel[i] = vel_in[i];
+            if (stage_id) stage_id[i] = id_in ? id_in[i] : (uint32_t)i;
         }
-        c = linear_cell(cc[0], cc[1], cc[2], grid);
-        cell[i] = c;
-        if (stage_pos) stage_pos[i] = p;
-        if (stage_vel) stage_vel[i] = vel_in[i];
-        if (stage_id) stage_id[i] = id_in ? id_in[i] : (uint32_t)i;
+        // warp-aggregated histogram: one atomic per distinct cell in the warp
+        const unsigned lane = threadIdx.x & 31;
+        const unsigned act = __ballot_sync(kFull, live);
+        if (live) {
+            const unsigned peers = __match_any_sync(act, c);
+            const int leader = __ffs(peers) - 1;
+            const unsigned below = peers & ((1u << lane) - 1u);
+            uint32_t b = 0;
+            if ((int)lane == leader) b = atomicAdd(&count[c], (uint32_t)__popc(peers));
+            b = __shfl_sync(peers, b, leader);
+            rank[i] = b + (uint32_t)__popc(below);
+        }
     }
-    // warp-aggregated histogram: one atomic per distinct cell in the warp
-    const unsigned lane = threadIdx.x & 31;
-    const unsigned act = __ballot_sync(kFull, live);
-    if (!live) return;
-    const unsigned peers = __match_any_sync(act, c);
-    const int leader = __ffs(peers) - 1;
-    const unsigned below = peers & ((1u << lane) - 1u);
-    uint32_t base = 0;
-    if ((int)lane == leader) base = atomicAdd(&count[c], (uint32_t)__popc(peers));
-    base = __shfl_sync(peers, base, leader);
-    rank[i] = base + (uint32_t)__popc(below);
 }
 
 // Inclusive scan of one value per thread across a 1024-thread block.
@@ -170,9 +175,8 @@ __global__ void k_scatter(int n, const uint32_t *__restrict__ cell, const uint32
                           const uint32_t *__restrict__ cell_start, uint32_t *__restrict__ tmp, const uint32_t *gate)
 {
     if (gated_off(gate)) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    tmp[cell_start[cell[i]] + rank[i]] = (uint32_t)i;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        tmp[cell_start[cell[i]] + rank[i]] = (uint32_t)i;
 }
 
 // Ascending bitonic sort of one value per lane across a full warp.
@@ -214,29 +218,31 @@ __global__ void k_sort_gather(BoxT<T> box, int ncell, const uint32_t *__restrict
                               uint32_t *__restrict__ perm, const uint32_t *gate)
 {
     if (gated_off(gate)) return;
-    const int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const unsigned lane = threadIdx.x & 31;
-    if (c >= ncell) return;  // whole warp leaves together
-    const uint32_t s = cell_start[c], e = cell_start[c + 1];
-    const uint32_t k = e - s;
-    if (k == 0) return;
-    if (k <= 32) {
-        uint32_t v = lane < k ? tmp[s + lane] : UINT_MAX;
-        v = warp_sort32(v);
-        if (lane < k) emit<T>(s + lane, v, box, pos_src, vel_src, id_src, pos_out, vel_out, id_out, perm);
-        return;
-    }
-    // larger cells: rank of each element = number of smaller input indices
-    for (uint32_t e0 = 0; e0 < k; e0 += 32) {
-        const bool mine = e0 + lane < k;
-        const uint32_t v = mine ? tmp[s + e0 + lane] : UINT_MAX;
-        uint32_t r = 0;
-        for (uint32_t m0 = 0; m0 < k; m0 += 32) {
-            const uint32_t w = (m0 + lane < k) ? tmp[s + m0 + lane] : UINT_MAX;
-#pragma unroll 8
-            for (int t = 0; t < 32; ++t) r += (__shfl_sync(kFull, w, t) < v) ? 1u : 0u;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < ncell; c += nwarps) {
+        // one warp per cell (the loop bound is uniform per warp)
+        const uint32_t s = cell_start[c], e = cell_start[c + 1];
+        const uint32_t k = e - s;
+        if (k == 0) continue;
+        if (k <= 32) {
+            uint32_t v = lane < k ? tmp[s + lane] : UINT_MAX;
+            v = warp_sort32(v);
+            if (lane < k) emit<T>(s + lane, v, box, pos_src, vel_src, id_src, pos_out, vel_out, id_out, perm);
+            continue;
         }
-        if (mine) emit<T>(s + r, v, box, pos_src, vel_src, id_src, pos_out, vel_out, id_out, perm);
+        // larger cells: rank of each element = number of smaller input indices
+        for (uint32_t e0 = 0; e0 < k; e0 += 32) {
+            const bool mine = e0 + lane < k;
+            const uint32_t v = mine ? tmp[s + e0 + lane] : UINT_MAX;
+            uint32_t r = 0;
+            for (uint32_t m0 = 0; m0 < k; m0 += 32) {
+                const uint32_t w = (m0 + lane < k) ? tmp[s + m0 + lane] : UINT_MAX;
+#pragma unroll 8
+                for (int t = 0; t < 32; ++t) r += (__shfl_sync(kFull, w, t) < v) ? 1u : 0u;
+            }
+            if (mine) emit<T>(s + r, v, box, pos_src, vel_src, id_src, pos_out, vel_out, id_out, perm);
+        }
     }
 }
 
@@ -278,17 +284,17 @@ static fpm_status celllist_launch(const fpm_box &b, const fpm_grid &g, int n, co
     const int ntiles = (ncell + kScanTile - 1) / kScanTile;
     k_zero<<<(ncell + 255) / 256 < 1184 ? (ncell + 255) / 256 : 1184, 256, 0, stream>>>(count, ncell, gate);
     if (n > 0)
-        k_bin<T><<<(n + 255) / 256, 256, 0, stream>>>(box, grid, n, pin, vin, id_in, spos, svel, sid, cell, rank,
+        k_bin<T><<<grid_cap((n + 255) / 256), 256, 0, stream>>>(box, grid, n, pin, vin, id_in, spos, svel, sid, cell, rank,
                                                       count, st, gate);
     k_scan_part<<<ntiles, kScanThreads, 0, stream>>>(count, ncell, tiles, gate);
     k_scan_final<<<ntiles, kScanThreads, 0, stream>>>(count, ncell, tiles, cell_start, n, gate);
     if (n > 0) {
-        k_scatter<<<(n + 255) / 256, 256, 0, stream>>>(n, cell, rank, cell_start, tmp, gate);
+        k_scatter<<<grid_cap((n + 255) / 256), 256, 0, stream>>>(n, cell, rank, cell_start, tmp, gate);
         const V4<T> *psrc = spos ? spos : pin;
         const V4<T> *vsrc = svel ? svel : vin;
         const uint32_t *isrc = sid ? sid : id_in;
         const int64_t threads = (int64_t)ncell * 32;
-        k_sort_gather<T><<<(unsigned)((threads + 255) / 256), 256, 0, stream>>>(
+        k_sort_gather<T><<<grid_cap((threads + 255) / 256), 256, 0, stream>>>(
             box, ncell, cell_start, tmp, psrc, vel_out ? vsrc : nullptr, isrc, (V4<T> *)pos_out,
             (V4<T> *)vel_out, id_out, perm, gate);
     }

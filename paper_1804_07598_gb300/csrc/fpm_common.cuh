@@ -250,4 +250,9 @@ __device__ void grid_reduce(TV (&v)[NV], double *part, unsigned *counter, double
 // Host-side error plumbing (api.cu).
 fpm_status fpm_fail(fpm_status s, const char *fmt, ...);
 fpm_status fpm_check_launch(const char *what);
+
+// Grid of a grid-stride kernel: `want` blocks, capped at 8 per SM.  The
+// gated rebuild kernels use it, so that a launch whose gate is off retires
+// in one short wave instead of one block per particle, cell or tile.
+int grid_cap(long long want);
 fpm_status fpm_check_grid(const fpm_box *box, const fpm_grid *grid, const char *who);

@@ -51,12 +51,13 @@ __device__ __forceinline__ float tait(const SphK &K, float drho)
     return K.b * (s * x);
 }
 
-// (dW/dr)/r for r2 inside the support.
+// (dW/dr)/r for r2 inside the support; KK = 0 Wendland C2, 1 cubic spline.
+template <int KK>
 __device__ __forceinline__ float grad_factor(const SphK &K, float r2)
 {
     const float ir = rsqrtf(r2);
     const float q = r2 * ir * K.inv_h;
-    if (K.kernel == 0) {
+    if (KK == 0) {
         const float t = 1.0f - 0.5f * q;
         return K.wcoef * t * t * t;
     }
@@ -65,11 +66,11 @@ __device__ __forceinline__ float grad_factor(const SphK &K, float r2)
     return q < 1.0f ? K.wcoef * (-3.0f + 2.25f * q) : -0.75f * K.wcoef * t * t * sph_rcp(q);
 }
 
-template <bool FAST, bool SMEM>
+template <bool FAST, bool SMEM, int KK>
 __device__ __forceinline__ void sph_pair(const TileCfg &cfg, const BoxT<float> &box, const TileDesc &d,
                                          const float4 *__restrict__ pos, const float4 *__restrict__ vr,
                                          const float4 *__restrict__ st, const float4 *__restrict__ sv,
-                                         const float4 &pi, const float4 &vi, float rho_i, float Pi_over, int s,
+                                         const float4 &pi, const float4 &vi, float rho_i, float P_i, int s,
                                          const SphK &K, float &ax, float &ay, float &az, float &dr, float &mumax)
 {
     float4 pj, vj;
@@ -83,7 +84,7 @@ __device__ __forceinline__ void sph_pair(const TileCfg &cfg, const BoxT<float> &
     float dx, dy, dz;
     const float r2 = tile_sep<FAST>(pi, pj, box, cfg, dx, dy, dz);
     const bool in = r2 < K.two_h2 && r2 > 0.0f;
-    const float F = in ? grad_factor(K, r2) : 0.0f;
+    const float F = in ? grad_factor<KK>(K, r2) : 0.0f;
     const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
     const float vdr = vx * dx + vy * dy + vz * dz;
     dr += K.m * F * vdr;
@@ -92,14 +93,14 @@ __device__ __forceinline__ void sph_pair(const TileCfg &cfg, const BoxT<float> &
     const float inv_rr = sph_rcp(rho_i * rho_j);
     const float mu = K.h * vdr * sph_rcp(r2 + K.eta2);
     const float visc = vdr < 0.0f ? -K.alpha * K.c0 * mu * 2.0f * sph_rcp(rho_i + rho_j) : 0.0f;
-    const float c = -K.m * ((Pi_over + Pj) * inv_rr + visc) * F;
+    const float c = -K.m * ((P_i + Pj) * inv_rr + visc) * F;
     ax += c * dx;
     ay += c * dy;
     az += c * dz;
     if (in) mumax = fmaxf(mumax, fabsf(mu));
 }
 
-template <bool FAST, bool SMEM>
+template <bool FAST, bool SMEM, int KK>
 __device__ __forceinline__ void sph_sweep(const TileCfg &cfg, const BoxT<float> &box, const TileDesc &d,
                                           const float4 *__restrict__ pos, const float4 *__restrict__ vr,
                                           const float4 *__restrict__ st, const float4 *__restrict__ sv,
@@ -107,18 +108,14 @@ __device__ __forceinline__ void sph_sweep(const TileCfg &cfg, const BoxT<float> 
                                           const uint32_t *__restrict__ col, int64_t ld, const SphK &K, float &ax,
                                           float &ay, float &az, float &dr, float &mumax)
 {
-    for (uint32_t wi = 0; wi < (m + 1u) >> 1; ++wi) {
-        const uint32_t wv = __ldcs(col + (int64_t)wi * ld);
-        sph_pair<FAST, SMEM>(cfg, box, d, pos, vr, st, sv, pi, vi, rho_i, Pi, (int)(wv & 0xffffu), K, ax, ay, az, dr,
-                             mumax);
-        if (2u * wi + 1u < m)
-            sph_pair<FAST, SMEM>(cfg, box, d, pos, vr, st, sv, pi, vi, rho_i, Pi, (int)(wv >> 16), K, ax, ay, az,
-                                 dr, mumax);
-    }
+    for_each_entry<4>(m, col, ld, [&](int s) {
+        sph_pair<FAST, SMEM, KK>(cfg, box, d, pos, vr, st, sv, pi, vi, rho_i, Pi, s, K, ax, ay, az, dr, mumax);
+    });
 }
 
 // The sweep of a tile whose neighbourhood did not fit in shared memory (rare;
 // out of line so that it does not add to the registers of the common path).
+template <int KK>
 __device__ __noinline__ void sph_sweep_spilled(const TileCfg &cfg, const BoxT<float> &box, const TileDesc &d,
                                                const float4 *__restrict__ pos, const float4 *__restrict__ vr,
                                                const float4 &pi, const float4 &vi, float rho_i, float P_i,
@@ -126,8 +123,8 @@ __device__ __noinline__ void sph_sweep_spilled(const TileCfg &cfg, const BoxT<fl
                                                const SphK &K, float *out5)
 {
     float ax = 0.0f, ay = 0.0f, az = 0.0f, dr = 0.0f, mumax = 0.0f;
-    sph_sweep<false, false>(cfg, box, d, pos, vr, nullptr, nullptr, pi, vi, rho_i, P_i, m, col, ld, K, ax, ay, az, dr,
-                            mumax);
+    sph_sweep<false, false, KK>(cfg, box, d, pos, vr, nullptr, nullptr, pi, vi, rho_i, P_i, m, col, ld, K, ax, ay, az,
+                                dr, mumax);
     out5[0] = ax;
     out5[1] = ay;
     out5[2] = az;
@@ -135,7 +132,8 @@ __device__ __noinline__ void sph_sweep_spilled(const TileCfg &cfg, const BoxT<fl
     out5[4] = mumax;
 }
 
-__global__ void __launch_bounds__(kTileThreads, 4)
+template <int KK>
+__global__ void __launch_bounds__(kTileThreads, 3)
     k_sph_tiles(TileCfg cfg, BoxT<float> box, const float4 *__restrict__ pos, const float4 *__restrict__ vr,
                 ListView lv, const uint32_t *__restrict__ nn, int64_t ld, int stage_cap, SphK K,
                 float4 *__restrict__ acc, float *dtcons, Sched sched, fpm_dev_status *status)
@@ -168,14 +166,14 @@ __global__ void __launch_bounds__(kTileThreads, 4)
         float ax = 0.0f, ay = 0.0f, az = 0.0f, dr = 0.0f;
         if (in_smem) {
             if (d.slow)
-                sph_sweep<false, true>(cfg, box, d, pos, vr, sp, sv, pi, vi, rho_i, P_i, m, words + i, ld, K, ax, ay,
-                                       az, dr, mumax);
+                sph_sweep<false, true, KK>(cfg, box, d, pos, vr, sp, sv, pi, vi, rho_i, P_i, m, words + i, ld, K, ax,
+                                           ay, az, dr, mumax);
             else
-                sph_sweep<true, true>(cfg, box, d, pos, vr, sp, sv, pi, vi, rho_i, P_i, m, words + i, ld, K, ax, ay,
-                                      az, dr, mumax);
+                sph_sweep<true, true, KK>(cfg, box, d, pos, vr, sp, sv, pi, vi, rho_i, P_i, m, words + i, ld, K, ax,
+                                          ay, az, dr, mumax);
         } else {
             float o5[5];
-            sph_sweep_spilled(cfg, box, d, pos, vr, pi, vi, rho_i, P_i, m, words + i, ld, K, o5);
+            sph_sweep_spilled<KK>(cfg, box, d, pos, vr, pi, vi, rho_i, P_i, m, words + i, ld, K, o5);
             ax = o5[0];
             ay = o5[1];
             az = o5[2];
@@ -364,13 +362,18 @@ extern "C" fpm_status fpm_sph_forces(const fpm_box *box, const fpm_grid *grid, i
     if (s != FPM_OK) return s;
     const TileCfg cfg = make_tile_cfg(*box, *grid);
     const ListLayout L = list_layout(n, cfg, cap);
-    const int sc = stage_capacity(n, *grid, 2 * sizeof(float4));
-    const size_t smem = 2 * (size_t)sc * sizeof(float4);
-    smem_opt_in((const void *)k_sph_tiles);
-    const int blocks = persistent_blocks((const void *)k_sph_tiles, kTileThreads, smem, *grid, cfg.ntiles);
-    k_sph_tiles<<<blocks, kTileThreads, smem, (cudaStream_t)stream>>>(
+    // staged per neighbour: position, velocity + drho
+    const size_t per = 2 * sizeof(float4);
+    const int sc = stage_capacity(n, *grid, per);
+    const size_t smem = (size_t)sc * per;
+    const SphK K = make_sph(*params);
+    const void *kern = K.kernel == 0 ? (const void *)k_sph_tiles<0> : (const void *)k_sph_tiles<1>;
+    smem_opt_in(kern);
+    const int blocks = persistent_blocks(kern, kTileThreads, smem, *grid, cfg.ntiles);
+    auto launch = K.kernel == 0 ? k_sph_tiles<0> : k_sph_tiles<1>;
+    launch<<<blocks, kTileThreads, smem, (cudaStream_t)stream>>>(
         cfg, make_box<float>(*box), (const float4 *)pos, (const float4 *)vr, list_view(list, L), nn, L.ld, sc,
-        make_sph(*params), (float4 *)acc, d_dtcons, Sched{r.work, r.done}, d_status);
+        K, (float4 *)acc, d_dtcons, Sched{r.work, r.done}, d_status);
     return fpm_check_launch("fpm_sph_forces");
 }
 

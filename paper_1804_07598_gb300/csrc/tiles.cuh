@@ -25,6 +25,8 @@
 // does): the image choice is frozen at build time.
 #pragma once
 
+#include <climits>
+
 #include "fpm_common.cuh"
 
 namespace fpm {
@@ -436,11 +438,51 @@ __device__ __forceinline__ T tile_sep(const V4<T> &pi, const V4<T> &pj, const Bo
     return rfma(dz, dz, rfma(dy, dy, rmul(dx, dx)));
 }
 
-// Verlet-list scan of one home particle i (staged slot `self`): the staged
-// cells t0..t1 of every stencil row, candidates inside r_list written as
-// 16-bit staged indices, two per word (entry k in half k & 1 of word
-// (k >> 1) * ld + i).  Returns the candidate count (entries beyond cap are
-// counted, not stored).
+// Calls f(s) for each of the m 16-bit entries of one particle's list (the
+// column `col` of the ELL words, leading dimension ld).  The 32-bit words
+// are loaded kChunk at a time, one chunk ahead of their use, so that the
+// loads' latency overlaps the pair arithmetic of the previous chunk; whole
+// chunks run without per-entry guards.
+template <uint32_t kChunk, typename F>
+__device__ __forceinline__ void for_each_entry(uint32_t m, const uint32_t *__restrict__ col, int64_t ld, F &&f)
+{
+    const uint32_t nw = (m + 1u) >> 1;
+    const uint32_t nfull = (m >> 1) / kChunk * kChunk;  // words whose both entries exist, in whole chunks
+    uint32_t cur[kChunk], nxt[kChunk];
+    const uint32_t *p = col;  // next word to load
+#pragma unroll
+    for (uint32_t q = 0; q < kChunk; ++q) {
+        cur[q] = q < nfull ? __ldcs(p) : 0u;
+        p += ld;
+    }
+    for (uint32_t w0 = 0; w0 < nfull; w0 += kChunk) {
+        const bool more = w0 + kChunk < nfull;
+#pragma unroll
+        for (uint32_t q = 0; q < kChunk; ++q) {
+            nxt[q] = more ? __ldcs(p) : 0u;
+            p += ld;
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < kChunk; ++q) {
+            f((int)(cur[q] & 0xffffu));
+            f((int)(cur[q] >> 16));
+        }
+#pragma unroll
+        for (uint32_t q = 0; q < kChunk; ++q) cur[q] = nxt[q];
+    }
+    for (uint32_t wi = nfull; wi < nw; ++wi) {
+        const uint32_t wv = __ldcs(col + (int64_t)wi * ld);
+        f((int)(wv & 0xffffu));
+        if (2u * wi + 1u < m) f((int)(wv >> 16));
+    }
+}
+
+// Verlet-list scan of one home particle i (staged slot `self`) over the
+// staged cells t0..t1 of every stencil row (its 27 cells): every candidate
+// inside r_list is written as a 16-bit staged index, two per word (entry k
+// in half k & 1 of word (k >> 1) * ld + i).  Returns the candidate count
+// (entries beyond cap are counted, not stored).  The append is branch-free
+// (a select and one predicated store), so the lanes of a warp stay converged.
 template <bool FAST, bool SMEM, typename T>
 __device__ __forceinline__ uint32_t scan_candidates(const TileCfg &cfg, const BoxT<T> &box, const TileGeom &g,
                                                     const TileDesc &d, const V4<T> *__restrict__ pos,
@@ -449,23 +491,22 @@ __device__ __forceinline__ uint32_t scan_candidates(const TileCfg &cfg, const Bo
                                                     uint32_t *__restrict__ words)
 {
     uint32_t cnt = 0, pending = 0;
+    const uint32_t ucap = (uint32_t)cap;
     for (int r = 0; r < g.nrows; ++r) {
         const int s0 = g.off[r][t0], s1 = g.off[r][t1 + 1];
         for (int s = s0; s < s1; ++s) {
-            if (s == self) continue;
             const V4<T> pj = SMEM ? st[s] : staged_global(d, box, pos, s);
             T dx, dy, dz;
             const T r2 = tile_sep<FAST>(pi, pj, box, cfg, dx, dy, dz);
-            if (r2 < rl2) {
-                if (cnt < (uint32_t)cap) {
-                    if (cnt & 1u) words[(int64_t)(cnt >> 1) * ld + i] = pending | ((uint32_t)s << 16);
-                    else pending = (uint32_t)s;
-                }
-                ++cnt;
-            }
+            const bool hit = (r2 < rl2) & (s != self);
+            const bool room = cnt < ucap;
+            const bool odd = (cnt & 1u) != 0u;
+            if (hit & room & odd) words[(int64_t)(cnt >> 1) * ld + i] = pending | ((uint32_t)s << 16);
+            pending = (hit & room & !odd) ? (uint32_t)s : pending;
+            cnt += hit ? 1u : 0u;
         }
     }
-    const uint32_t stored = cnt < (uint32_t)cap ? cnt : (uint32_t)cap;
+    const uint32_t stored = cnt < ucap ? cnt : ucap;
     if (stored & 1u) words[(int64_t)(stored >> 1) * ld + i] = pending;
     return cnt;
 }

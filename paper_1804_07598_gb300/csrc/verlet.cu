@@ -20,12 +20,15 @@ __global__ void __launch_bounds__(128)
     if (gated_off(gate)) return;
     __shared__ TileGeom g;
     __shared__ TileDesc d;
-    tile_geometry(cfg, blockIdx.x, cs, g, d);
-    const int nw = (int)(sizeof(TileDesc) / 4);
-    uint32_t *o = (uint32_t *)(descs + blockIdx.x);
-    const uint32_t *s = (const uint32_t *)&d;
-    for (int k = threadIdx.x; k < nw; k += blockDim.x) o[k] = s[k];
-    if (threadIdx.x == 0 && st && d.h1 > d.h0) atomicMax(&st->max_staged, (uint32_t)d.M);
+    for (int tile = blockIdx.x; tile < cfg.ntiles; tile += gridDim.x) {
+        tile_geometry(cfg, tile, cs, g, d);
+        const int nw = (int)(sizeof(TileDesc) / 4);
+        uint32_t *o = (uint32_t *)(descs + tile);
+        const uint32_t *s = (const uint32_t *)&d;
+        for (int k = threadIdx.x; k < nw; k += blockDim.x) o[k] = s[k];
+        if (threadIdx.x == 0 && st && d.h1 > d.h0) atomicMax(&st->max_staged, (uint32_t)d.M);
+        __syncthreads();  // d and g are rewritten for the next tile
+    }
 }
 
 // Phase 2, one block: the non-empty tiles in increasing order (a block-wide
@@ -181,7 +184,7 @@ static fpm_status verlet_launch(const fpm_box &b, const fpm_grid &g, int n, cons
         TileDesc *descs = (TileDesc *)(lb + L.off_tiles);
         uint32_t *active = (uint32_t *)(lb + L.off_active);
         uint32_t *count = (uint32_t *)lb;
-        k_tile_desc<<<cfg.ntiles, 128, 0, stream>>>(cfg, cs, descs, st, gate);
+        k_tile_desc<<<grid_cap(cfg.ntiles), 128, 0, stream>>>(cfg, cs, descs, st, gate);
         k_tile_compact<<<1, 1024, 0, stream>>>(descs, cfg.ntiles, active, count, gate);
         const size_t smem = (size_t)sc * sizeof(V4<T>);
         smem_opt_in((const void *)k_verlet_scan<T>);

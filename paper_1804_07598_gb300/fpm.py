@@ -21,6 +21,8 @@ FPM_OK, FPM_ERR_INVALID, FPM_ERR_CAPACITY, FPM_ERR_DOMAIN, FPM_ERR_CUDA, FPM_ERR
 FPM_F32, FPM_F64 = 0, 1
 FPM_FLAG_CAPACITY, FPM_FLAG_DOMAIN, FPM_FLAG_TIMEOUT = 1, 2, 4
 STATUS_BYTES = 64
+# int32 word of fpm_dev_status.max_staged in a status tensor
+STATUS_MAX_STAGED = 6
 
 _c = ctypes
 _VP = _c.c_void_p

@@ -70,6 +70,23 @@ class LJSystem:
         self.size_staging()
         self.compute_forces()
 
+    def retile(self, tiles_x, sweep_blocks=None):
+        """New number of tiles per cell row (a launch-shape choice):
+        reallocates the list, rebuilds it and resizes the staging
+        (synchronises)."""
+        self.grid.tiles_x = int(tiles_x)
+        self.grid.stage_cap = 0
+        if sweep_blocks is not None:
+            self.grid.sweep_blocks = int(sweep_blocks)
+        self.nbr = torch.zeros(fpm.fpm_verlet_list_bytes(self.n, self.grid, self.cap), dtype=torch.uint8,
+                               device=self.device)
+        self.ws_red = torch.zeros(fpm.fpm_reduce_workspace(self.n, self.grid), dtype=torch.uint8, device=self.device)
+        self._graph = None
+        self.status[fpm.STATUS_MAX_STAGED] = 0  # the staging size follows the new tiles
+        self.rebuild()
+        self.size_staging()
+        self.compute_forces()
+
     def size_staging(self, margin: float = 1.15):
         """Set the grid's shared-memory staging capacity from the largest tile
         neighbourhood the last Verlet build saw (synchronises)."""

@@ -22,7 +22,8 @@ from . import fpm
 
 class SPHSystem:
     def __init__(self, pos, vel, rho, L, h, m, rho0=1000.0, c0=None, gamma=7.0, alpha=0.1, g=(0.0, 0.0, -9.81),
-                 kernel="wendland", periodic=(0, 0, 0), skin=None, cfl=0.2, cap=None, h_swl=0.3, device="cuda"):
+                 kernel="wendland", periodic=(0, 0, 0), skin=None, cfl=0.2, cap=None, h_swl=0.3, tile_target=170,
+                 device="cuda"):
         self.device = torch.device(device)
         pos = np.asarray(pos, np.float64)
         n = pos.shape[0]
@@ -42,12 +43,8 @@ class SPHSystem:
         self.skin = float(skin) if skin is not None else 0.25 * h
         self.r_list = 2.0 * h + self.skin
         self.grid = fpm.fpm_grid_make(self.box, self.r_list, n)
-        # tiles sized for the fluid's own density (the box is mostly empty):
-        # about 170 particles per tile at one particle per dp^3
-        dp = (m / rho0) ** (1.0 / 3.0)
-        per_cell = (self.L[0] / self.grid.nc[0]) * (self.L[1] / self.grid.nc[1]) * (self.L[2] / self.grid.nc[2]) / dp ** 3
-        width = int(min(14, max(1, round(170.0 / per_cell))))
-        self.grid.tiles_x = (self.grid.nc[0] + width - 1) // width
+        self._dp = (m / rho0) ** (1.0 / 3.0)
+        self._set_tiles(tile_target)
         self.cap = int(cap) if cap else max(32, int(math.ceil(1.6 * 4.0 / 3.0 * math.pi * (self.r_list / (m / rho0)
                                                                                            ** (1 / 3)) ** 3 / 8)) * 8)
         dev = self.device
@@ -75,6 +72,30 @@ class SPHSystem:
         self.dt = torch.zeros(1, dtype=f32, device=dev)
         self.ws_red = torch.zeros(fpm.fpm_reduce_workspace(n, self.grid), dtype=torch.uint8, device=dev)
         self._graph = None
+        self.rebuild()
+        self.size_staging()
+
+    def _set_tiles(self, tile_target):
+        """Tile width for about `tile_target` particles per tile at the
+        fluid's own density (the box is mostly empty)."""
+        g = self.grid
+        per_cell = (self.L[0] / g.nc[0]) * (self.L[1] / g.nc[1]) * (self.L[2] / g.nc[2]) / self._dp ** 3
+        width = int(min(14, max(1, round(float(tile_target) / per_cell))))
+        g.tiles_x = (g.nc[0] + width - 1) // width
+        g.stage_cap = 0
+        self.tile_target = int(tile_target)
+
+    def retile(self, tile_target, sweep_blocks=None):
+        """New tile width (a launch-shape choice): reallocates the list,
+        rebuilds it and resizes the staging (synchronises)."""
+        self._set_tiles(tile_target)
+        if sweep_blocks is not None:
+            self.grid.sweep_blocks = int(sweep_blocks)
+        self.nbr = torch.zeros(fpm.fpm_verlet_list_bytes(self.n, self.grid, self.cap), dtype=torch.uint8,
+                               device=self.device)
+        self.ws_red = torch.zeros(fpm.fpm_reduce_workspace(self.n, self.grid), dtype=torch.uint8, device=self.device)
+        self._graph = None
+        self.status[fpm.STATUS_MAX_STAGED] = 0  # the staging size follows the new tiles
         self.rebuild()
         self.size_staging()
 
