@@ -387,15 +387,17 @@ fpm_status fpm_lj_backward(const fpm_box *box, const fpm_grid *grid, int32_t n, 
 
 /* One reverse velocity-Verlet update of the FP64 adjoint state (xbar, vbar:
  * double4 [n]).  For every k, with j = perm[k] (perm from the cell-list build
- * that reordered the particles during this step) or j = k (perm NULL):
+ * that reordered the particles during this step) or j = k (perm NULL, or
+ * d_gate given and *d_gate == 0):
  *   xbar_out[j] = xbar_in[k];  vbar_out[j] = vbar_in[k] + dt * xbar_in[k];
  *   a_out[j] = (T)(c * vbar_out[j])   (float4|double4, the vector for the next
  *                                      fpm_lj_backward).
- * With perm, inputs and outputs must be distinct arrays; without, they may
- * alias. */
-fpm_status fpm_vv_adjoint(int32_t n, fpm_prec prec, const uint32_t *perm, double dt, double c,
-                          const double *xbar_in, const double *vbar_in, double *xbar_out, double *vbar_out,
-                          void *a_out, fpm_stream stream);
+ * d_gate (device word, may be NULL) lets a captured graph apply perm only in
+ * the steps whose rebuild ran.  With perm, inputs and outputs must be
+ * distinct arrays; without, they may alias. */
+fpm_status fpm_vv_adjoint(int32_t n, fpm_prec prec, const uint32_t *perm, const uint32_t *d_gate, double dt,
+                          double c, const double *xbar_in, const double *vbar_in, double *xbar_out,
+                          double *vbar_out, void *a_out, fpm_stream stream);
 
 /* Seed of the loss L = U(x_T) + sum_i |F_i(x_T)|^2: xbar = -F, vbar = 0,
  * a_out = F (so that fpm_lj_backward(a_out, scale = 2) adds 2 J F and

@@ -5,22 +5,26 @@ behind a torch.autograd.Function, with step checkpointing and recomputation.
 Loss: L = U(x_T) + sum_i |F_i(x_T)|^2 after T NVE steps from (x0, v0).
 Gradients: dL/dx0, dL/dv0, dL/deps, dL/dsigma.
 
-Forward: T steps of LJSystem; every `every` steps the full state (positions,
+Forward: T steps of LJSystem in segments of `every` steps, each segment one
+CUDA-graph replay; before each segment the full state (positions,
 velocities, ids, reference positions, force, cell list and Verlet list) is
-copied aside.  Backward, segment by segment from the last: restore the
-checkpoint, recompute the segment (bit-identical: every kernel is
-deterministic), keeping each step's positions, the list in force at each step
-and the permutation of each rebuild, then walk the steps in reverse:
+copied aside on the device.  Backward, segment by segment from the last:
+restore the checkpoint and replay a recording graph of the segment
+(bit-identical to the forward: every kernel is deterministic) that also keeps
+each step's positions, the list in force at each step, the permutation of
+the step's cell-list build and whether that build ran; then replay a reverse
+graph of the segment:
 
     seed      xbar = -F_T + 2 J(x_T) F_T,  vbar = 0,  thbar = dU/dth + 2 F_T.dF/dth
-    step n    undo the reorder of step n's rebuild (if any); vbar += dt xbar;
-              xbar += J(x_n) (c vbar);  thbar += (c vbar).dF/dth(x_n)
-              with c = dt, and c = dt/2 for n = 0
+    step n    undo the reorder of step n's rebuild (if it ran: a device-side
+              gate); vbar += dt xbar; xbar += J(x_n) (c vbar);
+              thbar += (c vbar).dF/dth(x_n), with c = dt, and c = dt/2 for n = 0
 
 (the two half-kick terms that meet at x_n are merged into one sweep with
 c = dt).  The adjoint state is FP64; pair arithmetic is in the positions'
-precision.  Every numeric step runs in libfpm's kernels; this module only
-orders the calls and keeps the buffers.
+precision.  No host synchronisation inside either pass: the rebuild
+decisions stay on the device.  Every numeric step runs in libfpm's kernels;
+this module only orders the calls and keeps the buffers.
 """
 from __future__ import annotations
 
@@ -31,6 +35,20 @@ from . import fpm
 from .md import LJSystem
 
 _STATE = ("pos", "vel", "ids", "pos_ref", "force", "cell_start", "nbr", "nn")
+_REBUILD_WORD = 2  # int32 word of fpm_dev_status.rebuild in a status tensor
+
+
+def _capture(fn):
+    """fn() captured into a CUDA graph on a side stream (nothing runs)."""
+    torch.cuda.synchronize()
+    st = torch.cuda.Stream()
+    st.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(st):
+        with torch.cuda.graph(g, stream=st):
+            fn()
+    torch.cuda.current_stream().wait_stream(st)
+    return g
 
 
 class LJAdjointRunner:
@@ -40,11 +58,19 @@ class LJAdjointRunner:
                             precision=precision, cap=cap)
         self.nsteps = int(nsteps)
         self.every = max(1, int(every))
-        self.checkpoints = []
+        self.nseg = -(-self.nsteps // self.every)
         self.x_final = None
         s = self.sys
         dev = s.device
         self.adtype = s.dtype
+        self.checkpoints = [{k: torch.empty_like(getattr(s, k)) for k in _STATE} for _ in range(self.nseg)]
+        E = self.every
+        self.xs = [torch.empty_like(s.pos) for _ in range(E + 1)]
+        self.nbrs = [torch.empty_like(s.nbr) for _ in range(E + 1)]
+        self.nns = [torch.empty_like(s.nn) for _ in range(E + 1)]
+        self.perms = [torch.empty_like(s.perm) for _ in range(E)]
+        self.rebuilt = torch.zeros(E, dtype=torch.int32, device=dev)
+        self.rebuilt_total = torch.zeros(1, dtype=torch.int64, device=dev)
         self.xbar = torch.zeros((s.n, 4), dtype=torch.float64, device=dev)
         self.vbar = torch.zeros_like(self.xbar)
         self.xbar2 = torch.zeros_like(self.xbar)
@@ -53,25 +79,40 @@ class LJAdjointRunner:
         self.theta_seed = torch.zeros(4, dtype=torch.float64, device=dev)
         self.theta_steps = torch.zeros(4, dtype=torch.float64, device=dev)
         self.sumf2 = torch.zeros(4, dtype=torch.float64, device=dev)
+        self._graphs = {}
+        self.reorders_undone = 0
+
+    def _seg_len(self, k: int) -> int:
+        return min(self.every, self.nsteps - k * self.every)
+
+    def _graph(self, key, fn):
+        g = self._graphs.get(key)
+        if g is None:
+            g = self._graphs[key] = _capture(fn)
+        return g
 
     # -- forward -----------------------------------------------------------
-    def _save(self):
+    def _save(self, k):
         s = self.sys
-        return {k: getattr(s, k).clone() for k in _STATE}
+        for name in _STATE:
+            self.checkpoints[k][name].copy_(getattr(s, name))
 
-    def _restore(self, ck):
+    def _restore(self, k):
         s = self.sys
-        for k in _STATE:
-            getattr(s, k).copy_(ck[k])
+        for name in _STATE:
+            getattr(s, name).copy_(self.checkpoints[k][name])
         s.status.zero_()
+
+    def _steps(self, L):
+        for _ in range(L):
+            self.sys._step()
 
     def forward(self) -> float:
         s = self.sys
-        self.checkpoints = []
-        for n in range(self.nsteps):
-            if n % self.every == 0:
-                self.checkpoints.append(self._save())
-            s.step(1)
+        for k in range(self.nseg):
+            L = self._seg_len(k)
+            self._save(k)
+            self._graph(("fwd", L), lambda L=L: self._steps(L)).replay()
         s.check_status()
         self.x_final = s.pos.clone()
         return self.loss()
@@ -83,69 +124,68 @@ class LJAdjointRunner:
         return float(s.energy[0].item() + 2.0 * self.sumf2[0].item())
 
     # -- backward ------------------------------------------------------------
-    def _recompute(self, k):
-        """Re-run segment k from its checkpoint; returns per-step positions, the
-        list in force at each step and the permutations of rebuilds."""
+    def _record(self, L):
+        """The forward steps of one segment (the same calls as LJSystem._step)
+        keeping, per step j, x_j, the list in force at x_j, the permutation of
+        the step's cell-list build and its gate word."""
         s = self.sys
-        start = k * self.every
-        end = min(start + self.every, self.nsteps)
-        self._restore(self.checkpoints[k])
-        xs = {start: s.pos.clone()}
-        cur = (s.nbr.clone(), s.nn.clone())
-        lists = {start: cur}
-        perms = {}
-        nr = s.device_status().nrebuild
-        for n in range(start, end):
-            s.step(1)
-            nr1 = s.device_status().nrebuild
-            if nr1 != nr:
-                perms[n] = s.perm.clone()
-                cur = (s.nbr.clone(), s.nn.clone())
-                nr = nr1
-            xs[n + 1] = s.pos.clone()
-            lists[n + 1] = cur
-        s.check_status()
-        return xs, lists, perms, start, end
+        self.xs[0].copy_(s.pos)
+        self.nbrs[0].copy_(s.nbr)
+        self.nns[0].copy_(s.nn)
+        for j in range(L):
+            fpm.fpm_vv_drift_check(s.box, s.n, s.prec, s.dt, s.pos, s.vel, s.force, s.pos_ref, s.skin, s.status)
+            self.rebuilt[j:j + 1].copy_(s.status[_REBUILD_WORD:_REBUILD_WORD + 1])
+            s.rebuild(gated=True)
+            self.perms[j].copy_(s.perm)
+            s.compute_forces()
+            fpm.fpm_vv_step(s.box, s.n, s.prec, 1, s.dt, None, s.vel, s.force)
+            self.xs[j + 1].copy_(s.pos)
+            self.nbrs[j + 1].copy_(s.nbr)
+            self.nns[j + 1].copy_(s.nn)
+        self.rebuilt_total += (self.rebuilt[:L] != 0).sum()
 
-    def _sweep(self, pos, lst, scale, theta):
+    def _sweep(self, j, scale, theta):
         s = self.sys
-        nbr, nn = lst
-        fpm.fpm_lj_backward(s.box, s.grid, s.n, s.prec, pos, nbr, nn, s.cap, s.eps, s.sigma, s.rc, self.avec, scale,
-                            self.xbar, theta, s.ws_red, s.status)
+        fpm.fpm_lj_backward(s.box, s.grid, s.n, s.prec, self.xs[j], self.nbrs[j], self.nns[j], s.cap, s.eps, s.sigma,
+                            s.rc, self.avec, scale, self.xbar, theta, s.ws_red, s.status)
+
+    def _reverse(self, L, first):
+        """The reverse steps of one segment, from xbar/vbar back into them."""
+        s = self.sys
+        dt = s.dt
+        xa, va, xb, vb = self.xbar, self.vbar, self.xbar2, self.vbar2
+        for j in range(L - 1, -1, -1):
+            c = 0.5 * dt if (first and j == 0) else dt
+            fpm.fpm_vv_adjoint(s.n, s.prec, self.perms[j], dt, c, xa, va, xb, vb, self.avec,
+                               d_gate=self.rebuilt[j:j + 1])
+            xa, xb, va, vb = xb, xa, vb, va
+            fpm.fpm_lj_backward(s.box, s.grid, s.n, s.prec, self.xs[j], self.nbrs[j], self.nns[j], s.cap, s.eps,
+                                s.sigma, s.rc, self.avec, 1.0, xa, self.theta_steps, s.ws_red, s.status)
+        if xa is not self.xbar:  # odd segment length: the state ends in the second buffers
+            self.xbar.copy_(xa)
+            self.vbar.copy_(va)
 
     def backward(self):
         """Returns (dL/dx0 [n,3], dL/dv0 [n,3], dL/deps, dL/dsigma) as FP64 tensors,
         rows in the order of the particles given to the constructor."""
         s = self.sys
-        dt = s.dt
         self.theta_seed.zero_()
         self.theta_steps.zero_()
-        self.reorders_undone = 0
-        # seed at x_T (the current state after forward / the last recomputation)
-        segs = list(range(len(self.checkpoints)))
-        xs, lists, perms, start, end = self._recompute(segs[-1])
-        if not torch.equal(xs[end], self.x_final):
-            raise RuntimeError("checkpoint recomputation is not bit-identical to the forward pass")
-        fpm.fpm_adjoint_seed(s.n, s.prec, s.force, self.xbar, self.vbar, self.avec)
-        # xbar += 2 J F; theta[0:2] += 2 F.dF/dth; theta[2:4] += dU/dth
-        self._sweep(xs[end], lists[end], 2.0, self.theta_seed)
-        for k in reversed(segs):
-            if k != segs[-1]:
-                xs, lists, perms, start, end = self._recompute(k)
-            for n in range(end - 1, start - 1, -1):
-                c = dt if n > 0 else 0.5 * dt
-                perm = perms.get(n)
-                if perm is not None:
-                    self.reorders_undone += 1
-                    fpm.fpm_vv_adjoint(s.n, s.prec, perm, dt, c, self.xbar, self.vbar, self.xbar2, self.vbar2,
-                                       self.avec)
-                    self.xbar, self.xbar2 = self.xbar2, self.xbar
-                    self.vbar, self.vbar2 = self.vbar2, self.vbar
-                else:
-                    fpm.fpm_vv_adjoint(s.n, s.prec, None, dt, c, self.xbar, self.vbar, self.xbar, self.vbar,
-                                       self.avec)
-                self._sweep(xs[n], lists[n], 1.0, self.theta_steps)  # J(x_n) (c vbar)
+        self.rebuilt_total.zero_()
+        last = self.nseg - 1
+        for k in range(last, -1, -1):
+            L = self._seg_len(k)
+            self._restore(k)
+            self._graph(("rec", L), lambda L=L: self._record(L)).replay()
+            if k == last:
+                if not torch.equal(self.xs[L], self.x_final):
+                    raise RuntimeError("checkpoint recomputation is not bit-identical to the forward pass")
+                # seed at x_T: xbar = -F, vbar = 0, a = F; xbar += 2 J F; theta += 2 F.dF/dth + dU/dth
+                fpm.fpm_adjoint_seed(s.n, s.prec, s.force, self.xbar, self.vbar, self.avec)
+                self._sweep(L, 2.0, self.theta_seed)
+            self._graph(("rev", L, k == 0), lambda L=L, f=(k == 0): self._reverse(L, f)).replay()
         s.check_status()
+        self.reorders_undone = int(self.rebuilt_total.item())
         # back to the caller's particle order (host-side): sorted slot k holds particle ids[k]
         ids = self.checkpoints[0]["ids"].cpu().numpy().view(np.uint32).astype(np.int64)  # order at step 0
         xb, vb = self.xbar.cpu().numpy(), self.vbar.cpu().numpy()

@@ -174,13 +174,14 @@ __global__ void __launch_bounds__(kTileThreads, 4)
 //   j = perm[k] (or k);  xo[j] = xi[k];  vo[j] = vi[k] + dt xi[k];
 //   a[j] = (T)(c vo[j])  (the vector for the next backward sweep).
 template <typename T>
-__global__ void k_vv_adjoint(int n, const uint32_t *__restrict__ perm, double dt, double c,
-                             const double4_32a *__restrict__ xi, const double4_32a *__restrict__ vi,
+__global__ void k_vv_adjoint(int n, const uint32_t *__restrict__ perm, const uint32_t *__restrict__ gate, double dt,
+                             double c, const double4_32a *__restrict__ xi, const double4_32a *__restrict__ vi,
                              double4_32a *__restrict__ xo, double4_32a *__restrict__ vo, V4<T> *__restrict__ a)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const int j = perm ? (int)perm[k] : k;
+    const bool use = perm != nullptr && (gate == nullptr || *gate != 0u);
+    const int j = use ? (int)perm[k] : k;
     const double4_32a x = xi[k];
     double4_32a v = vi[k];
     v.x += dt * x.x;
@@ -273,9 +274,9 @@ extern "C" fpm_status fpm_lj_backward(const fpm_box *box, const fpm_grid *grid, 
                               d_status, st);
 }
 
-extern "C" fpm_status fpm_vv_adjoint(int32_t n, fpm_prec prec, const uint32_t *perm, double dt, double c,
-                                     const double *xbar_in, const double *vbar_in, double *xbar_out,
-                                     double *vbar_out, void *a_out, fpm_stream stream)
+extern "C" fpm_status fpm_vv_adjoint(int32_t n, fpm_prec prec, const uint32_t *perm, const uint32_t *d_gate,
+                                     double dt, double c, const double *xbar_in, const double *vbar_in,
+                                     double *xbar_out, double *vbar_out, void *a_out, fpm_stream stream)
 {
     if (n < 0 || (n > 0 && (!xbar_in || !vbar_in || !xbar_out || !vbar_out || !a_out)))
         return fpm_fail(FPM_ERR_INVALID, "fpm_vv_adjoint: null pointer or bad size");
@@ -286,11 +287,11 @@ extern "C" fpm_status fpm_vv_adjoint(int32_t n, fpm_prec prec, const uint32_t *p
     cudaStream_t st = (cudaStream_t)stream;
     const unsigned blocks = (unsigned)((n + 255) / 256);
     if (prec == FPM_F32)
-        k_vv_adjoint<float><<<blocks, 256, 0, st>>>(n, perm, dt, c, (const double4_32a *)xbar_in,
+        k_vv_adjoint<float><<<blocks, 256, 0, st>>>(n, perm, d_gate, dt, c, (const double4_32a *)xbar_in,
                                                     (const double4_32a *)vbar_in, (double4_32a *)xbar_out,
                                                     (double4_32a *)vbar_out, (float4 *)a_out);
     else
-        k_vv_adjoint<double><<<blocks, 256, 0, st>>>(n, perm, dt, c, (const double4_32a *)xbar_in,
+        k_vv_adjoint<double><<<blocks, 256, 0, st>>>(n, perm, d_gate, dt, c, (const double4_32a *)xbar_in,
                                                      (const double4_32a *)vbar_in, (double4_32a *)xbar_out,
                                                      (double4_32a *)vbar_out, (double4_32a *)a_out);
     return fpm_check_launch("fpm_vv_adjoint");

@@ -54,45 +54,19 @@ __device__ __forceinline__ void lj_pair(const TileCfg &cfg, const BoxT<T> &box, 
     np += in ? 1u : 0u;
 }
 
+// The LJ sums of one home particle over its list (list words prefetched
+// kLjChunk at a time, see for_each_entry).
+constexpr uint32_t kLjChunk = 4;
+
 template <typename T, bool FAST, bool SMEM>
 __device__ __forceinline__ void lj_sweep(const TileCfg &cfg, const BoxT<T> &box, const TileDesc &d,
                                          const V4<T> *__restrict__ pos, const V4<T> *__restrict__ st,
                                          const V4<T> &pi, uint32_t m, const uint32_t *__restrict__ col, int64_t ld,
                                          const LJParams<T> &P, T &fx, T &fy, T &fz, T &u, T &w, uint32_t &np)
 {
-    // list words are loaded kChunk at a time, one chunk ahead of their use;
-    // full chunks run without per-entry guards
-    constexpr uint32_t kChunk = 4;
-    const uint32_t nw = (m + 1u) >> 1;
-    const uint32_t nfull = (m >> 1) / kChunk * kChunk;  // words whose both entries exist, in whole chunks
-    uint32_t cur[kChunk], nxt[kChunk];
-    const uint32_t *p = col;  // next word to load
-#pragma unroll
-    for (uint32_t q = 0; q < kChunk; ++q) {
-        cur[q] = q < nfull ? __ldcs(p) : 0u;
-        p += ld;
-    }
-    for (uint32_t w0 = 0; w0 < nfull; w0 += kChunk) {
-        const bool more = w0 + kChunk < nfull;
-#pragma unroll
-        for (uint32_t q = 0; q < kChunk; ++q) {
-            nxt[q] = more ? __ldcs(p) : 0u;
-            p += ld;
-        }
-#pragma unroll
-        for (uint32_t q = 0; q < kChunk; ++q) {
-            lj_pair<T, FAST, SMEM>(cfg, box, d, pos, st, pi, (int)(cur[q] & 0xffffu), P, fx, fy, fz, u, w, np);
-            lj_pair<T, FAST, SMEM>(cfg, box, d, pos, st, pi, (int)(cur[q] >> 16), P, fx, fy, fz, u, w, np);
-        }
-#pragma unroll
-        for (uint32_t q = 0; q < kChunk; ++q) cur[q] = nxt[q];
-    }
-    for (uint32_t wi = nfull; wi < nw; ++wi) {
-        const uint32_t wv = __ldcs(col + (int64_t)wi * ld);
-        lj_pair<T, FAST, SMEM>(cfg, box, d, pos, st, pi, (int)(wv & 0xffffu), P, fx, fy, fz, u, w, np);
-        if (2u * wi + 1u < m)
-            lj_pair<T, FAST, SMEM>(cfg, box, d, pos, st, pi, (int)(wv >> 16), P, fx, fy, fz, u, w, np);
-    }
+    for_each_entry<kLjChunk>(m, col, ld, [&](int s) {
+        lj_pair<T, FAST, SMEM>(cfg, box, d, pos, st, pi, s, P, fx, fy, fz, u, w, np);
+    });
 }
 
 }  // namespace fpm

@@ -117,8 +117,8 @@ _SIG = {
     "fpm_lj_backward": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _c.c_int, _VP, _VP, _VP,
                                    _c.c_int32, _c.c_double, _c.c_double, _c.c_double, _VP, _c.c_double, _VP, _VP,
                                    _VP, _c.c_size_t, _VP, _VP]),
-    "fpm_vv_adjoint": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _c.c_double, _c.c_double, _VP, _VP, _VP, _VP, _VP,
-                                  _VP]),
+    "fpm_vv_adjoint": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _VP, _c.c_double, _c.c_double, _VP, _VP, _VP, _VP,
+                                  _VP, _VP]),
     "fpm_adjoint_seed": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _VP, _VP, _VP, _VP]),
     "fpm_kinetic": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _VP, _VP, _c.c_size_t, _VP]),
     "fpm_batch_plan": (_c.c_int, [_c.c_int32, _c.POINTER(fpm_box), _c.POINTER(_c.c_int32), _c.c_double, _c.c_int32,
@@ -338,9 +338,9 @@ def fpm_lj_backward(box, grid, n, prec, pos, list_obj, nn, cap, eps, sigma, rc, 
     _count(1 if n > 0 else 0)
 
 
-def fpm_vv_adjoint(n, prec, perm, dt, c, xbar_in, vbar_in, xbar_out, vbar_out, a_out, stream=None):
-    _check(lib().fpm_vv_adjoint(int(n), int(prec), _ptr(perm), float(dt), float(c), _ptr(xbar_in), _ptr(vbar_in),
-                                _ptr(xbar_out), _ptr(vbar_out), _ptr(a_out), _stream(stream)))
+def fpm_vv_adjoint(n, prec, perm, dt, c, xbar_in, vbar_in, xbar_out, vbar_out, a_out, d_gate=None, stream=None):
+    _check(lib().fpm_vv_adjoint(int(n), int(prec), _ptr(perm), _ptr(d_gate), float(dt), float(c), _ptr(xbar_in),
+                                _ptr(vbar_in), _ptr(xbar_out), _ptr(vbar_out), _ptr(a_out), _stream(stream)))
     _count(1 if n > 0 else 0)
 
 
