@@ -389,6 +389,7 @@ __global__ void __launch_bounds__(kTileThreads)
         float usum = 0.0f, wsum = 0.0f;
         uint32_t npsum = 0;
         if (d.h1 > d.h0) {
+            if (d.h0 + threadIdx.x < d.h1) prefetch_home(pos, nn, words, ld, d.h0 + threadIdx.x, (int)kLjChunk);
             const bool in_smem = d.M <= stage_cap;
             if (!in_smem) note_spill(status);
             const bool staged = in_smem ? stage_positions(d, box, pos, sp, &bar, phase, status) : true;

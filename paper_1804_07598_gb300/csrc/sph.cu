@@ -154,6 +154,10 @@ __global__ void __launch_bounds__(kTileThreads, 3)
     for (uint32_t k = blockIdx.x; k < ntodo; k = ticket_next(ahead, &s_k)) {
         ahead = ticket_ahead(sched);
     load_desc(lv.descs + lv.active[k], d);
+    if (d.h0 + threadIdx.x < d.h1) {
+        prefetch_home(pos, nn, words, ld, d.h0 + threadIdx.x, 4);
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(vr + d.h0 + threadIdx.x));
+    }
     const bool in_smem = d.M <= stage_cap;
     if (!in_smem) note_spill(status);
     const bool staged = in_smem ? stage_positions(d, box, pos, sp, &bar, phase, status, vr, sv) : true;

@@ -438,6 +438,18 @@ __device__ __forceinline__ T tile_sep(const V4<T> &pi, const V4<T> &pj, const Bo
     return rfma(dz, dz, rfma(dy, dy, rmul(dx, dx)));
 }
 
+// Fire-and-forget L2 prefetch of the first list words (k = 0 .. 2*nwords-1),
+// the position and the entry count of home particle i, issued before a
+// tile's staging wait so that the sweep's first loads hit in L2.
+template <typename V>
+__device__ __forceinline__ void prefetch_home(const V *pos, const uint32_t *nn, const uint32_t *words, int64_t ld,
+                                              uint32_t i, int nwords)
+{
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(pos + i));
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(nn + i));
+    for (int q = 0; q < nwords; ++q) asm volatile("prefetch.global.L2 [%0];" ::"l"(words + (int64_t)q * ld + i));
+}
+
 // Calls f(s) for each of the m 16-bit entries of one particle's list (the
 // column `col` of the ELL words, leading dimension ld).  The 32-bit words
 // are loaded kChunk at a time, one chunk ahead of their use, so that the

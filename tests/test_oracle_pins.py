@@ -4,6 +4,7 @@ the oracle (a dropped term, a wrong sign or index, a transposed operand) would
 fail it.
 """
 import itertools
+import os
 import math
 
 import numpy as np
@@ -295,3 +296,41 @@ def test_max_disp():
     pos[1, 1] += 0.16
     flag, m = oracle.max_disp(pos, ref, L, PER, 0.3)
     assert flag == 1
+
+
+def _golden(name):
+    vals = {}
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                k, v = line.split("=")
+                vals[k.strip()] = float(v)
+    return vals
+
+
+@pytest.mark.parametrize("m,R,d", [(11, 7.1, 1.1), (12, 8.1, 1.1), (12, 8.1, 1.0)])
+def test_fcc_lattice_sums_published(m, R, d):
+    """The oracle's LJ energy and virial of a perfect FCC crystal with a long
+    cutoff R*d equal the published FCC lattice sums A12, A6
+    (tests/golden/fcc_lattice_sums.txt) minus the sites beyond the cutoff,
+    counted as a continuum of density sqrt(2)/d^3:
+    tail_n = 4 pi sqrt(2) / ((n - 3) R^(n-3)).  (R^2 is not an integer, so no
+    shell sits on the cutoff.)  The tolerance is relative to the sum of the
+    two terms' magnitudes (the energy and virial are differences of them);
+    the continuum tail is good to about 1e-5 of it.  Checks the pair
+    potential, the 1/2 of the energy bookkeeping and the virial sign and
+    scale."""
+    g = _golden("fcc_lattice_sums.txt")
+    a = d * math.sqrt(2.0)
+    x = inputs.fcc_lattice((m, m, m), a)
+    L = np.array([m * a] * 3)
+    f, U, W, _ = oracle.lj_forces(x, L, PER, 1.0, 1.0, R * d)
+    n = x.shape[0]
+    a12 = g["A12"] - 4 * math.pi * math.sqrt(2.0) / (9 * R ** 9)
+    a6 = g["A6"] - 4 * math.pi * math.sqrt(2.0) / (3 * R ** 3)
+    u = 2.0 * (a12 * d ** -12 - a6 * d ** -6)
+    w = 12.0 * (2.0 * a12 * d ** -12 - a6 * d ** -6)
+    assert abs(U / n - u) < 3e-5 * 2.0 * (a12 * d ** -12 + a6 * d ** -6), (U / n, u)
+    assert abs(W / n - w) < 3e-5 * 12.0 * (2.0 * a12 * d ** -12 + a6 * d ** -6), (W / n, w)
+    assert np.max(np.abs(f[:, :3])) < 1e-10
