@@ -100,17 +100,22 @@ __device__ __forceinline__ void sph_pair(const TileCfg &cfg, const BoxT<float> &
     if (in) mumax = fmaxf(mumax, fabsf(mu));
 }
 
+// One half of a home particle's list: words half, half + 2, ... (two threads
+// share each particle and add their sums).
 template <bool FAST, bool SMEM, int KK>
 __device__ __forceinline__ void sph_sweep(const TileCfg &cfg, const BoxT<float> &box, const TileDesc &d,
                                           const float4 *__restrict__ pos, const float4 *__restrict__ vr,
                                           const float4 *__restrict__ st, const float4 *__restrict__ sv,
                                           const float4 &pi, const float4 &vi, float rho_i, float Pi, uint32_t m,
-                                          const uint32_t *__restrict__ col, int64_t ld, const SphK &K, float &ax,
-                                          float &ay, float &az, float &dr, float &mumax)
+                                          uint32_t half, const uint32_t *__restrict__ col, int64_t ld,
+                                          const SphK &K, float &ax, float &ay, float &az, float &dr, float &mumax)
 {
-    for_each_entry<4>(m, col, ld, [&](int s) {
-        sph_pair<FAST, SMEM, KK>(cfg, box, d, pos, vr, st, sv, pi, vi, rho_i, Pi, s, K, ax, ay, az, dr, mumax);
-    });
+    for_each_entry<4, 2>(
+        m, col, ld,
+        [&](int s) {
+            sph_pair<FAST, SMEM, KK>(cfg, box, d, pos, vr, st, sv, pi, vi, rho_i, Pi, s, K, ax, ay, az, dr, mumax);
+        },
+        half);
 }
 
 // The sweep of a tile whose neighbourhood did not fit in shared memory (rare;
@@ -119,12 +124,12 @@ template <int KK>
 __device__ __noinline__ void sph_sweep_spilled(const TileCfg &cfg, const BoxT<float> &box, const TileDesc &d,
                                                const float4 *__restrict__ pos, const float4 *__restrict__ vr,
                                                const float4 &pi, const float4 &vi, float rho_i, float P_i,
-                                               uint32_t m, const uint32_t *__restrict__ col, int64_t ld,
-                                               const SphK &K, float *out5)
+                                               uint32_t m, uint32_t half, const uint32_t *__restrict__ col,
+                                               int64_t ld, const SphK &K, float *out5)
 {
     float ax = 0.0f, ay = 0.0f, az = 0.0f, dr = 0.0f, mumax = 0.0f;
-    sph_sweep<false, false, KK>(cfg, box, d, pos, vr, nullptr, nullptr, pi, vi, rho_i, P_i, m, col, ld, K, ax, ay, az,
-                                dr, mumax);
+    sph_sweep<false, false, KK>(cfg, box, d, pos, vr, nullptr, nullptr, pi, vi, rho_i, P_i, m, half, col, ld, K, ax,
+                                ay, az, dr, mumax);
     out5[0] = ax;
     out5[1] = ay;
     out5[2] = az;
@@ -132,8 +137,11 @@ __device__ __noinline__ void sph_sweep_spilled(const TileCfg &cfg, const BoxT<fl
     out5[4] = mumax;
 }
 
+// Two threads per home particle: blocks of 2 x kTileThreads threads.
+constexpr int kSphThreads = 2 * kTileThreads;
+
 template <int KK>
-__global__ void __launch_bounds__(kTileThreads, 3)
+__global__ void __launch_bounds__(kSphThreads, 2)
     k_sph_tiles(TileCfg cfg, BoxT<float> box, const float4 *__restrict__ pos, const float4 *__restrict__ vr,
                 ListView lv, const uint32_t *__restrict__ nn, int64_t ld, int stage_cap, SphK K,
                 float4 *__restrict__ acc, float *dtcons, Sched sched, fpm_dev_status *status)
@@ -161,7 +169,9 @@ __global__ void __launch_bounds__(kTileThreads, 3)
     const bool in_smem = d.M <= stage_cap;
     if (!in_smem) note_spill(status);
     const bool staged = in_smem ? stage_positions(d, box, pos, sp, &bar, phase, status, vr, sv) : true;
-    for (uint32_t i = d.h0 + threadIdx.x; staged && i < d.h1; i += blockDim.x) {
+    // lanes 2t and 2t + 1 share home particle h0 + t, each walking half its list
+    for (uint32_t t = threadIdx.x; staged && d.h0 + (t >> 1) < d.h1; t += blockDim.x) {
+        const uint32_t i = d.h0 + (t >> 1), half = t & 1u;
         const float4 pi = pos[i];
         const float4 vi = vr[i];
         const uint32_t m = nn[i];
@@ -170,31 +180,42 @@ __global__ void __launch_bounds__(kTileThreads, 3)
         float ax = 0.0f, ay = 0.0f, az = 0.0f, dr = 0.0f;
         if (in_smem) {
             if (d.slow)
-                sph_sweep<false, true, KK>(cfg, box, d, pos, vr, sp, sv, pi, vi, rho_i, P_i, m, words + i, ld, K, ax,
-                                           ay, az, dr, mumax);
+                sph_sweep<false, true, KK>(cfg, box, d, pos, vr, sp, sv, pi, vi, rho_i, P_i, m, half, words + i, ld,
+                                           K, ax, ay, az, dr, mumax);
             else
-                sph_sweep<true, true, KK>(cfg, box, d, pos, vr, sp, sv, pi, vi, rho_i, P_i, m, words + i, ld, K, ax,
-                                          ay, az, dr, mumax);
+                sph_sweep<true, true, KK>(cfg, box, d, pos, vr, sp, sv, pi, vi, rho_i, P_i, m, half, words + i, ld,
+                                          K, ax, ay, az, dr, mumax);
         } else {
             float o5[5];
-            sph_sweep_spilled<KK>(cfg, box, d, pos, vr, pi, vi, rho_i, P_i, m, words + i, ld, K, o5);
+            sph_sweep_spilled<KK>(cfg, box, d, pos, vr, pi, vi, rho_i, P_i, m, half, words + i, ld, K, o5);
             ax = o5[0];
             ay = o5[1];
             az = o5[2];
             dr = o5[3];
             mumax = fmaxf(mumax, o5[4]);
         }
-        float4 a;
-        if (pi.w == 0.0f) {
-            a.x = ax + K.g[0];
-            a.y = ay + K.g[1];
-            a.z = az + K.g[2];
-            amax = fmaxf(amax, sqrtf(a.x * a.x + a.y * a.y + a.z * a.z));
-        } else {
-            a.x = a.y = a.z = 0.0f;
+        // the lanes of this warp still in the loop: a prefix (t < 2 (h1 - h0)),
+        // which holds both lanes of every pair
+        const uint32_t tw = t - (threadIdx.x & 31u);
+        const uint32_t live = 2u * (d.h1 - d.h0) - tw;
+        const unsigned act = live >= 32u ? kFull : ((1u << live) - 1u);
+        ax += __shfl_xor_sync(act, ax, 1);
+        ay += __shfl_xor_sync(act, ay, 1);
+        az += __shfl_xor_sync(act, az, 1);
+        dr += __shfl_xor_sync(act, dr, 1);
+        if (half == 0u) {
+            float4 a;
+            if (pi.w == 0.0f) {
+                a.x = ax + K.g[0];
+                a.y = ay + K.g[1];
+                a.z = az + K.g[2];
+                amax = fmaxf(amax, sqrtf(a.x * a.x + a.y * a.y + a.z * a.z));
+            } else {
+                a.x = a.y = a.z = 0.0f;
+            }
+            a.w = dr;
+            acc[i] = a;
         }
-        a.w = dr;
-        acc[i] = a;
     }
     }
     // one atomic max per warp on the (non-negative) float bits
@@ -373,9 +394,9 @@ extern "C" fpm_status fpm_sph_forces(const fpm_box *box, const fpm_grid *grid, i
     const SphK K = make_sph(*params);
     const void *kern = K.kernel == 0 ? (const void *)k_sph_tiles<0> : (const void *)k_sph_tiles<1>;
     smem_opt_in(kern);
-    const int blocks = persistent_blocks(kern, kTileThreads, smem, *grid, cfg.ntiles);
+    const int blocks = persistent_blocks(kern, kSphThreads, smem, *grid, cfg.ntiles);
     auto launch = K.kernel == 0 ? k_sph_tiles<0> : k_sph_tiles<1>;
-    launch<<<blocks, kTileThreads, smem, (cudaStream_t)stream>>>(
+    launch<<<blocks, kSphThreads, smem, (cudaStream_t)stream>>>(
         cfg, make_box<float>(*box), (const float4 *)pos, (const float4 *)vr, list_view(list, L), nn, L.ld, sc,
         K, (float4 *)acc, d_dtcons, Sched{r.work, r.done}, d_status);
     return fpm_check_launch("fpm_sph_forces");

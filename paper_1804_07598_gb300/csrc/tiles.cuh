@@ -450,29 +450,36 @@ __device__ __forceinline__ void prefetch_home(const V *pos, const uint32_t *nn, 
     for (int q = 0; q < nwords; ++q) asm volatile("prefetch.global.L2 [%0];" ::"l"(words + (int64_t)q * ld + i));
 }
 
-// Calls f(s) for each of the m 16-bit entries of one particle's list (the
-// column `col` of the ELL words, leading dimension ld).  The 32-bit words
-// are loaded kChunk at a time, one chunk ahead of their use, so that the
-// loads' latency overlaps the pair arithmetic of the previous chunk; whole
-// chunks run without per-entry guards.
-template <uint32_t kChunk, typename F>
-__device__ __forceinline__ void for_each_entry(uint32_t m, const uint32_t *__restrict__ col, int64_t ld, F &&f)
+// Calls f(s) for the 16-bit entries of one particle's list held in words
+// w_first, w_first + kStride, w_first + 2 kStride, ... (the column `col` of
+// the ELL words, leading dimension ld; word w holds entries 2w and 2w + 1,
+// of which the first m exist).  With kStride = 1 and w_first = 0 that is the
+// whole list; kStride = 2 splits it between two threads.  The words are
+// loaded kChunk at a time, one chunk ahead of their use, so that the loads'
+// latency overlaps the pair arithmetic of the previous chunk; whole chunks
+// run without per-entry guards.
+template <uint32_t kChunk, uint32_t kStride = 1, typename F>
+__device__ __forceinline__ void for_each_entry(uint32_t m, const uint32_t *__restrict__ col, int64_t ld, F &&f,
+                                               uint32_t w_first = 0)
 {
-    const uint32_t nw = (m + 1u) >> 1;
-    const uint32_t nfull = (m >> 1) / kChunk * kChunk;  // words whose both entries exist, in whole chunks
+    const uint32_t nw = (m + 1u) >> 1;  // words holding entries
+    const uint32_t nfw = m >> 1;        // words whose both entries exist
+    const uint32_t mine = nfw > w_first ? (nfw - w_first + kStride - 1u) / kStride : 0u;
+    const uint32_t nfull = mine / kChunk * kChunk;  // this walker's full words, in whole chunks
+    const int64_t step = (int64_t)kStride * ld;
     uint32_t cur[kChunk], nxt[kChunk];
-    const uint32_t *p = col;  // next word to load
+    const uint32_t *p = col + (int64_t)w_first * ld;  // next word to load
 #pragma unroll
     for (uint32_t q = 0; q < kChunk; ++q) {
         cur[q] = q < nfull ? __ldcs(p) : 0u;
-        p += ld;
+        p += step;
     }
-    for (uint32_t w0 = 0; w0 < nfull; w0 += kChunk) {
-        const bool more = w0 + kChunk < nfull;
+    for (uint32_t k0 = 0; k0 < nfull; k0 += kChunk) {
+        const bool more = k0 + kChunk < nfull;
 #pragma unroll
         for (uint32_t q = 0; q < kChunk; ++q) {
             nxt[q] = more ? __ldcs(p) : 0u;
-            p += ld;
+            p += step;
         }
 #pragma unroll
         for (uint32_t q = 0; q < kChunk; ++q) {
@@ -482,10 +489,10 @@ __device__ __forceinline__ void for_each_entry(uint32_t m, const uint32_t *__res
 #pragma unroll
         for (uint32_t q = 0; q < kChunk; ++q) cur[q] = nxt[q];
     }
-    for (uint32_t wi = nfull; wi < nw; ++wi) {
-        const uint32_t wv = __ldcs(col + (int64_t)wi * ld);
+    for (uint32_t w = w_first + nfull * kStride; w < nw; w += kStride) {
+        const uint32_t wv = __ldcs(col + (int64_t)w * ld);
         f((int)(wv & 0xffffu));
-        if (2u * wi + 1u < m) f((int)(wv >> 16));
+        if (2u * w + 1u < m) f((int)(wv >> 16));
     }
 }
 

@@ -121,3 +121,47 @@ def test_sph_graph_equals_eager(cuda):
     bnd = pos[:, 3] == 1
     assert np.all(vel[bnd] == 0.0)
     assert np.all(np.isfinite(pos)) and np.all(np.isfinite(vel))
+
+
+def test_sph_full_dam_break_sampled(cuda):
+    """The benchmark's dam break (1.51M fluid + 0.62M boundary particles) in
+    the launch configuration bench.py times, after graph-replayed steps: the
+    rates of the particles inside three sample windows (the floor corner,
+    the free surface, the column's middle) against the oracle run on the
+    particles within the windows plus a 2h margin (every neighbour of a
+    window particle is present, so their oracle sums are the full ones)."""
+    d = inputs.dam_break(inputs.SPH_DP)
+    s = SPHSystem(d["pos"], d["vel"], d["rho"], d["L"], d["h"], d["m"], c0=d["c0"])
+    s.step(2)
+    s.capture(steps_per_graph=1)
+    s.run(20)
+    s.rates()
+    torch.cuda.synchronize()
+    s.check_status()
+    pos, vel, rho, _ = s.state_numpy()
+    acc = s.acc.cpu().numpy().astype(np.float64)
+    params = oracle_params(d, "wendland")
+    off = 3 * inputs.SPH_DP
+    margin = 2.0 * d["h"] * 1.001
+    g = np.array([0.0, 0.0, -9.81])
+    windows = [((off - 0.01, off - 0.01, off - 0.01), (off + 0.05, off + 0.05, off + 0.04)),  # floor corner
+               ((off + 0.15, off + 0.30, off + 0.26), (off + 0.21, off + 0.36, off + 0.32)),  # free surface
+               ((off + 0.17, off + 0.30, off + 0.12), (off + 0.22, off + 0.35, off + 0.17))]  # middle
+    for lo, hi in windows:
+        lo, hi = np.array(lo), np.array(hi)
+        x = pos[:, :3].astype(np.float64)
+        core = np.all((x >= lo) & (x < hi), axis=1)
+        near = np.all((x >= lo - margin) & (x < hi + margin), axis=1)
+        assert core.sum() > 500, core.sum()
+        idx = np.nonzero(near)[0]
+        oacc, odr, _ = oracle.sph_rates(pos[idx].astype(np.float64), vel[idx].astype(np.float64), rho[idx],
+                                        f32box(s.L), s.periodic, params, mask_f32=True)
+        c = core[idx]
+        fluid = pos[idx, 3] == 0
+        sel = c & fluid
+        ra = np.sqrt(np.mean(np.sum((oacc[sel, :3] - g) ** 2, axis=1)))
+        ea = np.max(np.linalg.norm(acc[idx][sel, :3] - oacc[sel, :3], axis=1)) / ra
+        rd = np.sqrt(np.mean(odr[c] ** 2))
+        ed = np.max(np.abs(acc[idx][c, 3] - odr[c])) / rd
+        assert ea <= 1e-4, (lo, ea)
+        assert ed <= 1e-4, (lo, ed)
