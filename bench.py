@@ -40,7 +40,10 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM traffic per launch of the force kernel from one ncu capture, valid only
 # while the kernel source hashes to the recorded value (else reported null).
 # Filled from the ncu summary under profiles/ (see the design doc).
-NCU_TRAFFIC = {"lj.cu": {"sha": "a7ecc8bd38425de0", "bytes_per_launch": 184805120}}
+# DRAM bytes per launch of the dominant kernel from one ncu capture
+# (profiles/lj_tiles_lj_1m.md), valid while its sources hash to `sha`.
+NCU_TRAFFIC = {"k_lj_tiles<float>": {"files": ["lj.cu", "lj_pair.cuh", "tiles.cuh", "fpm_common.cuh", "reduce.cuh"],
+                                    "sha": "0a41e7352851602a", "bytes_per_launch": 184734208}}
 
 
 def parse():
@@ -49,14 +52,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--profile", default=None, choices=["forces", "step", "sph", "verlet", "batch"],
+    ap.add_argument("--profile", default=None, choices=["forces", "step", "sph", "verlet", "batch", "adjoint"],
                     help="profiling target for ncu: build the 1M-atom system, then run --steps force sweeps "
                          "or eager steps (no timing, no JSON line)")
     ap.add_argument("--fp64-steps", type=int, default=100)
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--kernel-reps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--sph-steps", type=int, default=500)
     ap.add_argument("--batch-steps", type=int, default=300)
@@ -184,13 +187,17 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def traffic_for(kernel_file: str):
-    rec = NCU_TRAFFIC.get(kernel_file)
-    if not rec or not rec["sha"]:
+def traffic_for(kernel: str):
+    """The recorded ncu DRAM traffic of `kernel`, or None once any of its
+    source files has changed since the capture."""
+    rec = NCU_TRAFFIC.get(kernel)
+    if not rec:
         return None
-    src = os.path.join(ROOT, "paper_1804_07598_gb300", "csrc", kernel_file)
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return rec["bytes_per_launch"] if sha == rec["sha"] else None
+    h = hashlib.sha256()
+    for f in rec["files"]:
+        with open(os.path.join(ROOT, "paper_1804_07598_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return rec["bytes_per_launch"] if h.hexdigest()[:16] == rec["sha"] else None
 
 
 # -------------------------------------------------------------- the arms ---
@@ -268,9 +275,16 @@ def run_ours(args, ws, rank, local):
         g.replay()
     s.check_status()
     torch.cuda.synchronize()
+    # kernels per replayed step: the eager step's launches, less the rebuild's
+    # (a conditional graph node runs them only in the steps that rebuild), plus
+    # the node's condition kernel
     l0 = fpm.launches
-    s.step(1)  # count the kernels of one step (eager, same calls as the graph)
-    per_step_launches = fpm.launches - l0
+    s.step(1)
+    eager_step = fpm.launches - l0
+    l0 = fpm.launches
+    s.rebuild(gated=True)  # gate off here: the kernels launch and exit, counted once
+    body = fpm.launches - l0
+    per_step_launches = eager_step - body + 1
     torch.cuda.synchronize()
     st0 = s.device_status().nrebuild
 
@@ -487,7 +501,7 @@ def run_ours(args, ws, rank, local):
         "fp64_steps_per_s": fp64_steps_per_s * ws,
         "fp32_over_fp64": steps_per_s / (fp64_steps_per_s * ws),
         "roofline": {"kernel": "k_lj_tiles<float>", "bound": "alu", "achieved": tflops, "peak": fp32_peak,
-                     "unit": "TFLOP/s", "frac": tflops / fp32_peak, "traffic": traffic_for("lj.cu"),
+                     "unit": "TFLOP/s", "frac": tflops / fp32_peak, "traffic": traffic_for("k_lj_tiles<float>"),
                      "peak_kind": f"FP32 CUDA cores: {n_sm} SMs x 128 lanes x 2 FLOP x {sm_mhz:.0f} MHz (median "
                                   f"SM clock sampled under load)",
                      "alg_flop_per_launch": alg_flop, "flop_per_list_slot": FLOP_PER_SLOT, "launch_us": force_us,
@@ -498,7 +512,7 @@ def run_ours(args, ws, rank, local):
         "adjoint": adj,
         "sph": sph,
         "batch": batch,
-        "gpu_launches": per_step_launches * args.steps,
+        "gpu_launches": per_step_launches * args.steps + body * int(rebuilds),
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
@@ -520,6 +534,16 @@ def run_profile_target(args):
         torch.cuda.synchronize()
         ss.check_status()
         print(f"profile target done: sph x{args.steps}, n={ss.n}", flush=True)
+        return
+    if args.profile == "adjoint":
+        from paper_1804_07598_gb300.adjoint import LJAdjointRunner
+        wla = inputs.WORKLOADS["lj_adjoint"]
+        xa, va, La = inputs.lj_state(wla)
+        runner = LJAdjointRunner(xa, va, La, nsteps=args.steps, every=20, precision="f32", dt=wla.dt)
+        runner.forward()
+        runner.backward()
+        torch.cuda.synchronize()
+        print(f"profile target done: adjoint x{args.steps}, n={wla.n}", flush=True)
         return
     if args.profile == "batch":
         from paper_1804_07598_gb300.batch import LJBatch

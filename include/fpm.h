@@ -126,6 +126,19 @@ fpm_status fpm_status_from_device(const fpm_dev_status *host_copy);
  * (n + 31) rounded down to a multiple of 32. */
 int64_t fpm_nbr_ld(int32_t n);
 
+/* A branch decided on the device inside a CUDA graph being captured on
+ * `stream`: fpm_graph_if_begin adds a conditional (IF) node, whose body runs
+ * in a replay only when *d_flag != 0 at that point of the replay, and starts
+ * capturing that body on `body_stream` (a different stream, not capturing);
+ * the caller enqueues the conditional work on body_stream and then calls
+ * fpm_graph_if_end(body_stream).  Work enqueued on `stream` afterwards runs
+ * after the conditional node.  When `stream` is not capturing, *capturing is
+ * set to 0 and nothing is added (the caller enqueues the work on `stream`,
+ * gated by the same flag).  Used for the Verlet rebuild of a step, so that a
+ * step without a rebuild does not launch the rebuild kernels. */
+fpm_status fpm_graph_if_begin(const uint32_t *d_flag, fpm_stream stream, fpm_stream body_stream, int32_t *capturing);
+fpm_status fpm_graph_if_end(fpm_stream body_stream);
+
 /* Cell grid for cutoff r_cell in box (see fpm_grid).  Host only.  n_hint,
  * the expected particle count (<= 0: unknown), only sets the tile width:
  * about 170 particles per tile, i.e. round(170 ncell / n_hint) cells.

@@ -88,6 +88,8 @@ _SIG = {
     "fpm_last_error": (_c.c_char_p, []),
     "fpm_status_from_device": (_c.c_int, [_c.POINTER(fpm_dev_status)]),
     "fpm_nbr_ld": (_c.c_int64, [_c.c_int32]),
+    "fpm_graph_if_begin": (_c.c_int, [_VP, _VP, _VP, _c.POINTER(_c.c_int32)]),
+    "fpm_graph_if_end": (_c.c_int, [_VP]),
     "fpm_grid_make": (_c.c_int, [_c.POINTER(fpm_box), _c.c_double, _c.c_int32, _c.POINTER(fpm_grid)]),
     "fpm_celllist_workspace": (_c.c_int, [_c.c_int32, _c.POINTER(fpm_grid), _c.c_int, _c.POINTER(_c.c_size_t)]),
     "fpm_celllist_build": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _c.c_int,
@@ -217,6 +219,20 @@ def fpm_last_error() -> str:
 
 def fpm_status_from_device(host_status: fpm_dev_status) -> int:
     return lib().fpm_status_from_device(_c.byref(host_status))
+
+
+def fpm_graph_if_begin(d_flag, body_stream, stream=None) -> bool:
+    """Opens a device-decided branch in the graph being captured on `stream`
+    (see include/fpm.h); returns False (nothing added) when not capturing."""
+    cap = _c.c_int32(0)
+    _check(lib().fpm_graph_if_begin(_ptr(d_flag), _stream(stream), _stream(body_stream), _c.byref(cap)))
+    if cap.value:
+        _count(1)
+    return bool(cap.value)
+
+
+def fpm_graph_if_end(body_stream):
+    _check(lib().fpm_graph_if_end(_stream(body_stream)))
 
 
 def fpm_nbr_ld(n: int) -> int:

@@ -9,6 +9,9 @@ One step (all on the current stream, no host synchronisation):
     fpm_verlet_build   [gated]  new list, x_ref := x, flag cleared
     fpm_lj_forces               F, U, W, pairs
     fpm_vv_step(half=1)         v += dt/2 F
+Under CUDA-graph capture the two gated calls sit in the body of a
+conditional node on the rebuild flag (fpm_graph_if_begin), so a replayed
+step without a rebuild launches none of their kernels.
 """
 from __future__ import annotations
 
@@ -65,6 +68,7 @@ class LJSystem:
         self.ws_red = torch.zeros(fpm.fpm_reduce_workspace(n, self.grid), dtype=torch.uint8, device=dev)
         self.energy = torch.zeros(3, dtype=torch.float64, device=dev)
         self.kin = torch.zeros(4, dtype=torch.float64, device=dev)
+        self._body = torch.cuda.Stream(device=dev)  # captures the conditional rebuild
         self._graph = None
         self.rebuild()
         self.size_staging()
@@ -98,12 +102,22 @@ class LJSystem:
     def gate_ptr(self) -> int:
         return self.status.data_ptr() + 8  # fpm_dev_status.rebuild
 
-    def rebuild(self, gated: bool = False):
+    def rebuild(self, gated: bool = False, stream=None):
         gate = self.gate_ptr if gated else None
         fpm.fpm_celllist_build(self.box, self.grid, self.n, self.prec, self.pos, self.vel, self.ids, self.pos,
-                               self.vel, self.ids, self.cell_start, self.perm, self.ws_cell, self.status, gate)
+                               self.vel, self.ids, self.cell_start, self.perm, self.ws_cell, self.status, gate,
+                               stream=stream)
         fpm.fpm_verlet_build(self.box, self.grid, self.n, self.prec, self.pos, self.cell_start, self.r_list,
-                             self.cap, self.nbr, self.nn, self.pos_ref, self.status, gate)
+                             self.cap, self.nbr, self.nn, self.pos_ref, self.status, gate, stream=stream)
+
+    def _gated_rebuild(self):
+        """The step's rebuild: a conditional graph node under capture, gated
+        launches otherwise."""
+        if fpm.fpm_graph_if_begin(self.gate_ptr, self._body):
+            self.rebuild(gated=True, stream=self._body)
+            fpm.fpm_graph_if_end(self._body)
+        else:
+            self.rebuild(gated=True)
 
     def compute_forces(self):
         fpm.fpm_lj_forces(self.box, self.grid, self.n, self.prec, self.pos, self.nbr, self.nn, self.cap, self.eps,
@@ -112,7 +126,7 @@ class LJSystem:
     def _step(self):
         fpm.fpm_vv_drift_check(self.box, self.n, self.prec, self.dt, self.pos, self.vel, self.force, self.pos_ref,
                                self.skin, self.status)
-        self.rebuild(gated=True)
+        self._gated_rebuild()
         self.compute_forces()
         fpm.fpm_vv_step(self.box, self.n, self.prec, 1, self.dt, None, self.vel, self.force)
 

@@ -9,6 +9,8 @@ One step (all on the current stream):
     fpm_sph_correct                 -> pos, vr (in place), rebuild flag
     fpm_celllist_build [gated]         re-bin and reorder pos, vr, ids
     fpm_verlet_build   [gated]         new list with r_list = 2h + skin
+Under CUDA-graph capture the gated calls sit in the body of a conditional
+node on the rebuild flag (fpm_graph_if_begin).
 """
 from __future__ import annotations
 
@@ -71,6 +73,7 @@ class SPHSystem:
         self.dtcons_h = torch.zeros(2, dtype=f32, device=dev)
         self.dt = torch.zeros(1, dtype=f32, device=dev)
         self.ws_red = torch.zeros(fpm.fpm_reduce_workspace(n, self.grid), dtype=torch.uint8, device=dev)
+        self._body = torch.cuda.Stream(device=dev)  # captures the conditional rebuild
         self._graph = None
         self.rebuild()
         self.size_staging()
@@ -109,12 +112,13 @@ class SPHSystem:
     def gate_ptr(self) -> int:
         return self.status.data_ptr() + 8
 
-    def rebuild(self, gated: bool = False):
+    def rebuild(self, gated: bool = False, stream=None):
         gate = self.gate_ptr if gated else None
         fpm.fpm_celllist_build(self.box, self.grid, self.n, fpm.FPM_F32, self.pos, self.vr, self.ids, self.pos,
-                               self.vr, self.ids, self.cell_start, self.perm, self.ws_cell, self.status, gate)
+                               self.vr, self.ids, self.cell_start, self.perm, self.ws_cell, self.status, gate,
+                               stream=stream)
         fpm.fpm_verlet_build(self.box, self.grid, self.n, fpm.FPM_F32, self.pos, self.cell_start, self.r_list,
-                             self.cap, self.nbr, self.nn, self.pos_ref, self.status, gate)
+                             self.cap, self.nbr, self.nn, self.pos_ref, self.status, gate, stream=stream)
 
     def rates(self, pos=None, vr=None, acc=None, dtcons=None):
         fpm.fpm_sph_forces(self.box, self.grid, self.n, self.pos if pos is None else pos,
@@ -129,7 +133,11 @@ class SPHSystem:
         self.rates(self.pos_h, self.vr_h, self.acc_h, self.dtcons_h)
         fpm.fpm_sph_correct(self.box, self.n, self.params, self.pos, self.vr, self.vr_h, self.acc_h, self.dt,
                             self.dtcons, self.pos_ref, self.skin, self.status)
-        self.rebuild(gated=True)
+        if fpm.fpm_graph_if_begin(self.gate_ptr, self._body):
+            self.rebuild(gated=True, stream=self._body)
+            fpm.fpm_graph_if_end(self._body)
+        else:
+            self.rebuild(gated=True)
 
     def step(self, nsteps: int = 1):
         for _ in range(int(nsteps)):

@@ -116,7 +116,8 @@ def test_sph_graph_equals_eager(cuda):
     b.run(20)
     torch.cuda.synchronize()
     assert torch.equal(a.pos, b.pos) and torch.equal(a.vr, b.vr)
-    a.check_status()
+    sa, sb = a.check_status(), b.check_status()
+    assert sa.nrebuild == sb.nrebuild  # the graph's conditional rebuild ran exactly when the eager one did
     pos, vel, rho, _ = a.state_numpy()
     bnd = pos[:, 3] == 1
     assert np.all(vel[bnd] == 0.0)
