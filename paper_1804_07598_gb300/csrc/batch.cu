@@ -23,14 +23,15 @@
 
 namespace fpm {
 
-constexpr int kBatchCellThreads = 512;
+constexpr int kBatchCellThreads = 1024;
 constexpr int kBatchMaxCells = 32768;   // cells of one replica (shared-memory counters)
 constexpr int kBatchMaxReplicas = 65535;
 constexpr int kBatchDescBlocks = 2048;  // grid of the descriptor kernel (grid-stride over tiles)
 
 __host__ __device__ inline int rep_ntiles(const fpm_grid &g) { return g.tiles_x * g.nc[1] * g.nc[2]; }
 
-// The replica holding particle i / tile t: the last r whose p0 / t0 is <= i.
+// The replica holding particle i: the last r whose p0 is <= i.  (Tiles look
+// their replica up in a map the Verlet build writes.)
 __device__ __forceinline__ int replica_of_particle(const fpm_replica *__restrict__ reps, int R, uint32_t i)
 {
     int lo = 0, hi = R - 1;
@@ -42,16 +43,6 @@ __device__ __forceinline__ int replica_of_particle(const fpm_replica *__restrict
     return lo;
 }
 
-__device__ __forceinline__ int replica_of_tile(const fpm_replica *__restrict__ reps, int R, uint32_t t)
-{
-    int lo = 0, hi = R - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if ((uint32_t)__ldg(&reps[mid].t0) <= t) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
 
 // ---- drift + per-replica rebuild test ---------------------------------------
 
@@ -233,33 +224,12 @@ __global__ void __launch_bounds__(kBatchCellThreads)
 
 // ---- Verlet lists of the flagged replicas -----------------------------------
 
-// Descriptors of every tile of a flagged replica (grid-stride over tiles).
-__global__ void __launch_bounds__(128)
-    k_btile_desc(int R, int ntiles, const fpm_replica *__restrict__ reps, const uint32_t *__restrict__ cs,
-                 TileDesc *__restrict__ descs, const uint32_t *__restrict__ flag, fpm_dev_status *st)
-{
-    __shared__ TileGeom g;
-    __shared__ TileDesc d;
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int r = replica_of_tile(reps, R, (uint32_t)tile);
-        if (flag && flag[r] == 0u) continue;
-        const fpm_replica rp = reps[r];
-        const TileCfg cfg = make_tile_cfg(rp.box, rp.grid);
-        tile_geometry(cfg, tile - rp.t0, cs + rp.c0, g, d);
-        const int nwd = (int)(sizeof(TileDesc) / 4);
-        uint32_t *o = (uint32_t *)(descs + tile);
-        const uint32_t *s = (const uint32_t *)&d;
-        for (int k = threadIdx.x; k < nwd; k += blockDim.x) o[k] = s[k];
-        if (threadIdx.x == 0 && st && d.h1 > d.h0) atomicMax(&st->max_staged, (uint32_t)d.M);
-        __syncthreads();  // d and g are rewritten for the next tile
-    }
-}
-
-// One block: the work list of the scan (every tile of every flagged replica,
-// in replica order), the scan's scheduling counters, and the flags cleared.
+// One block: the tile -> replica map of every tile, the work list of the
+// build (every tile of every flagged replica, in replica order), the scan's
+// scheduling counters, and the flags cleared.
 __global__ void __launch_bounds__(1024)
     k_bwork(int R, const fpm_replica *__restrict__ reps, uint32_t *__restrict__ flag, uint32_t *__restrict__ work,
-            uint32_t *__restrict__ header, fpm_dev_status *st)
+            uint32_t *__restrict__ map, uint32_t *__restrict__ header, fpm_dev_status *st)
 {
     __shared__ uint32_t wsum[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -267,14 +237,14 @@ __global__ void __launch_bounds__(1024)
     for (int base = 0; base < R; base += blockDim.x) {
         const int r = base + threadIdx.x;
         bool f = false;
-        uint32_t nt = 0, t0 = 0;
+        uint32_t nt = 0, t0 = 0, nr = 0;
         if (r < R) {
             f = !flag || flag[r] != 0u;
             if (flag) flag[r] = 0u;
-            if (f) {
-                nt = (uint32_t)rep_ntiles(reps[r].grid);
-                t0 = (uint32_t)reps[r].t0;
-            }
+            nr = (uint32_t)rep_ntiles(reps[r].grid);
+            t0 = (uint32_t)reps[r].t0;
+            for (uint32_t j = 0; j < nr; ++j) map[t0 + j] = (uint32_t)r;
+            nt = f ? nr : 0u;
         }
         nflag += (uint32_t)__syncthreads_count(f);
         uint32_t x = nt;
@@ -308,10 +278,33 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
+// Descriptors of the tiles on the work list (grid-stride).
+__global__ void __launch_bounds__(128)
+    k_btile_desc(const fpm_replica *__restrict__ reps, const uint32_t *__restrict__ work,
+                 const uint32_t *__restrict__ map, const uint32_t *__restrict__ header,
+                 const uint32_t *__restrict__ cs, TileDesc *__restrict__ descs, fpm_dev_status *st)
+{
+    __shared__ TileGeom g;
+    __shared__ TileDesc d;
+    const uint32_t count = header[0];
+    for (uint32_t k = blockIdx.x; k < count; k += gridDim.x) {
+        const uint32_t tile = work[k];
+        const fpm_replica rp = reps[map[tile]];
+        const TileCfg cfg = make_tile_cfg(rp.box, rp.grid);
+        tile_geometry(cfg, (int)tile - rp.t0, cs + rp.c0, g, d);
+        const int nwd = (int)(sizeof(TileDesc) / 4);
+        uint32_t *o = (uint32_t *)(descs + tile);
+        const uint32_t *s = (const uint32_t *)&d;
+        for (int q = threadIdx.x; q < nwd; q += blockDim.x) o[q] = s[q];
+        if (threadIdx.x == 0 && st && d.h1 > d.h0) atomicMax(&st->max_staged, (uint32_t)d.M);
+        __syncthreads();  // d and g are rewritten for the next tile
+    }
+}
+
 __global__ void __launch_bounds__(kTileThreads)
-    k_bverlet_scan(int R, const fpm_replica *__restrict__ reps, const float4 *__restrict__ pos,
-                   const uint32_t *__restrict__ cs, float rl2, int cap, int64_t ld, int stage_cap,
-                   const uint32_t *__restrict__ work, const uint32_t *__restrict__ count, Sched sched,
+    k_bverlet_scan(const fpm_replica *__restrict__ reps, const uint32_t *__restrict__ map,
+                   const float4 *__restrict__ pos, const uint32_t *__restrict__ cs, float rl2, int cap, int64_t ld,
+                   int stage_cap, const uint32_t *__restrict__ work, const uint32_t *__restrict__ count, Sched sched,
                    uint32_t *__restrict__ words, uint32_t *__restrict__ nn, float4 *__restrict__ pos_ref,
                    fpm_dev_status *st)
 {
@@ -332,8 +325,7 @@ __global__ void __launch_bounds__(kTileThreads)
         ahead = ticket_ahead(sched);
         if (threadIdx.x == 0) {
             const uint32_t tile = work[k];
-            const int r = replica_of_tile(reps, R, tile);
-            const fpm_replica rp = reps[r];
+            const fpm_replica rp = reps[map[tile]];
             s_cfg = make_tile_cfg(rp.box, rp.grid);
             s_box = make_box<float>(rp.box);
             s_tile = (int)tile - rp.t0;
@@ -354,8 +346,8 @@ __global__ void __launch_bounds__(kTileThreads)
 // ---- LJ forces over every tile of the batch ---------------------------------
 
 __global__ void __launch_bounds__(kTileThreads)
-    k_blj_tiles(int R, int ntiles, const fpm_replica *__restrict__ reps, const float4 *__restrict__ pos,
-                ListView lv, const uint32_t *__restrict__ nn, int64_t ld, int stage_cap, LJParams<float> P,
+    k_blj_tiles(int ntiles, const fpm_replica *__restrict__ reps, const uint32_t *__restrict__ map,
+                const float4 *__restrict__ pos, ListView lv, const uint32_t *__restrict__ nn, int64_t ld, int stage_cap, LJParams<float> P,
                 float4 *__restrict__ force, Sched sched, double *part, uint32_t *rep_done, double *out,
                 fpm_dev_status *status)
 {
@@ -375,7 +367,7 @@ __global__ void __launch_bounds__(kTileThreads)
     for (uint32_t k = blockIdx.x; k < (uint32_t)ntiles; k = ticket_next(ahead, &s_k)) {
         ahead = ticket_ahead(sched);
         if (threadIdx.x == 0) {
-            const int r = replica_of_tile(reps, R, k);
+            const int r = (int)map[k];
             const fpm_replica rp = reps[r];
             s_cfg = make_tile_cfg(rp.box, rp.grid);
             s_box = make_box<float>(rp.box);
@@ -602,11 +594,25 @@ extern "C" fpm_status fpm_batch_celllist_build(const fpm_batch *batch, const fpm
     return fpm_check_launch("fpm_batch_celllist_build");
 }
 
-static ListLayout batch_list_layout(const fpm_batch &b, int cap)
+// The batch's Verlet-list object: the single-system layout (header, tile
+// descriptors, work list, ELL words) with one more region after the work
+// list: the tile -> replica map (ntiles_total uint32).
+static ListLayout batch_list_layout(const fpm_batch &b, int cap, size_t *off_map = nullptr)
 {
-    TileCfg c{};
-    c.ntiles = b.ntiles_total;
-    return list_layout(b.n_total, c, cap);
+    ListLayout L{};
+    const size_t nt = (size_t)b.ntiles_total;
+    L.ld = fpm_nbr_ld(b.n_total);
+    L.words_per_particle = (cap + 1) / 2;
+    L.off_tiles = 256;
+    size_t t = L.off_tiles + nt * sizeof(TileDesc);
+    L.off_active = (t + 255) & ~(size_t)255;
+    t = L.off_active + nt * 4;
+    const size_t om = (t + 255) & ~(size_t)255;
+    if (off_map) *off_map = om;
+    t = om + nt * 4;
+    L.off_words = (t + 255) & ~(size_t)255;
+    L.total = L.off_words + (size_t)L.words_per_particle * (size_t)L.ld * 4;
+    return L;
 }
 
 extern "C" fpm_status fpm_batch_list_bytes(const fpm_batch *batch, int32_t cap, size_t *bytes)
@@ -633,22 +639,25 @@ extern "C" fpm_status fpm_batch_verlet_build(const fpm_batch *batch, const fpm_r
     if (((uintptr_t)list & 255u) != 0)
         return fpm_fail(FPM_ERR_INVALID, "fpm_batch_verlet_build: list not 256-B aligned");
     cudaStream_t st = (cudaStream_t)stream;
+    size_t off_map = 0;
+    batch_list_layout(*batch, cap, &off_map);
     char *lb = (char *)list;
     TileDesc *descs = (TileDesc *)(lb + L.off_tiles);
     uint32_t *work = (uint32_t *)(lb + L.off_active);
+    uint32_t *map = (uint32_t *)(lb + off_map);
     uint32_t *header = (uint32_t *)lb;
     const int R = batch->R;
     const int nt = batch->ntiles_total;
-    k_btile_desc<<<std::min(nt, kBatchDescBlocks), 128, 0, st>>>(R, nt, d_reps, cell_start, descs, d_rep_flag,
+    k_bwork<<<1, 1024, 0, st>>>(R, d_reps, d_rep_flag, work, map, header, d_status);
+    k_btile_desc<<<std::min(nt, kBatchDescBlocks), 128, 0, st>>>(d_reps, work, map, header, cell_start, descs,
                                                                 d_status);
-    k_bwork<<<1, 1024, 0, st>>>(R, d_reps, d_rep_flag, work, header, d_status);
     const int sc = batch_stage_cap(*batch);
     const size_t smem = (size_t)sc * sizeof(float4);
     smem_opt_in((const void *)k_bverlet_scan);
     fpm_grid gg{};
     gg.sweep_blocks = batch->sweep_blocks;
     const int blocks = persistent_blocks((const void *)k_bverlet_scan, kTileThreads, smem, gg, nt);
-    k_bverlet_scan<<<blocks, kTileThreads, smem, st>>>(R, d_reps, (const float4 *)pos, cell_start,
+    k_bverlet_scan<<<blocks, kTileThreads, smem, st>>>(d_reps, map, (const float4 *)pos, cell_start,
                                                        (float)(r_list * r_list), cap, L.ld, sc, work, header,
                                                        Sched{(unsigned *)(lb + 16), (unsigned *)(lb + 20)},
                                                        (uint32_t *)(lb + L.off_words), nn, (float4 *)pos_ref,
@@ -692,7 +701,8 @@ extern "C" fpm_status fpm_batch_lj_forces(const fpm_batch *batch, const fpm_repl
     if (((uintptr_t)workspace & 15u) != 0)
         return fpm_fail(FPM_ERR_WORKSPACE, "fpm_batch_lj_forces: workspace not 16-B aligned");
     char *w = (char *)workspace;
-    const ListLayout L = batch_list_layout(*batch, cap);
+    size_t off_map = 0;
+    const ListLayout L = batch_list_layout(*batch, cap, &off_map);
     LJParams<float> P;
     P.eps24 = (float)(24.0 * eps);
     P.eps4 = (float)(4.0 * eps);
@@ -706,7 +716,8 @@ extern "C" fpm_status fpm_batch_lj_forces(const fpm_batch *batch, const fpm_repl
     const int nt = batch->ntiles_total;
     const int blocks = persistent_blocks((const void *)k_blj_tiles, kTileThreads, smem, gg, nt);
     k_blj_tiles<<<blocks, kTileThreads, smem, (cudaStream_t)stream>>>(
-        batch->R, nt, d_reps, (const float4 *)pos, list_view(list, L), nn, L.ld, sc, P, (float4 *)force,
+        nt, d_reps, (const uint32_t *)((const char *)list + off_map), (const float4 *)pos, list_view(list, L), nn,
+        L.ld, sc, P, (float4 *)force,
         Sched{(unsigned *)(w + 16), (unsigned *)(w + 32)}, (double *)(w + 256), (uint32_t *)(w + off_done),
         d_energy, d_status);
     return fpm_check_launch("fpm_batch_lj_forces");
