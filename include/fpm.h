@@ -141,7 +141,7 @@ fpm_status fpm_graph_if_end(fpm_stream body_stream);
 
 /* Cell grid for cutoff r_cell in box (see fpm_grid).  Host only.  n_hint,
  * the expected particle count (<= 0: unknown), only sets the tile width:
- * about 170 particles per tile, i.e. round(170 ncell / n_hint) cells.
+ * about 200 particles per tile, i.e. round(200 ncell / n_hint) cells.
  * FPM_ERR_INVALID if r_cell <= 0, a length <= 0, a periodic length below
  * 2 r_cell (1 + 2^-10) or more than 2^24 cells. */
 fpm_status fpm_grid_make(const fpm_box *box, double r_cell, int32_t n_hint, fpm_grid *out);
@@ -457,7 +457,7 @@ typedef struct {
 /* Plans a batch of R replicas (host only): replica r has counts[r]
  * particles in boxes[r] (every dimension periodic, L > 2 r_cell (1 + 2^-10)),
  * a cell grid made as by fpm_grid_make(boxes[r], r_cell, counts[r]) but with
- * tile widths aimed at tile_target particles per tile (0: 170), and the
+ * tile widths aimed at tile_target particles per tile (0: 200), and the
  * offsets p0, c0, t0 in replica order.  reps : [R] host array, written.
  * Limits: R <= 65535, max_ncell <= 32768 cells per replica. */
 fpm_status fpm_batch_plan(int32_t R, const fpm_box *boxes, const int32_t *counts, double r_cell,

@@ -98,7 +98,7 @@ def tune(key: str, space: dict, apply, measure, use_cache: bool = True) -> dict:
     return {**out, "cached": False, "seconds": time.time() - t0}
 
 
-def tune_batch(system, steps: int = 20, warmup: int = 5, tile_targets=(96, 128, 170, 256),
+def tune_batch(system, steps: int = 20, warmup: int = 5, tile_targets=(128, 170, 200, 230),
                sweep_blocks=None, use_cache: bool = True) -> dict:
     """Tunes an LJBatch: tile_target (re-plans and rebuilds) x sweep_blocks."""
     if sweep_blocks is None:

@@ -107,7 +107,7 @@ __device__ __noinline__ void hvp_sweep_spilled(const TileCfg &cfg, const BoxT<T>
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kTileThreads, 4)
+__global__ void __launch_bounds__(kTileThreads, 3)
     k_lj_hvp_tiles(TileCfg cfg, BoxT<T> box, const V4<T> *__restrict__ pos, const V4<T> *__restrict__ avec,
                    ListView lv, const uint32_t *__restrict__ nn, int64_t ld, int stage_cap, HvpParams<T> P,
                    double hscale, double e24, double e24s, double eps4, double *__restrict__ adj_pos, Sched sched,

@@ -4,7 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 
-#include "fpm_common.cuh"
+#include "tiles.cuh"
 
 static thread_local char g_last_error[512] = "";
 
@@ -80,9 +80,9 @@ extern "C" fpm_status fpm_grid_make(const fpm_box *box, double r_cell, int32_t n
     if (total > (int64_t)(1u << 24))
         return fpm_fail(FPM_ERR_INVALID, "fpm_grid_make: %lld cells exceed the 2^24 limit", (long long)total);
     g.ncell = (int32_t)total;
-    // tile width along x: about 170 particles per tile, at most 14 cells
+    // tile width along x: about kTileTarget particles per tile, at most 14 cells
     const double per_cell = n_hint > 0 ? (double)n_hint / (double)total : 16.0;
-    int w = (int)std::lround(170.0 / (per_cell > 1e-9 ? per_cell : 1e-9));
+    int w = (int)std::lround((double)fpm::kTileTarget / (per_cell > 1e-9 ? per_cell : 1e-9));
     if (w < 1) w = 1;
     if (w > 14) w = 14;
     int tiles = (g.nc[0] + w - 1) / w;

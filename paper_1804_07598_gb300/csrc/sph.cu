@@ -137,8 +137,9 @@ __device__ __noinline__ void sph_sweep_spilled(const TileCfg &cfg, const BoxT<fl
     out5[4] = mumax;
 }
 
-// Two threads per home particle: blocks of 2 x kTileThreads threads.
-constexpr int kSphThreads = 2 * kTileThreads;
+// Two threads per home particle (tiles of about 170 particles): 384-thread
+// blocks, two per SM at 80 registers.
+constexpr int kSphThreads = 384;
 
 template <int KK>
 __global__ void __launch_bounds__(kSphThreads, 2)

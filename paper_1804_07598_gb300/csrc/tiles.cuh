@@ -33,8 +33,9 @@ namespace fpm {
 
 enum : int { kModeOpen = 0, kModeWrap = 1, kModeAll = 2 };
 
-constexpr int kTileThreads = 192;          // threads per tile block
-constexpr int kTileTarget = 170;           // particles per tile the grid's tile width aims at
+constexpr int kTileThreads = 256;          // threads per tile block (one per home particle)
+constexpr int kTileTarget = 200;           // particles per tile the grid's tile width aims at (a tile
+                                           // stays below kTileThreads, so no thread takes two particles)
 constexpr int kMaxTileCells = 14;          // home cells per tile along x
 constexpr int kMaxSeq = kMaxTileCells + 2; // staged cells per stencil row
 constexpr int kMaxRows = 9;
