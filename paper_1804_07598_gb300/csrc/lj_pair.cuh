@@ -56,7 +56,7 @@ __device__ __forceinline__ void lj_pair(const TileCfg &cfg, const BoxT<T> &box, 
 
 // The LJ sums of one home particle over its list (list words prefetched
 // kLjChunk at a time, see for_each_entry).
-constexpr uint32_t kLjChunk = 4;
+constexpr uint32_t kLjChunk = 3;
 
 template <typename T, bool FAST, bool SMEM>
 __device__ __forceinline__ void lj_sweep(const TileCfg &cfg, const BoxT<T> &box, const TileDesc &d,

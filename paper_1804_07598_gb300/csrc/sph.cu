@@ -110,7 +110,7 @@ __device__ __forceinline__ void sph_sweep(const TileCfg &cfg, const BoxT<float> 
                                           uint32_t half, const uint32_t *__restrict__ col, int64_t ld,
                                           const SphK &K, float &ax, float &ay, float &az, float &dr, float &mumax)
 {
-    for_each_entry<4, 2>(
+    for_each_entry<2, 2>(
         m, col, ld,
         [&](int s) {
             sph_pair<FAST, SMEM, KK>(cfg, box, d, pos, vr, st, sv, pi, vi, rho_i, Pi, s, K, ax, ay, az, dr, mumax);

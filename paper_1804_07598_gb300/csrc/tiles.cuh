@@ -514,6 +514,7 @@ __device__ __forceinline__ uint32_t scan_candidates(const TileCfg &cfg, const Bo
     const uint32_t ucap = (uint32_t)cap;
     for (int r = 0; r < g.nrows; ++r) {
         const int s0 = g.off[r][t0], s1 = g.off[r][t1 + 1];
+#pragma unroll 4
         for (int s = s0; s < s1; ++s) {
             const V4<T> pj = SMEM ? st[s] : staged_global(d, box, pos, s);
             T dx, dy, dz;
