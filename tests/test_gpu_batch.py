@@ -213,3 +213,31 @@ def test_batch_full_ensemble_sampled(cuda):
     for r in sample:
         check_lists(b, r, pref, nbr, nn)
         check_forces(b, r, pos, force, energy)
+
+
+def test_batch_edge_cases(cuda):
+    """A replica with no particles between two others, a batch of one
+    replica, and a replica whose box is just above the smallest legal one
+    (L = 5.61 > 2 r_list (1 + 2^-10) = 5.6055: one cell, all pairs): lists and
+    forces still match the oracle and the empty replica's energies are zero."""
+    L = 5.61
+    tiny = inputs.replica_state(64, 64 / L ** 3, 1.0, 5)
+    big = inputs.replica_state(300, 0.9, 1.0, 6)
+    empty = (np.zeros((0, 4)), np.zeros((0, 4)), np.array([8.0, 8.0, 8.0]))
+    for reps in ([big, empty, tiny], [big]):
+        b = LJBatch(reps)
+        b.step(2)
+        b.compute_forces()
+        torch.cuda.synchronize()
+        b.check_status()
+        pos, _, _ = b.state_numpy()
+        pref = b.pos_ref.cpu().numpy()
+        nbr, nn = b.neighbor_lists()
+        force, energy = b.force.cpu().numpy(), b.energies()
+        for r in range(b.R):
+            p0, p1 = b.replica_range(r)
+            if p1 == p0:
+                assert np.all(energy[r] == 0.0)
+                continue
+            check_lists(b, r, pref, nbr, nn)
+            check_forces(b, r, pos, force, energy)
