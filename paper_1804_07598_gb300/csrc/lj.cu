@@ -3,12 +3,13 @@
 // 24 eps (2 s^12/r^14 - s^6/r^8)(x_p - x_q) of Listing 4.1, truncated at
 // r_cut).
 //
-// One block per cell tile: the tile's neighbourhood positions are staged in
-// shared memory (tiles.cuh), then one thread per home particle walks its
-// 16-bit list entries, two per 32-bit word, reading neighbours from shared
-// memory.  The sweep covers the FULL list (each pair from both sides): no
-// atomics, bit-reproducible forces.  Energy, virial and the pair count are
-// reduced per block in FP64 and then in a fixed order across blocks.
+// Per cell tile (persistent blocks take tiles by ticket): the tile's
+// neighbourhood positions are staged in shared memory (tiles.cuh), then one
+// thread per home particle walks its 16-bit list entries, two per 32-bit
+// word, reading neighbours from shared memory.  The sweep covers the FULL
+// list (each pair from both sides): no atomics, bit-reproducible forces.
+// Energy, virial and the pair count are reduced per tile in FP64 and then
+// over the tiles in a fixed order.
 #include <mutex>
 
 #include "lj_pair.cuh"

@@ -3,10 +3,11 @@
 // Sec. 2, used for the MD benchmark of Sec. 4.1; rebuild when a particle has
 // moved more than half the skin).
 //
-// One block per tile (tiles.cuh): the tile's neighbourhood is staged in
-// shared memory, one thread per home particle scans the three staged cells
-// around its own cell in each of the up-to-9 stencil rows, and writes the
-// staged index of every neighbour inside r_list as a 16-bit entry.
+// Per tile (tiles.cuh; persistent blocks take tiles by ticket): the tile's
+// neighbourhood is staged in shared memory, one thread per home particle
+// scans the three staged cells around its own cell in each of the up-to-9
+// stencil rows, and writes the staged index of every neighbour inside
+// r_list as a 16-bit entry.
 #include "tiles.cuh"
 
 namespace fpm {
