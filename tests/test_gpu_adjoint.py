@@ -79,13 +79,13 @@ def test_full_gradient_fp64_matches_oracle(cuda):
 
 
 def test_fp32_gradient_against_fp64_oracle(cuda):
-    """The 32,768-particle workload (FCC 16x16x32), 60 steps, checkpoints
-    every 20: FP32 forward with FP64 adjoint accumulation against the FP64
-    oracle gradient.  Observed relative error (max over particles of the
+    """The 32,768-particle workload (FCC 16x16x32), its full 200 steps,
+    checkpoints every 20 (the bench's configuration): FP32 forward with FP64
+    adjoint accumulation against the FP64 oracle gradient.  Observed relative error (max over particles of the
     gradient row difference / max row norm) is printed; bound 1e-2."""
     wl = inputs.WORKLOADS["lj_adjoint"]
     x, v, L = inputs.lj_state(wl)
-    steps = 60
+    steps = 200
     r = LJAdjointRunner(x, v, L, nsteps=steps, every=20, precision="f32", dt=wl.dt)
     loss = r.forward()
     gx, gv, ge, gs = r.backward()

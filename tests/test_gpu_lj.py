@@ -147,3 +147,30 @@ def test_graph_replay_equals_eager(cuda):
     assert torch.equal(a.pos, b.pos) and torch.equal(a.vel, b.vel) and torch.equal(a.ids, b.ids)
     assert torch.equal(a.energy, b.energy)
     assert a.device_status().nrebuild == b.device_status().nrebuild >= 1
+
+
+def test_graph_steps_1m_match_oracle(cuda):
+    """The benchmark configuration: the 1M-atom FP32 system stepped by CUDA
+    graph replays (the rebuild as a conditional graph node) over several
+    rebuilds; then the forces and energies at the final positions against
+    the oracle, every particle within skin/2 of its reference position, and
+    the Verlet list of sampled particles against an O(n) scan of the
+    reference positions."""
+    wl, s = make("lj_1m", "f32", jitter=0.0)
+    s.step(2)
+    s.capture(steps_per_graph=1)
+    s.run(40)
+    torch.cuda.synchronize()
+    st = s.check_status()
+    assert st.nrebuild >= 3
+    check_forces(s, "f32")
+    pos = s.pos.cpu().numpy().astype(np.float64)
+    ref = s.pos_ref.cpu().numpy()
+    d = pos[:, :3] - ref[:, :3].astype(np.float64)
+    assert np.max(np.sum(d * d, axis=1)) <= (0.5 * s.skin) ** 2 * (1 + 1e-5)
+    nbr, nn = s.neighbor_lists()
+    rng = np.random.default_rng(1)
+    for i in rng.choice(s.n, 12, replace=False):
+        want = np.sort(oracle.neighbors_one(ref, s.L, s.periodic, s.r_list, int(i)).astype(np.int64))
+        got = np.sort(nbr[:nn[i], i].astype(np.int64))
+        assert np.array_equal(got, want), i
