@@ -345,35 +345,45 @@ def run_ours(args, ws, rank, local):
     del s64, g64
 
     # end to end through the public API with host buffers: every step copies the
-    # state in from pinned host memory and reads state + energies back.  The
-    # round trip of one array overlaps the other's (the link carries both
-    # directions at once): D2H pos, then H2D pos on a second stream while D2H
-    # vel runs, then H2D vel; the next step waits for both.  The host buffers
-    # carry each step's result into the next step's input.
-    hp = torch.empty_like(s.pos, device="cpu").pin_memory()
-    hv = torch.empty_like(s.vel, device="cpu").pin_memory()
+    # state in from pinned host memory and reads state + energies back, in the
+    # host's layout (packed x, y, z: fpm_pack_xyz / fpm_unpack_xyz on the
+    # device).  The round trip of one array overlaps the other's (the link
+    # carries both directions at once): D2H pos, then H2D pos on a second
+    # stream while D2H vel runs, then H2D vel; the next step waits for both.
+    # The host buffers carry each step's result into the next step's input.
+    f32 = torch.float32
+    hp = torch.empty((s.n, 3), dtype=f32).pin_memory()
+    hv = torch.empty((s.n, 3), dtype=f32).pin_memory()
     he = torch.empty(3, dtype=torch.float64).pin_memory()
-    hp.copy_(s.pos)
-    hv.copy_(s.vel)
+    hp.copy_(s.pos[:, :3])
+    hv.copy_(s.vel[:, :3])
+    dp_in, dv_in = torch.empty((s.n, 3), dtype=f32, device=s.device), torch.empty((s.n, 3), dtype=f32, device=s.device)
+    dp_out, dv_out = torch.empty_like(dp_in), torch.empty_like(dv_in)
     main, side = torch.cuda.current_stream(), torch.cuda.Stream()
     ev_p, ev_v, ev_in = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    s.pos.copy_(hp, non_blocking=True)
-    s.vel.copy_(hv, non_blocking=True)
+    dp_in.copy_(hp, non_blocking=True)
+    fpm.fpm_unpack_xyz(s.n, s.prec, dp_in, s.pos)
+    dv_in.copy_(hv, non_blocking=True)
+    fpm.fpm_unpack_xyz(s.n, s.prec, dv_in, s.vel)
     for k in range(args.e2e_steps):
         g.replay()
         he.copy_(s.energy, non_blocking=True)
-        hp.copy_(s.pos, non_blocking=True)
+        fpm.fpm_pack_xyz(s.n, s.prec, s.pos, dp_out)
+        hp.copy_(dp_out, non_blocking=True)
         ev_p.record(main)
-        hv.copy_(s.vel, non_blocking=True)
+        fpm.fpm_pack_xyz(s.n, s.prec, s.vel, dv_out)
+        hv.copy_(dv_out, non_blocking=True)
         ev_v.record(main)
         if k + 1 < args.e2e_steps:
             with torch.cuda.stream(side):
                 side.wait_event(ev_p)
-                s.pos.copy_(hp, non_blocking=True)
+                dp_in.copy_(hp, non_blocking=True)
+                fpm.fpm_unpack_xyz(s.n, s.prec, dp_in, s.pos, stream=side)
                 side.wait_event(ev_v)
-                s.vel.copy_(hv, non_blocking=True)
+                dv_in.copy_(hv, non_blocking=True)
+                fpm.fpm_unpack_xyz(s.n, s.prec, dv_in, s.vel, stream=side)
                 ev_in.record(side)
             main.wait_event(ev_in)
     torch.cuda.synchronize()

@@ -312,6 +312,14 @@ fpm_status fpm_vv_drift_check(const fpm_box *box, int32_t n, fpm_prec prec, doub
                               const void *force, const void *pos_ref, double skin, fpm_dev_status *d_status,
                               fpm_stream stream);
 
+/* Transfers in the host's layout: packed (x, y, z) triples (float or double
+ * [3n], device memory) to and from the 4-vector state (float4|double4 [n]).
+ * unpack writes x, y, z of dst4 and keeps its w; pack writes 3n values.
+ * With these, an end-to-end step moves 12 (24) bytes per vector across the
+ * host link instead of 16 (32). */
+fpm_status fpm_unpack_xyz(int32_t n, fpm_prec prec, const void *src_xyz, void *dst4, fpm_stream stream);
+fpm_status fpm_pack_xyz(int32_t n, fpm_prec prec, const void *src4, void *dst_xyz, fpm_stream stream);
+
 /* Kinetic energy and momentum in FP64 (fixed-order, bit-reproducible):
  * d_out[0] = 1/2 sum |v|^2, d_out[1..3] = sum v. */
 fpm_status fpm_kinetic(int32_t n, fpm_prec prec, const void *vel, double *d_out,

@@ -151,3 +151,56 @@ extern "C" fpm_status fpm_kinetic(int32_t n, fpm_prec prec, const void *vel, dou
         k_kinetic<double><<<blocks, 256, 0, st>>>(n, (const double4_32a *)vel, r.part, r.counter, d_out);
     return fpm_check_launch("fpm_kinetic");
 }
+
+// ---- host-layout transfers: packed (x, y, z) <-> the 4-vector state ---------
+
+namespace fpm {
+
+template <typename T>
+__global__ void k_unpack_xyz(int n, const T *__restrict__ src, V4<T> *__restrict__ dst)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    V4<T> v = dst[i];
+    v.x = src[3 * (size_t)i];
+    v.y = src[3 * (size_t)i + 1];
+    v.z = src[3 * (size_t)i + 2];
+    dst[i] = v;
+}
+
+template <typename T>
+__global__ void k_pack_xyz(int n, const V4<T> *__restrict__ src, T *__restrict__ dst)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const V4<T> v = src[i];
+    dst[3 * (size_t)i] = v.x;
+    dst[3 * (size_t)i + 1] = v.y;
+    dst[3 * (size_t)i + 2] = v.z;
+}
+
+}  // namespace fpm
+
+extern "C" fpm_status fpm_unpack_xyz(int32_t n, fpm_prec prec, const void *src_xyz, void *dst4, fpm_stream stream)
+{
+    if (n < 0 || (n > 0 && (!src_xyz || !dst4))) return fpm_fail(FPM_ERR_INVALID, "fpm_unpack_xyz: bad argument");
+    if (prec != FPM_F32 && prec != FPM_F64) return fpm_fail(FPM_ERR_INVALID, "fpm_unpack_xyz: bad precision");
+    if (n == 0) return FPM_OK;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == FPM_F32) k_unpack_xyz<float><<<blocks, 256, 0, st>>>(n, (const float *)src_xyz, (float4 *)dst4);
+    else k_unpack_xyz<double><<<blocks, 256, 0, st>>>(n, (const double *)src_xyz, (double4_32a *)dst4);
+    return fpm_check_launch("fpm_unpack_xyz");
+}
+
+extern "C" fpm_status fpm_pack_xyz(int32_t n, fpm_prec prec, const void *src4, void *dst_xyz, fpm_stream stream)
+{
+    if (n < 0 || (n > 0 && (!src4 || !dst_xyz))) return fpm_fail(FPM_ERR_INVALID, "fpm_pack_xyz: bad argument");
+    if (prec != FPM_F32 && prec != FPM_F64) return fpm_fail(FPM_ERR_INVALID, "fpm_pack_xyz: bad precision");
+    if (n == 0) return FPM_OK;
+    const unsigned blocks = (unsigned)((n + 255) / 256);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == FPM_F32) k_pack_xyz<float><<<blocks, 256, 0, st>>>(n, (const float4 *)src4, (float *)dst_xyz);
+    else k_pack_xyz<double><<<blocks, 256, 0, st>>>(n, (const double4_32a *)src4, (double *)dst_xyz);
+    return fpm_check_launch("fpm_pack_xyz");
+}

@@ -123,6 +123,8 @@ _SIG = {
                                   _VP, _VP]),
     "fpm_adjoint_seed": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _VP, _VP, _VP, _VP]),
     "fpm_kinetic": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _VP, _VP, _c.c_size_t, _VP]),
+    "fpm_unpack_xyz": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _VP, _VP]),
+    "fpm_pack_xyz": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _VP, _VP]),
     "fpm_batch_plan": (_c.c_int, [_c.c_int32, _c.POINTER(fpm_box), _c.POINTER(_c.c_int32), _c.c_double, _c.c_int32,
                                   _c.POINTER(fpm_replica), _c.POINTER(fpm_batch)]),
     "fpm_batch_drift_check": (_c.c_int, [_c.POINTER(fpm_batch), _VP, _c.c_double, _VP, _VP, _VP, _VP, _c.c_double,
@@ -456,3 +458,15 @@ def fpm_batch_lj_forces(batch, d_reps, pos, list_obj, nn, cap, eps, sigma, rc, f
                                      float(eps), float(sigma), float(rc), _ptr(force), _ptr(d_energy),
                                      _ptr(workspace), _nbytes(workspace), _ptr(d_status), _stream(stream)))
     _count(1)
+
+
+# ------------------------------------------------------------------ host-layout transfers
+
+def fpm_unpack_xyz(n, prec, src_xyz, dst4, stream=None):
+    _check(lib().fpm_unpack_xyz(int(n), int(prec), _ptr(src_xyz), _ptr(dst4), _stream(stream)))
+    _count(1 if n > 0 else 0)
+
+
+def fpm_pack_xyz(n, prec, src4, dst_xyz, stream=None):
+    _check(lib().fpm_pack_xyz(int(n), int(prec), _ptr(src4), _ptr(dst_xyz), _stream(stream)))
+    _count(1 if n > 0 else 0)

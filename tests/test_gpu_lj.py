@@ -174,3 +174,22 @@ def test_graph_steps_1m_match_oracle(cuda):
         want = np.sort(oracle.neighbors_one(ref, s.L, s.periodic, s.r_list, int(i)).astype(np.int64))
         got = np.sort(nbr[:nn[i], i].astype(np.int64))
         assert np.array_equal(got, want), i
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_pack_unpack_xyz(cuda, prec):
+    """fpm_pack_xyz / fpm_unpack_xyz move x, y, z between the packed host
+    layout and the 4-vector state exactly, keeping the state's w."""
+    dt_ = torch.float32 if prec == "f32" else torch.float64
+    fp = fpm.FPM_F32 if prec == "f32" else fpm.FPM_F64
+    n = 100003
+    g = torch.Generator().manual_seed(3)
+    x4 = torch.rand((n, 4), generator=g, dtype=dt_).cuda()
+    w = x4[:, 3].clone()
+    xyz = torch.empty((n, 3), dtype=dt_, device="cuda")
+    fpm.fpm_pack_xyz(n, fp, x4, xyz)
+    y4 = torch.full_like(x4, -1.0)
+    y4[:, 3] = w
+    fpm.fpm_unpack_xyz(n, fp, xyz, y4)
+    torch.cuda.synchronize()
+    assert torch.equal(xyz, x4[:, :3]) and torch.equal(y4, x4)
