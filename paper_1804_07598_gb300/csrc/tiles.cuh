@@ -501,8 +501,9 @@ __device__ __forceinline__ void for_each_entry(uint32_t m, const uint32_t *__res
 // staged cells t0..t1 of every stencil row (its 27 cells): every candidate
 // inside r_list is written as a 16-bit staged index, two per word (entry k
 // in half k & 1 of word (k >> 1) * ld + i).  Returns the candidate count
-// (entries beyond cap are counted, not stored).  The append is branch-free
-// (a select and one predicated store), so the lanes of a warp stay converged.
+// (entries beyond cap are counted, not stored).  Candidates are tested 32 at
+// a time into a bit mask (one shift-in per test); then only the set bits are
+// appended, in increasing slot order.
 template <bool FAST, bool SMEM, typename T>
 __device__ __forceinline__ uint32_t scan_candidates(const TileCfg &cfg, const BoxT<T> &box, const TileGeom &g,
                                                     const TileDesc &d, const V4<T> *__restrict__ pos,
@@ -514,17 +515,27 @@ __device__ __forceinline__ uint32_t scan_candidates(const TileCfg &cfg, const Bo
     const uint32_t ucap = (uint32_t)cap;
     for (int r = 0; r < g.nrows; ++r) {
         const int s0 = g.off[r][t0], s1 = g.off[r][t1 + 1];
+        for (int base = s0; base < s1; base += 32) {
+            const int e = base + 32 < s1 ? base + 32 : s1;
+            uint32_t mask = 0;
 #pragma unroll 4
-        for (int s = s0; s < s1; ++s) {
-            const V4<T> pj = SMEM ? st[s] : staged_global(d, box, pos, s);
-            T dx, dy, dz;
-            const T r2 = tile_sep<FAST>(pi, pj, box, cfg, dx, dy, dz);
-            const bool hit = (r2 < rl2) & (s != self);
-            const bool room = cnt < ucap;
-            const bool odd = (cnt & 1u) != 0u;
-            if (hit & room & odd) words[(int64_t)(cnt >> 1) * ld + i] = pending | ((uint32_t)s << 16);
-            pending = (hit & room & !odd) ? (uint32_t)s : pending;
-            cnt += hit ? 1u : 0u;
+            for (int s = base; s < e; ++s) {
+                const V4<T> pj = SMEM ? st[s] : staged_global(d, box, pos, s);
+                T dx, dy, dz;
+                const T r2 = tile_sep<FAST>(pi, pj, box, cfg, dx, dy, dz);
+                mask = (mask << 1) | (r2 < rl2 ? 1u : 0u);
+            }
+            if (self >= base && self < e) mask &= ~(1u << (e - 1 - self));
+            while (mask) {
+                const int bit = 31 - __clz(mask);
+                mask &= ~(1u << bit);
+                const uint32_t s = (uint32_t)(e - 1 - bit);
+                const bool room = cnt < ucap;
+                const bool odd = (cnt & 1u) != 0u;
+                if (room & odd) words[(int64_t)(cnt >> 1) * ld + i] = pending | (s << 16);
+                pending = (room & !odd) ? s : pending;
+                ++cnt;
+            }
         }
     }
     const uint32_t stored = cnt < ucap ? cnt : ucap;
