@@ -518,7 +518,7 @@ __device__ __forceinline__ uint32_t scan_candidates(const TileCfg &cfg, const Bo
         for (int base = s0; base < s1; base += 32) {
             const int e = base + 32 < s1 ? base + 32 : s1;
             uint32_t mask = 0;
-#pragma unroll 4
+#pragma unroll 8
             for (int s = base; s < e; ++s) {
                 const V4<T> pj = SMEM ? st[s] : staged_global(d, box, pos, s);
                 T dx, dy, dz;
