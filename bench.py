@@ -43,7 +43,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per launch of the dominant kernel from one ncu capture
 # (profiles/lj_tiles_lj_1m.md), valid while its sources hash to `sha`.
 NCU_TRAFFIC = {"k_lj_tiles<float>": {"files": ["lj.cu", "lj_pair.cuh", "tiles.cuh", "fpm_common.cuh", "reduce.cuh"],
-                                    "sha": "f4f8ee67e6c939c1", "bytes_per_launch": 183730432}}
+                                    "sha": "3b4a3a305a566bc9", "bytes_per_launch": 183673856}}
 
 
 def parse():
