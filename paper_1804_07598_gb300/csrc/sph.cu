@@ -33,12 +33,15 @@ struct SphK {
     int kernel;      // 0 Wendland C2, 1 cubic spline
 };
 
+// 1/x by the hardware approximation alone (within 1 ulp, as the PTX ISA
+// states for rcp.approx.f32): the SPH rates are held to 1e-4 of their RMS,
+// four orders above that rounding.  (The LJ sweep refines its 1/r^2 with a
+// Newton step: its forces are held to 1e-5 and carry r^-14.)
 __device__ __forceinline__ float sph_rcp(float x)
 {
     float y;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    const float e = __fmaf_rn(-x, y, 1.0f);
-    return __fmaf_rn(y, e, y);
+    return y;
 }
 
 // b * ((1 + x)^gamma - 1) by Horner on the binomial coefficients.
