@@ -69,7 +69,10 @@ __device__ __forceinline__ float grad_factor(const SphK &K, float r2)
     return q < 1.0f ? K.wcoef * (-3.0f + 2.25f * q) : -0.75f * K.wcoef * t * t * sph_rcp(q);
 }
 
-template <bool FAST, bool SMEM, int KK>
+// PRE: the staged slots already hold P_q in the position's w and rho_q in the
+// velocity's w (written once per tile by k_sph_tiles for tiles without
+// periodic-wall flags, whose position w is otherwise unused).
+template <bool FAST, bool SMEM, int KK, bool PRE = false>
 __device__ __forceinline__ void sph_pair(const TileCfg &cfg, const BoxT<float> &box, const TileDesc &d,
                                          const float4 *__restrict__ pos, const float4 *__restrict__ vr,
                                          const float4 *__restrict__ st, const float4 *__restrict__ sv,
@@ -91,8 +94,8 @@ __device__ __forceinline__ void sph_pair(const TileCfg &cfg, const BoxT<float> &
     const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
     const float vdr = vx * dx + vy * dy + vz * dz;
     dr += K.m * F * vdr;
-    const float rho_j = K.rho0 + vj.w;
-    const float Pj = tait(K, vj.w);
+    const float rho_j = PRE ? vj.w : K.rho0 + vj.w;
+    const float Pj = PRE ? pj.w : tait(K, vj.w);
     const float inv_rr = sph_rcp(rho_i * rho_j);
     const float mu = K.h * vdr * sph_rcp(r2 + K.eta2);
     const float visc = vdr < 0.0f ? -K.alpha * K.c0 * mu * 2.0f * sph_rcp(rho_i + rho_j) : 0.0f;
@@ -105,7 +108,7 @@ __device__ __forceinline__ void sph_pair(const TileCfg &cfg, const BoxT<float> &
 
 // One half of a home particle's list: words half, half + 2, ... (two threads
 // share each particle and add their sums).
-template <bool FAST, bool SMEM, int KK>
+template <bool FAST, bool SMEM, int KK, bool PRE = false>
 __device__ __forceinline__ void sph_sweep(const TileCfg &cfg, const BoxT<float> &box, const TileDesc &d,
                                           const float4 *__restrict__ pos, const float4 *__restrict__ vr,
                                           const float4 *__restrict__ st, const float4 *__restrict__ sv,
@@ -116,7 +119,8 @@ __device__ __forceinline__ void sph_sweep(const TileCfg &cfg, const BoxT<float> 
     for_each_entry<2, 2>(
         m, col, ld,
         [&](int s) {
-            sph_pair<FAST, SMEM, KK>(cfg, box, d, pos, vr, st, sv, pi, vi, rho_i, Pi, s, K, ax, ay, az, dr, mumax);
+            sph_pair<FAST, SMEM, KK, PRE>(cfg, box, d, pos, vr, st, sv, pi, vi, rho_i, Pi, s, K, ax, ay, az, dr,
+                                          mumax);
         },
         half);
 }
@@ -173,6 +177,15 @@ __global__ void __launch_bounds__(kSphThreads, 2)
     const bool in_smem = d.M <= stage_cap;
     if (!in_smem) note_spill(status);
     const bool staged = in_smem ? stage_positions(d, box, pos, sp, &bar, phase, status, vr, sv) : true;
+    // once per staged neighbour instead of once per pair: P_q and rho_q
+    if (in_smem && staged && !d.slow) {
+        for (int s = threadIdx.x; s < d.M; s += blockDim.x) {
+            const float drho = sv[s].w;
+            sp[s].w = tait(K, drho);
+            sv[s].w = K.rho0 + drho;
+        }
+        __syncthreads();
+    }
     // lanes 2t and 2t + 1 share home particle h0 + t, each walking half its list
     for (uint32_t t = threadIdx.x; staged && d.h0 + (t >> 1) < d.h1; t += blockDim.x) {
         const uint32_t i = d.h0 + (t >> 1), half = t & 1u;
@@ -187,8 +200,8 @@ __global__ void __launch_bounds__(kSphThreads, 2)
                 sph_sweep<false, true, KK>(cfg, box, d, pos, vr, sp, sv, pi, vi, rho_i, P_i, m, half, words + i, ld,
                                            K, ax, ay, az, dr, mumax);
             else
-                sph_sweep<true, true, KK>(cfg, box, d, pos, vr, sp, sv, pi, vi, rho_i, P_i, m, half, words + i, ld,
-                                          K, ax, ay, az, dr, mumax);
+                sph_sweep<true, true, KK, true>(cfg, box, d, pos, vr, sp, sv, pi, vi, rho_i, P_i, m, half, words + i,
+                                                ld, K, ax, ay, az, dr, mumax);
         } else {
             float o5[5];
             sph_sweep_spilled<KK>(cfg, box, d, pos, vr, pi, vi, rho_i, P_i, m, half, words + i, ld, K, o5);
