@@ -26,7 +26,8 @@ namespace fpm {
 struct SphK {
     float h, m, rho0, inv_rho0, c0, alpha, eta2, b, g[3];
     float two_h2;    // (2h)^2, the support test
-    float wcoef;     // Wendland: F = wcoef (1 - q/2)^3;  cubic: s/h^2
+    float wcoef;     // m times (Wendland: F = wcoef (1 - q/2)^3;  cubic: s/h^2)
+    float visc2;     // -2 alpha c0 (Pi_pq = visc2 mu / (rho_p + rho_q))
     float inv_h;
     float binom[8];  // C(gamma, k), k = 1..gamma (0 beyond)
     int gamma;
@@ -54,7 +55,7 @@ __device__ __forceinline__ float tait(const SphK &K, float drho)
     return K.b * (s * x);
 }
 
-// (dW/dr)/r for r2 inside the support; KK = 0 Wendland C2, 1 cubic spline.
+// m (dW/dr)/r for r2 inside the support; KK = 0 Wendland C2, 1 cubic spline.
 template <int KK>
 __device__ __forceinline__ float grad_factor(const SphK &K, float r2)
 {
@@ -90,19 +91,19 @@ __device__ __forceinline__ void sph_pair(const TileCfg &cfg, const BoxT<float> &
     float dx, dy, dz;
     const float r2 = tile_sep<FAST>(pi, pj, box, cfg, dx, dy, dz);
     const bool in = r2 < K.two_h2 && r2 > 0.0f;
-    const float F = in ? grad_factor<KK>(K, r2) : 0.0f;
+    const float Fm = in ? grad_factor<KK>(K, r2) : 0.0f;  // m F
     const float vx = vi.x - vj.x, vy = vi.y - vj.y, vz = vi.z - vj.z;
     const float vdr = vx * dx + vy * dy + vz * dz;
-    dr += K.m * F * vdr;
+    dr = fmaf(Fm, vdr, dr);
     const float rho_j = PRE ? vj.w : K.rho0 + vj.w;
     const float Pj = PRE ? pj.w : tait(K, vj.w);
     const float inv_rr = sph_rcp(rho_i * rho_j);
     const float mu = K.h * vdr * sph_rcp(r2 + K.eta2);
-    const float visc = vdr < 0.0f ? -K.alpha * K.c0 * mu * 2.0f * sph_rcp(rho_i + rho_j) : 0.0f;
-    const float c = -K.m * ((P_i + Pj) * inv_rr + visc) * F;
-    ax += c * dx;
-    ay += c * dy;
-    az += c * dz;
+    const float visc = vdr < 0.0f ? K.visc2 * mu * sph_rcp(rho_i + rho_j) : 0.0f;
+    const float c = ((P_i + Pj) * inv_rr + visc) * Fm;
+    ax = fmaf(-c, dx, ax);
+    ay = fmaf(-c, dy, ay);
+    az = fmaf(-c, dz, az);
     if (in) mumax = fmaxf(mumax, fabsf(mu));
 }
 
@@ -359,10 +360,11 @@ static SphK make_sph(const fpm_sph_params &p)
     K.kernel = p.kernel;
     if (p.kernel == 0) {
         const double a = 21.0 / (16.0 * pi * p.h * p.h * p.h);
-        K.wcoef = (float)(-5.0 * a / (p.h * p.h));
+        K.wcoef = (float)(p.mass * -5.0 * a / (p.h * p.h));
     } else {
-        K.wcoef = (float)(1.0 / (pi * p.h * p.h * p.h) / (p.h * p.h));
+        K.wcoef = (float)(p.mass / (pi * p.h * p.h * p.h) / (p.h * p.h));
     }
+    K.visc2 = (float)(-2.0 * p.alpha * p.c0);
     // C(gamma, k) for k = 1..gamma in binom[k-1], Horner from the highest
     double c = 1.0;
     for (int k = 1; k <= 8; ++k) {
