@@ -335,28 +335,44 @@ __device__ bool stage_positions(const TileDesc &d, const BoxT<T> &box, const V4<
                                 const V4<T> *__restrict__ aux = nullptr, V4<T> *__restrict__ aux_st = nullptr)
 {
     const uint32_t b = smem_u32(bar);
-    if (threadIdx.x == 0) {
-        // order this block's earlier generic accesses of the buffers before the async copies
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        const uint32_t bytes = (uint32_t)d.M * (uint32_t)sizeof(V4<T>) * (aux ? 2u : 1u);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
-        for (int p = 0; p < kMaxPieces; ++p) {
-            const Piece pc = d.piece[p];
-            if (pc.len == 0) continue;
-            const uint32_t nb = (uint32_t)pc.len * (uint32_t)sizeof(V4<T>);
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    smem_u32(st + pc.soff)),
-                "l"(pos + pc.gstart), "r"(nb), "r"(b)
-                : "memory");
-            if (aux)
+    static_assert(kMaxPieces <= 32, "one lane of warp 0 per piece");
+    const int lane = (int)(threadIdx.x & 31u);
+    if (threadIdx.x < 32u) {
+        // lane 0 arms the barrier with the byte count; then lane p issues the
+        // copy (or copies) of piece p.  Each issuing lane first orders the
+        // block's earlier generic accesses of the buffers (made visible to it by
+        // the caller's barrier) before its async copies.
+        if (lane == 0) {
+            const uint32_t bytes = (uint32_t)d.M * (uint32_t)sizeof(V4<T>) * (aux ? 2u : 1u);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
+        }
+        __syncwarp();
+        if (lane < kMaxPieces) {
+            const Piece pc = d.piece[lane];
+            if (pc.len != 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                const uint32_t nb = (uint32_t)pc.len * (uint32_t)sizeof(V4<T>);
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                        smem_u32(aux_st + pc.soff)),
-                    "l"(aux + pc.gstart), "r"(nb), "r"(b)
+                        smem_u32(st + pc.soff)),
+                    "l"(pos + pc.gstart), "r"(nb), "r"(b)
                     : "memory");
+                if (aux)
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            smem_u32(aux_st + pc.soff)),
+                        "l"(aux + pc.gstart), "r"(nb), "r"(b)
+                        : "memory");
+            }
         }
     }
+    // the pieces that need the shifts or the flags: one piece per lane, every warp
+    bool fix = false;
+    if (lane < kMaxPieces) {
+        const Piece pc = d.piece[lane];
+        fix = pc.len != 0 && (pc.flags != 0 || d.slow);
+    }
+    uint32_t todo = __ballot_sync(kFull, fix);
     bool ok = mbar_wait(b, phase, kWaitCycles);
     if (!ok) {
         latch_flag(status, FPM_FLAG_TIMEOUT);
@@ -364,9 +380,11 @@ __device__ bool stage_positions(const TileDesc &d, const BoxT<T> &box, const V4<
     }
     phase ^= 1u;
     if (!__syncthreads_and(ok)) return false;
-    for (int p = 0; p < kMaxPieces; ++p) {
+    if (todo == 0u) return true;  // nothing written: the copies' completion was observed by every thread
+    while (todo) {
+        const int p = __ffs(todo) - 1;
+        todo &= todo - 1u;
         const Piece pc = d.piece[p];
-        if (pc.len == 0 || (pc.flags == 0 && !d.slow)) continue;
         const T sx = (pc.flags & kLoX) ? box.L[0] : (T)0;
         const T sy = (pc.flags & kLoY) ? box.L[1] : (T)0;
         const T sz = (pc.flags & kLoZ) ? box.L[2] : (T)0;
