@@ -26,15 +26,16 @@ template <typename T> struct LJParams {
 };
 
 // One list entry, masked (not branched) by the cutoff test.  With
-// s6 = (sigma^2/r^2)^3 and a = 2 s6^2 - s6, the pair force is
-// 24 eps a / r^2 (x_i - x_j), its virial 24 eps a and its energy
-// 4 eps (s6^2 - s6); the constant factors 24 eps and 4 eps are applied once
-// per particle by the caller, so the sums here are of a/r^2 * d, a, and
-// s6^2 - s6.
+// s6 = (sigma^2/r^2)^3 (zero beyond the cutoff) and a = 2 s6^2 - s6, the
+// pair force is 24 eps a / r^2 (x_i - x_j), its virial 24 eps a and its
+// energy 4 eps (s6^2 - s6).  The entry adds a / r^2 * d to the force sums
+// and s6^2, s6 to S12, S6, from which the caller forms the energy sum
+// S12 - S6 and the virial sum 2 S12 - S6; the constant factors 24 eps and
+// 4 eps are applied once per particle.
 template <typename T, bool FAST, bool SMEM>
 __device__ __forceinline__ void lj_pair(const TileCfg &cfg, const BoxT<T> &box, const TileDesc &d,
                                         const V4<T> *__restrict__ pos, const V4<T> *__restrict__ st, const V4<T> &pi,
-                                        int s, const LJParams<T> &P, T &fx, T &fy, T &fz, T &u, T &w, uint32_t &np)
+                                        int s, const LJParams<T> &P, T &fx, T &fy, T &fz, T &S12, T &S6, uint32_t &np)
 {
     const V4<T> pj = SMEM ? st[s] : staged_global(d, box, pos, s);
     T dx, dy, dz;
@@ -42,15 +43,15 @@ __device__ __forceinline__ void lj_pair(const TileCfg &cfg, const BoxT<T> &box, 
     const bool in = r2 < P.rc2;
     const T ir2 = recip(r2);
     const T s2 = P.sig2 * ir2;
-    const T s6 = s2 * s2 * s2;
+    const T s6 = in ? s2 * s2 * s2 : (T)0;
     const T s12 = s6 * s6;
-    const T a = in ? (T)2 * s12 - s6 : (T)0;
+    const T a = (T)2 * s12 - s6;
     const T g = a * ir2;
     fx += g * dx;
     fy += g * dy;
     fz += g * dz;
-    w += a;
-    u += in ? s12 - s6 : (T)0;
+    S12 += s12;
+    S6 += s6;
     np += in ? 1u : 0u;
 }
 
@@ -64,9 +65,12 @@ __device__ __forceinline__ void lj_sweep(const TileCfg &cfg, const BoxT<T> &box,
                                          const V4<T> &pi, uint32_t m, const uint32_t *__restrict__ col, int64_t ld,
                                          const LJParams<T> &P, T &fx, T &fy, T &fz, T &u, T &w, uint32_t &np)
 {
+    T S12 = 0, S6 = 0;
     for_each_entry<kLjChunk>(m, col, ld, [&](int s) {
-        lj_pair<T, FAST, SMEM>(cfg, box, d, pos, st, pi, s, P, fx, fy, fz, u, w, np);
+        lj_pair<T, FAST, SMEM>(cfg, box, d, pos, st, pi, s, P, fx, fy, fz, S12, S6, np);
     });
+    u += S12 - S6;
+    w += (T)2 * S12 - S6;
 }
 
 }  // namespace fpm
