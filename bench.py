@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--profile", default=None, choices=["forces", "step", "sph", "verlet", "batch", "adjoint"],
+    ap.add_argument("--profile", default=None, choices=["forces", "step", "sph", "verlet", "batch", "adjoint",
+                                                         "celllist"],
                     help="profiling target for ncu: build the 1M-atom system, then run --steps force sweeps "
                          "or eager steps (no timing, no JSON line)")
     ap.add_argument("--fp64-steps", type=int, default=100)
@@ -63,6 +64,7 @@ def parse():
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--sph-steps", type=int, default=500)
     ap.add_argument("--batch-steps", type=int, default=300)
+    ap.add_argument("--celllist-builds", type=int, default=50)
     return ap.parse_args()
 
 
@@ -485,6 +487,42 @@ def run_ours(args, ws, rank, local):
                               "cached": tuned["cached"]}}
         del bb, gb
 
+    # cell-list build from HBM: 8M particles (positions and velocities twice
+    # the L2), the in-place rebuild of an already sorted state, replayed from a
+    # CUDA graph of one build (six kernels)
+    cell = None
+    if args.celllist_builds > 0:
+        cs = CellListState(torch, fpm, inputs)
+        cstream = torch.cuda.Stream()
+        cstream.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(cstream):
+            for _ in range(3):
+                cs.build(stream=cstream)
+        torch.cuda.current_stream().wait_stream(cstream)
+        torch.cuda.synchronize()
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(cg, stream=cstream):
+            cs.build(stream=cstream)
+        for _ in range(3):
+            cg.replay()
+        torch.cuda.synchronize()
+        with clk.window():
+            e0.record()
+            for _ in range(args.celllist_builds):
+                cg.replay()
+            e1.record()
+            torch.cuda.synchronize()
+        cs.check_status()
+        cus = 1e3 * e0.elapsed_time(e1) / args.celllist_builds
+        cgbs = cs.alg_bytes / (cus * 1e-6) / 1e9
+        cell = {"workload": f"lj_8m: {cs.n} particles (FCC 126^3 x 4, jittered), {cs.grid.ncell} cells of r_list "
+                            f"2.8, FP32 pos + vel + ids reordered in place, already sorted (the MD rebuild)",
+                "us_per_build": cus, "alg_bytes_per_build": cs.alg_bytes,
+                "alg_bytes_per_particle": CELL_BYTES_PER_PARTICLE, "alg_bytes_per_cell": CELL_BYTES_PER_CELL,
+                "achieved_gbs": cgbs, "peak_gbs": peak, "frac": cgbs / peak, "peak_kind": f"{peak_kind} (burst)",
+                "launches_per_build": 6}
+        del cs, cg
+
     clk.__exit__()
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
@@ -522,6 +560,7 @@ def run_ours(args, ws, rank, local):
         "adjoint": adj,
         "sph": sph,
         "batch": batch,
+        "celllist": cell,
         "gpu_launches": per_step_launches * args.steps + body * int(rebuilds),
         "clocks": clocks,
         "cpu_baseline": cpu,
@@ -529,11 +568,61 @@ def run_ours(args, ws, rank, local):
     print(json.dumps(line), flush=True)
 
 
+# Algorithmic bytes of one in-place FP32 cell-list build (positions,
+# velocities and ids reordered), per particle: k_bin reads pos/vel/id (36 B)
+# and writes their staged copies (36 B), the cell id and the arrival rank
+# (8 B); k_scatter reads cell id and rank and writes the slot (12 B);
+# k_sort_gather reads the slot and the staged pos/vel/id (40 B) and writes
+# pos/vel/id and perm (40 B).  Per cell: count zeroed, incremented (read +
+# write), read by both scan passes, cell_start written and read three times
+# (36 B).
+CELL_BYTES_PER_PARTICLE = 80 + 12 + 80
+CELL_BYTES_PER_CELL = 36
+
+
+class CellListState:
+    """The lj_8m lattice (jittered), sorted once: the state of an MD rebuild,
+    whose input is the previous build's order."""
+
+    def __init__(self, torch, fpm, inputs):
+        wl = inputs.WORKLOADS["lj_8m"]
+        pos, vel, L = inputs.lj_state(wl, jitter=0.05)
+        self.wl, self.n = wl, wl.n
+        dev = torch.device("cuda")
+        self.box = fpm.make_box(L)
+        self.grid = fpm.fpm_grid_make(self.box, wl.rc + wl.skin, self.n)
+        self.pos = torch.as_tensor(pos, dtype=torch.float32).to(dev)
+        self.vel = torch.as_tensor(vel, dtype=torch.float32).to(dev)
+        self.ids = torch.arange(self.n, dtype=torch.int32, device=dev)
+        self.perm = torch.zeros(self.n, dtype=torch.int32, device=dev)
+        self.cell_start = torch.zeros(self.grid.ncell + 1, dtype=torch.int32, device=dev)
+        self.status = torch.zeros(fpm.STATUS_BYTES // 4, dtype=torch.int32, device=dev)
+        self.ws = torch.zeros(fpm.fpm_celllist_workspace(self.n, self.grid, fpm.FPM_F32), dtype=torch.uint8,
+                              device=dev)
+        self.fpm = fpm
+        self.build()
+
+    def check_status(self):
+        st = self.fpm.read_status(self.status)
+        code = self.fpm.fpm_status_from_device(st)
+        if code != self.fpm.FPM_OK:
+            raise self.fpm.FpmError(code, f"cell-list build: device status flags={st.flags}")
+
+    def build(self, stream=None):
+        self.fpm.fpm_celllist_build(self.box, self.grid, self.n, self.fpm.FPM_F32, self.pos, self.vel, self.ids,
+                                    self.pos, self.vel, self.ids, self.cell_start, self.perm, self.ws, self.status,
+                                    None, stream=stream)
+
+    @property
+    def alg_bytes(self):
+        return CELL_BYTES_PER_PARTICLE * self.n + CELL_BYTES_PER_CELL * self.grid.ncell
+
+
 def run_profile_target(args):
     """A small, self-contained launch sequence for ncu captures."""
     import torch
     from paper_1804_07598_gb300 import build as fbuild
-    from paper_1804_07598_gb300 import inputs
+    from paper_1804_07598_gb300 import fpm, inputs
     from paper_1804_07598_gb300.md import LJSystem
     fbuild.build()
     if args.profile == "sph":
@@ -554,6 +643,14 @@ def run_profile_target(args):
         runner.backward()
         torch.cuda.synchronize()
         print(f"profile target done: adjoint x{args.steps}, n={wla.n}", flush=True)
+        return
+    if args.profile == "celllist":
+        cs = CellListState(torch, fpm, inputs)
+        for _ in range(args.steps):
+            cs.build()
+        torch.cuda.synchronize()
+        cs.check_status()
+        print(f"profile target done: celllist x{args.steps}, n={cs.n}", flush=True)
         return
     if args.profile == "batch":
         from paper_1804_07598_gb300.batch import LJBatch

@@ -211,6 +211,31 @@ __device__ __forceinline__ void emit(uint32_t slot, uint32_t src, const BoxT<T> 
     perm[slot] = src;
 }
 
+// A cell of more than 32 particles, by one warp: the rank of each element is
+// the number of smaller input indices in the cell.
+template <typename T>
+__device__ __noinline__ void sort_gather_large(uint32_t s, uint32_t k, const uint32_t *__restrict__ tmp,
+                                               const BoxT<T> &box, const V4<T> *pos_src, const V4<T> *vel_src,
+                                               const uint32_t *id_src, V4<T> *pos_out, V4<T> *vel_out,
+                                               uint32_t *id_out, uint32_t *__restrict__ perm)
+{
+    const unsigned lane = threadIdx.x & 31;
+    for (uint32_t e0 = 0; e0 < k; e0 += 32) {
+        const bool mine = e0 + lane < k;
+        const uint32_t v = mine ? tmp[s + e0 + lane] : UINT_MAX;
+        uint32_t r = 0;
+        for (uint32_t m0 = 0; m0 < k; m0 += 32) {
+            const uint32_t w = (m0 + lane < k) ? tmp[s + m0 + lane] : UINT_MAX;
+#pragma unroll 8
+            for (int t = 0; t < 32; ++t) r += (__shfl_sync(kFull, w, t) < v) ? 1u : 0u;
+        }
+        if (mine) emit<T>(s + r, v, box, pos_src, vel_src, id_src, pos_out, vel_out, id_out, perm);
+    }
+}
+
+// One warp per cell, two cells at a time (cells c and c + nwarps): both cells'
+// bounds, slot lists and gathered records are loaded before either is stored,
+// so each warp keeps two cells' memory accesses in flight.
 template <typename T>
 __global__ void k_sort_gather(BoxT<T> box, int ncell, const uint32_t *__restrict__ cell_start,
                               const uint32_t *__restrict__ tmp, const V4<T> *pos_src, const V4<T> *vel_src,
@@ -220,28 +245,63 @@ __global__ void k_sort_gather(BoxT<T> box, int ncell, const uint32_t *__restrict
     if (gated_off(gate)) return;
     const unsigned lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < ncell; c += nwarps) {
-        // one warp per cell (the loop bound is uniform per warp)
-        const uint32_t s = cell_start[c], e = cell_start[c + 1];
-        const uint32_t k = e - s;
-        if (k == 0) continue;
-        if (k <= 32) {
-            uint32_t v = lane < k ? tmp[s + lane] : UINT_MAX;
-            v = warp_sort32(v);
-            if (lane < k) emit<T>(s + lane, v, box, pos_src, vel_src, id_src, pos_out, vel_out, id_out, perm);
+    // the loop bound is uniform per warp
+    for (int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; c < ncell; c += 2 * nwarps) {
+        const int64_t c1 = c + nwarps;
+        const bool two = c1 < ncell;
+        const uint32_t s0 = cell_start[c], k0 = cell_start[c + 1] - s0;
+        const uint32_t s1 = two ? cell_start[c1] : 0u, k1 = two ? cell_start[c1 + 1] - s1 : 0u;
+        if (k0 > 32u || k1 > 32u) {  // rare: a crowded cell; each cell on its own
+            if (k0 > 32u)
+                sort_gather_large<T>(s0, k0, tmp, box, pos_src, vel_src, id_src, pos_out, vel_out, id_out, perm);
+            else if (k0 > 0u) {
+                uint32_t v = lane < k0 ? tmp[s0 + lane] : UINT_MAX;
+                v = warp_sort32(v);
+                if (lane < k0) emit<T>(s0 + lane, v, box, pos_src, vel_src, id_src, pos_out, vel_out, id_out, perm);
+            }
+            if (k1 > 32u)
+                sort_gather_large<T>(s1, k1, tmp, box, pos_src, vel_src, id_src, pos_out, vel_out, id_out, perm);
+            else if (k1 > 0u) {
+                uint32_t v = lane < k1 ? tmp[s1 + lane] : UINT_MAX;
+                v = warp_sort32(v);
+                if (lane < k1) emit<T>(s1 + lane, v, box, pos_src, vel_src, id_src, pos_out, vel_out, id_out, perm);
+            }
             continue;
         }
-        // larger cells: rank of each element = number of smaller input indices
-        for (uint32_t e0 = 0; e0 < k; e0 += 32) {
-            const bool mine = e0 + lane < k;
-            const uint32_t v = mine ? tmp[s + e0 + lane] : UINT_MAX;
-            uint32_t r = 0;
-            for (uint32_t m0 = 0; m0 < k; m0 += 32) {
-                const uint32_t w = (m0 + lane < k) ? tmp[s + m0 + lane] : UINT_MAX;
-#pragma unroll 8
-                for (int t = 0; t < 32; ++t) r += (__shfl_sync(kFull, w, t) < v) ? 1u : 0u;
-            }
-            if (mine) emit<T>(s + r, v, box, pos_src, vel_src, id_src, pos_out, vel_out, id_out, perm);
+        const bool a0 = lane < k0, a1 = lane < k1;
+        uint32_t v0 = a0 ? tmp[s0 + lane] : UINT_MAX;
+        uint32_t v1 = a1 ? tmp[s1 + lane] : UINT_MAX;
+        v0 = warp_sort32(v0);
+        v1 = warp_sort32(v1);
+        V4<T> p0{}, p1{}, q0{}, q1{};
+        uint32_t i0 = v0, i1 = v1;
+        if (a0) p0 = pos_src[v0];
+        if (a1) p1 = pos_src[v1];
+        if (vel_out) {
+            if (a0) q0 = vel_src[v0];
+            if (a1) q1 = vel_src[v1];
+        }
+        if (id_out && id_src) {
+            if (a0) i0 = id_src[v0];
+            if (a1) i1 = id_src[v1];
+        }
+        if (a0) {
+            if (box.per[0]) p0.x = wrap1(p0.x, box.L[0]);
+            if (box.per[1]) p0.y = wrap1(p0.y, box.L[1]);
+            if (box.per[2]) p0.z = wrap1(p0.z, box.L[2]);
+            pos_out[s0 + lane] = p0;
+            if (vel_out) vel_out[s0 + lane] = q0;
+            if (id_out) id_out[s0 + lane] = i0;
+            perm[s0 + lane] = v0;
+        }
+        if (a1) {
+            if (box.per[0]) p1.x = wrap1(p1.x, box.L[0]);
+            if (box.per[1]) p1.y = wrap1(p1.y, box.L[1]);
+            if (box.per[2]) p1.z = wrap1(p1.z, box.L[2]);
+            pos_out[s1 + lane] = p1;
+            if (vel_out) vel_out[s1 + lane] = q1;
+            if (id_out) id_out[s1 + lane] = i1;
+            perm[s1 + lane] = v1;
         }
     }
 }

@@ -11,6 +11,9 @@ the standard reduced-unit LJ fluid at density 0.8442):
 * ``lj_small``   : 4000 particles, FCC 10^3 cells, FP64 path, 100 NVE steps.
 * ``lj_1m``      : 1,000,188 particles, FCC 63^3 cells, FP32 path, 1000 steps.
 * ``lj_adjoint`` : 32,768 particles, FCC 16x16x32 cells (orthorhombic box).
+* ``lj_8m``      : 8,001,504 particles, FCC 126^3 cells: the cell-list build
+  measured from HBM (its positions and velocities alone, 256 MB in FP32, are
+  twice the GPU's L2).
 * ``lj_batched`` : 512 replicas, log-uniform sizes in [256, 16384].
 """
 from __future__ import annotations
@@ -56,6 +59,7 @@ WORKLOADS = {
     "lj_small": LJWorkload("lj_small", (10, 10, 10), steps=100, precision="f64"),
     "lj_1m": LJWorkload("lj_1m", (63, 63, 63), steps=1000, precision="f32"),
     "lj_adjoint": LJWorkload("lj_adjoint", (16, 16, 32), steps=200, precision="f32"),
+    "lj_8m": LJWorkload("lj_8m", (126, 126, 126), steps=0, precision="f32"),
 }
 
 

@@ -89,6 +89,29 @@ def test_celllist_workloads(cuda, name, prec):
     assert np.array_equal(g2["perm"], g["perm"]) and np.array_equal(g2["pos"], g["pos"])
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_celllist_crowded_cells_among_many(cuda, prec):
+    """More cells than the sort kernel has warps (31^3), so each warp sorts
+    cells two at a time, with a dense cluster whose cells hold hundreds of
+    particles next to ordinary ones: bit-exact against the oracle."""
+    L = np.array([80.0, 80.0, 80.0])
+    rng = np.random.default_rng(5)
+    x = np.concatenate([rng.uniform(0.0, 80.0, size=(200000, 3)), rng.uniform(40.0, 47.5, size=(20000, 3))])
+    x = x[rng.permutation(x.shape[0])]
+    dt = np.float32 if prec == "f32" else np.float64
+    pos = inputs.as4(x, dt)
+    vel = inputs.as4(rng.normal(size=x.shape), dt)
+    o = oracle_cells(pos, L, (1, 1, 1), 2.5, vel=vel)
+    k = np.diff(o["cell_start"])
+    assert len(k) > 20000 and k.max() > 32 and np.sum(k > 32) < len(k) // 100
+    g = gpu_celllist(pos, L, (1, 1, 1), 2.5, prec, vel4=vel)
+    assert fpm_ok(g)
+    assert np.array_equal(g["cell_start"], o["cell_start"])
+    assert np.array_equal(g["perm"], o["perm"])
+    assert np.array_equal(g["pos"], o["pos"].astype(dt))
+    assert np.array_equal(g["vel"], o["vel"])
+
+
 def test_celllist_empty(cuda):
     g = gpu_celllist(np.zeros((0, 4), np.float32), (10.0, 10.0, 10.0), (1, 1, 1), 2.8, "f32")
     assert np.all(g["cell_start"] == 0)
