@@ -43,7 +43,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per launch of the dominant kernel from one ncu capture
 # (profiles/lj_tiles_lj_1m.md), valid while its sources hash to `sha`.
 NCU_TRAFFIC = {"k_lj_tiles<float>": {"files": ["lj.cu", "lj_pair.cuh", "tiles.cuh", "fpm_common.cuh", "reduce.cuh"],
-                                    "sha": "3b4a3a305a566bc9", "bytes_per_launch": 183673856}}
+                                    "sha": "69079cd037ce6a71", "bytes_per_launch": 184328192}}
 
 
 def parse():
@@ -349,49 +349,51 @@ def run_ours(args, ws, rank, local):
     # end to end through the public API with host buffers: every step copies the
     # state in from pinned host memory and reads state + energies back, in the
     # host's layout (packed x, y, z: fpm_pack_xyz / fpm_unpack_xyz on the
-    # device).  The round trip of one array overlaps the other's (the link
-    # carries both directions at once): D2H pos, then H2D pos on a second
-    # stream while D2H vel runs, then H2D vel; the next step waits for both.
-    # The host buffers carry each step's result into the next step's input.
+    # device).  The host buffers carry each step's result into the next step's
+    # input.  Positions and velocities travel as one packed [2, n, 3] array in
+    # E2E_CHUNKS pieces: piece k goes back to the device (second stream) as soon
+    # as it has reached the host, so the two directions of the link overlap.
+    E2E_CHUNKS = 3
     f32 = torch.float32
-    hp = torch.empty((s.n, 3), dtype=f32).pin_memory()
-    hv = torch.empty((s.n, 3), dtype=f32).pin_memory()
+    hbuf = torch.empty((2, s.n, 3), dtype=f32).pin_memory()
     he = torch.empty(3, dtype=torch.float64).pin_memory()
-    hp.copy_(s.pos[:, :3])
-    hv.copy_(s.vel[:, :3])
-    dp_in, dv_in = torch.empty((s.n, 3), dtype=f32, device=s.device), torch.empty((s.n, 3), dtype=f32, device=s.device)
-    dp_out, dv_out = torch.empty_like(dp_in), torch.empty_like(dv_in)
+    hbuf[0].copy_(s.pos[:, :3])
+    hbuf[1].copy_(s.vel[:, :3])
+    d_in = torch.empty((2, s.n, 3), dtype=f32, device=s.device)
+    d_out = torch.empty_like(d_in)
+    h_flat, in_flat, out_flat = hbuf.view(-1), d_in.view(-1), d_out.view(-1)
+    tot = h_flat.numel()
+    csz = ((tot + E2E_CHUNKS - 1) // E2E_CHUNKS + 63) // 64 * 64
+    pieces = [(a, min(a + csz, tot)) for a in range(0, tot, csz)]
     main, side = torch.cuda.current_stream(), torch.cuda.Stream()
-    ev_p, ev_v, ev_in = torch.cuda.Event(), torch.cuda.Event(), torch.cuda.Event()
+    ev_d2h = [torch.cuda.Event() for _ in pieces]
+    ev_in = torch.cuda.Event()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    dp_in.copy_(hp, non_blocking=True)
-    fpm.fpm_unpack_xyz(s.n, s.prec, dp_in, s.pos)
-    dv_in.copy_(hv, non_blocking=True)
-    fpm.fpm_unpack_xyz(s.n, s.prec, dv_in, s.vel)
+    d_in.copy_(hbuf, non_blocking=True)
+    fpm.fpm_unpack_xyz(s.n, s.prec, d_in[0], s.pos)
+    fpm.fpm_unpack_xyz(s.n, s.prec, d_in[1], s.vel)
     for k in range(args.e2e_steps):
         g.replay()
         he.copy_(s.energy, non_blocking=True)
-        fpm.fpm_pack_xyz(s.n, s.prec, s.pos, dp_out)
-        hp.copy_(dp_out, non_blocking=True)
-        ev_p.record(main)
-        fpm.fpm_pack_xyz(s.n, s.prec, s.vel, dv_out)
-        hv.copy_(dv_out, non_blocking=True)
-        ev_v.record(main)
+        fpm.fpm_pack_xyz(s.n, s.prec, s.pos, d_out[0])
+        fpm.fpm_pack_xyz(s.n, s.prec, s.vel, d_out[1])
+        for (a, b), ev in zip(pieces, ev_d2h):
+            h_flat[a:b].copy_(out_flat[a:b], non_blocking=True)
+            ev.record(main)
         if k + 1 < args.e2e_steps:
             with torch.cuda.stream(side):
-                side.wait_event(ev_p)
-                dp_in.copy_(hp, non_blocking=True)
-                fpm.fpm_unpack_xyz(s.n, s.prec, dp_in, s.pos, stream=side)
-                side.wait_event(ev_v)
-                dv_in.copy_(hv, non_blocking=True)
-                fpm.fpm_unpack_xyz(s.n, s.prec, dv_in, s.vel, stream=side)
+                for (a, b), ev in zip(pieces, ev_d2h):
+                    side.wait_event(ev)
+                    in_flat[a:b].copy_(h_flat[a:b], non_blocking=True)
+                fpm.fpm_unpack_xyz(s.n, s.prec, d_in[0], s.pos, stream=side)
+                fpm.fpm_unpack_xyz(s.n, s.prec, d_in[1], s.vel, stream=side)
                 ev_in.record(side)
             main.wait_event(ev_in)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_s = max_over_ranks(e2e_s, ws)
-    h2d = hp.numel() * hp.element_size() + hv.numel() * hv.element_size()
+    h2d = hbuf.numel() * hbuf.element_size()
     d2h = h2d + he.numel() * he.element_size()
     s.check_status()
 

@@ -124,16 +124,34 @@ __device__ __forceinline__ uint32_t block_inclusive_scan(uint32_t v, uint32_t *s
     return r;
 }
 
+// count[base .. base + 4) (zero past ncell): one 16-byte load when all four
+// exist (count is 256-byte aligned and base a multiple of 4).
+__device__ __forceinline__ void load_counts(const uint32_t *count, int ncell, int64_t base, uint32_t (&v)[kScanItems])
+{
+    static_assert(kScanItems == 4, "one uint4 per thread");
+    if (base + kScanItems <= ncell) {
+        const uint4 q = *reinterpret_cast<const uint4 *>(count + base);
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+        v[3] = q.w;
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) v[k] = (base + k < ncell) ? count[base + k] : 0u;
+    }
+}
+
 __global__ void __launch_bounds__(kScanThreads) k_scan_part(const uint32_t *count, int ncell, uint32_t *tiles,
                                                             const uint32_t *gate)
 {
     if (gated_off(gate)) return;
     __shared__ uint32_t sh[32];
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    load_counts(count, ncell, base, v);
     uint32_t s = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k)
-        if (base + k < ncell) s += count[base + k];
+    for (int k = 0; k < kScanItems; ++k) s += v[k];
     uint32_t total;
     block_inclusive_scan(s, sh, total);
     if (threadIdx.x == 0) tiles[blockIdx.x] = total;
@@ -154,12 +172,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_final(const uint32_t *cou
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     uint32_t v[kScanItems];
+    load_counts(count, ncell, base, v);
     uint32_t s = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {
-        v[k] = (base + k < ncell) ? count[base + k] : 0u;
-        s += v[k];
-    }
+    for (int k = 0; k < kScanItems; ++k) s += v[k];
     uint32_t total;
     uint32_t incl = block_inclusive_scan(s, sh, total);
     uint32_t run = tile_off + incl - s;
@@ -175,7 +191,20 @@ __global__ void k_scatter(int n, const uint32_t *__restrict__ cell, const uint32
                           const uint32_t *__restrict__ cell_start, uint32_t *__restrict__ tmp, const uint32_t *gate)
 {
     if (gated_off(gate)) return;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    // four particles per thread from 16-byte loads of cell and rank (both
+    // 256-byte aligned), then the tail
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n4 = n >> 2;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += stride) {
+        const uint4 c = reinterpret_cast<const uint4 *>(cell)[q];
+        const uint4 r = reinterpret_cast<const uint4 *>(rank)[q];
+        const uint32_t i = (uint32_t)(q << 2);
+        tmp[cell_start[c.x] + r.x] = i;
+        tmp[cell_start[c.y] + r.y] = i + 1u;
+        tmp[cell_start[c.z] + r.z] = i + 2u;
+        tmp[cell_start[c.w] + r.w] = i + 3u;
+    }
+    for (int64_t i = (n4 << 2) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
         tmp[cell_start[cell[i]] + rank[i]] = (uint32_t)i;
 }
 
@@ -349,7 +378,7 @@ static fpm_status celllist_launch(const fpm_box &b, const fpm_grid &g, int n, co
     k_scan_part<<<ntiles, kScanThreads, 0, stream>>>(count, ncell, tiles, gate);
     k_scan_final<<<ntiles, kScanThreads, 0, stream>>>(count, ncell, tiles, cell_start, n, gate);
     if (n > 0) {
-        k_scatter<<<grid_cap((n + 255) / 256), 256, 0, stream>>>(n, cell, rank, cell_start, tmp, gate);
+        k_scatter<<<grid_cap((n / 4 + 255) / 256 + 1), 256, 0, stream>>>(n, cell, rank, cell_start, tmp, gate);
         const V4<T> *psrc = spos ? spos : pin;
         const V4<T> *vsrc = svel ? svel : vin;
         const uint32_t *isrc = sid ? sid : id_in;
