@@ -451,3 +451,108 @@ def sph_step(pos, vel, rho, L, periodic, p, cfl=0.2):
     if dt < 0:
         raise ValueError("box too small for the support")
     return x, v, r, dt
+
+
+# ---------------------------------------------------------------------------
+# DEM (Sec. 4.5, Eqs. 9-13): the Silbert grain model with Hertzian contacts.
+# The readings the paper leaves open are listed with the C functions.
+
+DEM_MAXC = 32  # contacts per particle the history holds (ORC_DEM_MAXC)
+
+
+class _DemParams(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_double), ("m", ctypes.c_double), ("I", ctypes.c_double), ("kn", ctypes.c_double),
+                ("kt", ctypes.c_double), ("gn", ctypes.c_double), ("gt", ctypes.c_double), ("mu", ctypes.c_double),
+                ("dt", ctypes.c_double), ("g", ctypes.c_double * 3)]
+
+
+def dem_params(R=0.06, m=1.0, I=1.44e-3, kn=7.849, kt=2.243, gn=3.401, gt=0.0, mu=0.5, dt=0.01,
+               g=(0.0, 0.0, 0.0)):
+    """DEM parameter block; defaults are the constants printed in Sec. 4.5
+    (gamma_t and mu are not printed: 0 and 0.5, the grain model's usual
+    values)."""
+    p = _DemParams()
+    p.R, p.m, p.I, p.kn, p.kt, p.gn, p.gt, p.mu, p.dt = R, m, I, kn, kt, gn, gt, mu, dt
+    for d in range(3):
+        p.g[d] = g[d]
+    return p
+
+
+def _dem_sig():
+    L_ = lib()
+    if getattr(L_, "_dem_set", False):
+        return L_
+    PP = ctypes.POINTER(_DemParams)
+    i64 = ctypes.c_int64
+    for name, res, args in [
+        ("orc_dem_forces", i64, [ctypes.c_int, _P(np.float64), _P(np.float64), _P(np.float64), _P(np.float64),
+                                 _P(np.int32), PP, _P(np.int32), _P(np.uint32), _P(np.float64), _P(np.float64),
+                                 _P(np.float64), _P(np.int32), _P(np.uint32), _P(np.float64)]),
+        ("orc_dem_leapfrog", None, [ctypes.c_int, _P(np.float64), _P(np.float64), _P(np.float64), _P(np.float64),
+                                    _P(np.float64), PP]),
+        ("orc_dem_run", i64, [ctypes.c_int, ctypes.c_int, _P(np.float64), _P(np.float64), _P(np.float64),
+                              _P(np.float64), _P(np.int32), PP, _P(np.int32), _P(np.uint32), _P(np.float64),
+                              _P(np.float64), _P(np.float64)]),
+    ]:
+        fn = getattr(L_, name)
+        fn.restype = res
+        fn.argtypes = args
+    L_._dem_set = True
+    return L_
+
+
+def dem_empty_history(n):
+    """No contacts: (cnt [n], partner [n, MAXC], u [n, MAXC, 3])."""
+    return (np.zeros(n, np.int32), np.zeros((n, DEM_MAXC), np.uint32), np.zeros((n, DEM_MAXC, 3)))
+
+
+def dem_forces(pos, vel, om, L, periodic, p, hist=None):
+    """Contact forces and torques at one state (Eqs. 9-12).  `hist` is the
+    contact history of the previous step (dem_empty_history for none);
+    returns (force [n,4], torque [n,4], new history, ordered contacts).
+    pos[:,3] != 0 marks a fixed particle."""
+    L_ = _dem_sig()
+    x, v, w = _pos4(pos, np.float64), _pos4(vel, np.float64), _pos4(om, np.float64)
+    n = x.shape[0]
+    Lb, pb = _box(L, periodic)
+    h_in = hist if hist is not None else dem_empty_history(n)
+    h_out = dem_empty_history(n)
+    F, T = np.zeros_like(x), np.zeros_like(x)
+    r = L_.orc_dem_forces(n, x, v, w, Lb, pb, ctypes.byref(p), h_in[0], h_in[1], h_in[2], F, T, h_out[0],
+                          h_out[1], h_out[2])
+    if r == -1:
+        raise ValueError("more than %d contacts on a particle" % DEM_MAXC)
+    if r < 0:
+        raise ValueError("box too small for the contact cell list")
+    return F, T, h_out, int(r)
+
+
+def dem_leapfrog(pos, vel, om, force, torque, p):
+    """Eq. 13 (fixed particles, pos[:,3] != 0, stay put); returns new arrays."""
+    L_ = _dem_sig()
+    x, v, w = _pos4(pos, np.float64), _pos4(vel, np.float64), _pos4(om, np.float64)
+    L_.orc_dem_leapfrog(x.shape[0], x, v, w, _pos4(force, np.float64), _pos4(torque, np.float64), ctypes.byref(p))
+    return x, v, w
+
+
+def dem_run(pos, vel, om, L, periodic, p, nsteps, hist=None):
+    """nsteps DEM steps; returns (pos, vel, om, force, torque of the last
+    step, history, contacts of the last step)."""
+    L_ = _dem_sig()
+    x, v, w = _pos4(pos, np.float64), _pos4(vel, np.float64), _pos4(om, np.float64)
+    n = x.shape[0]
+    Lb, pb = _box(L, periodic)
+    h = tuple(a.copy() for a in hist) if hist is not None else dem_empty_history(n)
+    F, T = np.zeros_like(x), np.zeros_like(x)
+    r = L_.orc_dem_run(n, int(nsteps), x, v, w, Lb, pb, ctypes.byref(p), h[0], h[1], h[2], F, T)
+    if r == -1:
+        raise ValueError("more than %d contacts on a particle" % DEM_MAXC)
+    if r < 0:
+        raise ValueError("box too small for the contact cell list")
+    return x, v, w, F, T, h, int(r)
+
+
+def dem_history_dict(hist):
+    """{(p, q): u_t} of a history triple (test helper)."""
+    cnt, ids, u = hist
+    return {(int(i), int(ids[i, k])): u[i, k].copy() for i in range(len(cnt)) for k in range(int(cnt[i]))}

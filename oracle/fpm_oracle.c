@@ -831,3 +831,188 @@ done:
     free(acc); free(dr); free(ph); free(vh); free(rh);
     return dt;
 }
+
+/* ------------------------------------------------------------------------ */
+/* DEM: the Silbert grain model with Hertzian contacts (Sec. 4.5, Eqs. 9-13) */
+/* ------------------------------------------------------------------------ */
+/* Readings (the paper states Eqs. 9-13 and defers the rest to its refs):
+ *  - n = r_pq / |r_pq| with r_pq = r_p - r_q (minimum image); contact iff
+ *    r2 < (2R)^2, i.e. delta = 2R - r > 0 (Eq. 9).
+ *  - Relative velocity of the contact points: v_pq = v_p - v_q,
+ *    v_n = (v_pq . n) n and v_t = v_pq - v_n - R (w_p + w_q) x n (the surface
+ *    points of p and q at the contact move with v_p - R w_p x n and
+ *    v_q + R w_q x n).
+ *  - Eq. 10 is applied first in a step: u_t = u_t(previous step) + v_t dt,
+ *    with u_t = 0 for a contact that is new in this step; a contact that has
+ *    ended (delta <= 0) forgets its u_t.
+ *  - Eqs. 11-12 with m_eff = m/2 and f = sqrt(delta / 2R).
+ *  - Coulomb's law: when |F_t| > mu |F_n|, F_t is scaled to length mu |F_n|
+ *    and u_t is set to the value that gives that F_t in Eq. 12,
+ *    u_t = -(F_t / f + gt m_eff v_t) / kt.
+ *  - Torque on p from the contact: -1/2 r_pq x F_t (with this form the pair
+ *    conserves total angular momentum exactly).
+ *  - Particles with w != 0 are fixed (walls): they take part in contacts and
+ *    receive force and torque sums, but Eq. 13 does not move them.  Eq. 13 adds
+ *    gravity: v += dt (F / m + g).
+ * History: per particle (in input order) up to ORC_DEM_MAXC contacts, each a
+ * partner index and its u_t, in the order the contacts were found. */
+#define ORC_DEM_MAXC 32
+
+typedef struct {
+    double R, m, I, kn, kt, gn, gt, mu, dt;
+    double g[3];
+} orc_dem_params;
+
+static void cross3(const double a[3], const double b[3], double c[3])
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double norm3(const double a[3]) { return sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]); }
+
+/* One contact of p with q: dv = r_p - r_q, r2 = |dv|^2 < (2R)^2.  Writes the
+ * force and torque on p and the contact's new u_t. */
+static void dem_contact(const orc_dem_params *P, const double dv[3], double r2, const double *vp, const double *vq,
+                        const double *wp, const double *wq, const double u_old[3], double F[3], double T[3],
+                        double u_new[3])
+{
+    const double r = sqrt(r2);
+    const double delta = 2.0 * P->R - r; /* Eq. 9 */
+    double n[3], vpq[3], w[3], wxn[3], vn[3], vt[3], Fn[3], Ft[3];
+    for (int d = 0; d < 3; ++d) {
+        n[d] = dv[d] / r;
+        vpq[d] = vp[d] - vq[d];
+        w[d] = wp[d] + wq[d];
+    }
+    const double vn_s = vpq[0] * n[0] + vpq[1] * n[1] + vpq[2] * n[2];
+    cross3(w, n, wxn);
+    for (int d = 0; d < 3; ++d) {
+        vn[d] = vn_s * n[d];
+        vt[d] = vpq[d] - vn[d] - P->R * wxn[d];
+        u_new[d] = u_old[d] + vt[d] * P->dt; /* Eq. 10 */
+    }
+    const double f = sqrt(delta / (2.0 * P->R));
+    const double meff = 0.5 * P->m;
+    for (int d = 0; d < 3; ++d) {
+        Fn[d] = f * (P->kn * delta * n[d] - P->gn * meff * vn[d]); /* Eq. 11 */
+        Ft[d] = f * (-P->kt * u_new[d] - P->gt * meff * vt[d]);   /* Eq. 12 */
+    }
+    const double fn = norm3(Fn), ft = norm3(Ft);
+    if (ft > P->mu * fn) { /* Coulomb */
+        const double s = P->mu * fn / ft;
+        for (int d = 0; d < 3; ++d) {
+            Ft[d] *= s;
+            u_new[d] = P->kt > 0.0 ? -(Ft[d] / f + P->gt * meff * vt[d]) / P->kt : 0.0;
+        }
+    }
+    double tq[3];
+    cross3(dv, Ft, tq);
+    for (int d = 0; d < 3; ++d) {
+        F[d] = Fn[d] + Ft[d];
+        T[d] = -0.5 * tq[d];
+    }
+}
+
+/* Contact forces and torques at one state (Eqs. 9-12), with the contact
+ * history of the previous step (cnt_in/id_in/u_in, may be NULL for none)
+ * turned into that of this step (cnt_out/id_out/u_out).  Contacts are
+ * found by a cell list of cell size 2R.  Returns the number of (ordered)
+ * contacts, -1 if a particle has more than ORC_DEM_MAXC, -2 on a bad box. */
+int64_t orc_dem_forces(int n, const double *pos4, const double *vel4, const double *om4, const double L[3],
+                       const int periodic[3], const orc_dem_params *P, const int32_t *cnt_in, const uint32_t *id_in,
+                       const double *u_in, double *force4, double *torque4, int32_t *cnt_out, uint32_t *id_out,
+                       double *u_out)
+{
+    orc_cells cl;
+    if (cells_build(&cl, n, NULL, pos4, L, periodic, 2.0 * P->R)) return -2;
+    const double c2 = (2.0 * P->R) * (2.0 * P->R);
+    uint32_t *cand = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    int64_t total = 0;
+    int over = 0;
+    for (int i = 0; i < n; ++i) {
+        double Fs[3] = {0, 0, 0}, Ts[3] = {0, 0, 0};
+        int c = 0;
+        const int m = stencil_candidates(&cl, periodic, cl.cell[i], cand);
+        for (int t = 0; t < m; ++t) {
+            const uint32_t j = cand[t];
+            if (j == (uint32_t)i) continue;
+            double dv[3];
+            const double r2 = sep_f64(pos4 + 4 * (size_t)i, pos4 + 4 * (size_t)j, L, periodic, dv);
+            if (!(r2 < c2)) continue;
+            double u_old[3] = {0, 0, 0}, F[3], T[3], u_new[3];
+            if (cnt_in)
+                for (int k = 0; k < cnt_in[i]; ++k)
+                    if (id_in[(size_t)i * ORC_DEM_MAXC + k] == j)
+                        for (int d = 0; d < 3; ++d) u_old[d] = u_in[((size_t)i * ORC_DEM_MAXC + k) * 3 + d];
+            dem_contact(P, dv, r2, vel4 + 4 * (size_t)i, vel4 + 4 * (size_t)j, om4 + 4 * (size_t)i,
+                        om4 + 4 * (size_t)j, u_old, F, T, u_new);
+            for (int d = 0; d < 3; ++d) {
+                Fs[d] += F[d];
+                Ts[d] += T[d];
+            }
+            if (c < ORC_DEM_MAXC) {
+                id_out[(size_t)i * ORC_DEM_MAXC + c] = j;
+                for (int d = 0; d < 3; ++d) u_out[((size_t)i * ORC_DEM_MAXC + c) * 3 + d] = u_new[d];
+            } else {
+                over = 1;
+            }
+            ++c;
+            ++total;
+        }
+        cnt_out[i] = c < ORC_DEM_MAXC ? c : ORC_DEM_MAXC;
+        for (int d = 0; d < 3; ++d) {
+            force4[4 * (size_t)i + d] = Fs[d];
+            torque4[4 * (size_t)i + d] = Ts[d];
+        }
+        force4[4 * (size_t)i + 3] = 0.0;
+        torque4[4 * (size_t)i + 3] = 0.0;
+    }
+    free(cand);
+    cells_free(&cl);
+    return over ? -1 : total;
+}
+
+/* Leapfrog of Eq. 13 for the particles with w == 0: v += dt (F/m + g),
+ * r += dt v (the new v), w += dt T / I. */
+void orc_dem_leapfrog(int n, double *pos4, double *vel4, double *om4, const double *force4, const double *torque4,
+                      const orc_dem_params *P)
+{
+    for (int i = 0; i < n; ++i) {
+        if (pos4[4 * (size_t)i + 3] != 0.0) continue;
+        for (int d = 0; d < 3; ++d) {
+            const size_t k = 4 * (size_t)i + d;
+            vel4[k] = vel4[k] + P->dt * (force4[k] / P->m + P->g[d]);
+            pos4[k] = pos4[k] + P->dt * vel4[k];
+            om4[k] = om4[k] + P->dt * torque4[k] / P->I;
+        }
+    }
+}
+
+/* nsteps DEM steps (forces of Eqs. 9-12 at the current state, then Eq. 13),
+ * carrying the contact history (cnt/id/u, updated in place; start with
+ * cnt = 0 for none).  force4/torque4 receive those of the last step.
+ * Returns the contacts of the last step, or a negative error of
+ * orc_dem_forces. */
+int64_t orc_dem_run(int n, int nsteps, double *pos4, double *vel4, double *om4, const double L[3],
+                    const int periodic[3], const orc_dem_params *P, int32_t *cnt, uint32_t *id, double *u,
+                    double *force4, double *torque4)
+{
+    const size_t nc = (size_t)(n > 0 ? n : 1) * ORC_DEM_MAXC;
+    int32_t *cnt2 = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    uint32_t *id2 = (uint32_t *)malloc(sizeof(uint32_t) * nc);
+    double *u2 = (double *)malloc(sizeof(double) * nc * 3);
+    int64_t r = 0;
+    for (int s = 0; s < nsteps && r >= 0; ++s) {
+        r = orc_dem_forces(n, pos4, vel4, om4, L, periodic, P, cnt, id, u, force4, torque4, cnt2, id2, u2);
+        memcpy(cnt, cnt2, sizeof(int32_t) * (size_t)n);
+        memcpy(id, id2, sizeof(uint32_t) * nc);
+        memcpy(u, u2, sizeof(double) * nc * 3);
+        if (r >= 0) orc_dem_leapfrog(n, pos4, vel4, om4, force4, torque4, P);
+    }
+    free(cnt2);
+    free(id2);
+    free(u2);
+    return r;
+}
