@@ -384,6 +384,81 @@ fpm_status fpm_sph_correct(const fpm_box *box, int32_t n, const fpm_sph_params *
                            const void *pos_ref, double skin, fpm_dev_status *d_status, fpm_stream stream);
 
 /* ------------------------------------------------------------------ */
+/* DEM: the Silbert grain model with Hertzian contacts (Sec. 4.5,        */
+/* Eqs. 9-13).  FP32 state, float4 arrays in the sorted order.            */
+/* ------------------------------------------------------------------ */
+
+/* R: particle radius (contact iff r < 2R, delta = 2R - r, Eq. 9); m, I:
+ * mass and moment of inertia of every particle; kn, kt, gn, gt: the elastic
+ * and damping constants of Eqs. 11-12 (m_eff = m/2); mu: Coulomb friction
+ * coefficient; dt: time step (Eqs. 10, 13); g: gravity (Eq. 13). */
+typedef struct {
+    double R, m, I, kn, kt, gn, gt, mu, dt, g[3];
+} fpm_dem_params;
+
+/* Contact forces and torques over a Verlet list built with r_list >= 2R
+ * (box, grid, list, nn, cap as for fpm_lj_forces), float4 [n] arrays:
+ *   pos (x, y, z, type): type 0 moving grain, nonzero fixed (wall) grain;
+ *   vel (vx, vy, vz, -), omega (wx, wy, wz, -);
+ *   force, torque (output, w = 0): for every list entry inside 2R, with
+ *   n = (x_p - x_q)/r, v_pq = v_p - v_q, v_n = (v_pq.n) n and the
+ *   contact-point velocity v_t = v_pq - v_n - R (w_p + w_q) x n:
+ *     u_t += v_t dt (Eq. 10; u_t from the entry's history),
+ *     F_n = f (kn delta n - gn m_eff v_n), F_t = f (-kt u_t - gt m_eff v_t),
+ *     f = sqrt(delta / 2R) (Eqs. 11-12); if |F_t| > mu |F_n| then F_t is
+ *     scaled to mu |F_n| and u_t = -(F_t/f + gt m_eff v_t)/kt (Coulomb);
+ *     force_p += F_n + F_t, torque_p += -1/2 (x_p - x_q) x F_t.
+ *   hist : float4 [cap * fpm_nbr_ld(n)], entry k of particle i at
+ *     k * ld + i: the tangential deformation (x, y, z, -) of that list entry,
+ *     read and rewritten by every call (0 for an entry not in contact; zero
+ *     it after a Verlet build that is not followed by fpm_dem_hist_unpack).
+ *   d_ncontact : optional uint32 [1], incremented by the number of (ordered)
+ *     contacts.
+ * workspace : fpm_reduce_workspace(n, grid) bytes, zero-filled once. */
+fpm_status fpm_dem_forces(const fpm_box *box, const fpm_grid *grid, int32_t n, const void *pos, const void *vel,
+                          const void *omega, const void *list, const uint32_t *nn, int32_t cap,
+                          const fpm_dem_params *params, void *hist, void *force, void *torque,
+                          uint32_t *d_ncontact, void *workspace, size_t workspace_bytes, fpm_dev_status *d_status,
+                          fpm_stream stream);
+
+/* Leapfrog of Eq. 13 for grains of type 0 (in place):
+ *   v += dt (force/m + g), x += dt v (the new v), w += dt torque / I.
+ * With pos_ref, sets d_status->rebuild when a grain moved (minimum image)
+ * by more than skin/2 since pos_ref (as fpm_verlet_check). */
+fpm_status fpm_dem_leapfrog(const fpm_box *box, int32_t n, const fpm_dem_params *params, void *pos, void *vel,
+                            void *omega, const void *force, const void *torque, const void *pos_ref, double skin,
+                            fpm_dev_status *d_status, fpm_stream stream);
+
+/* The DEM state across a Verlet rebuild: the contacts' u_t follow their
+ * particle pairs, and omega follows its particle, through the cell-list
+ * reorder.  A rebuild is
+ *   fpm_dem_rebuild_begin -> fpm_celllist_build (pos, vel, ids) ->
+ *   fpm_verlet_build -> fpm_dem_rebuild_end,
+ * all gated by the same rebuild flag (the Verlet build clears it; `pending`,
+ * a caller-owned device uint32 that starts at 0, carries it to the end call).
+ * Bytes of the `packed` buffer (device memory, no initialisation needed): */
+size_t fpm_dem_packed_bytes(int32_t n);
+
+/* Runs only when *d_gate != 0 (always when d_gate is NULL), and then sets
+ * *d_pending = 1.  For every particle i (current order) the list entries with
+ * nonzero u_t are saved in `packed` as (partner's current index, u_t), at most
+ * 16 per particle (more latches FPM_FLAG_CAPACITY in d_status and drops the
+ * rest), and omega is saved.  list, nn, cap, grid: the list that hist
+ * belongs to. */
+fpm_status fpm_dem_rebuild_begin(const fpm_grid *grid, int32_t n, int32_t cap, const void *list, const uint32_t *nn,
+                                 const void *hist, const void *omega, void *packed, const uint32_t *d_gate,
+                                 uint32_t *d_pending, fpm_dev_status *d_status, fpm_stream stream);
+
+/* Runs only when *d_pending != 0, and clears it.  With perm from the
+ * rebuild's fpm_celllist_build (new index -> previous index) and the new
+ * list: omega[i] = saved omega[perm[i]], and hist entry k of new particle i
+ * receives the saved u_t of the pair (perm[i], perm[j]), j that entry's
+ * partner, or 0 when the pair had none. */
+fpm_status fpm_dem_rebuild_end(const fpm_grid *grid, int32_t n, int32_t cap, const void *list, const uint32_t *nn,
+                               const uint32_t *perm, const void *packed, void *hist, void *omega,
+                               uint32_t *d_pending, fpm_stream stream);
+
+/* ------------------------------------------------------------------ */
 /* Adjoint of the LJ force and of velocity Verlet (not in the paper:     */
 /* the chain rule applied to the force of Sec. 4.1 and the integrator    */
 /* of Listing 4.1, for gradients w.r.t. positions, eps and sigma)        */

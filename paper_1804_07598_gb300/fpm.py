@@ -70,6 +70,12 @@ class fpm_sph_params(_c.Structure):
                 ("kernel", _c.c_int32)]
 
 
+class fpm_dem_params(_c.Structure):
+    _fields_ = [("R", _c.c_double), ("m", _c.c_double), ("I", _c.c_double), ("kn", _c.c_double),
+                ("kt", _c.c_double), ("gn", _c.c_double), ("gt", _c.c_double), ("mu", _c.c_double),
+                ("dt", _c.c_double), ("g", _c.c_double * 3)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -116,6 +122,16 @@ _SIG = {
                                    _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _c.c_double, _VP, _VP]),
     "fpm_sph_correct": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.POINTER(fpm_sph_params), _VP, _VP, _VP, _VP,
                                    _VP, _VP, _VP, _c.c_double, _VP, _VP]),
+    "fpm_dem_forces": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _VP, _VP, _VP, _VP, _VP,
+                                  _c.c_int32, _c.POINTER(fpm_dem_params), _VP, _VP, _VP, _VP, _VP, _c.c_size_t, _VP,
+                                  _VP]),
+    "fpm_dem_leapfrog": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.POINTER(fpm_dem_params), _VP, _VP, _VP, _VP,
+                                    _VP, _VP, _c.c_double, _VP, _VP]),
+    "fpm_dem_packed_bytes": (_c.c_size_t, [_c.c_int32]),
+    "fpm_dem_rebuild_begin": (_c.c_int, [_c.POINTER(fpm_grid), _c.c_int32, _c.c_int32, _VP, _VP, _VP, _VP, _VP, _VP,
+                                         _VP, _VP, _VP]),
+    "fpm_dem_rebuild_end": (_c.c_int, [_c.POINTER(fpm_grid), _c.c_int32, _c.c_int32, _VP, _VP, _VP, _VP, _VP, _VP,
+                                       _VP, _VP]),
     "fpm_lj_backward": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _c.c_int, _VP, _VP, _VP,
                                    _c.c_int32, _c.c_double, _c.c_double, _c.c_double, _VP, _c.c_double, _VP, _VP,
                                    _VP, _c.c_size_t, _VP, _VP]),
@@ -374,6 +390,50 @@ def fpm_sph_forces(box, grid, n, pos, vr, list_obj, nn, cap, params, acc, d_dtco
                                 _ptr(nn), int(cap), _c.byref(params), _ptr(acc), _ptr(d_dtcons), _ptr(workspace),
                                 _nbytes(workspace), _ptr(d_status), _stream(stream)))
     _count(1 if n > 0 else 0)
+
+
+def dem_params(R=0.06, m=1.0, I=1.44e-3, kn=7.849, kt=2.243, gn=3.401, gt=0.0, mu=0.5, dt=0.01,
+               g=(0.0, 0.0, 0.0)) -> fpm_dem_params:
+    p = fpm_dem_params()
+    p.R, p.m, p.I, p.kn, p.kt, p.gn, p.gt, p.mu, p.dt = R, m, I, kn, kt, gn, gt, mu, dt
+    for d in range(3):
+        p.g[d] = g[d]
+    return p
+
+
+def fpm_dem_forces(box, grid, n, pos, vel, omega, list_obj, nn, cap, params, hist, force, torque, d_ncontact=None,
+                   workspace=None, d_status=None, stream=None):
+    _check(lib().fpm_dem_forces(_c.byref(box), _c.byref(grid), int(n), _ptr(pos), _ptr(vel), _ptr(omega),
+                                _ptr(list_obj), _ptr(nn), int(cap), _c.byref(params), _ptr(hist), _ptr(force),
+                                _ptr(torque), _ptr(d_ncontact), _ptr(workspace), _nbytes(workspace), _ptr(d_status),
+                                _stream(stream)))
+    _count(1 if n > 0 else 0)
+
+
+def fpm_dem_leapfrog(box, n, params, pos, vel, omega, force, torque, pos_ref=None, skin=0.0, d_status=None,
+                     stream=None):
+    _check(lib().fpm_dem_leapfrog(_c.byref(box), int(n), _c.byref(params), _ptr(pos), _ptr(vel), _ptr(omega),
+                                  _ptr(force), _ptr(torque), _ptr(pos_ref), float(skin), _ptr(d_status),
+                                  _stream(stream)))
+    _count(1 if n > 0 else 0)
+
+
+def fpm_dem_packed_bytes(n) -> int:
+    return int(lib().fpm_dem_packed_bytes(int(n)))
+
+
+def fpm_dem_rebuild_begin(grid, n, cap, list_obj, nn, hist, omega, packed, d_gate, d_pending, d_status=None,
+                          stream=None):
+    _check(lib().fpm_dem_rebuild_begin(_c.byref(grid), int(n), int(cap), _ptr(list_obj), _ptr(nn), _ptr(hist),
+                                       _ptr(omega), _ptr(packed), _ptr(d_gate), _ptr(d_pending), _ptr(d_status),
+                                       _stream(stream)))
+    _count(2 if n > 0 else 0)
+
+
+def fpm_dem_rebuild_end(grid, n, cap, list_obj, nn, perm, packed, hist, omega, d_pending, stream=None):
+    _check(lib().fpm_dem_rebuild_end(_c.byref(grid), int(n), int(cap), _ptr(list_obj), _ptr(nn), _ptr(perm),
+                                     _ptr(packed), _ptr(hist), _ptr(omega), _ptr(d_pending), _stream(stream)))
+    _count(2 if n > 0 else 0)
 
 
 def fpm_sph_predict(box, n, params, cfl, pos, vr, acc, d_dtcons, pos_h, vr_h, d_dt, d_dtcons_h, pos_ref=None,

@@ -208,3 +208,63 @@ def dam_break(dp: float, tank=(1.6, 0.67, 0.4), column=(0.4, 0.67, 0.3), layers:
 
 
 SPH_DP = 3.7704e-3  # dam break with ~1.51M fluid particles (106 x 178 x 80)
+
+
+# ---------------------------------------------------------------------------
+# DEM avalanche (Sec. 4.5): grains on a cubic lattice in the upstream part of
+# a box inclined by 30 degrees (gravity rotated), a floor and two x-walls of
+# fixed grains (type 1), periodic in y, open in z.  The printed constants
+# are kept (R = 0.06, m = 1, I = 1.44e-3, kn = 7.849, kt = 2.243,
+# gn = 3.401); gamma_t = 0 and mu = 0.5 (not printed).  |g| and dt are not
+# printed either: |g| is chosen so that the weight of an nz-grain column
+# compresses the lowest contact by about 1 % of 2R under that kn, and dt
+# resolves the contact oscillation (period ~2 pi sqrt(m_eff / (kn f)) ~ 5)
+# with ~100 steps.
+
+DEM_PARAMS = dict(R=0.06, m=1.0, I=1.44e-3, kn=7.849, kt=2.243, gn=3.401, gt=0.0, mu=0.5, dt=0.05)
+DEM_SKIN = 0.012  # 0.2 R: r_list = 2R + skin
+
+
+def dem_gravity(nz: int, R: float = 0.06, kn: float = 7.849, tilt_deg: float = 30.0, overlap: float = 0.01):
+    """Gravity vector for an nz-high pile: nz m |g| = kn sqrt(d / 2R) d with
+    d = overlap * 2R, tilted by tilt_deg about y (down-slope along +x)."""
+    d = overlap * 2.0 * R
+    gmag = kn * math.sqrt(d / (2.0 * R)) * d / nz
+    t = math.radians(tilt_deg)
+    return (gmag * math.sin(t), 0.0, -gmag * math.cos(t))
+
+
+def dem_avalanche(nx: int, ny: int, nz: int, R: float = 0.06, gap: float = 0.02, seed: int = 17,
+                  vel_scale: float = 1e-3):
+    """(pos4, vel4, omega4, L, periodic, gravity) of the avalanche: nx*ny*nz
+    moving grains (lattice spacing s = 2R(1 + gap)) from x = 3R, z = 3R; a
+    floor of fixed grains at z = R (spacing >= 2R, periodic in y); fixed walls
+    at x = R and x = L_x - R up to the block's top; the box is 2 nx + 4
+    diameters long (room to flow), ny spacings wide (periodic), and open above
+    (twice the block's height).  Small seeded random velocities."""
+    s = 2.0 * R * (1.0 + gap)
+    Lx = (2 * nx + 4) * 2.0 * R
+    Ly = ny * s
+    Lz = 2.0 * (nz * s + 4.0 * R)
+    ix, iy, iz = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    moving = np.stack([3.0 * R + ix.ravel() * s, 0.5 * s + iy.ravel() * s, 3.0 * R + iz.ravel() * s], 1)
+    nfx = int(math.floor(Lx / (2.0 * R)))
+    nfy = int(math.floor(Ly / (2.0 * R)))
+    fx, fy = np.meshgrid(np.arange(nfx), np.arange(nfy), indexing="ij")
+    floor = np.stack([R + fx.ravel() * (Lx - 2.0 * R) / max(nfx - 1, 1), (fy.ravel() + 0.5) * (Ly / nfy),
+                      np.full(fx.size, R)], 1)
+    top = 3.0 * R + (nz - 1) * s + R
+    nwz = int(math.floor((top - 2.0 * R) / (2.0 * R))) + 1
+    wy, wz = np.meshgrid(np.arange(nfy), np.arange(1, nwz + 1), indexing="ij")
+    wall = np.stack([np.zeros(wy.size), (wy.ravel() + 0.5) * (Ly / nfy), R + wz.ravel() * 2.0 * R], 1)
+    walls = np.concatenate([wall + [R, 0.0, 0.0], wall + [Lx - R, 0.0, 0.0]])
+    x = np.concatenate([moving, floor, walls])
+    kind = np.concatenate([np.zeros(len(moving)), np.ones(len(floor) + len(walls))])
+    pos = np.zeros((len(x), 4))
+    pos[:, :3] = x
+    pos[:, 3] = kind
+    rng = np.random.default_rng(seed)
+    vel = np.zeros_like(pos)
+    vel[: len(moving), :3] = rng.normal(scale=vel_scale, size=(len(moving), 3))
+    om = np.zeros_like(pos)
+    return pos, vel, om, np.array([Lx, Ly, Lz]), (0, 1, 0), dem_gravity(nz, R)

@@ -1,0 +1,260 @@
+"""GPU parity of the DEM path (Sec. 4.5, Eqs. 9-13) against the oracle:
+contact forces, torques and tangential histories at identical states (with
+and without stored histories), the histories carried through Verlet
+rebuilds, multi-step runs with rebuilds and walls, conservation of momentum
+and angular momentum, and graph replays against eager steps."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1804_07598_gb300 import inputs
+from paper_1804_07598_gb300.dem import DEMSystem
+
+pytestmark = pytest.mark.gpu
+
+R = 0.06
+SKIN = inputs.DEM_SKIN
+
+
+def f32(a):
+    return np.asarray(a, np.float32).astype(np.float64)
+
+
+def dense_box(k, seed, spacing=0.116, jitter=0.003, v=0.05, w=0.5):
+    """k^3 grains on a jittered cubic lattice (overlaps of ~4e-3 with the
+    axis neighbours) in a periodic box, random velocities and spins; FP32
+    values."""
+    rng = np.random.default_rng(seed)
+    g = np.stack(np.meshgrid(*[np.arange(k)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    n = len(g)
+    pos = np.zeros((n, 4))
+    pos[:, :3] = (g + 0.5) * spacing + rng.uniform(-jitter, jitter, size=(n, 3))
+    vel = np.zeros((n, 4))
+    vel[:, :3] = rng.normal(scale=v, size=(n, 3))
+    om = np.zeros((n, 4))
+    om[:, :3] = rng.normal(scale=w, size=(n, 3))
+    L = np.full(3, k * spacing)
+    return f32(pos), f32(vel), f32(om), L
+
+
+def params(**kw):
+    p = dict(inputs.DEM_PARAMS)
+    p.update(kw)
+    return p
+
+
+def oracle_p(pd):
+    return oracle.dem_params(**pd)
+
+
+def rms(a):
+    return float(np.sqrt((a[:, :3] ** 2).sum(1).mean()))
+
+
+def dict_to_hist(n, d):
+    cnt, ids, u = oracle.dem_empty_history(n)
+    for (i, j), val in sorted(d.items()):
+        c = cnt[i]
+        ids[i, c] = j
+        u[i, c] = val
+        cnt[i] += 1
+    return cnt, ids, u
+
+
+def delta_of(pos, L, per, i, j):
+    d = pos[i, :3] - pos[j, :3]
+    for a in range(3):
+        if per[a]:
+            d[a] -= L[a] * np.round(d[a] / L[a])
+    return 2 * R - np.linalg.norm(d)
+
+
+def compare_hist(gd, od, pos, L, per, tol):
+    """Same contacts (up to pairs within 1e-6 of touching, where FP32 and FP64
+    may decide differently) and u_t within tol."""
+    for key in set(gd) ^ set(od):
+        assert abs(delta_of(pos, L, per, *key)) < 1e-6, key
+    common = set(gd) & set(od)
+    assert len(common) > 0.9 * max(len(od), 1)
+    err = max(np.abs(gd[k] - od[k]).max() for k in common)
+    assert err <= tol, err
+
+
+# FP32 bound on forces and torques, as a fraction of their RMS.  The overlap
+# delta = 2R - r is a difference of nearly equal numbers: in FP32 it carries an
+# absolute error of a few ulps of 2R (~1e-8), and f = sqrt(delta / 2R)
+# magnifies that without limit as a contact opens (d ln f / d delta =
+# 1 / (2 delta)), while the damping force f gn m_eff v_n stays finite there.
+# Contacts within ~1e-5 of touching therefore carry errors of order 1e-5 of
+# a typical contact force, above the 1e-5-of-RMS bound of the smooth LJ pair;
+# the DEM bound is 1e-4 of RMS.
+TOL_F = 1e-4
+
+
+def test_dem_forces_match_oracle(cuda):
+    """One force evaluation at a state with fresh contacts: F and T within
+    TOL_F of their RMS, u_t = v_t dt per contact."""
+    pos, vel, om, L = dense_box(12, 1)
+    pd = params()
+    s = DEMSystem(pos, vel, om, L, (1, 1, 1), pd, SKIN)
+    s.compute_forces()
+    torch.cuda.synchronize()
+    s.check_status()
+    _, _, _, F, T = s.state_by_id()
+    Fo, To, ho, c = oracle.dem_forces(pos, vel, om, L, (1, 1, 1), oracle_p(pd))
+    assert c > 3 * len(pos)
+    assert np.abs(F[:, :3] - Fo[:, :3]).max() <= TOL_F * rms(Fo)
+    assert np.abs(T[:, :3] - To[:, :3]).max() <= TOL_F * rms(To)
+    od = oracle.dem_history_dict(ho)
+    umax = max(np.abs(u).max() for u in od.values())
+    compare_hist(s.history_by_id(), od, pos, L, (1, 1, 1), 1e-5 * umax)
+    assert s.contacts() == c or abs(s.contacts() - c) <= 4
+
+
+def test_dem_forces_with_stored_history(cuda):
+    """A state with aged contacts (sliding ones at the Coulomb limit): the GPU
+    loads the oracle's u_t, then both evaluate the forces once."""
+    pos, vel, om, L = dense_box(10, 2)
+    pd = params()
+    po = oracle_p(pd)
+    x, v, w, _, _, h, c = oracle.dem_run(pos, vel, om, L, (1, 1, 1), po, 25)
+    x, v, w = f32(x), f32(v), f32(w)
+    hd = {k: f32(u) for k, u in oracle.dem_history_dict(h).items()}
+    s = DEMSystem(x, v, w, L, (1, 1, 1), pd, SKIN)
+    s.set_history_by_id(hd)
+    s.compute_forces()
+    torch.cuda.synchronize()
+    s.check_status()
+    _, _, _, F, T = s.state_by_id()
+    Fo, To, ho, c = oracle.dem_forces(x, v, w, L, (1, 1, 1), po, hist=dict_to_hist(len(x), hd))
+    assert np.abs(F[:, :3] - Fo[:, :3]).max() <= TOL_F * rms(Fo)
+    assert np.abs(T[:, :3] - To[:, :3]).max() <= TOL_F * rms(To)
+    od = oracle.dem_history_dict(ho)
+    umax = max(np.abs(u).max() for u in od.values())
+    compare_hist(s.history_by_id(), od, x, L, (1, 1, 1), 1e-5 * umax)
+
+
+def test_dem_history_and_spin_survive_rebuild(cuda):
+    """A rebuild reorders the grains; every contact's u_t and every grain's
+    omega stay with their ids, bit for bit."""
+    pos, vel, om, L = dense_box(10, 3, v=0.2)
+    s = DEMSystem(pos, vel, om, L, (1, 1, 1), params(), SKIN)
+    s.step(6)
+    s.compute_forces()
+    torch.cuda.synchronize()
+    before = s.history_by_id()
+    om0 = s.state_by_id()[2]
+    ids0 = s.ids.cpu().numpy().copy()
+    s.rebuild()
+    torch.cuda.synchronize()
+    s.check_status()
+    assert not np.array_equal(s.ids.cpu().numpy(), ids0)  # the order did change
+    after = s.history_by_id()
+    assert set(after) == set(before) and len(before) > 100
+    assert all(np.array_equal(after[k], before[k]) for k in before)
+    np.testing.assert_array_equal(s.state_by_id()[2], om0)
+
+
+def run_pair(pos, vel, om, L, per, pd, steps, seed=9):
+    """GPU run and oracle run of `steps` steps, plus the oracle from inputs
+    one FP32 ulp away: the spread of the two oracle runs is the dynamics'
+    own sensitivity, the scale the GPU's FP32 error is held to."""
+    s = DEMSystem(pos, vel, om, L, per, pd, SKIN)
+    s.step(steps)
+    torch.cuda.synchronize()
+    st = s.check_status()
+    po = oracle_p(pd)
+    A = oracle.dem_run(pos, vel, om, L, per, po, steps)
+    rng = np.random.default_rng(seed)
+    moving = pos[:, 3] == 0
+    pert = pos.copy()
+    pert[moving, :3] *= 1.0 + rng.choice([-1.0, 1.0], size=(moving.sum(), 3)) * 2.0 ** -24
+    B = oracle.dem_run(pert, vel, om, L, per, po, steps)
+    return s, st, A, B
+
+
+@pytest.mark.parametrize("case", ["periodic", "avalanche"])
+def test_dem_run_matches_oracle(cuda, case):
+    """Steps with Verlet rebuilds (the history crossing each reorder): final
+    positions, velocities and spins within 20x the oracle's own one-ulp
+    spread (plus a floor of a few FP32 ulps)."""
+    if case == "periodic":
+        pos, vel, om, L = dense_box(10, 4, v=0.1)
+        per, pd, steps = (1, 1, 1), params(), 40
+    else:
+        pos, vel, om, L, per, g = inputs.dem_avalanche(12, 8, 8, vel_scale=0.02)
+        pos, vel, om = f32(pos), f32(vel), f32(om)
+        per, pd, steps = per, params(g=g), 60
+    s, st, A, B = run_pair(pos, vel, om, L, per, pd, steps)
+    assert st.nrebuild >= 2
+    x, v, w, F, T = s.state_by_id()
+
+    def diff(a, b, is_pos):
+        d = a[:, :3].astype(np.float64) - b[:, :3]
+        if is_pos:  # the GPU's rebuilds wrap positions into the box
+            for ax in range(3):
+                if per[ax]:
+                    d[:, ax] -= L[ax] * np.round(d[:, ax] / L[ax])
+        return np.abs(d).max()
+
+    for k, (g_, a_, b_) in enumerate([(x, A[0], B[0]), (v, A[1], B[1]), (w, A[2], B[2])]):
+        spread = diff(a_, b_, k == 0)
+        floor = 4 * 2.0 ** -24 * max(np.abs(a_[:, :3]).max(), 1e-30)
+        err = diff(g_, a_, k == 0)
+        assert err <= 20 * spread + floor, (k, err, spread)
+    if case == "avalanche":
+        fixed = pos[:, 3] != 0
+        np.testing.assert_array_equal(x[fixed], pos[fixed].astype(np.float32))
+
+
+def test_dem_conserves_momentum_and_angular_momentum(cuda):
+    """An isolated cluster (open box, no gravity): total P and L stay within
+    FP32 rounding of their start over 100 steps with rebuilds."""
+    k, sp = 8, 0.115
+    rng = np.random.default_rng(6)
+    g = np.stack(np.meshgrid(*[np.arange(k)] * 3, indexing="ij"), -1).reshape(-1, 3)
+    n = len(g)
+    pos = np.zeros((n, 4))
+    pos[:, :3] = 1.0 + g * sp + rng.uniform(-0.003, 0.003, size=(n, 3))
+    vel = np.zeros((n, 4))
+    vel[:, :3] = rng.normal(scale=0.05, size=(n, 3))
+    om = np.zeros((n, 4))
+    om[:, :3] = rng.normal(scale=0.5, size=(n, 3))
+    pos, vel, om = f32(pos), f32(vel), f32(om)
+    pd = params(gt=1.0)
+    s = DEMSystem(pos, vel, om, (4.0, 4.0, 4.0), (0, 0, 0), pd, SKIN)
+
+    def momenta():
+        x, v, w, _, _ = s.state_by_id()
+        x, v, w = x.astype(np.float64), v.astype(np.float64), w.astype(np.float64)
+        P = pd["m"] * v[:, :3].sum(0)
+        Lm = pd["m"] * np.cross(x[:, :3], v[:, :3]).sum(0) + pd["I"] * w[:, :3].sum(0)
+        return P, Lm
+
+    P0, L0 = momenta()
+    s.step(100)
+    torch.cuda.synchronize()
+    assert s.check_status().nrebuild >= 1
+    P1, L1 = momenta()
+    scale_p = pd["m"] * np.abs(vel[:, :3]).sum()
+    scale_l = pd["m"] * np.abs(np.cross(pos[:, :3], vel[:, :3])).sum() + pd["I"] * np.abs(om[:, :3]).sum()
+    assert np.abs(P1 - P0).max() <= 1e-5 * scale_p
+    assert np.abs(L1 - L0).max() <= 1e-5 * scale_l
+
+
+def test_dem_graph_replay_equals_eager(cuda):
+    """Steps replayed from a CUDA graph (rebuild in a conditional node) give
+    the same state, bit for bit, as the same steps launched eagerly."""
+    pos, vel, om, L = dense_box(10, 5, v=0.15)
+    a = DEMSystem(pos, vel, om, L, (1, 1, 1), params(), SKIN)
+    b = DEMSystem(pos, vel, om, L, (1, 1, 1), params(), SKIN)
+    a.step(20)
+    g = b.capture(1)
+    for _ in range(20):
+        g.replay()
+    torch.cuda.synchronize()
+    assert a.check_status().nrebuild == b.check_status().nrebuild >= 2
+    for x, y in zip(a.state_by_id(), b.state_by_id()):
+        np.testing.assert_array_equal(x, y)
+    assert a.history_by_id().keys() == b.history_by_id().keys()
