@@ -3,13 +3,17 @@
 // (Eqs. 9-12), Coulomb's limit, the leapfrog with rotation (Eq. 13), and the
 // contact history carried through the Verlet rebuild's reorder.
 //
-// The contact sweep is a tile sweep like the LJ one: persistent blocks take
-// cell tiles by ticket, stage the neighbourhood's positions, velocities and
-// angular velocities in shared memory (three bulk copies per piece on one
-// barrier), and one thread per home particle walks its list.  The history
-// u_t of list entry k of particle i lives at hist[k * ld + i] (float4, w
-// unused), read and rewritten for every entry: coalesced across the home
-// particles of a warp, and 0 for an entry that is not in contact.
+// The contact sweep walks the tiled Verlet list like the LJ sweep
+// (persistent blocks take cell tiles by ticket, one thread per home
+// particle), but a grain has only ~6 list entries against a staged
+// neighbourhood of ~10 slots per home grain, so the neighbourhood is not
+// copied: each tile builds a slot map in shared memory (4 bytes per staged
+// slot: the sorted index and the piece's periodic flags), and every entry
+// gathers its neighbour's position (and, for a contact, its velocity and spin)
+// from L2, with the lower-wall shift applied exactly as staging would.  The
+// history u_t of list entry k of particle i lives at hist[k * ld + i]
+// (float4, w unused), read and rewritten for every entry: coalesced across the
+// home particles of a warp, and 0 for an entry that is not in contact.
 #include "reduce.cuh"
 #include "tiles.cuh"
 
@@ -42,34 +46,34 @@ static DemK make_dem(const fpm_dem_params &p)
     return K;
 }
 
-// One list entry of home particle i (staged slot s): the contact of
+// Slot map entry: sorted index in the low 26 bits, the piece's flags above.
+constexpr int kMapShift = 26;
+constexpr uint32_t kMapIndex = (1u << kMapShift) - 1u;
+
+// One list entry of home particle i (slot map entry e): the contact of
 // Eqs. 9-12 when r < 2R, adding to the force and torque sums and updating
 // the entry's u_t; u_t = 0 otherwise.
-template <bool FAST, bool SMEM>
-__device__ __forceinline__ void dem_pair(const TileCfg &cfg, const BoxT<float> &box, const TileDesc &d,
-                                         const float4 *__restrict__ pos, const float4 *__restrict__ vel,
-                                         const float4 *__restrict__ om, const float4 *__restrict__ sp,
-                                         const float4 *__restrict__ sv, const float4 *__restrict__ sw,
-                                         const float4 &pi, const float4 &vi, const float4 &wi, int s, const DemK &K,
+template <bool FAST>
+__device__ __forceinline__ void dem_pair(const TileCfg &cfg, const BoxT<float> &box, const float4 *__restrict__ pos,
+                                         const float4 *__restrict__ vel, const float4 *__restrict__ om, uint32_t e,
+                                         const float4 &pi, const float4 &vi, const float4 &wi, const DemK &K,
                                          float4 &u, float3 &F, float3 &T, uint32_t &nc)
 {
-    float4 pj, vj, wj;
-    if (SMEM) {
-        pj = sp[s];
-        vj = sv[s];
-        wj = sw[s];
-    } else {
-        pj = staged_global(d, box, pos, s);
-        const uint32_t j = staged_index(d, s);
-        vj = ldg4(vel + j);
-        wj = ldg4(om + j);
-    }
+    const uint32_t j = e & kMapIndex;
+    const int fl = (int)(e >> kMapShift);
+    float4 pj = __ldg(pos + j);
+    // the staged form of the neighbour: lower-wall images shifted by -L (exact)
+    pj.x = rsub(pj.x, (fl & kLoX) ? box.L[0] : 0.0f);
+    pj.y = rsub(pj.y, (fl & kLoY) ? box.L[1] : 0.0f);
+    pj.z = rsub(pj.z, (fl & kLoZ) ? box.L[2] : 0.0f);
+    pj.w = flags_as<float>(fl);
     float dx, dy, dz;
     const float r2 = tile_sep<FAST>(pi, pj, box, cfg, dx, dy, dz);
     if (!(r2 < K.c2 && r2 > 0.0f)) {
         u = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         return;
     }
+    const float4 vj = __ldg(vel + j), wj = __ldg(om + j);
     const float r = sqrtf(r2);
     const float ir = 1.0f / r;
     const float delta = K.twoR - r;  // Eq. 9
@@ -111,25 +115,34 @@ __device__ __forceinline__ void dem_pair(const TileCfg &cfg, const BoxT<float> &
 }
 
 // The contacts of home particle i over its m list entries (entry k in half
-// k & 1 of word (k >> 1) * ld of col), with their histories.
-template <bool FAST, bool SMEM>
+// k & 1 of word (k >> 1) * ld of col), with their histories.  MAP: the slot
+// map is in shared memory (else each slot is resolved from the pieces).
+template <bool FAST, bool MAP>
 __device__ __forceinline__ void dem_sweep(const TileCfg &cfg, const BoxT<float> &box, const TileDesc &d,
                                           const float4 *__restrict__ pos, const float4 *__restrict__ vel,
-                                          const float4 *__restrict__ om, const float4 *__restrict__ sp,
-                                          const float4 *__restrict__ sv, const float4 *__restrict__ sw,
+                                          const float4 *__restrict__ om, const uint32_t *__restrict__ smap,
                                           const float4 &pi, const float4 &vi, const float4 &wi, uint32_t m,
                                           const uint32_t *__restrict__ col, float4 *__restrict__ hcol, int64_t ld,
                                           const DemK &K, float3 &F, float3 &T, uint32_t &nc)
 {
+    auto entry = [&](int s) -> uint32_t {
+        if (MAP) return smap[s];
+        uint32_t e = 0u;
+        for (int p = 0; p < kMaxPieces; ++p) {
+            const Piece pc = d.piece[p];
+            if (pc.len > 0 && s >= pc.soff && s < pc.soff + pc.len)
+                e = (pc.gstart + (uint32_t)(s - pc.soff)) | ((uint32_t)pc.flags << kMapShift);
+        }
+        return e;
+    };
     for (uint32_t k = 0; k < m; k += 2) {
         const uint32_t w = __ldcs(col + (int64_t)(k >> 1) * ld);
         float4 u0 = __ldcs(hcol + (int64_t)k * ld);
-        dem_pair<FAST, SMEM>(cfg, box, d, pos, vel, om, sp, sv, sw, pi, vi, wi, (int)(w & 0xffffu), K, u0, F, T, nc);
+        dem_pair<FAST>(cfg, box, pos, vel, om, entry((int)(w & 0xffffu)), pi, vi, wi, K, u0, F, T, nc);
         __stcs(hcol + (int64_t)k * ld, u0);
         if (k + 1 < m) {
             float4 u1 = __ldcs(hcol + (int64_t)(k + 1) * ld);
-            dem_pair<FAST, SMEM>(cfg, box, d, pos, vel, om, sp, sv, sw, pi, vi, wi, (int)(w >> 16), K, u1, F, T,
-                                 nc);
+            dem_pair<FAST>(cfg, box, pos, vel, om, entry((int)(w >> 16)), pi, vi, wi, K, u1, F, T, nc);
             __stcs(hcol + (int64_t)(k + 1) * ld, u1);
         }
     }
@@ -138,42 +151,43 @@ __device__ __forceinline__ void dem_sweep(const TileCfg &cfg, const BoxT<float> 
 __global__ void __launch_bounds__(kTileThreads)
     k_dem_tiles(TileCfg cfg, BoxT<float> box, const float4 *__restrict__ pos, const float4 *__restrict__ vel,
                 const float4 *__restrict__ om, ListView lv, const uint32_t *__restrict__ nn, int64_t ld,
-                int stage_cap, DemK K, float4 *__restrict__ hist, float4 *__restrict__ force,
-                float4 *__restrict__ torque, uint32_t *ncontact, Sched sched, fpm_dev_status *status)
+                int map_cap, DemK K, float4 *__restrict__ hist, float4 *__restrict__ force,
+                float4 *__restrict__ torque, uint32_t *ncontact, Sched sched)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    float4 *sp = (float4 *)smem_raw;
-    float4 *sv = sp + stage_cap;
-    float4 *sw = sv + stage_cap;
+    extern __shared__ __align__(16) uint32_t smap[];
     __shared__ TileDesc d;
-    __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t s_k;
     __shared__ bool s_last;
-    stage_init(&bar);
-    uint32_t phase = 0;
     const uint32_t *__restrict__ words = lv.words;
     const uint32_t ntodo = *lv.count;
+    const int lane = (int)(threadIdx.x & 31u), warp = (int)(threadIdx.x >> 5), nwarp = (int)(blockDim.x >> 5);
     uint32_t ahead = 0, nc = 0;
     for (uint32_t k = blockIdx.x; k < ntodo; k = ticket_next(ahead, &s_k)) {
         ahead = ticket_ahead(sched);
         load_desc(lv.descs + lv.active[k], d);
-        const bool in_smem = d.M <= stage_cap;
-        if (!in_smem) note_spill(status);
-        const bool staged = in_smem ? stage_positions(d, box, pos, sp, &bar, phase, status, vel, sv, om, sw) : true;
-        for (uint32_t i = d.h0 + threadIdx.x; staged && i < d.h1; i += blockDim.x) {
+        const bool map = d.M <= map_cap;
+        if (map) {  // one warp per piece
+            for (int p = warp; p < kMaxPieces; p += nwarp) {
+                const Piece pc = d.piece[p];
+                const uint32_t fl = (uint32_t)pc.flags << kMapShift;
+                for (int e = lane; e < pc.len; e += 32) smap[pc.soff + e] = (pc.gstart + (uint32_t)e) | fl;
+            }
+            __syncthreads();
+        }
+        for (uint32_t i = d.h0 + threadIdx.x; i < d.h1; i += blockDim.x) {
             const float4 pi = pos[i], vi = vel[i], wi = om[i];
             const uint32_t m = nn[i];
             float3 F = make_float3(0.0f, 0.0f, 0.0f), T = make_float3(0.0f, 0.0f, 0.0f);
-            if (in_smem) {
+            if (map) {
                 if (d.slow)
-                    dem_sweep<false, true>(cfg, box, d, pos, vel, om, sp, sv, sw, pi, vi, wi, m, words + i, hist + i,
-                                           ld, K, F, T, nc);
+                    dem_sweep<false, true>(cfg, box, d, pos, vel, om, smap, pi, vi, wi, m, words + i, hist + i, ld, K,
+                                           F, T, nc);
                 else
-                    dem_sweep<true, true>(cfg, box, d, pos, vel, om, sp, sv, sw, pi, vi, wi, m, words + i, hist + i,
-                                          ld, K, F, T, nc);
+                    dem_sweep<true, true>(cfg, box, d, pos, vel, om, smap, pi, vi, wi, m, words + i, hist + i, ld, K,
+                                          F, T, nc);
             } else {
-                dem_sweep<false, false>(cfg, box, d, pos, vel, om, sp, sv, sw, pi, vi, wi, m, words + i, hist + i,
-                                        ld, K, F, T, nc);
+                dem_sweep<false, false>(cfg, box, d, pos, vel, om, smap, pi, vi, wi, m, words + i, hist + i, ld, K,
+                                        F, T, nc);
             }
             force[i] = make_float4(F.x, F.y, F.z, 0.0f);
             torque[i] = make_float4(T.x, T.y, T.z, 0.0f);
@@ -181,7 +195,7 @@ __global__ void __launch_bounds__(kTileThreads)
     }
     if (ncontact) {
         const unsigned t = __reduce_add_sync(kFull, nc);
-        if ((threadIdx.x & 31) == 0 && t) atomicAdd(ncontact, t);
+        if (lane == 0 && t) atomicAdd(ncontact, t);
     }
     sched_finish(sched, &s_last);
 }
@@ -353,7 +367,8 @@ extern "C" fpm_status fpm_dem_forces(const fpm_box *box, const fpm_grid *grid, i
     if (s != FPM_OK) return s;
     s = dem_params_ok(params, "fpm_dem_forces");
     if (s != FPM_OK) return s;
-    if (n < 0 || cap < 1 || (n > 0 && (!pos || !vel || !omega || !list || !nn || !hist || !force || !torque)))
+    if (n < 0 || n > (int32_t)kMapIndex || cap < 1 ||
+        (n > 0 && (!pos || !vel || !omega || !list || !nn || !hist || !force || !torque)))
         return fpm_fail(FPM_ERR_INVALID, "fpm_dem_forces: null pointer or bad size");
     if (((uintptr_t)list & 255u) != 0) return fpm_fail(FPM_ERR_INVALID, "fpm_dem_forces: list not 256-B aligned");
     if (((uintptr_t)hist & 15u) != 0) return fpm_fail(FPM_ERR_INVALID, "fpm_dem_forces: hist not 16-B aligned");
@@ -363,15 +378,14 @@ extern "C" fpm_status fpm_dem_forces(const fpm_box *box, const fpm_grid *grid, i
     if (s != FPM_OK) return s;
     const TileCfg cfg = make_tile_cfg(*box, *grid);
     const ListLayout L = list_layout(n, cfg, cap);
-    const size_t per = 3 * sizeof(float4);  // staged position, velocity, angular velocity
-    const int sc = stage_capacity(n, *grid, per);
-    const size_t smem = (size_t)sc * per;
+    const int mc = stage_capacity(n, *grid, sizeof(uint32_t));  // slot-map entries per tile
+    const size_t smem = (size_t)mc * sizeof(uint32_t);
     smem_opt_in((const void *)k_dem_tiles);
     const int blocks = persistent_blocks((const void *)k_dem_tiles, kTileThreads, smem, *grid, cfg.ntiles);
     k_dem_tiles<<<blocks, kTileThreads, smem, (cudaStream_t)stream>>>(
         cfg, make_box<float>(*box), (const float4 *)pos, (const float4 *)vel, (const float4 *)omega,
-        list_view(list, L), nn, L.ld, sc, make_dem(*params), (float4 *)hist, (float4 *)force, (float4 *)torque,
-        d_ncontact, Sched{r.work, r.done}, d_status);
+        list_view(list, L), nn, L.ld, mc, make_dem(*params), (float4 *)hist, (float4 *)force, (float4 *)torque,
+        d_ncontact, Sched{r.work, r.done});
     return fpm_check_launch("fpm_dem_forces");
 }
 

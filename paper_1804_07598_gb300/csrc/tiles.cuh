@@ -323,17 +323,16 @@ __device__ __forceinline__ void stage_init(uint64_t *bar)
 
 // Stages the neighbourhood positions of a tile into shared memory: slot s of
 // piece p holds pos[gstart + (s - soff)] with the lower-wall shifts applied
-// and (in tiles that need them) the piece flags in w.  When aux (aux2) is
-// given, the same slots of a second (third) per-particle array are copied
-// unchanged into aux_st (aux2_st) on the same barrier.  `phase` is the barrier's parity, flipped per use.
+// and (in tiles that need them) the piece flags in w.  When aux is given, the
+// same slots of a second per-particle array are copied unchanged into aux_st
+// on the same barrier.  `phase` is the barrier's parity, flipped per use.
 // Every thread must have finished with the previous tile's staged data (a
 // __syncthreads) before the call.  Returns false, the same in every thread,
 // if the copies did not complete within the wait budget.
 template <typename T>
 __device__ bool stage_positions(const TileDesc &d, const BoxT<T> &box, const V4<T> *__restrict__ pos,
                                 V4<T> *__restrict__ st, uint64_t *bar, uint32_t &phase, fpm_dev_status *status,
-                                const V4<T> *__restrict__ aux = nullptr, V4<T> *__restrict__ aux_st = nullptr,
-                                const V4<T> *__restrict__ aux2 = nullptr, V4<T> *__restrict__ aux2_st = nullptr)
+                                const V4<T> *__restrict__ aux = nullptr, V4<T> *__restrict__ aux_st = nullptr)
 {
     const uint32_t b = smem_u32(bar);
     static_assert(kMaxPieces <= 32, "one lane of warp 0 per piece");
@@ -344,7 +343,7 @@ __device__ bool stage_positions(const TileDesc &d, const BoxT<T> &box, const V4<
         // block's earlier generic accesses of the buffers (made visible to it by
         // the caller's barrier) before its async copies.
         if (lane == 0) {
-            const uint32_t bytes = (uint32_t)d.M * (uint32_t)sizeof(V4<T>) * (1u + (aux ? 1u : 0u) + (aux2 ? 1u : 0u));
+            const uint32_t bytes = (uint32_t)d.M * (uint32_t)sizeof(V4<T>) * (aux ? 2u : 1u);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
         }
         __syncwarp();
@@ -363,12 +362,6 @@ __device__ bool stage_positions(const TileDesc &d, const BoxT<T> &box, const V4<
                         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                             smem_u32(aux_st + pc.soff)),
                         "l"(aux + pc.gstart), "r"(nb), "r"(b)
-                        : "memory");
-                if (aux2)
-                    asm volatile(
-                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                            smem_u32(aux2_st + pc.soff)),
-                        "l"(aux2 + pc.gstart), "r"(nb), "r"(b)
                         : "memory");
             }
         }

@@ -139,7 +139,7 @@ def test_dem_history_and_spin_survive_rebuild(cuda):
     """A rebuild reorders the grains; every contact's u_t and every grain's
     omega stay with their ids, bit for bit."""
     pos, vel, om, L = dense_box(10, 3, v=0.2)
-    s = DEMSystem(pos, vel, om, L, (1, 1, 1), params(), SKIN)
+    s = DEMSystem(pos, vel, om, L, (1, 1, 1), params(), SKIN, cell_factor=1.0)  # 8^3 cells: grains change cells
     s.step(6)
     s.compute_forces()
     torch.cuda.synchronize()
@@ -156,11 +156,11 @@ def test_dem_history_and_spin_survive_rebuild(cuda):
     np.testing.assert_array_equal(s.state_by_id()[2], om0)
 
 
-def run_pair(pos, vel, om, L, per, pd, steps, seed=9):
+def run_pair(pos, vel, om, L, per, pd, steps, seed=9, cell_factor=3.0):
     """GPU run and oracle run of `steps` steps, plus the oracle from inputs
     one FP32 ulp away: the spread of the two oracle runs is the dynamics'
     own sensitivity, the scale the GPU's FP32 error is held to."""
-    s = DEMSystem(pos, vel, om, L, per, pd, SKIN)
+    s = DEMSystem(pos, vel, om, L, per, pd, SKIN, cell_factor=cell_factor)
     s.step(steps)
     torch.cuda.synchronize()
     st = s.check_status()
@@ -179,14 +179,14 @@ def test_dem_run_matches_oracle(cuda, case):
     """Steps with Verlet rebuilds (the history crossing each reorder): final
     positions, velocities and spins within 20x the oracle's own one-ulp
     spread (plus a floor of a few FP32 ulps)."""
-    if case == "periodic":
+    if case == "periodic":  # cells of r_list: wrapped tiles, grains crossing cells
         pos, vel, om, L = dense_box(10, 4, v=0.1)
-        per, pd, steps = (1, 1, 1), params(), 40
-    else:
+        per, pd, steps, cf = (1, 1, 1), params(), 40, 1.0
+    else:  # the default cells; y (periodic, 2 cells wide) in all-pairs mode
         pos, vel, om, L, per, g = inputs.dem_avalanche(12, 8, 8, vel_scale=0.02)
         pos, vel, om = f32(pos), f32(vel), f32(om)
-        per, pd, steps = per, params(g=g), 60
-    s, st, A, B = run_pair(pos, vel, om, L, per, pd, steps)
+        per, pd, steps, cf = per, params(g=g), 60, 3.0
+    s, st, A, B = run_pair(pos, vel, om, L, per, pd, steps, cell_factor=cf)
     assert st.nrebuild >= 2
     x, v, w, F, T = s.state_by_id()
 
