@@ -42,7 +42,13 @@ class DEMSystem:
         self.skin = float(skin)
         self.r_list = 2.0 * self.R + self.skin
         self.box = fpm.make_box(self.L, self.periodic)
-        self.grid = fpm.fpm_grid_make(self.box, cell_factor * self.r_list, n)
+        # cells of cell_factor * r_list, no wider than a periodic length allows
+        # (the grid needs L > 2 r_cell (1 + 2^-10) there), and never below r_list
+        r_cell = cell_factor * self.r_list
+        for d in range(3):
+            if self.periodic[d]:
+                r_cell = min(r_cell, self.L[d] / (2.0 * (1.0 + 2.0 ** -9)))
+        self.grid = fpm.fpm_grid_make(self.box, max(r_cell, self.r_list), n)
         self.cap = int(cap) + int(cap) % 2
         self.ld = fpm.fpm_nbr_ld(n)
         dev, f32 = self.device, torch.float32
