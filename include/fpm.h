@@ -378,10 +378,12 @@ fpm_status fpm_sph_predict(const fpm_box *box, int32_t n, const fpm_sph_params *
  *   v1 = v0 + dt a, x1 = x0 + dt (v0 + v1)/2 (fluid only),
  *   rho1 = rho0 (2 - e)/(2 + e) with e = -(Drho / rho_half) dt (all), in place
  *   on pos, vr; d_dtcons[0..1] = 0.  With pos_ref, sets d_status->rebuild when
- *   |x1 - x_ref| + dt |v1| > skin/2 (room for the next half step). */
+ *   |x1 - x_ref| + dt |v1| > skin/2 (room for the next half step).  With
+ *   d_time (optional, one double), *d_time += dt: the simulated time. */
 fpm_status fpm_sph_correct(const fpm_box *box, int32_t n, const fpm_sph_params *params, void *pos, void *vr,
                            const void *vr_h, const void *acc_h, const float *d_dt, float *d_dtcons,
-                           const void *pos_ref, double skin, fpm_dev_status *d_status, fpm_stream stream);
+                           const void *pos_ref, double skin, fpm_dev_status *d_status, double *d_time,
+                           fpm_stream stream);
 
 /* ------------------------------------------------------------------ */
 /* DEM: the Silbert grain model with Hertzian contacts (Sec. 4.5,        */

@@ -303,7 +303,7 @@ __global__ void k_sph_predict(int n, BoxT<float> box, const float4 *__restrict__
 __global__ void k_sph_correct(int n, BoxT<float> box, float4 *__restrict__ pos, float4 *__restrict__ vr,
                               const float4 *__restrict__ vr_h, const float4 *__restrict__ acc_h,
                               const float *__restrict__ d_dt, float rho0, float *dtcons,
-                              const float4 *__restrict__ ref, float half_skin, fpm_dev_status *st)
+                              const float4 *__restrict__ ref, float half_skin, fpm_dev_status *st, double *time)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const float dt = *d_dt;
@@ -337,6 +337,7 @@ __global__ void k_sph_correct(int n, BoxT<float> box, float4 *__restrict__ pos, 
     if (i == 0) {
         dtcons[0] = 0.0f;
         dtcons[1] = 0.0f;
+        if (time) *time += (double)dt;
     }
     if (ref) disp_report(over, d2, st);
 }
@@ -442,7 +443,7 @@ extern "C" fpm_status fpm_sph_predict(const fpm_box *box, int32_t n, const fpm_s
 extern "C" fpm_status fpm_sph_correct(const fpm_box *box, int32_t n, const fpm_sph_params *params, void *pos,
                                       void *vr, const void *vr_h, const void *acc_h, const float *d_dt,
                                       float *d_dtcons, const void *pos_ref, double skin, fpm_dev_status *d_status,
-                                      fpm_stream stream)
+                                      double *d_time, fpm_stream stream)
 {
     fpm_status s = sph_params_ok(params, "fpm_sph_correct");
     if (s != FPM_OK) return s;
@@ -452,6 +453,6 @@ extern "C" fpm_status fpm_sph_correct(const fpm_box *box, int32_t n, const fpm_s
     const int blocks = n > 0 ? (n + 255) / 256 : 1;
     k_sph_correct<<<blocks, 256, 0, (cudaStream_t)stream>>>(
         n, make_box<float>(*box), (float4 *)pos, (float4 *)vr, (const float4 *)vr_h, (const float4 *)acc_h, d_dt,
-        (float)params->rho0, d_dtcons, (const float4 *)pos_ref, (float)(0.5 * skin), d_status);
+        (float)params->rho0, d_dtcons, (const float4 *)pos_ref, (float)(0.5 * skin), d_status, d_time);
     return fpm_check_launch("fpm_sph_correct");
 }

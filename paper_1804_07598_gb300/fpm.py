@@ -121,7 +121,7 @@ _SIG = {
     "fpm_sph_predict": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.POINTER(fpm_sph_params), _c.c_double, _VP,
                                    _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _c.c_double, _VP, _VP]),
     "fpm_sph_correct": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.POINTER(fpm_sph_params), _VP, _VP, _VP, _VP,
-                                   _VP, _VP, _VP, _c.c_double, _VP, _VP]),
+                                   _VP, _VP, _VP, _c.c_double, _VP, _VP, _VP]),
     "fpm_dem_forces": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _VP, _VP, _VP, _VP, _VP,
                                   _c.c_int32, _c.POINTER(fpm_dem_params), _VP, _VP, _VP, _VP, _VP, _c.c_size_t, _VP,
                                   _VP]),
@@ -445,10 +445,10 @@ def fpm_sph_predict(box, n, params, cfl, pos, vr, acc, d_dtcons, pos_h, vr_h, d_
 
 
 def fpm_sph_correct(box, n, params, pos, vr, vr_h, acc_h, d_dt, d_dtcons, pos_ref=None, skin=0.0, d_status=None,
-                    stream=None):
+                    d_time=None, stream=None):
     _check(lib().fpm_sph_correct(_c.byref(box), int(n), _c.byref(params), _ptr(pos), _ptr(vr), _ptr(vr_h),
                                  _ptr(acc_h), _ptr(d_dt), _ptr(d_dtcons), _ptr(pos_ref), float(skin), _ptr(d_status),
-                                 _stream(stream)))
+                                 _ptr(d_time), _stream(stream)))
     _count(1)
 
 

@@ -167,8 +167,14 @@ def ensemble(count: int = 512, seed: int = 2024, nmin: int = 256, nmax: int = 16
 # SPH dam break (Sec. 4.2 test case, the tank shape of the SPH workload)
 # ---------------------------------------------------------------------------
 
+# The fixed obstacle of the paper's dam break (shown, not dimensioned there):
+# a box of (0.12, 0.12, 0.45) with its low corner at (0.9, 0.24, 0) of the
+# tank's interior.
+DAM_OBSTACLE = ((0.9, 0.24, 0.0), (0.12, 0.12, 0.45))
+
+
 def dam_break(dp: float, tank=(1.6, 0.67, 0.4), column=(0.4, 0.67, 0.3), layers: int = 3, lz: float = 1.0,
-              rho0: float = 1000.0, g: float = 9.81, gamma: float = 7.0, coef: float = 20.0):
+              rho0: float = 1000.0, g: float = 9.81, gamma: float = 7.0, coef: float = 20.0, obstacle=None):
     """A fluid column at one end of an open-top tank with `layers` layers of
     fixed boundary particles on the floor and the four walls, all on a cubic
     lattice of spacing dp.  Coordinates start at 0 (the boundary layers fill
@@ -176,7 +182,9 @@ def dam_break(dp: float, tank=(1.6, 0.67, 0.4), column=(0.4, 0.67, 0.3), layers:
     0 fluid / 1 boundary), vel [n,3] (zero), rho [n] (hydrostatic:
     rho0 (1 + rho0 g depth / b)^(1/gamma), b = c0^2 rho0 / gamma,
     c0 = coef sqrt(g h_swl)), the box L, and the SPH constants h = 1.3 dp,
-    m = rho0 dp^3."""
+    m = rho0 dp^3.  obstacle ((x0, y0, z0), (sx, sy, sz)) in the tank's
+    interior coordinates (e.g. DAM_OBSTACLE) adds a box filled with fixed
+    boundary particles on the lattice."""
     nb = int(layers)
     nxt, nyt, nzt = (int(round(t / dp)) for t in tank)
     nxf, nyf, nzf = (int(round(c / dp)) for c in column)
@@ -191,7 +199,12 @@ def dam_break(dp: float, tank=(1.6, 0.67, 0.4), column=(0.4, 0.67, 0.3), layers:
     xw = np.concatenate([grid(nb, nyt + 2 * nb, nzt, 0.0, 0.0, off),
                          grid(nb, nyt + 2 * nb, nzt, off + nxt * dp, 0.0, off)])
     yw = np.concatenate([grid(nxt, nb, nzt, off, 0.0, off), grid(nxt, nb, nzt, off, off + nyt * dp, off)])
-    bnd = np.concatenate([floor, xw, yw])
+    bnd = [floor, xw, yw]
+    if obstacle is not None:
+        (ox, oy, oz), (sx, sy, sz) = obstacle
+        sz = min(sz, nzt * dp - oz)
+        bnd.append(grid(int(round(sx / dp)), int(round(sy / dp)), int(round(sz / dp)), off + ox, off + oy, off + oz))
+    bnd = np.concatenate(bnd)
     h_swl = column[2]  # the nominal fluid height of the paper's setup
     c0 = coef * math.sqrt(g * h_swl)
     b = c0 * c0 * rho0 / gamma

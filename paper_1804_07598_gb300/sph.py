@@ -72,6 +72,7 @@ class SPHSystem:
         self.dtcons = torch.zeros(2, dtype=f32, device=dev)
         self.dtcons_h = torch.zeros(2, dtype=f32, device=dev)
         self.dt = torch.zeros(1, dtype=f32, device=dev)
+        self.t_sim = torch.zeros(1, dtype=torch.float64, device=dev)  # simulated time (sum of the steps' dt)
         self.ws_red = torch.zeros(fpm.fpm_reduce_workspace(n, self.grid), dtype=torch.uint8, device=dev)
         self._body = torch.cuda.Stream(device=dev)  # captures the conditional rebuild
         self._graph = None
@@ -132,7 +133,7 @@ class SPHSystem:
                             self.pos_h, self.vr_h, self.dt, self.dtcons_h, self.pos_ref, self.skin, self.status)
         self.rates(self.pos_h, self.vr_h, self.acc_h, self.dtcons_h)
         fpm.fpm_sph_correct(self.box, self.n, self.params, self.pos, self.vr, self.vr_h, self.acc_h, self.dt,
-                            self.dtcons, self.pos_ref, self.skin, self.status)
+                            self.dtcons, self.pos_ref, self.skin, self.status, d_time=self.t_sim)
         if fpm.fpm_graph_if_begin(self.gate_ptr, self._body):
             self.rebuild(gated=True, stream=self._body)
             fpm.fpm_graph_if_end(self._body)
@@ -164,6 +165,10 @@ class SPHSystem:
         for _ in range(nsteps // k):
             g.replay()
         self.step(nsteps % k)
+
+    def simulated_time(self) -> float:
+        """Simulated time so far (synchronises)."""
+        return float(self.t_sim.item())
 
     def check_status(self):
         st = fpm.read_status(self.status)

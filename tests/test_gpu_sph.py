@@ -19,8 +19,10 @@ def f32box(L):
     return np.asarray(L, np.float64).astype(np.float32).astype(np.float64)
 
 
-def make(dp=0.02, kernel="wendland", perturb=True, seed=3):
-    d = inputs.dam_break(dp)
+def make(dp=0.02, kernel="wendland", perturb=True, seed=3, obstacle=False, h=None):
+    d = inputs.dam_break(dp, obstacle=inputs.DAM_OBSTACLE if obstacle else None)
+    if h is not None:
+        d["h"] = h
     rng = np.random.default_rng(seed)
     vel = d["vel"].copy()
     rho = d["rho"].copy()
@@ -40,9 +42,13 @@ def oracle_params(d, kernel):
     return oracle.sph_params(d["h"], d["m"], rho0=d["rho0"], c0=d["c0"], kernel=kernel)
 
 
-@pytest.mark.parametrize("kernel", ["wendland", "cubic"])
-def test_sph_rates_match_oracle(cuda, kernel):
-    d, s = make(kernel=kernel)
+@pytest.mark.parametrize("kernel,variant", [("wendland", ""), ("cubic", ""), ("cubic", "sqrt3"),
+                                            ("wendland", "obstacle")])
+def test_sph_rates_match_oracle(cuda, kernel, variant):
+    """Rates against the oracle; variants: the cubic kernel with the paper's
+    cutoff 2 sqrt(3) dp (smoothing length sqrt(3) dp), and the dam break with
+    its fixed obstacle."""
+    d, s = make(kernel=kernel, obstacle=(variant == "obstacle"), h=(3.0 ** 0.5 * 0.02 if variant == "sqrt3" else None))
     s.rates()
     torch.cuda.synchronize()
     s.check_status()
@@ -166,3 +172,14 @@ def test_sph_full_dam_break_sampled(cuda):
         ed = np.max(np.abs(acc[idx][c, 3] - odr[c])) / rd
         assert ea <= 1e-4, (lo, ea)
         assert ed <= 1e-4, (lo, ed)
+
+
+def test_sph_simulated_time(cuda):
+    """The corrector's time accumulator is the sum of the steps' dt (each
+    step's FP32 dt added in FP64, in step order)."""
+    d, s = make(dp=0.03, perturb=False, obstacle=True)
+    t = 0.0
+    for _ in range(15):
+        s.step(1)
+        t += float(np.float64(s.dt.cpu().numpy()[0]))
+    assert s.simulated_time() == t and t > 0.0
