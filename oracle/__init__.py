@@ -556,3 +556,64 @@ def dem_history_dict(hist):
     """{(p, q): u_t} of a history triple (test helper)."""
     cnt, ids, u = hist
     return {(int(i), int(ids[i, k])): u[i, k].copy() for i in range(len(cnt)) for k in range(int(cnt[i]))}
+
+
+# ---------------------------------------------------------------------------
+# Particle-mesh interpolation with the M'4 kernel (Sec. 4.4: the vortex
+# method's particle-to-mesh and mesh-to-particle interpolations).
+# Reading: a periodic mesh of N[d] nodes per dimension at x = i h_d,
+# h_d = L_d / N_d; a particle at x (wrapped into [0, L)) touches the nodes
+# i0 - 1 .. i0 + 2 (mod N), i0 = floor(x / h), with weight
+# prod_d M'4((x_d - i_d h_d) / h_d).  Plain numpy, FP64.
+
+def m4p(x):
+    """The M'4 kernel (Monaghan's third-order B-spline correction):
+    1 - 5/2 x^2 + 3/2 |x|^3 for |x| < 1, (2 - |x|)^2 (1 - |x|) / 2 for
+    1 <= |x| < 2, 0 beyond."""
+    a = np.abs(np.asarray(x, np.float64))
+    return np.where(a < 1.0, 1.0 - 2.5 * a ** 2 + 1.5 * a ** 3,
+                    np.where(a < 2.0, 0.5 * (2.0 - a) ** 2 * (1.0 - a), 0.0))
+
+
+def _m4_stencil(pos, L, N):
+    """Per particle and dimension: the 4 node indices and weights."""
+    x = np.asarray(pos, np.float64)[:, :3] % np.asarray(L, np.float64)
+    h = np.asarray(L, np.float64) / np.asarray(N)
+    s = x / h
+    i0 = np.floor(s).astype(np.int64)
+    idx, w = [], []
+    for d in range(3):
+        nodes = i0[:, d:d + 1] + np.arange(-1, 3)[None, :]
+        idx.append(np.mod(nodes, N[d]))
+        w.append(m4p(s[:, d:d + 1] - nodes))
+    return idx, w
+
+
+def p2m(pos, val, L, N):
+    """Particle-to-mesh: mesh[k, j, i] = sum_p val_p W(x_node - x_p); val
+    [n, c], mesh [Nz, Ny, Nx, c] (FP64)."""
+    N = tuple(int(v) for v in N)
+    val = np.asarray(val, np.float64)
+    c = val.shape[1]
+    mesh = np.zeros((N[2], N[1], N[0], c))
+    (ix, iy, iz), (wx, wy, wz) = _m4_stencil(pos, L, N)
+    for a in range(4):
+        for b in range(4):
+            for e in range(4):
+                wgt = wx[:, a] * wy[:, b] * wz[:, e]
+                np.add.at(mesh, (iz[:, e], iy[:, b], ix[:, a]), wgt[:, None] * val)
+    return mesh
+
+
+def m2p(pos, mesh, L):
+    """Mesh-to-particle: val_p = sum_nodes mesh[node] W(x_node - x_p)."""
+    mesh = np.asarray(mesh, np.float64)
+    N = (mesh.shape[2], mesh.shape[1], mesh.shape[0])
+    (ix, iy, iz), (wx, wy, wz) = _m4_stencil(pos, L, N)
+    out = np.zeros((np.asarray(pos).shape[0], mesh.shape[3]))
+    for a in range(4):
+        for b in range(4):
+            for e in range(4):
+                wgt = wx[:, a] * wy[:, b] * wz[:, e]
+                out += wgt[:, None] * mesh[iz[:, e], iy[:, b], ix[:, a]]
+    return out
