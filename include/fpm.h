@@ -461,6 +461,39 @@ fpm_status fpm_dem_rebuild_end(const fpm_grid *grid, int32_t n, int32_t cap, con
                                uint32_t *d_pending, fpm_stream stream);
 
 /* ------------------------------------------------------------------ */
+/* Particle-mesh interpolation with the moment-conserving M'4 kernel     */
+/* (Sec. 4.4: the vortex method's particle-to-mesh and mesh-to-particle  */
+/* interpolations).  FP32.                                                */
+/* ------------------------------------------------------------------ */
+/* Mesh: N[d] nodes per dimension at x = i L_d / N_d, periodic in every
+ * dimension; node (i, j, k) at index (k N1 + j) N0 + i of a float4 array.  A
+ * particle with s = x N / L in cell c = floor(s) touches the nodes
+ * c - 1 .. c + 2 (mod N) with weight prod_d M'4(s_d - node_d), M'4(x) =
+ * 1 - 5/2 x^2 + 3/2 |x|^3 (|x| < 1), (2 - |x|)^2 (1 - |x|)/2 (1 <= |x| < 2),
+ * 0 beyond. */
+
+/* The cell grid whose cells are the mesh cells (nc = N), for binning the
+ * particles with fpm_celllist_build before fpm_p2m.  Host only.
+ * FPM_ERR_INVALID unless N[d] >= 3 and the box is periodic in every
+ * dimension, or for more than 2^24 nodes. */
+fpm_status fpm_mesh_grid(const fpm_box *box, const int32_t N[3], fpm_grid *out);
+
+/* mesh[node] = sum_p val_p W(x_node - x_p) (every node written).  pos and
+ * val : float4 [n] binned by mesh cell, with cell_start, by
+ * fpm_celllist_build(box, mesh_grid, ...) (val as its vel); w of val is
+ * interpolated like x, y, z.  A gather over each node's 4x4x4 cells:
+ * deterministic, no atomics.  A node tile whose cells hold more particles
+ * than the staging room reads them from global memory (counted in
+ * d_status->spilled when d_status is given). */
+fpm_status fpm_p2m(const fpm_box *box, const fpm_grid *mesh_grid, int32_t n, const void *pos, const void *val,
+                   const uint32_t *cell_start, void *mesh, fpm_dev_status *d_status, fpm_stream stream);
+
+/* val[p] = sum_nodes mesh[node] W(x_node - x_p), float4 [n]; pos in any
+ * order (wrapped into the box as the cell-list build does). */
+fpm_status fpm_m2p(const fpm_box *box, const fpm_grid *mesh_grid, int32_t n, const void *pos, const void *mesh,
+                   void *val, fpm_stream stream);
+
+/* ------------------------------------------------------------------ */
 /* Adjoint of the LJ force and of velocity Verlet (not in the paper:     */
 /* the chain rule applied to the force of Sec. 4.1 and the integrator    */
 /* of Listing 4.1, for gradients w.r.t. positions, eps and sigma)        */

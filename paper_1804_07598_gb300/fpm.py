@@ -132,6 +132,9 @@ _SIG = {
                                          _VP, _VP, _VP]),
     "fpm_dem_rebuild_end": (_c.c_int, [_c.POINTER(fpm_grid), _c.c_int32, _c.c_int32, _VP, _VP, _VP, _VP, _VP, _VP,
                                        _VP, _VP]),
+    "fpm_mesh_grid": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(_c.c_int32), _c.POINTER(fpm_grid)]),
+    "fpm_p2m": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "fpm_m2p": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _VP, _VP, _VP, _VP]),
     "fpm_lj_backward": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _c.c_int, _VP, _VP, _VP,
                                    _c.c_int32, _c.c_double, _c.c_double, _c.c_double, _VP, _c.c_double, _VP, _VP,
                                    _VP, _c.c_size_t, _VP, _VP]),
@@ -434,6 +437,25 @@ def fpm_dem_rebuild_end(grid, n, cap, list_obj, nn, perm, packed, hist, omega, d
     _check(lib().fpm_dem_rebuild_end(_c.byref(grid), int(n), int(cap), _ptr(list_obj), _ptr(nn), _ptr(perm),
                                      _ptr(packed), _ptr(hist), _ptr(omega), _ptr(d_pending), _stream(stream)))
     _count(2 if n > 0 else 0)
+
+
+def fpm_mesh_grid(box, N) -> fpm_grid:
+    g = fpm_grid()
+    arr = (_c.c_int32 * 3)(*[int(v) for v in N])
+    _check(lib().fpm_mesh_grid(_c.byref(box), arr, _c.byref(g)))
+    return g
+
+
+def fpm_p2m(box, mesh_grid, n, pos, val, cell_start, mesh, d_status=None, stream=None):
+    _check(lib().fpm_p2m(_c.byref(box), _c.byref(mesh_grid), int(n), _ptr(pos), _ptr(val), _ptr(cell_start),
+                         _ptr(mesh), _ptr(d_status), _stream(stream)))
+    _count(1)
+
+
+def fpm_m2p(box, mesh_grid, n, pos, mesh, val, stream=None):
+    _check(lib().fpm_m2p(_c.byref(box), _c.byref(mesh_grid), int(n), _ptr(pos), _ptr(mesh), _ptr(val),
+                         _stream(stream)))
+    _count(1 if n > 0 else 0)
 
 
 def fpm_sph_predict(box, n, params, cfl, pos, vr, acc, d_dtcons, pos_h, vr_h, d_dt, d_dtcons_h, pos_ref=None,
