@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--profile", default=None, choices=["forces", "step", "sph", "verlet", "batch", "adjoint",
-                                                         "celllist", "dem"],
+                                                         "celllist", "dem", "p2m"],
                     help="profiling target for ncu: build the 1M-atom system, then run --steps force sweeps "
                          "or eager steps (no timing, no JSON line)")
     ap.add_argument("--fp64-steps", type=int, default=100)
@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--celllist-builds", type=int, default=50)
     ap.add_argument("--dem-steps", type=int, default=500)
     ap.add_argument("--sph-full", type=int, default=1, help="run the full-length SPH dam break (1) or not (0)")
+    ap.add_argument("--p2m-reps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -570,6 +571,46 @@ def run_ours(args, ws, rank, local):
                "paper": "0.32 s per step for 677,310 grains on one Xeon E5-2680v3 core (context only)"}
         del ds, dgr
 
+    # M'4 particle-mesh interpolation (Sec. 4.4), the paper's size: 2M particles
+    # (uniform, seeded) onto a 128^3 periodic mesh, float4 values; the full
+    # interpolation from unsorted particles (binning by mesh cell + the gather)
+    # and its parts, and mesh-to-particle
+    p2m = None
+    if args.p2m_reps > 0:
+        from paper_1804_07598_gb300.p2m import ParticleMesh
+        import numpy as np
+        rng = np.random.default_rng(7)
+        npm = 2_000_000
+        xp = torch.zeros((npm, 4), dtype=torch.float32, device="cuda")
+        xp[:, :3] = torch.as_tensor(rng.uniform(0.0, 1.0, size=(npm, 3)), dtype=torch.float32, device="cuda")
+        vp = torch.as_tensor(rng.normal(size=(npm, 4)), dtype=torch.float32, device="cuda")
+        pm = ParticleMesh((1.0, 1.0, 1.0), (128, 128, 128), npm)
+        outp = torch.empty_like(vp)
+
+        def timed(fn):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            k0.record()
+            for _ in range(args.p2m_reps):
+                fn()
+            k1.record()
+            torch.cuda.synchronize()
+            return 1e3 * k0.elapsed_time(k1) / args.p2m_reps
+
+        with clk.window():
+            full_us = timed(lambda: pm.p2m(xp, vp))
+            bin_us = timed(lambda: pm.bin(xp, vp))
+            gather_us = timed(lambda: fpm.fpm_p2m(pm.box, pm.grid, npm, pm.pos_s, pm.val_s, pm.cell_start, pm.mesh,
+                                                  pm.status))
+            m2p_us = timed(lambda: pm.m2p(xp, pm.mesh, outp))
+        pm.check_status()
+        p2m = {"workload": "2,000,000 particles (uniform, seeded) onto a 128^3 periodic mesh, float4 values, M'4",
+               "p2m_us": full_us, "bin_us": bin_us, "gather_us": gather_us, "m2p_us": m2p_us,
+               "gather_bytes": 32 * npm + 16 * 128 ** 3,
+               "paper": "the same interpolation: 0.41 s in OpenFPM and 3.4 s in PPM on a single core (context only)"}
+        del pm, xp, vp, outp
+
     # cell-list build from HBM: 8M particles (positions and velocities twice
     # the L2), the in-place rebuild of an already sorted state, replayed from a
     # CUDA graph of one build (six kernels)
@@ -646,6 +687,7 @@ def run_ours(args, ws, rank, local):
         "batch": batch,
         "celllist": cell,
         "dem": dem,
+        "p2m": p2m,
         "gpu_launches": per_step_launches * args.steps + body * int(rebuilds),
         "clocks": clocks,
         "cpu_baseline": cpu,
@@ -748,6 +790,21 @@ def run_profile_target(args):
         runner.backward()
         torch.cuda.synchronize()
         print(f"profile target done: adjoint x{args.steps}, n={wla.n}", flush=True)
+        return
+    if args.profile == "p2m":
+        import numpy as np
+        from paper_1804_07598_gb300.p2m import ParticleMesh
+        rng = np.random.default_rng(7)
+        xp = torch.zeros((2_000_000, 4), dtype=torch.float32, device="cuda")
+        xp[:, :3] = torch.as_tensor(rng.uniform(0.0, 1.0, size=(2_000_000, 3)), dtype=torch.float32, device="cuda")
+        vp = torch.as_tensor(rng.normal(size=(2_000_000, 4)), dtype=torch.float32, device="cuda")
+        pm = ParticleMesh((1.0, 1.0, 1.0), (128, 128, 128), 2_000_000)
+        for _ in range(args.steps):
+            pm.p2m(xp, vp)
+            pm.m2p(xp)
+        torch.cuda.synchronize()
+        pm.check_status()
+        print(f"profile target done: p2m x{args.steps}", flush=True)
         return
     if args.profile == "dem":
         from paper_1804_07598_gb300.dem import DEMSystem

@@ -62,19 +62,27 @@ __device__ __forceinline__ void cell_s(float x, float L, float inv, int N, float
     if (c > N - 1) c = N - 1;
 }
 
-// Staged record of one particle: 12 weights and the value.
-struct P2mRec {
-    float w[12];
-    float4 v;
-};
+// i mod N for i in [-2, N + kCX): one add, then subtractions (a tile wraps a
+// mesh of fewer nodes than its cells more than once).
+__device__ __forceinline__ int wrapi(int i, int N)
+{
+    if (i < 0) i += N;
+    while (i >= N) i -= N;
+    return i;
+}
 
+// Staged particles, component-major (so that the threads of a warp, each
+// reading another particle, spread over the banks): 12 weight rows of `cap`
+// floats, then `cap` float4 values.
 __global__ void __launch_bounds__(kP2mThreads)
     k_p2m(MeshD m, const float4 *__restrict__ pos, const float4 *__restrict__ val,
           const uint32_t *__restrict__ cs, int cap, float4 *__restrict__ mesh, fpm_dev_status *st)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    P2mRec *rec = (P2mRec *)smem_raw;
+    float4 *sv = (float4 *)smem_raw;
+    float *sw = (float *)(sv + cap);  // sw[j * cap + e], j = 0..11
     __shared__ uint32_t coff[kTileCells + 1];  // staged offset of each tile cell
+    __shared__ uint32_t cstart[kTileCells];    // its first particle (sorted index)
     __shared__ uint32_t wsum[kP2mThreads / 32];
     const int tilesx = (m.N[0] + kTX - 1) / kTX, tilesy = (m.N[1] + kTY - 1) / kTY;
     const int tx = blockIdx.x % tilesx, ty = (blockIdx.x / tilesx) % tilesy, tz = blockIdx.x / (tilesx * tilesy);
@@ -90,15 +98,15 @@ __global__ void __launch_bounds__(kP2mThreads)
         cnt[r] = 0;
         if (q < kTileCells) {
             const int cx = q % kCX, cy = (q / kCX) % kCY, cz = q / (kCX * kCY);
-            const int gx = (x0 - 2 + cx + 2 * m.N[0]) % m.N[0];
-            const int gy = (y0 - 2 + cy + 2 * m.N[1]) % m.N[1];
-            const int gz = (z0 - 2 + cz + 2 * m.N[2]) % m.N[2];
-            const uint32_t g = ((uint32_t)gz * (uint32_t)m.N[1] + (uint32_t)gy) * (uint32_t)m.N[0] + (uint32_t)gx;
-            cnt[r] = cs[g + 1] - cs[g];
+            const uint32_t g = ((uint32_t)wrapi(z0 - 2 + cz, m.N[2]) * (uint32_t)m.N[1] +
+                                (uint32_t)wrapi(y0 - 2 + cy, m.N[1])) * (uint32_t)m.N[0] +
+                               (uint32_t)wrapi(x0 - 2 + cx, m.N[0]);
+            const uint32_t a = cs[g];
+            cstart[q] = a;
+            cnt[r] = cs[g + 1] - a;
         }
         mine += cnt[r];
     }
-    // block exclusive scan of `mine`
     const int lane = t & 31, warp = t >> 5;
     uint32_t incl = mine;
 #pragma unroll
@@ -124,81 +132,82 @@ __global__ void __launch_bounds__(kP2mThreads)
     __syncthreads();
     const bool staged = total <= (uint32_t)cap;
     if (!staged && t == 0 && st) atomicAdd(&st->spilled, 1u);
-    // 2. stage the particles of every tile cell with their weights
+    // 2. stage the particles of every tile cell with their 12 weights (a
+    //    thread per cell: cells hold about one particle)
     if (staged) {
-        for (int q = warp; q < kTileCells; q += kP2mThreads / 32) {
-            const int cx = q % kCX, cy = (q / kCX) % kCY, cz = q / (kCX * kCY);
-            const int gx = (x0 - 2 + cx + 2 * m.N[0]) % m.N[0];
-            const int gy = (y0 - 2 + cy + 2 * m.N[1]) % m.N[1];
-            const int gz = (z0 - 2 + cz + 2 * m.N[2]) % m.N[2];
-            const uint32_t g = ((uint32_t)gz * (uint32_t)m.N[1] + (uint32_t)gy) * (uint32_t)m.N[0] + (uint32_t)gx;
-            const uint32_t p0 = cs[g], k = coff[q + 1] - coff[q];
-            for (uint32_t e = lane; e < k; e += 32) {
+        for (int q = t; q < kTileCells; q += kP2mThreads) {
+            const uint32_t p0 = cstart[q], o = coff[q], k = coff[q + 1] - o;
+            for (uint32_t e = 0; e < k; ++e) {
                 const float4 p = pos[p0 + e];
-                P2mRec r;
-                float s;
+                float w[12], s;
                 int c;
                 cell_s(p.x, m.L[0], m.inv[0], m.N[0], s, c);
-                m4p4(s, c, r.w);
+                m4p4(s, c, w);
                 cell_s(p.y, m.L[1], m.inv[1], m.N[1], s, c);
-                m4p4(s, c, r.w + 4);
+                m4p4(s, c, w + 4);
                 cell_s(p.z, m.L[2], m.inv[2], m.N[2], s, c);
-                m4p4(s, c, r.w + 8);
-                r.v = val[p0 + e];
-                rec[coff[q] + e] = r;
+                m4p4(s, c, w + 8);
+#pragma unroll
+                for (int j = 0; j < 12; ++j) sw[j * cap + o + e] = w[j];
+                sv[o + e] = val[p0 + e];
             }
         }
     }
     __syncthreads();
-    // 3. node (x0 + a, y0 + b, z0 + c): cells of local index node + 0 .. 3 in
-    //    each dimension; a particle of local cell node + k has weight index 3 - k
+    // 3. node (x0 + a, y0 + b, z0 + c): in each of its 16 cell rows the cells
+    //    a .. a+3 (local x) are consecutive in the staging; a particle of local
+    //    cell node + k (per dimension) has weight index 3 - k.  The node walks
+    //    the particles of its 16 rows as one sequence (row by row, in staging
+    //    order), so that the lanes of a warp diverge only on their totals.
     const int a = t % kTX, b = (t / kTX) % kTY, c = t / (kTX * kTY);
     const int gx = x0 + a, gy = y0 + b, gz = z0 + c;
     if (gx >= m.N[0] || gy >= m.N[1] || gz >= m.N[2]) return;
     float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    for (int kz = 0; kz < 4; ++kz) {
-        for (int ky = 0; ky < 4; ++ky) {
-            for (int kx = 0; kx < 4; ++kx) {
-                const int q = ((c + kz) * kCY + (b + ky)) * kCX + (a + kx);
-                const uint32_t s0 = coff[q], s1 = coff[q + 1];
-                for (uint32_t e = s0; e < s1; ++e) {
-                    float wx, wy, wz;
-                    float4 v;
-                    if (staged) {
-                        wx = rec[e].w[3 - kx];
-                        wy = rec[e].w[4 + 3 - ky];
-                        wz = rec[e].w[8 + 3 - kz];
-                        v = rec[e].v;
-                    } else {  // the particle from global memory: cell q's (e - s0)-th
-                        const int cx = a + kx, cy = b + ky, cz = c + kz;
-                        const int hx = (x0 - 2 + cx + 2 * m.N[0]) % m.N[0];
-                        const int hy = (y0 - 2 + cy + 2 * m.N[1]) % m.N[1];
-                        const int hz = (z0 - 2 + cz + 2 * m.N[2]) % m.N[2];
-                        const uint32_t g =
-                            ((uint32_t)hz * (uint32_t)m.N[1] + (uint32_t)hy) * (uint32_t)m.N[0] + (uint32_t)hx;
-                        const uint32_t i = cs[g] + (e - s0);
-                        const float4 p = pos[i];
-                        float w4[4], s;
-                        int cc;
-                        cell_s(p.x, m.L[0], m.inv[0], m.N[0], s, cc);
-                        m4p4(s, cc, w4);
-                        wx = w4[3 - kx];
-                        cell_s(p.y, m.L[1], m.inv[1], m.N[1], s, cc);
-                        m4p4(s, cc, w4);
-                        wy = w4[3 - ky];
-                        cell_s(p.z, m.L[2], m.inv[2], m.N[2], s, cc);
-                        m4p4(s, cc, w4);
-                        wz = w4[3 - kz];
-                        v = val[i];
-                    }
-                    const float w = wx * wy * wz;
-                    acc.x = fmaf(w, v.x, acc.x);
-                    acc.y = fmaf(w, v.y, acc.y);
-                    acc.z = fmaf(w, v.z, acc.z);
-                    acc.w = fmaf(w, v.w, acc.w);
-                }
-            }
+    int row = -1;  // ky + 4 kz of the current row
+    int q0 = 0;
+    uint32_t e = 0, b1 = 0, b2 = 0, b3 = 0, rend = 0;
+    for (;;) {
+        while (e == rend) {  // next non-empty row
+            if (++row == 16) break;
+            q0 = ((c + (row >> 2)) * kCY + (b + (row & 3))) * kCX + a;
+            e = coff[q0];
+            b1 = coff[q0 + 1];
+            b2 = coff[q0 + 2];
+            b3 = coff[q0 + 3];
+            rend = coff[q0 + 4];
         }
+        if (row == 16) break;
+        const int kx = (e >= b1) + (e >= b2) + (e >= b3);
+        const int ky = row & 3, kz = row >> 2;
+        float wx, wy, wz;
+        float4 v;
+        if (staged) {
+            wx = sw[(3 - kx) * cap + e];
+            wy = sw[(7 - ky) * cap + e];
+            wz = sw[(11 - kz) * cap + e];
+            v = sv[e];
+        } else {  // the particle from global memory
+            const uint32_t i = cstart[q0 + kx] + (e - coff[q0 + kx]);
+            const float4 p = pos[i];
+            float w4[4], s;
+            int cc;
+            cell_s(p.x, m.L[0], m.inv[0], m.N[0], s, cc);
+            m4p4(s, cc, w4);
+            wx = w4[3 - kx];
+            cell_s(p.y, m.L[1], m.inv[1], m.N[1], s, cc);
+            m4p4(s, cc, w4);
+            wy = w4[3 - ky];
+            cell_s(p.z, m.L[2], m.inv[2], m.N[2], s, cc);
+            m4p4(s, cc, w4);
+            wz = w4[3 - kz];
+            v = val[i];
+        }
+        const float w = wx * wy * wz;
+        acc.x = fmaf(w, v.x, acc.x);
+        acc.y = fmaf(w, v.y, acc.y);
+        acc.z = fmaf(w, v.z, acc.z);
+        acc.w = fmaf(w, v.w, acc.w);
+        ++e;
     }
     mesh[((size_t)gz * (size_t)m.N[1] + (size_t)gy) * (size_t)m.N[0] + (size_t)gx] = acc;
 }
@@ -288,12 +297,16 @@ extern "C" fpm_status fpm_p2m(const fpm_box *box, const fpm_grid *mesh_grid, int
     if (n < 0 || !cell_start || !mesh || (n > 0 && (!pos || !val)))
         return fpm_fail(FPM_ERR_INVALID, "fpm_p2m: null pointer or bad size");
     const int tiles = ((m.N[0] + kTX - 1) / kTX) * ((m.N[1] + kTY - 1) / kTY) * ((m.N[2] + kTZ - 1) / kTZ);
-    // staging room: twice the tile cells' mean load, at least 256, within the budget
+    // staging room: 1.15x the tile cells' mean load + 96 (a uniform load stays
+    // far below it: ~800 +- 30 particles at the paper's density), 64 B per
+    // particle, within the budget; three blocks per SM at that size
     const double mean = (double)n / (double)mesh_grid->ncell * kTileCells;
-    int cap = (int)(2.0 * mean) + 256;
-    const int maxcap = kP2mSmem / (int)sizeof(P2mRec);
+    int cap = (int)(1.15 * mean) + 96;
+    cap = (cap + 3) / 4 * 4;
+    const int per = 12 * (int)sizeof(float) + (int)sizeof(float4);
+    const int maxcap = kP2mSmem / per / 4 * 4;
     if (cap > maxcap) cap = maxcap;
-    const size_t smem = (size_t)cap * sizeof(P2mRec);
+    const size_t smem = (size_t)cap * per;
     cudaFuncSetAttribute((const void *)k_p2m, cudaFuncAttributeMaxDynamicSharedMemorySize, kP2mSmem);
     k_p2m<<<tiles, kP2mThreads, smem, (cudaStream_t)stream>>>(m, (const float4 *)pos, (const float4 *)val,
                                                                 cell_start, cap, (float4 *)mesh, d_status);
