@@ -11,7 +11,8 @@
 //   k_scatter    tmp[cell_start[c] + rank] = i (arrival order inside a cell)
 //   k_sort_gather one warp per cell sorts the cell's slice of tmp by input
 //                index (this makes the sort stable and deterministic), writes
-//                perm and gathers pos / vel / id into sorted order
+//                perm and gathers pos / vel / id into sorted order; on sparse
+//                grids k_sort_gather_sparse gives small cells a lane each
 #include <climits>
 
 #include "fpm_common.cuh"
@@ -243,7 +244,7 @@ __device__ __forceinline__ void emit(uint32_t slot, uint32_t src, const BoxT<T> 
 // A cell of more than 32 particles, by one warp: the rank of each element is
 // the number of smaller input indices in the cell.
 template <typename T>
-__device__ __noinline__ void sort_gather_large(uint32_t s, uint32_t k, const uint32_t *__restrict__ tmp,
+__device__ __forceinline__ void sort_gather_large(uint32_t s, uint32_t k, const uint32_t *__restrict__ tmp,
                                                const BoxT<T> &box, const V4<T> *pos_src, const V4<T> *vel_src,
                                                const uint32_t *id_src, V4<T> *pos_out, V4<T> *vel_out,
                                                uint32_t *id_out, uint32_t *__restrict__ perm)
@@ -335,6 +336,72 @@ __global__ void k_sort_gather(BoxT<T> box, int ncell, const uint32_t *__restrict
     }
 }
 
+// Sparse grids (a few particles per cell on average): a lane per cell.  A
+// cell of up to kLaneCell particles is sorted by input index in registers
+// (Batcher's odd-even merge network for 8 inputs, 19 compare-exchanges,
+// empty slots padded with UINT_MAX) and gathered by its lane; the warp then
+// takes its larger cells one by one as the dense kernel does.
+constexpr uint32_t kLaneCell = 8;
+
+__device__ __forceinline__ void cmpx(uint32_t &a, uint32_t &b)
+{
+    const uint32_t lo = min(a, b), hi = max(a, b);
+    a = lo;
+    b = hi;
+}
+
+__device__ __forceinline__ void sort8(uint32_t (&v)[8])
+{
+    cmpx(v[0], v[1]); cmpx(v[2], v[3]); cmpx(v[4], v[5]); cmpx(v[6], v[7]);
+    cmpx(v[0], v[2]); cmpx(v[1], v[3]); cmpx(v[4], v[6]); cmpx(v[5], v[7]);
+    cmpx(v[1], v[2]); cmpx(v[5], v[6]);
+    cmpx(v[0], v[4]); cmpx(v[1], v[5]); cmpx(v[2], v[6]); cmpx(v[3], v[7]);
+    cmpx(v[2], v[4]); cmpx(v[3], v[5]);
+    cmpx(v[1], v[2]); cmpx(v[3], v[4]); cmpx(v[5], v[6]);
+}
+
+template <typename T>
+__global__ void k_sort_gather_sparse(BoxT<T> box, int ncell, const uint32_t *__restrict__ cell_start,
+                                     const uint32_t *__restrict__ tmp, const V4<T> *pos_src, const V4<T> *vel_src,
+                                     const uint32_t *id_src, V4<T> *pos_out, V4<T> *vel_out, uint32_t *id_out,
+                                     uint32_t *__restrict__ perm, const uint32_t *gate)
+{
+    if (gated_off(gate)) return;
+    const unsigned lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // the loop bound is uniform per warp (base is the warp's first cell)
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31u); base < ncell; base += stride) {
+        const int64_t c = base + lane;
+        uint32_t s = 0, k = 0;
+        if (c < ncell) {
+            s = cell_start[c];
+            k = cell_start[c + 1] - s;
+        }
+        if (k <= kLaneCell) {
+            uint32_t v[8];
+#pragma unroll
+            for (uint32_t i = 0; i < 8; ++i) v[i] = i < k ? tmp[s + i] : UINT_MAX;
+            sort8(v);
+#pragma unroll
+            for (uint32_t i = 0; i < 8; ++i)
+                if (i < k) emit<T>(s + i, v[i], box, pos_src, vel_src, id_src, pos_out, vel_out, id_out, perm);
+        }
+        unsigned big = __ballot_sync(kFull, k > kLaneCell);
+        while (big) {
+            const int l = __ffs(big) - 1;
+            big &= big - 1u;
+            const uint32_t sb = __shfl_sync(kFull, s, l), kb = __shfl_sync(kFull, k, l);
+            if (kb > 32u) {
+                sort_gather_large<T>(sb, kb, tmp, box, pos_src, vel_src, id_src, pos_out, vel_out, id_out, perm);
+            } else {
+                uint32_t v = lane < kb ? tmp[sb + lane] : UINT_MAX;
+                v = warp_sort32(v);
+                if (lane < kb) emit<T>(sb + lane, v, box, pos_src, vel_src, id_src, pos_out, vel_out, id_out, perm);
+            }
+        }
+    }
+}
+
 template <typename T>
 __global__ void k_reorder(int n, const uint32_t *__restrict__ perm, const T *__restrict__ src, T *__restrict__ dst,
                           const uint32_t *gate)
@@ -382,10 +449,16 @@ static fpm_status celllist_launch(const fpm_box &b, const fpm_grid &g, int n, co
         const V4<T> *psrc = spos ? spos : pin;
         const V4<T> *vsrc = svel ? svel : vin;
         const uint32_t *isrc = sid ? sid : id_in;
-        const int64_t threads = (int64_t)ncell * 32;
-        k_sort_gather<T><<<grid_cap((threads + 255) / 256), 256, 0, stream>>>(
-            box, ncell, cell_start, tmp, psrc, vel_out ? vsrc : nullptr, isrc, (V4<T> *)pos_out,
-            (V4<T> *)vel_out, id_out, perm, gate);
+        if ((double)n < 4.0 * (double)ncell) {  // sparse: a lane per cell
+            k_sort_gather_sparse<T><<<grid_cap(((int64_t)ncell + 255) / 256), 256, 0, stream>>>(
+                box, ncell, cell_start, tmp, psrc, vel_out ? vsrc : nullptr, isrc, (V4<T> *)pos_out,
+                (V4<T> *)vel_out, id_out, perm, gate);
+        } else {  // a warp per cell
+            const int64_t threads = (int64_t)ncell * 32;
+            k_sort_gather<T><<<grid_cap((threads + 255) / 256), 256, 0, stream>>>(
+                box, ncell, cell_start, tmp, psrc, vel_out ? vsrc : nullptr, isrc, (V4<T> *)pos_out,
+                (V4<T> *)vel_out, id_out, perm, gate);
+        }
     }
     return fpm_check_launch("fpm_celllist_build");
 }

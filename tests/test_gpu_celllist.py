@@ -112,6 +112,34 @@ def test_celllist_crowded_cells_among_many(cuda, prec):
     assert np.array_equal(g["vel"], o["vel"])
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_celllist_sparse_grid(cuda, prec):
+    """Far fewer particles than cells (the sparse sort: a lane per cell of up
+    to 8), with cells of 9-32 and of hundreds of particles among them (taken
+    by the warp): bit-exact against the oracle."""
+    L = np.array([20.0, 20.0, 20.0])
+    rng = np.random.default_rng(12)
+    parts = [rng.uniform(0.0, 20.0, size=(40000, 3)),  # ~0.04 per cell
+             rng.uniform(5.0, 5.19, size=(600, 3)),    # one crowded cell
+             rng.uniform(11.0, 11.19, size=(20, 3))]   # a cell of ~20
+    parts += [rng.uniform(c, c + 0.19, size=(int(k), 3)) for c, k in zip(np.linspace(1.0, 18.0, 40),
+                                                                         rng.integers(2, 12, 40))]
+    x = np.concatenate(parts)
+    x = x[rng.permutation(len(x))]
+    dt = np.float32 if prec == "f32" else np.float64
+    pos = inputs.as4(x, dt)
+    vel = inputs.as4(rng.normal(size=x.shape), dt)
+    o = oracle_cells(pos, L, (1, 1, 1), 0.2, vel=vel)
+    k = np.diff(o["cell_start"])
+    assert len(x) < 4 * len(k) and k.max() > 32 and np.sum((k > 8) & (k <= 32)) >= 1 and np.sum(k == 0) > 0
+    g = gpu_celllist(pos, L, (1, 1, 1), 0.2, prec, vel4=vel)
+    assert fpm_ok(g)
+    assert np.array_equal(g["cell_start"], o["cell_start"])
+    assert np.array_equal(g["perm"], o["perm"])
+    assert np.array_equal(g["pos"], o["pos"].astype(dt))
+    assert np.array_equal(g["vel"], o["vel"])
+
+
 def test_celllist_empty(cuda):
     g = gpu_celllist(np.zeros((0, 4), np.float32), (10.0, 10.0, 10.0), (1, 1, 1), 2.8, "f32")
     assert np.all(g["cell_start"] == 0)
