@@ -603,10 +603,12 @@ def run_ours(args, ws, rank, local):
             bin_us = timed(lambda: pm.bin(xp, vp))
             gather_us = timed(lambda: fpm.fpm_p2m(pm.box, pm.grid, npm, pm.pos_s, pm.val_s, pm.cell_start, pm.mesh,
                                                   pm.status))
-            m2p_us = timed(lambda: pm.m2p(xp, pm.mesh, outp))
+            m2p_us = timed(lambda: pm.m2p(xp, pm.mesh, outp, binned=True))
+            m2p_unsorted_us = timed(lambda: pm.m2p(xp, pm.mesh, outp))
         pm.check_status()
         p2m = {"workload": "2,000,000 particles (uniform, seeded) onto a 128^3 periodic mesh, float4 values, M'4",
                "p2m_us": full_us, "bin_us": bin_us, "gather_us": gather_us, "m2p_us": m2p_us,
+               "m2p_unbinned_order_us": m2p_unsorted_us,
                "gather_bytes": 32 * npm + 16 * 128 ** 3,
                "paper": "the same interpolation: 0.41 s in OpenFPM and 3.4 s in PPM on a single core (context only)"}
         del pm, xp, vp, outp

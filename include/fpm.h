@@ -489,9 +489,12 @@ fpm_status fpm_p2m(const fpm_box *box, const fpm_grid *mesh_grid, int32_t n, con
                    const uint32_t *cell_start, void *mesh, fpm_dev_status *d_status, fpm_stream stream);
 
 /* val[p] = sum_nodes mesh[node] W(x_node - x_p), float4 [n]; pos in any
- * order (wrapped into the box as the cell-list build does). */
+ * order (wrapped into the box as the cell-list build does).  order
+ * (optional, a permutation of 0..n-1, e.g. the perm of the binning of the
+ * same positions): the particles are taken in that order, which only
+ * changes speed (neighbouring threads share nodes); each val[p] is the same. */
 fpm_status fpm_m2p(const fpm_box *box, const fpm_grid *mesh_grid, int32_t n, const void *pos, const void *mesh,
-                   void *val, fpm_stream stream);
+                   const uint32_t *order, void *val, fpm_stream stream);
 
 /* ------------------------------------------------------------------ */
 /* Adjoint of the LJ force and of velocity Verlet (not in the paper:     */

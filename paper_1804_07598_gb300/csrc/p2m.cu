@@ -212,12 +212,15 @@ __global__ void __launch_bounds__(kP2mThreads)
     mesh[((size_t)gz * (size_t)m.N[1] + (size_t)gy) * (size_t)m.N[0] + (size_t)gx] = acc;
 }
 
-// Mesh-to-particle: one thread per particle gathers its 64 nodes.
+// Mesh-to-particle: one thread per particle gathers its 64 nodes; thread t
+// takes particle order[t] (neighbouring threads on neighbouring particles when
+// order is a binning's permutation, so that their nodes are shared in L1).
 __global__ void k_m2p(MeshD m, int n, const float4 *__restrict__ pos, const float4 *__restrict__ mesh,
-                      float4 *__restrict__ out)
+                      const uint32_t *__restrict__ order, float4 *__restrict__ out)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int i = order ? (int)order[t] : t;
     const float4 p = pos[i];
     float wx[4], wy[4], wz[4], s;
     int cx, cy, cz;
@@ -314,7 +317,7 @@ extern "C" fpm_status fpm_p2m(const fpm_box *box, const fpm_grid *mesh_grid, int
 }
 
 extern "C" fpm_status fpm_m2p(const fpm_box *box, const fpm_grid *mesh_grid, int32_t n, const void *pos,
-                              const void *mesh, void *val, fpm_stream stream)
+                              const void *mesh, const uint32_t *order, void *val, fpm_stream stream)
 {
     MeshD m{};
     fpm_status s = mesh_ok(box, mesh_grid, "fpm_m2p", m);
@@ -322,6 +325,6 @@ extern "C" fpm_status fpm_m2p(const fpm_box *box, const fpm_grid *mesh_grid, int
     if (n < 0 || !mesh || (n > 0 && (!pos || !val))) return fpm_fail(FPM_ERR_INVALID, "fpm_m2p: null pointer");
     if (n == 0) return FPM_OK;
     k_m2p<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(m, n, (const float4 *)pos, (const float4 *)mesh,
-                                                           (float4 *)val);
+                                                           order, (float4 *)val);
     return fpm_check_launch("fpm_m2p");
 }

@@ -134,7 +134,7 @@ _SIG = {
                                        _VP, _VP]),
     "fpm_mesh_grid": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(_c.c_int32), _c.POINTER(fpm_grid)]),
     "fpm_p2m": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _VP, _VP, _VP, _VP, _VP, _VP]),
-    "fpm_m2p": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _VP, _VP, _VP, _VP]),
+    "fpm_m2p": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _VP, _VP, _VP, _VP, _VP]),
     "fpm_lj_backward": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _c.c_int, _VP, _VP, _VP,
                                    _c.c_int32, _c.c_double, _c.c_double, _c.c_double, _VP, _c.c_double, _VP, _VP,
                                    _VP, _c.c_size_t, _VP, _VP]),
@@ -452,8 +452,8 @@ def fpm_p2m(box, mesh_grid, n, pos, val, cell_start, mesh, d_status=None, stream
     _count(1)
 
 
-def fpm_m2p(box, mesh_grid, n, pos, mesh, val, stream=None):
-    _check(lib().fpm_m2p(_c.byref(box), _c.byref(mesh_grid), int(n), _ptr(pos), _ptr(mesh), _ptr(val),
+def fpm_m2p(box, mesh_grid, n, pos, mesh, val, order=None, stream=None):
+    _check(lib().fpm_m2p(_c.byref(box), _c.byref(mesh_grid), int(n), _ptr(pos), _ptr(mesh), _ptr(order), _ptr(val),
                          _stream(stream)))
     _count(1 if n > 0 else 0)
 

@@ -49,12 +49,15 @@ class ParticleMesh:
                     self.status, stream=stream)
         return self.mesh
 
-    def m2p(self, pos, mesh=None, out=None, stream=None):
-        """The M'4 interpolation of the mesh at the particles."""
+    def m2p(self, pos, mesh=None, out=None, binned=False, stream=None):
+        """The M'4 interpolation of the mesh at the particles.  binned=True:
+        `pos` are the positions last given to p2m/bin, whose permutation then
+        orders the work (faster; the same values)."""
         mesh = self.mesh if mesh is None else mesh
         if out is None:
             out = torch.empty((pos.shape[0], 4), dtype=torch.float32, device=self.device)
-        fpm.fpm_m2p(self.box, self.grid, pos.shape[0], pos, mesh, out, stream=stream)
+        order = self.perm if binned and pos.shape[0] > 0 else None
+        fpm.fpm_m2p(self.box, self.grid, pos.shape[0], pos, mesh, out, order=order, stream=stream)
         return out
 
     def check_status(self):

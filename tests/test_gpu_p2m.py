@@ -101,6 +101,12 @@ def test_m2p_matches_oracle(cuda):
     torch.cuda.synchronize()
     o = oracle.m2p(x, mesh, L)
     assert np.abs(out.cpu().numpy() - o).max() <= 1e-5 * rms(o)
+    # taken in the binning's order: the same values, bit for bit
+    xt = torch.as_tensor(x, dtype=torch.float32, device="cuda")
+    pm.bin(xt, torch.zeros_like(xt))
+    out2 = pm.m2p(xt, torch.as_tensor(mesh, dtype=torch.float32, device="cuda"), binned=True)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out2.cpu().numpy(), out.cpu().numpy())
 
 
 def test_p2m_paper_size_sampled(cuda):
