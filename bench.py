@@ -347,6 +347,26 @@ def run_ours(args, ws, rank, local):
     e1.record()
     torch.cuda.synchronize()
     fp64_steps_per_s = args.fp64_steps / (e1_ms := e0.elapsed_time(e1)) * 1e3
+    # the FP64 force sweep alone, against the FP64 peak (not measured on this
+    # pool: the nominal 1.25 TFLOP/s of GB300)
+    nn64 = int(s64.nn[: s64.n].sum().item())
+    for _ in range(2):
+        s64.compute_forces()
+    k0.record()
+    for _ in range(5):
+        s64.compute_forces()
+    k1.record()
+    torch.cuda.synchronize()
+    force64_us = 1e3 * k0.elapsed_time(k1) / 5
+    fp64_tflops = FLOP_PER_SLOT * nn64 / (force64_us * 1e-6) / 1e12
+    # the Verlet rebuild on its own (cell list + Verlet build, 1M atoms, eager)
+    torch.cuda.synchronize()
+    k0.record()
+    for _ in range(5):
+        s.rebuild()
+    k1.record()
+    torch.cuda.synchronize()
+    rebuild_us = 1e3 * k0.elapsed_time(k1) / 5
     del s64, g64
 
     # end to end through the public API with host buffers: every step copies the
@@ -674,6 +694,12 @@ def run_ours(args, ws, rank, local):
         "rebuilds_in_timed_region": int(rebuilds),
         "fp64_steps_per_s": fp64_steps_per_s * ws,
         "fp32_over_fp64": steps_per_s / (fp64_steps_per_s * ws),
+        "fp64_force_kernel": {"launch_us": force64_us, "achieved_tflops": fp64_tflops, "peak_tflops": 1.25,
+                              "frac": fp64_tflops / 1.25, "peak_kind": "nominal GB300 FP64 (not measured here)"},
+        "list_slots_per_s": nn_sum * steps_per_s,
+        "rebuild": {"us": rebuild_us, "rebuilds_per_step": rebuilds / args.steps,
+                    "amortised_us_per_step": rebuild_us * rebuilds / args.steps,
+                    "note": "cell list + Verlet build (eager), gated by the displacement test in the timed steps"},
         "roofline": {"kernel": "k_lj_tiles<float>", "bound": "alu", "achieved": tflops, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": tflops / fp32_peak, "traffic": traffic_for("k_lj_tiles<float>"),
                      "peak_kind": f"FP32 CUDA cores: {n_sm} SMs x 128 lanes x 2 FLOP x {sm_mhz:.0f} MHz (median "
