@@ -261,6 +261,7 @@ fpm_status fpm_reduce_workspace(int32_t n, const fpm_grid *grid, size_t *bytes);
  * d_energy  : [3] double: U = sum_{i<j} V, W = sum_{i<j} r_ij . F_ij and
  *             the number of interacting pairs.  Reduced in FP64 in a fixed
  *             order (bit-reproducible).  May be NULL (no reduction).
+ *             With n == 0 it receives zeros and nothing is launched.
  * workspace : fpm_reduce_workspace(n, grid) bytes (zero-filled once; always
  *             needed: it holds the sweep's tile-scheduling counters).
  * d_status  : device status block or NULL; FPM_FLAG_TIMEOUT is latched if a

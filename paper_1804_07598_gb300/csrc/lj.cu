@@ -113,6 +113,14 @@ static fpm_status lj_args(const fpm_box *box, const fpm_grid *grid, int32_t n, f
     return FPM_OK;
 }
 
+// U, W and the pair count of an empty system: zeros, written on the stream.
+static fpm_status zero_energy(double *d_energy, cudaStream_t st, const char *who)
+{
+    if (d_energy && cudaMemsetAsync(d_energy, 0, 3 * sizeof(double), st) != cudaSuccess)
+        return fpm_fail(FPM_ERR_CUDA, "%s: cudaMemsetAsync failed", who);
+    return FPM_OK;
+}
+
 }  // namespace fpm
 
 using namespace fpm;
@@ -124,7 +132,7 @@ extern "C" fpm_status fpm_lj_forces(const fpm_box *box, const fpm_grid *grid, in
 {
     fpm_status s = lj_args(box, grid, n, prec, pos, list, nn, cap, sigma, rc, force, "fpm_lj_forces");
     if (s != FPM_OK) return s;
-    if (n == 0) return FPM_OK;
+    if (n == 0) return zero_energy(d_energy, (cudaStream_t)stream, "fpm_lj_forces");
     RedWs r{};
     s = red_ws(n, grid, workspace, workspace_bytes, "fpm_lj_forces", r);
     if (s != FPM_OK) return s;
@@ -187,7 +195,7 @@ extern "C" fpm_status fpm_lj_forces_noalloc(const fpm_box *box, const fpm_grid *
     if ((int64_t)grid->tiles_x * grid->nc[1] * grid->nc[2] > kNoAllocMaxBlocks)
         return fpm_fail(FPM_ERR_INVALID, "fpm_lj_forces_noalloc: more than %d tiles exceed the built-in scratch limit",
                         kNoAllocMaxBlocks);
-    if (n == 0) return FPM_OK;
+    if (n == 0) return zero_energy(d_energy, (cudaStream_t)stream, "fpm_lj_forces_noalloc");
     RedWs r{};
     cudaStream_t st = (cudaStream_t)stream;
     {
