@@ -2,7 +2,8 @@
 contact forces, torques and tangential histories at identical states (with
 and without stored histories), the histories carried through Verlet
 rebuilds, multi-step runs with rebuilds and walls, conservation of momentum
-and angular momentum, and graph replays against eager steps."""
+and angular momentum, graph replays against eager steps, and single
+contacts against the closed forms of Eqs. 10-12."""
 import numpy as np
 import pytest
 import torch
@@ -258,3 +259,82 @@ def test_dem_graph_replay_equals_eager(cuda):
     for x, y in zip(a.state_by_id(), b.state_by_id()):
         np.testing.assert_array_equal(x, y)
     assert a.history_by_id().keys() == b.history_by_id().keys()
+
+
+def contact_pair(n, delta, c=(1.0, 1.0, 1.0)):
+    """Grains 0 and 1 whose centres are 2R - delta apart along n (0 at
+    c + r n / 2), positions rounded to FP32."""
+    r = 2 * R - delta
+    x = np.zeros((2, 4))
+    x[0, :3] = np.asarray(c) + 0.5 * r * n
+    x[1, :3] = np.asarray(c) - 0.5 * r * n
+    return f32(x)
+
+
+@pytest.mark.parametrize("seed,delta", [(1, 1e-3), (2, 5e-3), (3, 2e-2)])
+def test_dem_static_contact_closed_form(cuda, seed, delta):
+    """One contact at rest, on the GPU: Eq. 11 alone, F_0 = sqrt(delta / 2R)
+    kn delta n = -F_1 with delta taken from the stored positions; no torque,
+    no tangential history, two ordered contacts."""
+    n = np.random.default_rng(seed).normal(size=3)
+    n /= np.linalg.norm(n)
+    x = contact_pair(n, delta)
+    pd = params()
+    ds = DEMSystem(x, np.zeros((2, 3)), np.zeros((2, 3)), (3.0, 3.0, 3.0), (1, 1, 1), pd, SKIN)
+    ds.compute_forces()
+    torch.cuda.synchronize()
+    _, _, _, F, T = ds.state_by_id()
+    d = x[0, :3] - x[1, :3]
+    r = np.linalg.norm(d)
+    dl = 2 * R - r
+    ref = np.sqrt(dl / (2 * R)) * pd["kn"] * dl * d / r
+    scale = np.linalg.norm(ref)
+    # delta = 2R - r carries a few ulps of 2R (TOL_F above): 1e-5 of delta at
+    # delta = 1e-3, 1.5e-5 of the force
+    assert np.max(np.abs(F[0, :3] - ref)) <= TOL_F * scale
+    assert np.max(np.abs(F[1, :3] + ref)) <= TOL_F * scale
+    assert np.all(np.abs(T[:, :3]) <= 1e-6 * scale * R)
+    assert ds.contacts() == 2
+    assert all(np.all(v == 0) for v in ds.history_by_id().values())
+
+
+def test_dem_sliding_contact_first_step_closed_form(cuda):
+    """A new contact sliding at v_t with no spin, on the GPU: Eq. 10 stores
+    u = v_t dt (and -u for the mirror entry), Eq. 12 gives F_t = f (-kt u -
+    gt m_eff v_t), the torque on each grain is -1/2 r_pq x F_t, and the two
+    grains get opposite forces."""
+    rng = np.random.default_rng(7)
+    n = np.array([1.0, 0.2, -0.3])
+    n /= np.linalg.norm(n)
+    t = rng.normal(size=3)
+    t -= t.dot(n) * n
+    t /= np.linalg.norm(t)
+    delta = 3e-3
+    x = contact_pair(n, delta)
+    v = f32(np.stack([0.4 * t, -0.1 * t]))
+    pd = params(gt=1.7, mu=1e3)  # no Coulomb limit here
+    ds = DEMSystem(x, v, np.zeros((2, 3)), (3.0, 3.0, 3.0), (1, 1, 1), pd, SKIN)
+    ds.compute_forces()
+    torch.cuda.synchronize()
+    _, _, _, F, T = ds.state_by_id()
+    d = x[0, :3] - x[1, :3]
+    r = np.linalg.norm(d)
+    nn_ = d / r
+    dl = 2 * R - r
+    f = np.sqrt(dl / (2 * R))
+    vpq = v[0] - v[1]
+    vt = vpq - vpq.dot(nn_) * nn_
+    u = vt * pd["dt"]
+    m_eff = 0.5 * pd["m"]
+    Fn = f * (pd["kn"] * dl * nn_ - pd["gn"] * m_eff * vpq.dot(nn_) * nn_)
+    Ft = f * (-pd["kt"] * u - pd["gt"] * m_eff * vt)
+    scale = np.linalg.norm(Fn + Ft)
+    assert np.max(np.abs(F[0, :3] - (Fn + Ft))) <= TOL_F * scale
+    assert np.max(np.abs(F[1, :3] + (Fn + Ft))) <= TOL_F * scale
+    Tref = -0.5 * np.cross(d, Ft)
+    tscale = max(np.linalg.norm(Tref), 1e-30)
+    assert np.max(np.abs(T[0, :3] - Tref)) <= 1e-4 * tscale
+    assert np.max(np.abs(T[1, :3] - Tref)) <= 1e-4 * tscale
+    hd = ds.history_by_id()
+    np.testing.assert_allclose(hd[(0, 1)], u, rtol=1e-5, atol=1e-5 * np.linalg.norm(u))
+    np.testing.assert_allclose(hd[(1, 0)], -u, rtol=1e-5, atol=1e-5 * np.linalg.norm(u))
