@@ -273,6 +273,18 @@ fpm_status fpm_lj_forces(const fpm_box *box, const fpm_grid *grid, int32_t n, fp
                          void *force, double *d_energy, void *workspace, size_t workspace_bytes,
                          fpm_dev_status *d_status, fpm_stream stream);
 
+/* fpm_lj_forces and the closing half-kick of velocity Verlet (Listing 4.1's
+ * time loop) in one launch: after F_i is written, vel[i] += dt/2 F_i, with
+ * the arithmetic of fpm_vv_step(half = 1), so the result is bit-identical to
+ * fpm_lj_forces followed by fpm_vv_step(half = 1) on the same stream.
+ * vel : [n] float4|double4 (same type as pos), updated; w kept.  It must not
+ *       alias pos or force.  Other arguments and results as fpm_lj_forces. */
+fpm_status fpm_lj_forces_kick(const fpm_box *box, const fpm_grid *grid, int32_t n, fpm_prec prec, const void *pos,
+                              const void *list, const uint32_t *nn, int32_t cap,
+                              double eps, double sigma, double rc,
+                              void *force, double *d_energy, void *workspace, size_t workspace_bytes,
+                              fpm_dev_status *d_status, void *vel, double dt, fpm_stream stream);
+
 /* fpm_lj_forces without a workspace argument, for callers that cannot
  * allocate device memory at all: a host program whose device memory is owned
  * by another runtime or a fixed pool it must not grow, or a real-time loop in

@@ -137,8 +137,7 @@ class LJAdjointRunner:
             self.rebuilt[j:j + 1].copy_(s.status[_REBUILD_WORD:_REBUILD_WORD + 1])
             s.rebuild(gated=True)
             self.perms[j].copy_(s.perm)
-            s.compute_forces()
-            fpm.fpm_vv_step(s.box, s.n, s.prec, 1, s.dt, None, s.vel, s.force)
+            s.forces_and_kick()
             self.xs[j + 1].copy_(s.pos)
             self.nbrs[j + 1].copy_(s.nbr)
             self.nns[j + 1].copy_(s.nn)

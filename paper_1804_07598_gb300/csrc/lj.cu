@@ -21,7 +21,7 @@ template <typename T>
 __global__ void __launch_bounds__(kTileThreads)
     k_lj_tiles(TileCfg cfg, BoxT<T> box, const V4<T> *__restrict__ pos, ListView lv, const uint32_t *__restrict__ nn,
                int64_t ld, int stage_cap, LJParams<T> P, V4<T> *__restrict__ force, Sched sched, double *part,
-               double *out, fpm_dev_status *status)
+               double *out, fpm_dev_status *status, V4<T> *__restrict__ vel, T hdt)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     V4<T> *sp = (V4<T> *)smem_raw;
@@ -62,6 +62,13 @@ __global__ void __launch_bounds__(kTileThreads)
             f.z = P.eps24 * fz;
             f.w = (T)0.5 * P.eps4 * u;
             force[i] = f;
+            if (vel) {  // the closing half-kick of velocity Verlet, v += dt/2 F
+                V4<T> v = vel[i];
+                v.x += hdt * f.x;
+                v.y += hdt * f.y;
+                v.z += hdt * f.z;
+                vel[i] = v;
+            }
             usum += P.eps4 * u;
             wsum += P.eps24 * w;
             npsum += np;
@@ -80,7 +87,8 @@ __global__ void __launch_bounds__(kTileThreads)
 template <typename T>
 static fpm_status lj_launch(const fpm_box &b, const fpm_grid &g, int n, const void *pos, const void *list,
                             const uint32_t *nn, int cap, double eps, double sigma, double rc, void *force,
-                            double *d_energy, const RedWs &r, fpm_dev_status *status, cudaStream_t stream)
+                            double *d_energy, const RedWs &r, fpm_dev_status *status, cudaStream_t stream,
+                            void *vel = nullptr, double dt = 0.0)
 {
     const TileCfg cfg = make_tile_cfg(b, g);
     const ListLayout L = list_layout(n, cfg, cap);
@@ -96,7 +104,7 @@ static fpm_status lj_launch(const fpm_box &b, const fpm_grid &g, int n, const vo
     const int blocks = persistent_blocks((const void *)k_lj_tiles<T>, kTileThreads, smem, g, cfg.ntiles);
     k_lj_tiles<T><<<blocks, kTileThreads, smem, stream>>>(cfg, box, (const V4<T> *)pos, list_view(list, L), nn, L.ld,
                                                           sc, P, (V4<T> *)force, Sched{r.work, r.done}, r.part,
-                                                          d_energy, status);
+                                                          d_energy, status, (V4<T> *)vel, (T)(0.5 * dt));
     return fpm_check_launch("fpm_lj_forces");
 }
 
@@ -140,6 +148,28 @@ extern "C" fpm_status fpm_lj_forces(const fpm_box *box, const fpm_grid *grid, in
     if (prec == FPM_F32)
         return lj_launch<float>(*box, *grid, n, pos, list, nn, cap, eps, sigma, rc, force, d_energy, r, d_status, st);
     return lj_launch<double>(*box, *grid, n, pos, list, nn, cap, eps, sigma, rc, force, d_energy, r, d_status, st);
+}
+
+extern "C" fpm_status fpm_lj_forces_kick(const fpm_box *box, const fpm_grid *grid, int32_t n, fpm_prec prec,
+                                         const void *pos, const void *list, const uint32_t *nn, int32_t cap,
+                                         double eps, double sigma, double rc, void *force, double *d_energy,
+                                         void *workspace, size_t workspace_bytes, fpm_dev_status *d_status,
+                                         void *vel, double dt, fpm_stream stream)
+{
+    fpm_status s = lj_args(box, grid, n, prec, pos, list, nn, cap, sigma, rc, force, "fpm_lj_forces_kick");
+    if (s != FPM_OK) return s;
+    if (n > 0 && !vel) return fpm_fail(FPM_ERR_INVALID, "fpm_lj_forces_kick: null vel");
+    if (vel == pos || vel == force) return fpm_fail(FPM_ERR_INVALID, "fpm_lj_forces_kick: vel aliases pos or force");
+    if (n == 0) return zero_energy(d_energy, (cudaStream_t)stream, "fpm_lj_forces_kick");
+    RedWs r{};
+    s = red_ws(n, grid, workspace, workspace_bytes, "fpm_lj_forces_kick", r);
+    if (s != FPM_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == FPM_F32)
+        return lj_launch<float>(*box, *grid, n, pos, list, nn, cap, eps, sigma, rc, force, d_energy, r, d_status, st,
+                                vel, dt);
+    return lj_launch<double>(*box, *grid, n, pos, list, nn, cap, eps, sigma, rc, force, d_energy, r, d_status, st,
+                             vel, dt);
 }
 
 // ---------------------------------------------------------------------------

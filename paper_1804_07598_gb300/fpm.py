@@ -110,6 +110,9 @@ _SIG = {
     "fpm_lj_forces": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _c.c_int, _VP, _VP, _VP,
                                  _c.c_int32, _c.c_double, _c.c_double, _c.c_double, _VP, _VP, _VP, _c.c_size_t, _VP,
                                  _VP]),
+    "fpm_lj_forces_kick": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _c.c_int, _VP, _VP,
+                                      _VP, _c.c_int32, _c.c_double, _c.c_double, _c.c_double, _VP, _VP, _VP,
+                                      _c.c_size_t, _VP, _VP, _c.c_double, _VP]),
     "fpm_lj_forces_noalloc": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _c.c_int, _VP, _VP,
                                          _VP, _c.c_int32, _c.c_double, _c.c_double, _c.c_double, _VP, _VP, _VP, _VP]),
     "fpm_vv_step": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.c_int, _c.c_int32, _c.c_double, _VP, _VP, _VP,
@@ -334,6 +337,16 @@ def fpm_lj_forces(box, grid, n, prec, pos, list_obj, nn, cap, eps, sigma, rc, fo
     _check(lib().fpm_lj_forces(_c.byref(box), _c.byref(grid), int(n), int(prec), _ptr(pos), _ptr(list_obj), _ptr(nn),
                                int(cap), float(eps), float(sigma), float(rc), _ptr(force), _ptr(d_energy),
                                _ptr(workspace), _nbytes(workspace), _ptr(d_status), _stream(stream)))
+    _count(1 if n > 0 else 0)
+
+
+def fpm_lj_forces_kick(box, grid, n, prec, pos, list_obj, nn, cap, eps, sigma, rc, force, d_energy, workspace,
+                       d_status, vel, dt, stream=None):
+    """fpm_lj_forces, then vel += dt/2 F in the same launch."""
+    _check(lib().fpm_lj_forces_kick(_c.byref(box), _c.byref(grid), int(n), int(prec), _ptr(pos), _ptr(list_obj),
+                                    _ptr(nn), int(cap), float(eps), float(sigma), float(rc), _ptr(force),
+                                    _ptr(d_energy), _ptr(workspace), _nbytes(workspace), _ptr(d_status), _ptr(vel),
+                                    float(dt), _stream(stream)))
     _count(1 if n > 0 else 0)
 
 

@@ -7,8 +7,7 @@ One step (all on the current stream, no host synchronisation):
                                 rebuild flag := max |x - x_ref| > skin/2
     fpm_celllist_build [gated]  wrap, re-bin and reorder in place
     fpm_verlet_build   [gated]  new list, x_ref := x, flag cleared
-    fpm_lj_forces               F, U, W, pairs
-    fpm_vv_step(half=1)         v += dt/2 F
+    fpm_lj_forces_kick          F, U, W, pairs; then v += dt/2 F in the same launch
 Under CUDA-graph capture the two gated calls sit in the body of a
 conditional node on the rebuild flag (fpm_graph_if_begin), so a replayed
 step without a rebuild launches none of their kernels.
@@ -123,12 +122,18 @@ class LJSystem:
         fpm.fpm_lj_forces(self.box, self.grid, self.n, self.prec, self.pos, self.nbr, self.nn, self.cap, self.eps,
                           self.sigma, self.rc, self.force, self.energy, self.ws_red, self.status)
 
+    def forces_and_kick(self):
+        """compute_forces, then the closing half-kick v += dt/2 F, in one
+        launch (bit-identical to the two calls)."""
+        fpm.fpm_lj_forces_kick(self.box, self.grid, self.n, self.prec, self.pos, self.nbr, self.nn, self.cap,
+                               self.eps, self.sigma, self.rc, self.force, self.energy, self.ws_red, self.status,
+                               self.vel, self.dt)
+
     def _step(self):
         fpm.fpm_vv_drift_check(self.box, self.n, self.prec, self.dt, self.pos, self.vel, self.force, self.pos_ref,
                                self.skin, self.status)
         self._gated_rebuild()
-        self.compute_forces()
-        fpm.fpm_vv_step(self.box, self.n, self.prec, 1, self.dt, None, self.vel, self.force)
+        self.forces_and_kick()
 
     # -- public -----------------------------------------------------------
     def step(self, nsteps: int = 1):

@@ -193,3 +193,25 @@ def test_pack_unpack_xyz(cuda, prec):
     fpm.fpm_unpack_xyz(n, fp, xyz, y4)
     torch.cuda.synchronize()
     assert torch.equal(xyz, x4[:, :3]) and torch.equal(y4, x4)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_forces_kick_equals_forces_then_kick(cuda, prec):
+    """fpm_lj_forces_kick writes the same forces and energies as
+    fpm_lj_forces and the same velocities as fpm_vv_step(half = 1) after it,
+    bit for bit."""
+    wl, s = make("lj_small", prec)
+    v0 = s.vel.clone()
+    s.compute_forces()
+    fpm.fpm_vv_step(s.box, s.n, s.prec, 1, s.dt, None, s.vel, s.force)
+    torch.cuda.synchronize()
+    f_ref, e_ref, v_ref = s.force.clone(), s.energy.clone(), s.vel.clone()
+    s.vel.copy_(v0)
+    s.force.zero_()
+    s.energy.zero_()
+    s.forces_and_kick()
+    torch.cuda.synchronize()
+    assert torch.equal(s.force, f_ref)
+    assert torch.equal(s.energy, e_ref)
+    assert torch.equal(s.vel, v_ref)
+    assert not torch.equal(v_ref, v0)
