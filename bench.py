@@ -43,7 +43,7 @@ FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes per launch of the dominant kernel from one ncu capture
 # (profiles/lj_tiles_lj_1m.md), valid while its sources hash to `sha`.
 NCU_TRAFFIC = {"k_lj_tiles<float>": {"files": ["lj.cu", "lj_pair.cuh", "tiles.cuh", "fpm_common.cuh", "reduce.cuh"],
-                                    "sha": "69079cd037ce6a71", "bytes_per_launch": 184328192}}
+                                    "sha": "15d8bde8a2a056d6", "bytes_per_launch": 184146176}}
 
 
 def parse():
