@@ -113,6 +113,41 @@ def test_dem_forces_match_oracle(cuda):
     assert s.contacts() == c or abs(s.contacts() - c) <= 4
 
 
+
+def test_dem_forces_full_avalanche(cuda):
+    """The avalanche the benchmark times, at full size (166 x 62 x 64 moving
+    grains + 28,304 fixed floor and wall grains, the default cells of 3
+    r_list, the benchmark's launch shape): one force evaluation with fresh
+    contacts, every grain against the oracle, and the same contact count.
+    The lattice's closest non-contacts (floor and wall grains) lie ~4e-6
+    beyond touching, far above the FP32 resolution of r^2 there, so both
+    sides find the same contacts.  A grain's net force is a sum of nearly
+    cancelling contact forces (opposite lattice neighbours), so its FP32
+    error follows the contact forces, not the net force: each carries the
+    rounding of delta = 2R - r (a few ulps of 2R, 5e-5 of the lattice's
+    overlap 6e-4, x 1.5 through delta^1.5).  The bound is TOL_F of 8 times
+    the largest contact force (elastic at that overlap plus damping at twice
+    the largest speed), and likewise for the torques."""
+    pos, vel, om, L, per, g = inputs.dem_avalanche(166, 62, 64, gap=-0.005)
+    pos, vel, om = f32(pos), f32(vel), f32(om)
+    pd = params(g=g)
+    s = DEMSystem(pos, vel, om, L, per, pd, SKIN)
+    s.compute_forces()
+    torch.cuda.synchronize()
+    s.check_status()
+    _, _, _, F, T = s.state_by_id()
+    Fo, To, _, c = oracle.dem_forces(pos, vel, om, L, per, oracle_p(pd))
+    assert len(pos) == 686992 and c > 3_900_000
+    assert s.contacts() == c
+    dmax = -2 * R * (-0.005)  # 2R - s: the lattice's overlap
+    f = np.sqrt(dmax / (2 * R))
+    vmax = 2 * np.linalg.norm(vel[:, :3], axis=1).max()  # largest relative speed
+    m_eff = 0.5 * pd["m"]
+    fc = f * (pd["kn"] * dmax + pd["gn"] * m_eff * vmax)
+    tc = R * f * (pd["kt"] * vmax * pd["dt"] + pd["gt"] * m_eff * vmax)
+    assert np.abs(F[:, :3] - Fo[:, :3]).max() <= TOL_F * 8 * fc
+    assert np.abs(T[:, :3] - To[:, :3]).max() <= TOL_F * 8 * tc
+
 def test_dem_forces_with_stored_history(cuda):
     """A state with aged contacts (sliding ones at the Coulomb limit): the GPU
     loads the oracle's u_t, then both evaluate the forces once."""
