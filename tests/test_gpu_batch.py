@@ -191,14 +191,21 @@ def test_batch_steps_keep_lists_valid(cuda):
         assert np.max(np.abs(vel[p0:p1, :3].astype(np.float64).sum(0))) < 1e-3 * (p1 - p0) ** 0.5
 
 
-def test_batch_full_ensemble_sampled(cuda):
-    """The 512-replica ensemble (about 1.9M particles) in the autotuned
-    launch configuration and under a CUDA graph: sampled replicas (smallest,
-    largest and three random) against the oracle after 20 steps."""
+@pytest.mark.parametrize("config", ["tuned", "bench"])
+def test_batch_full_ensemble_sampled(cuda, config):
+    """The 512-replica ensemble (about 1.9M particles) under a CUDA graph,
+    in the autotuned launch configuration ("tuned") and in the one the
+    benchmark's tuner picks on GB300 ("bench": 230 particles per tile, one
+    block per tile): sampled replicas (smallest, largest and three random)
+    against the oracle after 20 steps."""
     reps, N, rho, T = inputs.ensemble()
     b = LJBatch(reps)
-    res = autotune.tune_batch(b, steps=6, warmup=2, tile_targets=(128, 170), sweep_blocks=(0, -1), use_cache=False)
-    assert res["config"]["tile_target"] in (128, 170)
+    if config == "tuned":
+        res = autotune.tune_batch(b, steps=6, warmup=2, tile_targets=(128, 170), sweep_blocks=(0, -1),
+                                  use_cache=False)
+        assert res["config"]["tile_target"] in (128, 170)
+    else:
+        b.plan(230, -1)
     b.step(2)
     b.capture(steps_per_graph=1)
     b.run(20)
