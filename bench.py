@@ -37,11 +37,9 @@ WORKLOAD = "lj_1m"
 FLOP_PER_SLOT = 25
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM traffic per launch of the force kernel from one ncu capture, valid only
-# while the kernel source hashes to the recorded value (else reported null).
-# Filled from the ncu summary under profiles/ (see the design doc).
 # DRAM bytes per launch of the dominant kernel from one ncu capture
-# (profiles/lj_tiles_lj_1m.md), valid while its sources hash to `sha`.
+# (profiles/lj_tiles_lj_1m.md), valid only while its source files hash to
+# `sha` (otherwise the bench line reports the traffic as null).
 NCU_TRAFFIC = {"k_lj_tiles<float>": {"files": ["lj.cu", "lj_pair.cuh", "tiles.cuh", "fpm_common.cuh", "reduce.cuh"],
                                     "sha": "15d8bde8a2a056d6", "bytes_per_launch": 184146176}}
 
