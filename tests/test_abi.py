@@ -84,3 +84,44 @@ def test_tile_width_rule(fpm_lib):
             per_tile = n / (g.nc[1] * g.nc[2] * g.tiles_x)
             assert per_tile < 2 * 200 + 2 * n / g.ncell
     assert fpm.fpm_nbr_ld(1000188) % 32 == 0 and fpm.fpm_nbr_ld(1000188) >= 1000188
+
+
+def test_later_entry_points_reject_bad_arguments(fpm_lib):
+    """Argument errors of the fused force-and-kick, DEM, SPH and particle-mesh
+    calls return FPM_ERR_INVALID before any device work.  The pointers are
+    aligned fakes that a valid call would dereference; none is touched."""
+    box = fpm.make_box((10.0,) * 3)
+    g = fpm.fpm_grid_make(box, 2.8, 100)
+    P, Q = 0x100000, 0x200000
+    bad = fpm.FPM_ERR_INVALID
+    # forces + kick: no vel, vel aliasing pos
+    assert fpm_lib.fpm_lj_forces_kick(ctypes.byref(box), ctypes.byref(g), 10, 0, P, P, P, 8, 1.0, 1.0, 2.5, Q, None,
+                                      None, 0, None, None, 0.005, None) == bad
+    assert "vel" in fpm.fpm_last_error()
+    assert fpm_lib.fpm_lj_forces_kick(ctypes.byref(box), ctypes.byref(g), 10, 0, P, P, P, 8, 1.0, 1.0, 2.5, Q, None,
+                                      None, 0, None, P, 0.005, None) == bad
+    # DEM: a non-positive radius; a history array off its 16-byte alignment
+    dp = fpm.dem_params(R=-0.06)
+    assert fpm_lib.fpm_dem_forces(ctypes.byref(box), ctypes.byref(g), 10, P, P, P, P, P, 8, ctypes.byref(dp), P, P,
+                                  P, None, None, 0, None, None) == bad
+    assert "DEM parameters" in fpm.fpm_last_error()
+    dp = fpm.dem_params()
+    assert fpm_lib.fpm_dem_forces(ctypes.byref(box), ctypes.byref(g), 10, P, P, P, P, P, 8, ctypes.byref(dp), P + 4,
+                                  P, P, None, None, 0, None, None) == bad
+    # SPH: a non-integer EOS exponent; an unknown kernel
+    sp = fpm.fpm_sph_params()
+    sp.h, sp.mass, sp.rho0, sp.c0, sp.gamma, sp.alpha, sp.eta2 = 0.01, 1e-3, 1000.0, 30.0, 7.5, 0.1, 1e-6
+    assert fpm_lib.fpm_sph_forces(ctypes.byref(box), ctypes.byref(g), 10, P, P, P, P, 8, ctypes.byref(sp), P, None,
+                                  None, 0, None, None) == bad
+    assert "gamma" in fpm.fpm_last_error()
+    sp.gamma, sp.kernel = 7.0, 2
+    assert fpm_lib.fpm_sph_forces(ctypes.byref(box), ctypes.byref(g), 10, P, P, P, P, 8, ctypes.byref(sp), P, None,
+                                  None, 0, None, None) == bad
+    # particle-mesh: a mesh under 3 nodes, an open dimension, no cell_start
+    with pytest.raises(fpm.FpmError):
+        fpm.fpm_mesh_grid(fpm.make_box((1.0,) * 3), (2, 8, 8))
+    with pytest.raises(fpm.FpmError):
+        fpm.fpm_mesh_grid(fpm.make_box((1.0,) * 3, (1, 0, 1)), (8, 8, 8))
+    mg = fpm.fpm_mesh_grid(fpm.make_box((1.0,) * 3), (8, 8, 8))
+    assert fpm_lib.fpm_p2m(ctypes.byref(fpm.make_box((1.0,) * 3)), ctypes.byref(mg), 10, P, P, None, P, None,
+                           None) == bad
