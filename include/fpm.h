@@ -297,11 +297,16 @@ fpm_status fpm_lj_forces_kick(const fpm_box *box, const fpm_grid *grid, int32_t 
  * return FPM_ERR_INVALID.  The call allocates and frees nothing.
  * - The first call on each device looks the scratch address up (with that
  *   device current); make that first call before any stream capture.
- * - Every call clears the scratch's completion counter on `stream` before
- *   using it, and all calls on a device share the one array: calls that may
- *   run at the same time on the GPU (different streams, or concurrently
- *   replayed graphs) race and give wrong energies.  Serialise them.
- * - With d_energy == NULL the scratch is not touched. */
+ * - Every call uses the scratch, with or without d_energy: it clears the
+ *   tile-scheduling counters held there (on `stream`), its blocks take their
+ *   tiles from those counters, and with d_energy it keeps the per-tile
+ *   energy partial sums there too.  All calls on a device share the one
+ *   array, which keeps whatever the last call left in it.
+ * - Calls that may run at the same time on the GPU (different streams, or
+ *   graphs replayed concurrently) race on that array: one call's blocks can
+ *   take another call's tiles, or its clear can reset counters still in
+ *   use, so forces can come out wrong or unwritten, not only energies.
+ *   Serialise such calls. */
 fpm_status fpm_lj_forces_noalloc(const fpm_box *box, const fpm_grid *grid, int32_t n, fpm_prec prec,
                                  const void *pos, const void *list, const uint32_t *nn, int32_t cap,
                                  double eps, double sigma, double rc,
