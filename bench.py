@@ -31,15 +31,22 @@ sys.path.insert(0, ROOT)
 METRIC = "LJ steps/s & pair-interactions/s at 1M atoms (FP32 vs FP64) ; adjoint/forward cost"
 UNIT = "steps/s"
 WORKLOAD = "lj_1m"
-# FP32 arithmetic of the LJ pair term per Verlet-list entry, an FMA counted as
-# two: separation 3, r^2 5, 1/r^2 1, s2 1, s6 2, s12 1, a = 2 s12 - s6 2,
-# a/r^2 1, force accumulation 6, virial 1, energy 2.
+# The method's FP32 work per interacting unordered pair (r < rc, each pair
+# once), an FMA counted as two: separation 3, r^2 5, 1/r^2 1, r^-6 2, the
+# force factor 4, the two 3-component accumulations (one per particle of the
+# pair) 12, energy and virial 2, the cutoff compare 1.  This is the roofline's
+# algorithmic work: what a sweep must do however it is organised.
+FLOP_PER_PAIR = 30
+# What the full-list sweep executes per Verlet-list entry (every entry of the
+# rc + skin list, each pair from both sides, masked at rc): separation 3, r^2 5,
+# 1/r^2 1, s2 1, s6 2, s12 1, a = 2 s12 - s6 2, a/r^2 1, force accumulation 6,
+# virial 1, energy 2.  Reported beside the roofline as the executed work.
 FLOP_PER_SLOT = 25
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM bytes per launch of the dominant kernel from one ncu capture
-# (profiles/lj_tiles_lj_1m.md), valid only while its source files hash to
-# `sha` (otherwise the bench line reports the traffic as null).
+# DRAM bytes per launch of the dominant kernel from one ncu capture of the
+# profiling target `--profile forces`, valid only while its source files hash
+# to `sha` (otherwise the bench line reports the traffic as null).
 NCU_TRAFFIC = {"k_lj_tiles<float>": {"files": ["lj.cu", "lj_pair.cuh", "tiles.cuh", "fpm_common.cuh", "reduce.cuh"],
                                     "sha": "15d8bde8a2a056d6", "bytes_per_launch": 184146176}}
 
@@ -59,6 +66,7 @@ def parse():
     ap.add_argument("--kernel-reps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=8)
+    ap.add_argument("--cpu-omp-steps", type=int, default=30)
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--sph-steps", type=int, default=500)
     ap.add_argument("--batch-steps", type=int, default=300)
@@ -205,54 +213,86 @@ def traffic_for(kernel: str):
 
 # -------------------------------------------------------------- the arms ---
 
-def cpu_baseline(nsteps: int):
-    """The oracle as it stands (single-threaded plain C, FP64) on the host:
-    `nsteps` NVE steps of the full 1,000,188-particle workload."""
-    import numpy as np  # noqa: F401
+def cpu_baseline(nsteps: int, omp_steps: int):
+    """The oracle as it stands, FP64, on the full 1,000,188-particle workload:
+    `nsteps` NVE steps of the plain C oracle on one thread (half list, each
+    pair once), and `omp_steps` steps of its OpenMP form on all host cores
+    (each particle's sum from its own side).  `value` is the all-core rate."""
     import oracle
     from paper_1804_07598_gb300 import inputs
     wl = inputs.WORKLOADS[WORKLOAD]
     pos, vel, L = inputs.lj_state(wl)
+    oracle.build()
     t0 = time.perf_counter()
     oracle.lj_nve(pos, vel, L, (1, 1, 1), wl.eps, wl.sigma, wl.rc, wl.dt, nsteps, record=False)
-    dt = time.perf_counter() - t0
-    # lj_nve evaluates nsteps + 1 force sweeps; count nsteps steps over the whole time
-    return {"value": nsteps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{nsteps} FP64 NVE steps of the full {wl.n}-particle workload "
-                      f"(+1 initial force sweep), plain C oracle, single thread, {dt:.1f} s"}
+    dt1 = time.perf_counter() - t0
+    threads = oracle.threads()
+    t0 = time.perf_counter()
+    oracle.lj_nve_omp(pos, vel, L, (1, 1, 1), wl.eps, wl.sigma, wl.rc, wl.dt, omp_steps)
+    dtn = time.perf_counter() - t0
+    # each run evaluates one force sweep more than it has steps; both count
+    # their steps over the whole time
+    return {"value": omp_steps / dtn, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "host": host_cpu(),
+            "sample": f"{omp_steps} FP64 NVE steps of the full {wl.n}-particle workload (+1 initial force "
+                      f"sweep), plain C oracle, OpenMP on {threads} threads, {dtn:.1f} s",
+            "single_thread": {"value": nsteps / dt1, "unit": UNIT, "cores": 1,
+                              "sample": f"{nsteps} FP64 NVE steps of the same workload (+1 initial sweep), "
+                                        f"one thread, {dt1:.1f} s"}}
+
+
+def host_cpu() -> str:
+    """The host's CPU model and logical core count, as the OS reports them."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k = line.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return f"{model or 'unknown CPU'}, nproc {os.cpu_count()}"
 
 
 def run_reference(args, ws, rank):
-    """The reference arm: the oracle as it stands (plain C, FP64, one thread)
-    on a bounded sample of the workload -- the same LJ liquid (rho 0.8442,
-    T* 0.72, rc 2.5) in a 16,384-particle periodic box, W warm-up and K timed
-    NVE steps -- reported in 1M-atom steps/s (the oracle's cost is linear in
-    the particle count: cell lists, fixed density)."""
+    """The reference arm: the oracle as it stands (plain C, FP64, its OpenMP
+    form on all host cores) on the benchmark's own workload, the 1,000,188-
+    particle LJ liquid: W warm-up and K timed NVE steps."""
     if rank != 0:
         return
     from paper_1804_07598_gb300 import inputs
     import oracle
     wl = inputs.WORKLOADS[WORKLOAD]
-    sample = inputs.LJWorkload("lj_sample", (16, 16, 16))
-    pos, vel, L = inputs.lj_state(sample)
+    pos, vel, L = inputs.lj_state(wl)
     oracle.build()
+    threads = oracle.threads()
     p, v = pos, vel
     if args.warmup > 0:
-        p, v, _ = oracle.lj_nve(p, v, L, (1, 1, 1), wl.eps, wl.sigma, wl.rc, wl.dt, args.warmup, record=False)
+        p, v = oracle.lj_nve_omp(p, v, L, (1, 1, 1), wl.eps, wl.sigma, wl.rc, wl.dt, args.warmup)
     t0 = time.perf_counter()
-    p, v, _ = oracle.lj_nve(p, v, L, (1, 1, 1), wl.eps, wl.sigma, wl.rc, wl.dt, args.steps, record=False)
+    p, v = oracle.lj_nve_omp(p, v, L, (1, 1, 1), wl.eps, wl.sigma, wl.rc, wl.dt, args.steps)
     dt = time.perf_counter() - t0
-    scale = sample.n / wl.n
-    val = args.steps / dt * scale
-    desc = (f"{args.steps} FP64 oracle NVE steps (one force sweep each, plus one initial sweep) of the same LJ "
-            f"liquid in a {sample.n}-particle box, single thread, {dt:.1f} s; steps/s scaled by "
-            f"{sample.n}/{wl.n} to the 1M-atom workload")
+    val = args.steps / dt
+    desc = (f"{args.steps} FP64 oracle NVE steps (one force sweep each, plus one initial sweep) of the full "
+            f"{wl.n}-particle workload, OpenMP on {threads} threads, {dt:.1f} s")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / val,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{WORKLOAD}: {wl.n} LJ particles, FCC 63^3x4, rho 0.8442, rc 2.5, skin 0.3, "
-                                   f"dt 0.005 (timed on a {sample.n}-particle sample)", "l2": "n/a (host)"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "config": {"workload": f"{WORKLOAD}: {wl.n} LJ particles (FCC 63^3 x 4), rho 0.8442, T* 0.72, rc 2.5, "
+                                   f"skin 0.3, dt 0.005", "l2": "n/a (host)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc,
+                             "host": host_cpu()},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -326,11 +366,15 @@ def run_ours(args, ws, rank, local):
     alg_bytes = 2 * nn_sum + 4 * s.n + 16 * s.n + 16 * s.n
     peak, peak_kind = hbm_peak()
     achieved = alg_bytes / (force_us * 1e-6) / 1e9
-    # FP32 arithmetic of one sweep: FLOP_PER_SLOT per list entry (every entry
-    # is evaluated and masked at rc); peak = SMs x 128 FP32 lanes x 2 x clock
+    # the method's FP32 work of one sweep: FLOP_PER_PAIR per interacting pair
+    # (r < rc, counted once); the executed work: FLOP_PER_SLOT per list entry
+    # (every entry is evaluated and masked at rc); peak = SMs x 128 FP32 lanes
+    # x 2 x clock
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-    alg_flop = FLOP_PER_SLOT * nn_sum
+    alg_flop = FLOP_PER_PAIR * pairs
     tflops = alg_flop / (force_us * 1e-6) / 1e12
+    exec_flop = FLOP_PER_SLOT * nn_sum
+    exec_tflops = exec_flop / (force_us * 1e-6) / 1e12
 
     # FP64 path, same workload
     s64 = LJSystem(pos, vel, L, eps=wl.eps, sigma=wl.sigma, rc=wl.rc, skin=wl.skin, dt=wl.dt, precision="f64")
@@ -356,7 +400,9 @@ def run_ours(args, ws, rank, local):
     k1.record()
     torch.cuda.synchronize()
     force64_us = 1e3 * k0.elapsed_time(k1) / 5
-    fp64_tflops = FLOP_PER_SLOT * nn64 / (force64_us * 1e-6) / 1e12
+    pairs64 = s64.observables()["pairs"]
+    fp64_tflops = FLOP_PER_PAIR * pairs64 / (force64_us * 1e-6) / 1e12
+    fp64_exec_tflops = FLOP_PER_SLOT * nn64 / (force64_us * 1e-6) / 1e12
     # the Verlet rebuild on its own (cell list + Verlet build, 1M atoms, eager)
     torch.cuda.synchronize()
     k0.record()
@@ -674,7 +720,7 @@ def run_ours(args, ws, rank, local):
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        cpu = cpu_baseline(args.cpu_steps)
+        cpu = cpu_baseline(args.cpu_steps, args.cpu_omp_steps)
 
     if rank != 0:
         return
@@ -693,7 +739,9 @@ def run_ours(args, ws, rank, local):
         "fp64_steps_per_s": fp64_steps_per_s * ws,
         "fp32_over_fp64": steps_per_s / (fp64_steps_per_s * ws),
         "fp64_force_kernel": {"launch_us": force64_us, "achieved_tflops": fp64_tflops, "peak_tflops": 1.25,
-                              "frac": fp64_tflops / 1.25, "peak_kind": "nominal GB300 FP64 (not measured here)"},
+                              "frac": fp64_tflops / 1.25, "peak_kind": "nominal GB300 FP64 (not measured here)",
+                              "work": f"{FLOP_PER_PAIR} FLOP per interacting pair",
+                              "executed_tflops": fp64_exec_tflops},
         "list_slots_per_s": nn_sum * steps_per_s,
         "rebuild": {"us": rebuild_us, "rebuilds_per_step": rebuilds / args.steps,
                     "amortised_us_per_step": rebuild_us * rebuilds / args.steps,
@@ -702,7 +750,11 @@ def run_ours(args, ws, rank, local):
                      "unit": "TFLOP/s", "frac": tflops / fp32_peak, "traffic": traffic_for("k_lj_tiles<float>"),
                      "peak_kind": f"FP32 CUDA cores: {n_sm} SMs x 128 lanes x 2 FLOP x {sm_mhz:.0f} MHz (median "
                                   f"SM clock sampled under load)",
-                     "alg_flop_per_launch": alg_flop, "flop_per_list_slot": FLOP_PER_SLOT, "launch_us": force_us,
+                     "alg_flop_per_launch": alg_flop, "flop_per_pair": FLOP_PER_PAIR, "pairs_per_launch": pairs,
+                     "launch_us": force_us,
+                     "executed": {"flop_per_list_slot": FLOP_PER_SLOT, "list_slots": nn_sum,
+                                  "flop_per_launch": exec_flop, "achieved": exec_tflops,
+                                  "frac": exec_tflops / fp32_peak, "unit": "TFLOP/s"},
                      "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                              "peak_kind": f"{peak_kind} (burst)", "alg_bytes_per_launch": alg_bytes}},
         "e2e": {"value": ws * args.e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,

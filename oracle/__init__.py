@@ -33,8 +33,11 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        # OpenMP only spreads the multi-core timing loop (orc_lj_nve_omp);
+        # without it that loop runs on one thread
+        if subprocess.call(cmd[:1] + ["-fopenmp"] + cmd[1:], stderr=subprocess.DEVNULL) != 0:
+            subprocess.check_call(cmd)
         os.replace(tmp, _SO)
     return _SO
 
@@ -271,6 +274,43 @@ def lj_nve(pos, vel, L, periodic, eps, sigma, rc, dt, nsteps, record=True):
                         ptr):
         raise ValueError("box too small for the cutoff")
     return p, v, e
+
+
+def threads() -> int:
+    """Threads the oracle's OpenMP loops use (1 if built without OpenMP)."""
+    L_ = lib()
+    L_.orc_threads.restype = ctypes.c_int
+    return int(L_.orc_threads())
+
+
+def lj_forces_omp(pos, L, periodic, eps, sigma, rc):
+    """orc_lj_forces on all host cores (each particle's sum from its own
+    side).  Returns (force [n,4], (U, W, pairs))."""
+    L_ = lib()
+    L_.orc_lj_forces_omp.restype = ctypes.c_int
+    L_.orc_lj_forces_omp.argtypes = [ctypes.c_int, _P(np.float64), _P(np.float64), _P(np.int32), ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, _P(np.float64), _P(np.float64)]
+    p = _pos4(pos, np.float64)
+    Lb, pb = _box(L, periodic)
+    f = np.zeros_like(p)
+    out = np.zeros(3)
+    if L_.orc_lj_forces_omp(p.shape[0], p, Lb, pb, float(eps), float(sigma), float(rc), f, out):
+        raise ValueError("box too small for the cutoff")
+    return f, out
+
+
+def lj_nve_omp(pos, vel, L, periodic, eps, sigma, rc, dt, nsteps):
+    """lj_nve on all host cores (for timing the oracle as a multi-core CPU
+    baseline).  Returns (pos, vel)."""
+    L_ = lib()
+    L_.orc_lj_nve_omp.restype = ctypes.c_int
+    L_.orc_lj_nve_omp.argtypes = [ctypes.c_int, _P(np.float64), _P(np.float64), _P(np.float64), _P(np.int32),
+                                  ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+    p, v = _pos4(pos, np.float64), _pos4(vel, np.float64)
+    Lb, pb = _box(L, periodic)
+    if L_.orc_lj_nve_omp(p.shape[0], p, v, Lb, pb, float(eps), float(sigma), float(rc), float(dt), int(nsteps)):
+        raise ValueError("box too small for the cutoff")
+    return p, v
 
 
 # --------------------------------------------------------------------------

@@ -32,6 +32,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_MARGIN_CELL (1.0 + 1.0 / 4096.0)
 #define ORC_MARGIN_HALF (1.0 + 1.0 / 1024.0)
@@ -558,6 +561,101 @@ int orc_lj_nve(int n, double *pos4, double *vel4, const double L[3], const int p
             energies[4 * (size_t)s + 2] = out[1];
             energies[4 * (size_t)s + 3] = out[2];
         }
+    }
+    free(f);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The NVE run on all host cores (OpenMP), used only to time the oracle as a */
+/* multi-core CPU baseline; compiled without OpenMP it runs on one thread.   */
+/* ------------------------------------------------------------------------ */
+
+/* Threads an OpenMP loop of this library uses (1 without OpenMP). */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* The forces of orc_lj_forces (Sec. 4.1, unshifted LJ truncated at rc) with
+ * every particle's sum taken from its own side, F_i = sum_{j != i, r < rc}
+ * f r_ij, so that threads write disjoint rows (each pair is evaluated once
+ * per side: the same sums up to the order of rounding).  out = (U, W, pairs)
+ * from the halved two-sided sums. */
+int orc_lj_forces_omp(int n, const double *pos4, const double L[3], const int periodic[3],
+                      double eps, double sigma, double rc, double *force4, double out[3])
+{
+    orc_cells cl;
+    if (cells_build(&cl, n, NULL, pos4, L, periodic, rc)) return 1;
+    uint32_t maxc = 0;
+    for (int c = 0; c < cl.ncell; ++c) {
+        uint32_t k = cl.cell_start[c + 1] - cl.cell_start[c];
+        if (k > maxc) maxc = k;
+    }
+    const size_t room = 27 * (size_t)maxc + 1;
+    const double s2 = sigma * sigma, s6 = s2 * s2 * s2, s12 = s6 * s6;
+    double U = 0.0, W = 0.0, pairs = 0.0;
+#pragma omp parallel reduction(+ : U, W, pairs)
+    {
+        uint32_t *cand = (uint32_t *)malloc(sizeof(uint32_t) * room);
+#pragma omp for schedule(static)
+        for (int i = 0; i < n; ++i) {
+            const double *xi = pos4 + 4 * (size_t)i;
+            double F[4] = {0.0, 0.0, 0.0, 0.0};
+            int m = stencil_candidates(&cl, periodic, cl.cell[i], cand);
+            for (int t = 0; t < m; ++t) {
+                uint32_t j = cand[t];
+                double dv[3];
+                if (j == (uint32_t)i || !pair_inside(xi, pos4 + 4 * (size_t)j, L, periodic, rc, 0, dv)) continue;
+                double r2 = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2];
+                double r6 = r2 * r2 * r2;
+                double f = 24.0 * eps * (2.0 * s12 / (r6 * r6 * r2) - s6 / (r6 * r2));
+                double v = 4.0 * eps * (s12 / (r6 * r6) - s6 / r6);
+                for (int d = 0; d < 3; ++d) F[d] += f * dv[d];
+                F[3] += 0.5 * v;
+                U += 0.5 * v;
+                W += 0.5 * f * r2;
+                pairs += 0.5;
+            }
+            memcpy(force4 + 4 * (size_t)i, F, sizeof(F));
+        }
+        free(cand);
+    }
+    cells_free(&cl);
+    out[0] = U;
+    out[1] = W;
+    out[2] = pairs;
+    return 0;
+}
+
+/* nsteps of orc_lj_nve (velocity Verlet, Listing 4.1's time loop) with the
+ * force sweep and both half steps spread over the host's cores. */
+int orc_lj_nve_omp(int n, double *pos4, double *vel4, const double L[3], const int periodic[3],
+                   double eps, double sigma, double rc, double dt, int nsteps)
+{
+    double *f = (double *)malloc(sizeof(double) * 4 * (size_t)(n > 0 ? n : 1));
+    double out[3];
+    if (orc_lj_forces_omp(n, pos4, L, periodic, eps, sigma, rc, f, out)) { free(f); return 1; }
+    for (int s = 1; s <= nsteps; ++s) {
+#pragma omp parallel for schedule(static)
+        for (int i = 0; i < n; ++i)
+            for (int d = 0; d < 3; ++d) {
+                size_t k = 4 * (size_t)i + d;
+                vel4[k] = vel4[k] + 0.5 * dt * f[k];
+                pos4[k] = pos4[k] + dt * vel4[k];
+                if (periodic[d]) pos4[k] = wrap_f64(pos4[k], L[d]);
+            }
+        orc_lj_forces_omp(n, pos4, L, periodic, eps, sigma, rc, f, out);
+#pragma omp parallel for schedule(static)
+        for (int i = 0; i < n; ++i)
+            for (int d = 0; d < 3; ++d) {
+                size_t k = 4 * (size_t)i + d;
+                vel4[k] = vel4[k] + 0.5 * dt * f[k];
+            }
     }
     free(f);
     return 0;

@@ -334,3 +334,21 @@ def test_fcc_lattice_sums_published(m, R, d):
     assert abs(U / n - u) < 3e-5 * 2.0 * (a12 * d ** -12 + a6 * d ** -6), (U / n, u)
     assert abs(W / n - w) < 3e-5 * 12.0 * (2.0 * a12 * d ** -12 + a6 * d ** -6), (W / n, w)
     assert np.max(np.abs(f[:, :3])) < 1e-10
+
+
+def test_multicore_oracle_matches_serial():
+    """The all-core timing variant (each particle's sum from its own side)
+    gives the serial half-list sums up to rounding order, and the same NVE
+    trajectory over a few steps."""
+    from paper_1804_07598_gb300 import inputs
+    wl = inputs.LJWorkload("omp_check", (5, 5, 5))
+    pos, vel, L = inputs.lj_state(wl, jitter=0.06)
+    f, U, W, npairs = oracle.lj_forces(pos, L, (1, 1, 1), 1.0, 1.0, 2.5)
+    fo, outo = oracle.lj_forces_omp(pos, L, (1, 1, 1), 1.0, 1.0, 2.5)
+    rms = np.sqrt(np.mean(np.sum(f[:, :3] ** 2, axis=1)))
+    assert np.max(np.abs(fo - f)) <= 1e-12 * rms
+    assert np.allclose(outo[:2], [U, W], rtol=1e-12) and outo[2] == npairs
+    p1, v1, _ = oracle.lj_nve(pos, vel, L, (1, 1, 1), 1.0, 1.0, 2.5, 0.005, 5, record=False)
+    p2, v2 = oracle.lj_nve_omp(pos, vel, L, (1, 1, 1), 1.0, 1.0, 2.5, 0.005, 5)
+    assert np.max(np.abs(p2 - p1)) < 1e-10 and np.max(np.abs(v2 - v1)) < 1e-10
+    assert oracle.threads() >= 1
