@@ -557,6 +557,29 @@ fpm_status fpm_vv_adjoint(int32_t n, fpm_prec prec, const uint32_t *perm, const 
 fpm_status fpm_adjoint_seed(int32_t n, fpm_prec prec, const void *force, double *xbar, double *vbar,
                             void *a_out, fpm_stream stream);
 
+/* The loss of the differentiable rollout, L = U(x_T) + sum_i |F_i(x_T)|^2,
+ * on the device: d_loss[0] = d_energy[0] + 2 d_half_sumf2[0], with d_energy
+ * the [3] output of fpm_lj_forces at x_T and d_half_sumf2[0] = 1/2 sum |F|^2
+ * (fpm_kinetic applied to the forces).  All three are device pointers to
+ * FP64; one single-thread launch. */
+fpm_status fpm_adjoint_loss(const double *d_energy, const double *d_half_sumf2, double *d_loss,
+                            fpm_stream stream);
+
+/* The results of the reverse pass, assembled on the device:
+ *   grad_x[3 ids[k] + c] = xbar[k][c], grad_v[3 ids[k] + c] = vbar[k][c]
+ *     (c = 0..2): dL/dx0 and dL/dv0 as [n][3] FP64 rows in the order the
+ *     particles had before the first cell-list build, ids being the particle
+ *     ids held in sorted slot k at step 0 (a permutation of 0..n-1);
+ *   d_grad_theta[0] = seed[0] + seed[2] + steps[0]   (dL/d eps),
+ *   d_grad_theta[1] = seed[1] + seed[3] + steps[1]   (dL/d sigma),
+ *     with d_theta_seed the [4] d_params of the seed's fpm_lj_backward
+ *     (2 F.dF/dtheta, then dU/dtheta) and d_theta_steps the [4] d_params
+ *     accumulated by the reverse steps (a.dF/dtheta; their dU entries unused).
+ * xbar, vbar: [n] double4.  grad_x and grad_v must not alias. */
+fpm_status fpm_adjoint_finish(int32_t n, const uint32_t *ids, const double *xbar, const double *vbar,
+                              const double *d_theta_seed, const double *d_theta_steps, double *grad_x,
+                              double *grad_v, double *d_grad_theta, fpm_stream stream);
+
 /* ------------------------------------------------------------------ */
 /* Batched replicas: R independent periodic LJ systems of uneven size    */
 /* advanced together (an ensemble of the MD system of Sec. 4.1; the      */

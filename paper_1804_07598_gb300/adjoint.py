@@ -28,7 +28,6 @@ this module only orders the calls and keeps the buffers.
 """
 from __future__ import annotations
 
-import numpy as np
 import torch
 
 from . import fpm
@@ -79,6 +78,10 @@ class LJAdjointRunner:
         self.theta_seed = torch.zeros(4, dtype=torch.float64, device=dev)
         self.theta_steps = torch.zeros(4, dtype=torch.float64, device=dev)
         self.sumf2 = torch.zeros(4, dtype=torch.float64, device=dev)
+        self.loss_dev = torch.zeros(1, dtype=torch.float64, device=dev)
+        self.grad_x = torch.zeros((s.n, 3), dtype=torch.float64, device=dev)
+        self.grad_v = torch.zeros_like(self.grad_x)
+        self.grad_theta = torch.zeros(2, dtype=torch.float64, device=dev)
         self._graphs = {}
         self.reorders_undone = 0
 
@@ -121,7 +124,8 @@ class LJAdjointRunner:
         """U(x_T) + sum |F(x_T)|^2 from the current force and energy."""
         s = self.sys
         fpm.fpm_kinetic(s.n, s.prec, s.force, self.sumf2, s.ws_red)  # 1/2 sum |F|^2 in FP64
-        return float(s.energy[0].item() + 2.0 * self.sumf2[0].item())
+        fpm.fpm_adjoint_loss(s.energy, self.sumf2, self.loss_dev)
+        return float(self.loss_dev.item())
 
     # -- backward ------------------------------------------------------------
     def _record(self, L):
@@ -185,16 +189,12 @@ class LJAdjointRunner:
             self._graph(("rev", L, k == 0), lambda L=L, f=(k == 0): self._reverse(L, f)).replay()
         s.check_status()
         self.reorders_undone = int(self.rebuilt_total.item())
-        # back to the caller's particle order (host-side): sorted slot k holds particle ids[k]
-        ids = self.checkpoints[0]["ids"].cpu().numpy().view(np.uint32).astype(np.int64)  # order at step 0
-        xb, vb = self.xbar.cpu().numpy(), self.vbar.cpu().numpy()
-        gx = np.empty((s.n, 3))
-        gv = np.empty((s.n, 3))
-        gx[ids] = xb[:, :3]
-        gv[ids] = vb[:, :3]
-        ts, tt = self.theta_seed.cpu().numpy(), self.theta_steps.cpu().numpy()
-        # the seed sweep holds 2 F.dF/dth and dU/dth; the step sweeps hold a.dF/dth (their dU terms are unused)
-        return torch.from_numpy(gx), torch.from_numpy(gv), float(ts[0] + ts[2] + tt[0]), float(ts[1] + ts[3] + tt[1])
+        # rows back to the caller's order (sorted slot k held particle ids[k] at
+        # step 0) and dL/d(eps, sigma) from the seed's and the steps' partials
+        fpm.fpm_adjoint_finish(s.n, self.checkpoints[0]["ids"], self.xbar, self.vbar, self.theta_seed,
+                               self.theta_steps, self.grad_x, self.grad_v, self.grad_theta)
+        gt = self.grad_theta.cpu().numpy()
+        return self.grad_x.cpu(), self.grad_v.cpu(), float(gt[0]), float(gt[1])
 
 
 class LJRollout(torch.autograd.Function):

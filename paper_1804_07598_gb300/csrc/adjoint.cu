@@ -220,6 +220,36 @@ __global__ void k_adjoint_seed(int n, const V4<T> *__restrict__ force, double4_3
     a[k] = av;
 }
 
+// L = U + 2 (1/2 sum |F|^2), one thread.
+__global__ void k_adjoint_loss(const double *__restrict__ energy, const double *__restrict__ half_sumf2,
+                               double *__restrict__ loss)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) loss[0] = energy[0] + 2.0 * half_sumf2[0];
+}
+
+// Rows of the adjoint state back to the caller's particle order, and the
+// parameter gradient assembled from its partial sums (thread 0 of block 0).
+__global__ void k_adjoint_finish(int n, const uint32_t *__restrict__ ids, const double4_32a *__restrict__ xbar,
+                                 const double4_32a *__restrict__ vbar, const double *__restrict__ th_seed,
+                                 const double *__restrict__ th_steps, double *__restrict__ gx,
+                                 double *__restrict__ gv, double *__restrict__ gtheta)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k == 0) {
+        gtheta[0] = th_seed[0] + th_seed[2] + th_steps[0];
+        gtheta[1] = th_seed[1] + th_seed[3] + th_steps[1];
+    }
+    if (k >= n) return;
+    const size_t o = 3 * (size_t)ids[k];
+    const double4_32a x = xbar[k], v = vbar[k];
+    gx[o] = x.x;
+    gx[o + 1] = x.y;
+    gx[o + 2] = x.z;
+    gv[o] = v.x;
+    gv[o + 1] = v.y;
+    gv[o + 2] = v.z;
+}
+
 template <typename T>
 static fpm_status hvp_launch(const fpm_box &b, const fpm_grid &g, int n, const void *pos, const void *list,
                              const uint32_t *nn, int cap, double eps, double sigma, double rc, const void *a,
@@ -313,4 +343,27 @@ extern "C" fpm_status fpm_adjoint_seed(int32_t n, fpm_prec prec, const void *for
         k_adjoint_seed<double><<<blocks, 256, 0, st>>>(n, (const double4_32a *)force, (double4_32a *)xbar,
                                                        (double4_32a *)vbar, (double4_32a *)a_out);
     return fpm_check_launch("fpm_adjoint_seed");
+}
+
+extern "C" fpm_status fpm_adjoint_loss(const double *d_energy, const double *d_half_sumf2, double *d_loss,
+                                       fpm_stream stream)
+{
+    if (!d_energy || !d_half_sumf2 || !d_loss) return fpm_fail(FPM_ERR_INVALID, "fpm_adjoint_loss: null pointer");
+    k_adjoint_loss<<<1, 32, 0, (cudaStream_t)stream>>>(d_energy, d_half_sumf2, d_loss);
+    return fpm_check_launch("fpm_adjoint_loss");
+}
+
+extern "C" fpm_status fpm_adjoint_finish(int32_t n, const uint32_t *ids, const double *xbar, const double *vbar,
+                                         const double *d_theta_seed, const double *d_theta_steps, double *grad_x,
+                                         double *grad_v, double *d_grad_theta, fpm_stream stream)
+{
+    if (n < 0 || !d_theta_seed || !d_theta_steps || !d_grad_theta ||
+        (n > 0 && (!ids || !xbar || !vbar || !grad_x || !grad_v)))
+        return fpm_fail(FPM_ERR_INVALID, "fpm_adjoint_finish: null pointer or bad size");
+    if (grad_x == grad_v) return fpm_fail(FPM_ERR_INVALID, "fpm_adjoint_finish: grad_x aliases grad_v");
+    const unsigned blocks = (unsigned)((n + 255) / 256 > 0 ? (n + 255) / 256 : 1);
+    k_adjoint_finish<<<blocks, 256, 0, (cudaStream_t)stream>>>(n, ids, (const double4_32a *)xbar,
+                                                             (const double4_32a *)vbar, d_theta_seed, d_theta_steps,
+                                                             grad_x, grad_v, d_grad_theta);
+    return fpm_check_launch("fpm_adjoint_finish");
 }

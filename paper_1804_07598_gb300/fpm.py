@@ -144,6 +144,8 @@ _SIG = {
     "fpm_vv_adjoint": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _VP, _c.c_double, _c.c_double, _VP, _VP, _VP, _VP,
                                   _VP, _VP]),
     "fpm_adjoint_seed": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _VP, _VP, _VP, _VP]),
+    "fpm_adjoint_loss": (_c.c_int, [_VP, _VP, _VP, _VP]),
+    "fpm_adjoint_finish": (_c.c_int, [_c.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "fpm_kinetic": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _VP, _VP, _c.c_size_t, _VP]),
     "fpm_unpack_xyz": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _VP, _VP]),
     "fpm_pack_xyz": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _VP, _VP]),
@@ -398,6 +400,17 @@ def fpm_adjoint_seed(n, prec, force, xbar, vbar, a_out, stream=None):
     _check(lib().fpm_adjoint_seed(int(n), int(prec), _ptr(force), _ptr(xbar), _ptr(vbar), _ptr(a_out),
                                   _stream(stream)))
     _count(1 if n > 0 else 0)
+
+
+def fpm_adjoint_loss(d_energy, d_half_sumf2, d_loss, stream=None):
+    _check(lib().fpm_adjoint_loss(_ptr(d_energy), _ptr(d_half_sumf2), _ptr(d_loss), _stream(stream)))
+    _count(1)
+
+
+def fpm_adjoint_finish(n, ids, xbar, vbar, theta_seed, theta_steps, grad_x, grad_v, grad_theta, stream=None):
+    _check(lib().fpm_adjoint_finish(int(n), _ptr(ids), _ptr(xbar), _ptr(vbar), _ptr(theta_seed), _ptr(theta_steps),
+                                    _ptr(grad_x), _ptr(grad_v), _ptr(grad_theta), _stream(stream)))
+    _count(1)
 
 
 def fpm_sph_forces(box, grid, n, pos, vr, list_obj, nn, cap, params, acc, d_dtcons=None, workspace=None,
