@@ -312,6 +312,19 @@ fpm_status fpm_lj_forces_noalloc(const fpm_box *box, const fpm_grid *grid, int32
                                  double eps, double sigma, double rc,
                                  void *force, double *d_energy, fpm_dev_status *d_status, fpm_stream stream);
 
+/* Test hook (the paper has no counterpart): the budget, in SM clock cycles,
+ * of the first bounded wait per tile of the force sweeps of fpm_lj_forces,
+ * fpm_lj_forces_kick and fpm_lj_forces_noalloc launched after the call, from
+ * any thread (the wait for the tile's neighbourhood to land in shared
+ * memory).  cycles <= 0 restores the default of about 2 s.  A short budget
+ * drives the expiry path that a stalled copy would take: FPM_FLAG_TIMEOUT is
+ * latched in d_status (fpm_status_from_device gives FPM_ERR_TIMEOUT); the
+ * kernel then waits for the copies with the full budget, so that none is
+ * still in flight when it exits, and sweeps the tile if they have landed
+ * (a tile whose copies never land is not swept: its forces are not
+ * written).  The other waits keep their budget. */
+fpm_status fpm_test_wait_budget(int64_t cycles);
+
 /* ------------------------------------------------------------------ */
 /* Velocity Verlet (Listing 4.1 time loop: v += dt/2 F; x += dt v; ...;   */
 /* v += dt/2 F), unit mass                                                */
@@ -379,6 +392,20 @@ fpm_status fpm_sph_forces(const fpm_box *box, const fpm_grid *grid, int32_t n, c
                           const void *list, const uint32_t *nn, int32_t cap, const fpm_sph_params *params,
                           void *acc, float *d_dtcons, void *workspace, size_t workspace_bytes,
                           fpm_dev_status *d_status, fpm_stream stream);
+
+/* Density by summation over the kernel of Sec. 4.2 (the SPH estimate
+ * rho_i = sum_j m W(|x_i - x_j|), the particle itself included, that Eqs. 1-2
+ * differentiate; a variant of evolving rho by Eq. 2):
+ *   rho[i] = m W(0) + sum over list entries with r2 < (2h)^2 of m W(r),
+ * W as in fpm_sph_params (kernel 0 Wendland C2, 1 cubic spline), r2 and the
+ * support test in single precision as in fpm_sph_forces.  Every particle
+ * (fluid and boundary) sums over every neighbour.  Same box, grid, list, nn,
+ * cap, workspace and status conventions as fpm_sph_forces; the list must be
+ * built with r_list >= 2h.
+ * rho : [n] float, the summed density of each particle (sorted order). */
+fpm_status fpm_sph_density(const fpm_box *box, const fpm_grid *grid, int32_t n, const void *pos, const void *list,
+                           const uint32_t *nn, int32_t cap, const fpm_sph_params *params, float *rho,
+                           void *workspace, size_t workspace_bytes, fpm_dev_status *d_status, fpm_stream stream);
 
 /* Symplectic predictor (the "Verlet time-stepping with dynamic step size" of
  * Sec. 4.2, read as the predictor-corrector of the DualSPHysics scheme):

@@ -10,6 +10,7 @@
 // list (each pair from both sides): no atomics, bit-reproducible forces.
 // Energy, virial and the pair count are reduced per tile in FP64 and then
 // over the tiles in a fixed order.
+#include <atomic>
 #include <mutex>
 
 #include "lj_pair.cuh"
@@ -21,7 +22,7 @@ template <typename T>
 __global__ void __launch_bounds__(kTileThreads)
     k_lj_tiles(TileCfg cfg, BoxT<T> box, const V4<T> *__restrict__ pos, ListView lv, const uint32_t *__restrict__ nn,
                int64_t ld, int stage_cap, LJParams<T> P, V4<T> *__restrict__ force, Sched sched, double *part,
-               double *out, fpm_dev_status *status, V4<T> *__restrict__ vel, T hdt)
+               double *out, fpm_dev_status *status, V4<T> *__restrict__ vel, T hdt, long long wait0)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     V4<T> *sp = (V4<T> *)smem_raw;
@@ -40,7 +41,9 @@ __global__ void __launch_bounds__(kTileThreads)
         if (d.h0 + threadIdx.x < d.h1) prefetch_home(pos, nn, words, ld, d.h0 + threadIdx.x, (int)kLjChunk);
         const bool in_smem = d.M <= stage_cap;
         if (!in_smem) note_spill(status);
-        const bool staged = in_smem ? stage_positions(d, box, pos, sp, &bar, phase, status) : true;
+        const bool staged =
+            in_smem ? stage_positions(d, box, pos, sp, &bar, phase, status, nullptr, nullptr, wait0) : true;
+        const bool all_mode = cfg.mode[0] == kModeAll || cfg.mode[1] == kModeAll || cfg.mode[2] == kModeAll;
         T usum = 0, wsum = 0;
         uint32_t npsum = 0;
         for (uint32_t i = d.h0 + threadIdx.x; staged && i < d.h1; i += blockDim.x) {
@@ -49,8 +52,10 @@ __global__ void __launch_bounds__(kTileThreads)
             T fx = 0, fy = 0, fz = 0, u = 0, w = 0;
             uint32_t np = 0;
             if (in_smem) {
-                if (d.slow)
+                if (d.slow && all_mode)
                     lj_sweep<T, false, true>(cfg, box, d, pos, sp, pi, m, words + i, ld, P, fx, fy, fz, u, w, np);
+                else if (d.slow)
+                    lj_sweep_wall<T>(box, sp, pi, m, words + i, ld, P, fx, fy, fz, u, w, np);
                 else
                     lj_sweep<T, true, true>(cfg, box, d, pos, sp, pi, m, words + i, ld, P, fx, fy, fz, u, w, np);
             } else {
@@ -84,6 +89,9 @@ __global__ void __launch_bounds__(kTileThreads)
     }
 }
 
+// Budget of the sweep's first wait on a tile's copies (fpm_test_wait_budget).
+static std::atomic<long long> g_first_wait{0};
+
 template <typename T>
 static fpm_status lj_launch(const fpm_box &b, const fpm_grid &g, int n, const void *pos, const void *list,
                             const uint32_t *nn, int cap, double eps, double sigma, double rc, void *force,
@@ -102,9 +110,11 @@ static fpm_status lj_launch(const fpm_box &b, const fpm_grid &g, int n, const vo
     const size_t smem = (size_t)sc * sizeof(V4<T>);
     smem_opt_in((const void *)k_lj_tiles<T>);
     const int blocks = persistent_blocks((const void *)k_lj_tiles<T>, kTileThreads, smem, g, cfg.ntiles);
+    const long long w0 = g_first_wait.load();
     k_lj_tiles<T><<<blocks, kTileThreads, smem, stream>>>(cfg, box, (const V4<T> *)pos, list_view(list, L), nn, L.ld,
                                                           sc, P, (V4<T> *)force, Sched{r.work, r.done}, r.part,
-                                                          d_energy, status, (V4<T> *)vel, (T)(0.5 * dt));
+                                                          d_energy, status, (V4<T> *)vel, (T)(0.5 * dt),
+                                                          w0 > 0 ? w0 : kWaitCycles);
     return fpm_check_launch("fpm_lj_forces");
 }
 
@@ -245,4 +255,10 @@ extern "C" fpm_status fpm_lj_forces_noalloc(const fpm_box *box, const fpm_grid *
     if (prec == FPM_F32)
         return lj_launch<float>(*box, *grid, n, pos, list, nn, cap, eps, sigma, rc, force, d_energy, r, d_status, st);
     return lj_launch<double>(*box, *grid, n, pos, list, nn, cap, eps, sigma, rc, force, d_energy, r, d_status, st);
+}
+
+extern "C" fpm_status fpm_test_wait_budget(int64_t cycles)
+{
+    g_first_wait.store(cycles > 0 ? (long long)cycles : 0);
+    return FPM_OK;
 }

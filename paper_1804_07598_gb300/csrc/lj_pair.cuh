@@ -55,6 +55,30 @@ __device__ __forceinline__ void lj_pair(const TileCfg &cfg, const BoxT<T> &box, 
     np += in ? 1u : 0u;
 }
 
+// lj_pair for a tile with periodic-wall flags and no "all"-mode dimension,
+// staged in shared memory (tile_sep_wall).
+template <typename T>
+__device__ __forceinline__ void lj_pair_wall(const V4<T> *__restrict__ st, const V4<T> &pi, const V4<T> &pim, int s,
+                                             const LJParams<T> &P, T &fx, T &fy, T &fz, T &S12, T &S6, uint32_t &np)
+{
+    const V4<T> pj = st[s];
+    T dx, dy, dz;
+    const T r2 = tile_sep_wall(pi, pim, pj, dx, dy, dz);
+    const bool in = r2 < P.rc2;
+    const T ir2 = recip(r2);
+    const T s2 = P.sig2 * ir2;
+    const T s6 = in ? s2 * s2 * s2 : (T)0;
+    const T s12 = s6 * s6;
+    const T a = (T)2 * s12 - s6;
+    const T g = a * ir2;
+    fx += g * dx;
+    fy += g * dy;
+    fz += g * dz;
+    S12 += s12;
+    S6 += s6;
+    np += in ? 1u : 0u;
+}
+
 // The LJ sums of one home particle over its list (list words prefetched
 // kLjChunk at a time, see for_each_entry).
 constexpr uint32_t kLjChunk = 3;
@@ -69,6 +93,21 @@ __device__ __forceinline__ void lj_sweep(const TileCfg &cfg, const BoxT<T> &box,
     for_each_entry<kLjChunk>(m, col, ld, [&](int s) {
         lj_pair<T, FAST, SMEM>(cfg, box, d, pos, st, pi, s, P, fx, fy, fz, S12, S6, np);
     });
+    u += S12 - S6;
+    w += (T)2 * S12 - S6;
+}
+
+template <typename T>
+__device__ __forceinline__ void lj_sweep_wall(const BoxT<T> &box, const V4<T> *__restrict__ st, const V4<T> &pi,
+                                              uint32_t m, const uint32_t *__restrict__ col, int64_t ld,
+                                              const LJParams<T> &P, T &fx, T &fy, T &fz, T &u, T &w, uint32_t &np)
+{
+    V4<T> pim = pi;
+    pim.x = rsub(pi.x, box.L[0]);
+    pim.y = rsub(pi.y, box.L[1]);
+    pim.z = rsub(pi.z, box.L[2]);
+    T S12 = 0, S6 = 0;
+    for_each_entry<kLjChunk>(m, col, ld, [&](int s) { lj_pair_wall<T>(st, pi, pim, s, P, fx, fy, fz, S12, S6, np); });
     u += S12 - S6;
     w += (T)2 * S12 - S6;
 }

@@ -29,6 +29,7 @@ struct SphK {
     float wcoef;     // m times (Wendland: F = wcoef (1 - q/2)^3;  cubic: s/h^2)
     float visc2;     // -2 alpha c0 (Pi_pq = visc2 mu / (rho_p + rho_q))
     float inv_h;
+    float wnorm;     // m W(0): m a (Wendland) or m s (cubic), the kernel's normalisation times m
     float binom[8];  // C(gamma, k), k = 1..gamma (0 beyond)
     int gamma;
     int kernel;      // 0 Wendland C2, 1 cubic spline
@@ -246,6 +247,84 @@ __global__ void __launch_bounds__(kSphThreads, 2)
     sched_finish(sched, &s_last);
 }
 
+// ---- density by summation ---------------------------------------------------
+// rho_i = m W(0) + sum over the list entries inside the support of m W(r_ij),
+// with W the kernel of Sec. 4.2 (Wendland C2: a (1 - q/2)^4 (2q + 1);
+// cubic spline: s [1 - 1.5 q^2 + 0.75 q^3] for q < 1, s (2 - q)^3 / 4 for
+// q < 2), q = r/h.  One thread per home particle, the tile's neighbourhood
+// staged as in the other sweeps.
+
+// m W(r) / (m W(0)) for r2 inside the support.
+template <int KK>
+__device__ __forceinline__ float kernel_shape(const SphK &K, float r2)
+{
+    const float q = sqrtf(r2) * K.inv_h;
+    if (KK == 0) {
+        const float t = 1.0f - 0.5f * q;
+        const float t2 = t * t;
+        return t2 * t2 * (2.0f * q + 1.0f);
+    }
+    if (q < 1.0f) return 1.0f - q * q * (1.5f - 0.75f * q);
+    const float t = 2.0f - q;
+    return 0.25f * t * t * t;
+}
+
+template <bool FAST, bool SMEM, int KK>
+__device__ __forceinline__ float density_sweep(const TileCfg &cfg, const BoxT<float> &box, const TileDesc &d,
+                                               const float4 *__restrict__ pos, const float4 *__restrict__ st,
+                                               const float4 &pi, uint32_t m, const uint32_t *__restrict__ col,
+                                               int64_t ld, const SphK &K)
+{
+    float sum = 1.0f;  // the particle itself, W(0)
+    for_each_entry<3>(m, col, ld, [&](int s) {
+        const float4 pj = SMEM ? st[s] : staged_global(d, box, pos, s);
+        float dx, dy, dz;
+        const float r2 = tile_sep<FAST>(pi, pj, box, cfg, dx, dy, dz);
+        sum += r2 < K.two_h2 ? kernel_shape<KK>(K, r2) : 0.0f;
+    });
+    return K.wnorm * sum;
+}
+
+template <int KK>
+__global__ void __launch_bounds__(kTileThreads)
+    k_sph_density_tiles(TileCfg cfg, BoxT<float> box, const float4 *__restrict__ pos, ListView lv,
+                        const uint32_t *__restrict__ nn, int64_t ld, int stage_cap, SphK K, float *__restrict__ rho,
+                        Sched sched, fpm_dev_status *status)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float4 *sp = (float4 *)smem_raw;
+    __shared__ TileDesc d;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t s_k;
+    __shared__ bool s_last;
+    stage_init(&bar);
+    uint32_t phase = 0;
+    const uint32_t *__restrict__ words = lv.words;
+    const uint32_t ntodo = *lv.count;
+    uint32_t ahead = 0;
+    for (uint32_t k = blockIdx.x; k < ntodo; k = ticket_next(ahead, &s_k)) {
+        ahead = ticket_ahead(sched);
+        load_desc(lv.descs + lv.active[k], d);
+        if (d.h0 + threadIdx.x < d.h1) prefetch_home(pos, nn, words, ld, d.h0 + threadIdx.x, 3);
+        const bool in_smem = d.M <= stage_cap;
+        if (!in_smem) note_spill(status);
+        const bool staged = in_smem ? stage_positions(d, box, pos, sp, &bar, phase, status) : true;
+        for (uint32_t i = d.h0 + threadIdx.x; staged && i < d.h1; i += blockDim.x) {
+            const float4 pi = pos[i];
+            const uint32_t m = nn[i];
+            float r;
+            if (!in_smem)
+                r = density_sweep<false, false, KK>(cfg, box, d, pos, sp, pi, m, words + i, ld, K);
+            else if (d.slow)
+                r = density_sweep<false, true, KK>(cfg, box, d, pos, sp, pi, m, words + i, ld, K);
+            else
+                r = density_sweep<true, true, KK>(cfg, box, d, pos, sp, pi, m, words + i, ld, K);
+            rho[i] = r;
+        }
+    }
+    sched_finish(sched, &s_last);
+}
+
 __device__ __forceinline__ float sph_dt(const float *dtcons, float h, float c0, float cfl)
 {
     const float amax = dtcons[0], mumax = dtcons[1];
@@ -366,6 +445,8 @@ static SphK make_sph(const fpm_sph_params &p)
         K.wcoef = (float)(p.mass / (pi * p.h * p.h * p.h) / (p.h * p.h));
     }
     K.visc2 = (float)(-2.0 * p.alpha * p.c0);
+    K.wnorm = p.kernel == 0 ? (float)(p.mass * 21.0 / (16.0 * pi * p.h * p.h * p.h))
+                            : (float)(p.mass / (pi * p.h * p.h * p.h));
     // C(gamma, k) for k = 1..gamma in binom[k-1], Horner from the highest
     double c = 1.0;
     for (int k = 1; k <= 8; ++k) {
@@ -420,6 +501,37 @@ extern "C" fpm_status fpm_sph_forces(const fpm_box *box, const fpm_grid *grid, i
         cfg, make_box<float>(*box), (const float4 *)pos, (const float4 *)vr, list_view(list, L), nn, L.ld, sc,
         K, (float4 *)acc, d_dtcons, Sched{r.work, r.done}, d_status);
     return fpm_check_launch("fpm_sph_forces");
+}
+
+extern "C" fpm_status fpm_sph_density(const fpm_box *box, const fpm_grid *grid, int32_t n, const void *pos,
+                                      const void *list, const uint32_t *nn, int32_t cap, const fpm_sph_params *params,
+                                      float *rho, void *workspace, size_t workspace_bytes, fpm_dev_status *d_status,
+                                      fpm_stream stream)
+{
+    fpm_status s = fpm_check_grid(box, grid, "fpm_sph_density");
+    if (s != FPM_OK) return s;
+    s = sph_params_ok(params, "fpm_sph_density");
+    if (s != FPM_OK) return s;
+    if (n < 0 || cap < 1 || (n > 0 && (!pos || !list || !nn || !rho)))
+        return fpm_fail(FPM_ERR_INVALID, "fpm_sph_density: null pointer or bad size");
+    if (((uintptr_t)list & 255u) != 0) return fpm_fail(FPM_ERR_INVALID, "fpm_sph_density: list not 256-B aligned");
+    if (n == 0) return FPM_OK;
+    RedWs r{};
+    s = red_ws(n, grid, workspace, workspace_bytes, "fpm_sph_density", r);
+    if (s != FPM_OK) return s;
+    const TileCfg cfg = make_tile_cfg(*box, *grid);
+    const ListLayout L = list_layout(n, cfg, cap);
+    const int sc = stage_capacity(n, *grid, sizeof(float4));
+    const size_t smem = (size_t)sc * sizeof(float4);
+    const SphK K = make_sph(*params);
+    const void *kern = K.kernel == 0 ? (const void *)k_sph_density_tiles<0> : (const void *)k_sph_density_tiles<1>;
+    smem_opt_in(kern);
+    const int blocks = persistent_blocks(kern, kTileThreads, smem, *grid, cfg.ntiles);
+    auto launch = K.kernel == 0 ? k_sph_density_tiles<0> : k_sph_density_tiles<1>;
+    launch<<<blocks, kTileThreads, smem, (cudaStream_t)stream>>>(cfg, make_box<float>(*box), (const float4 *)pos,
+                                                               list_view(list, L), nn, L.ld, sc, K, rho,
+                                                               Sched{r.work, r.done}, d_status);
+    return fpm_check_launch("fpm_sph_density");
 }
 
 extern "C" fpm_status fpm_sph_predict(const fpm_box *box, int32_t n, const fpm_sph_params *params, double cfl,

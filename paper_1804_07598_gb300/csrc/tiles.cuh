@@ -294,11 +294,23 @@ constexpr long long kWaitCycles = 4000000000LL;  // about 2 s of SM clock
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// Each round tests the phase without blocking, then gives up once the budget
+// is spent or waits in the hardware's own suspended wait; a budget shorter
+// than one suspended wait therefore expires unless the phase is complete.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long budget)
 {
     const long long t0 = clock64();
     for (;;) {
         uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > budget) return false;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -307,7 +319,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
             : "r"(bar), "r"(parity)
             : "memory");
         if (done) return true;
-        if (clock64() - t0 > budget) return false;
     }
 }
 
@@ -326,13 +337,16 @@ __device__ __forceinline__ void stage_init(uint64_t *bar)
 // and (in tiles that need them) the piece flags in w.  When aux is given, the
 // same slots of a second per-particle array are copied unchanged into aux_st
 // on the same barrier.  `phase` is the barrier's parity, flipped per use.
+// wait0 is the budget of the first wait for the copies (the wait that lets
+// copies in flight land after an expiry always has the full budget).
 // Every thread must have finished with the previous tile's staged data (a
 // __syncthreads) before the call.  Returns false, the same in every thread,
 // if the copies did not complete within the wait budget.
 template <typename T>
 __device__ bool stage_positions(const TileDesc &d, const BoxT<T> &box, const V4<T> *__restrict__ pos,
                                 V4<T> *__restrict__ st, uint64_t *bar, uint32_t &phase, fpm_dev_status *status,
-                                const V4<T> *__restrict__ aux = nullptr, V4<T> *__restrict__ aux_st = nullptr)
+                                const V4<T> *__restrict__ aux = nullptr, V4<T> *__restrict__ aux_st = nullptr,
+                                long long wait0 = kWaitCycles)
 {
     const uint32_t b = smem_u32(bar);
     static_assert(kMaxPieces <= 32, "one lane of warp 0 per piece");
@@ -373,7 +387,7 @@ __device__ bool stage_positions(const TileDesc &d, const BoxT<T> &box, const V4<
         fix = pc.len != 0 && (pc.flags != 0 || d.slow);
     }
     uint32_t todo = __ballot_sync(kFull, fix);
-    bool ok = mbar_wait(b, phase, kWaitCycles);
+    bool ok = mbar_wait(b, phase, wait0);
     if (!ok) {
         latch_flag(status, FPM_FLAG_TIMEOUT);
         ok = mbar_wait(b, phase, kWaitCycles);  // let copies in flight land before leaving
@@ -454,6 +468,20 @@ __device__ __forceinline__ T tile_sep(const V4<T> &pi, const V4<T> &pj, const Bo
         dz = cfg.mode[2] == kModeAll ? sep1(pi.z, pj.z, box.L[2], box.h[2])
                                      : rsub((f & kUpZ) ? rsub(pi.z, box.L[2]) : pi.z, pj.z);
     }
+    return rfma(dz, dz, rfma(dy, dy, rmul(dx, dx)));
+}
+
+// Separation for a staged neighbour of a tile with periodic-wall flags and
+// no "all"-mode dimension: the home coordinate x_i - L (pim, computed once
+// per home particle) where the neighbour's flags say so.  The same roundings
+// as tile_sep<false> in "wrap" mode.
+template <typename T>
+__device__ __forceinline__ T tile_sep_wall(const V4<T> &pi, const V4<T> &pim, const V4<T> &pj, T &dx, T &dy, T &dz)
+{
+    const int f = flags_of(pj.w);
+    dx = rsub((f & kUpX) ? pim.x : pi.x, pj.x);
+    dy = rsub((f & kUpY) ? pim.y : pi.y, pj.y);
+    dz = rsub((f & kUpZ) ? pim.z : pi.z, pj.z);
     return rfma(dz, dz, rfma(dy, dy, rmul(dx, dx)));
 }
 

@@ -121,6 +121,8 @@ _SIG = {
                                       _c.c_double, _VP, _VP]),
     "fpm_sph_forces": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _VP, _VP, _VP, _VP,
                                   _c.c_int32, _c.POINTER(fpm_sph_params), _VP, _VP, _VP, _c.c_size_t, _VP, _VP]),
+    "fpm_sph_density": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _VP, _VP, _VP,
+                                   _c.c_int32, _c.POINTER(fpm_sph_params), _VP, _VP, _c.c_size_t, _VP, _VP]),
     "fpm_sph_predict": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.POINTER(fpm_sph_params), _c.c_double, _VP,
                                    _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _c.c_double, _VP, _VP]),
     "fpm_sph_correct": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.POINTER(fpm_sph_params), _VP, _VP, _VP, _VP,
@@ -145,6 +147,7 @@ _SIG = {
                                   _VP, _VP]),
     "fpm_adjoint_seed": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _VP, _VP, _VP, _VP]),
     "fpm_adjoint_loss": (_c.c_int, [_VP, _VP, _VP, _VP]),
+    "fpm_test_wait_budget": (_c.c_int, [_c.c_int64]),
     "fpm_adjoint_finish": (_c.c_int, [_c.c_int32, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP]),
     "fpm_kinetic": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _VP, _VP, _c.c_size_t, _VP]),
     "fpm_unpack_xyz": (_c.c_int, [_c.c_int32, _c.c_int, _VP, _VP, _VP]),
@@ -363,6 +366,12 @@ def fpm_lj_forces_noalloc(box, grid, n, prec, pos, list_obj, nn, cap, eps, sigma
     _count(1 if n > 0 else 0)
 
 
+def fpm_test_wait_budget(cycles):
+    """Test hook: budget (SM cycles) of the LJ sweeps' first wait per work
+    item; 0 restores the default."""
+    _check(lib().fpm_test_wait_budget(int(cycles)))
+
+
 def fpm_vv_step(box, n, prec, half, dt, pos, vel, force, stream=None):
     _check(lib().fpm_vv_step(_c.byref(box), int(n), int(prec), int(half), float(dt), _ptr(pos), _ptr(vel),
                              _ptr(force), _stream(stream)))
@@ -481,6 +490,13 @@ def fpm_p2m(box, mesh_grid, n, pos, val, cell_start, mesh, d_status=None, stream
 def fpm_m2p(box, mesh_grid, n, pos, mesh, val, order=None, stream=None):
     _check(lib().fpm_m2p(_c.byref(box), _c.byref(mesh_grid), int(n), _ptr(pos), _ptr(mesh), _ptr(order), _ptr(val),
                          _stream(stream)))
+    _count(1 if n > 0 else 0)
+
+
+def fpm_sph_density(box, grid, n, pos, list_obj, nn, cap, params, rho, workspace, d_status=None, stream=None):
+    _check(lib().fpm_sph_density(_c.byref(box), _c.byref(grid), int(n), _ptr(pos), _ptr(list_obj), _ptr(nn),
+                                 int(cap), _c.byref(params), _ptr(rho), _ptr(workspace), _nbytes(workspace),
+                                 _ptr(d_status), _stream(stream)))
     _count(1 if n > 0 else 0)
 
 

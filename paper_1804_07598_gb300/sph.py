@@ -127,6 +127,14 @@ class SPHSystem:
                            self.acc if acc is None else acc, self.dtcons if dtcons is None else dtcons, self.ws_red,
                            self.status)
 
+    def density(self, out=None):
+        """Density by summation, sum_j m W(r_ij) over the current list
+        (the particle itself included), [n] float32 in sorted order."""
+        rho = out if out is not None else torch.empty(self.n, dtype=torch.float32, device=self.device)
+        fpm.fpm_sph_density(self.box, self.grid, self.n, self.pos, self.nbr, self.nn, self.cap, self.params, rho,
+                            self.ws_red, self.status)
+        return rho
+
     def _step(self):
         self.rates()
         fpm.fpm_sph_predict(self.box, self.n, self.params, self.cfl, self.pos, self.vr, self.acc, self.dtcons,

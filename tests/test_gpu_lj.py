@@ -215,3 +215,37 @@ def test_forces_kick_equals_forces_then_kick(cuda, prec):
     assert torch.equal(s.energy, e_ref)
     assert torch.equal(s.vel, v_ref)
     assert not torch.equal(v_ref, v0)
+
+
+def test_sweep_wait_expiry_latches_timeout(cuda):
+    """The bounded wait of the force sweep driven to expiry through the test
+    hook (a 1-cycle budget for the first wait of each work item on its tile's
+    copies): the call completes, FPM_FLAG_TIMEOUT is latched
+    (FPM_ERR_TIMEOUT from the device status), and with the default budget
+    restored the next sweep is clean and gives the earlier forces bit for
+    bit."""
+    wl = inputs.WORKLOADS["lj_small"]
+    pos, vel, L = inputs.lj_state(wl, jitter=0.06)
+    s = LJSystem(pos, vel, L, precision="f32")
+    s.compute_forces()
+    torch.cuda.synchronize()
+    s.check_status()
+    f0 = s.force.clone()
+    latched = False
+    try:
+        for _ in range(5):
+            s.status.zero_()
+            fpm.fpm_test_wait_budget(1)
+            s.compute_forces()
+            torch.cuda.synchronize()
+            if fpm.fpm_status_from_device(fpm.read_status(s.status)) == fpm.FPM_ERR_TIMEOUT:
+                latched = True
+                break
+    finally:
+        fpm.fpm_test_wait_budget(0)
+    assert latched
+    s.status.zero_()
+    s.compute_forces()
+    torch.cuda.synchronize()
+    s.check_status()
+    assert torch.equal(s.force, f0)
