@@ -223,6 +223,21 @@ fpm_status fpm_verlet_build(const fpm_box *box, const fpm_grid *grid, int32_t n,
                             void *list, size_t list_bytes, uint32_t *nn, void *pos_ref,
                             fpm_dev_status *d_status, uint32_t *d_gate, fpm_stream stream);
 
+/* fpm_verlet_build for the symmetric sweep (fpm_lj_forces_half): a half list
+ * that holds each pair {i, j} with r2 < (T)(r_list^2) once, in the list of
+ * the particle whose cell comes first in the half stencil: the cells
+ * (dz, dy, dx) lexicographically after (0, 0, 0), and in the particle's own
+ * cell the particles after it in the sorted order (the cell list of
+ * getCellListSym, Listing 4.1).  A tile stages its own row and the four rows
+ * after it, each piece of the staging at an offset of the parity of its
+ * first particle index (free slots between pieces belong to no particle).
+ * Same arguments, layout and errors as fpm_verlet_build; about half the
+ * entries, so cap can be about half. */
+fpm_status fpm_verlet_build_half(const fpm_box *box, const fpm_grid *grid, int32_t n, fpm_prec prec, const void *pos,
+                                 const uint32_t *cell_start, double r_list, int32_t cap, void *list,
+                                 size_t list_bytes, uint32_t *nn, void *pos_ref, fpm_dev_status *d_status,
+                                 uint32_t *d_gate, fpm_stream stream);
+
 /* Particle indices of a Verlet list: out[k*ld + i] = j for k < nn[i]
  * (out : [cap * fpm_nbr_ld(n)] uint32; other slots untouched).  The order of
  * entries within a list is not part of the contract; the set is. */
@@ -311,6 +326,33 @@ fpm_status fpm_lj_forces_noalloc(const fpm_box *box, const fpm_grid *grid, int32
                                  const void *pos, const void *list, const uint32_t *nn, int32_t cap,
                                  double eps, double sigma, double rc,
                                  void *force, double *d_energy, fpm_dev_status *d_status, fpm_stream stream);
+
+/* The symmetric sweep of Sec. 4.1 (each pair once, the force applied to both
+ * particles, the reactions summed back as Sec. 3.4's ghost_put with a sum
+ * does), single precision, over a half list from fpm_verlet_build_half:
+ *   F_i = sum over pairs {i, j} with r2 < (float)(rc^2) of
+ *         24 eps (2 s^12/r^14 - s^6/r^8) (x_i - x_j),
+ * the same forces as fpm_lj_forces up to rounding.  Each home particle's own
+ * sum runs in FP32; every contribution is then added as a 64-bit fixed-point
+ * integer (units of 2^-32 of force), so the result does not depend on the
+ * order of the additions: bit-reproducible.
+ * force    : [n] float4, w = 0 (the per-particle energy share is not formed).
+ * d_energy : [3] double, U, W and the pair count as fpm_lj_forces, or NULL.
+ * acc      : fpm_lj_half_acc_bytes(n) bytes, 16-byte aligned, ZERO-FILLED
+ *            before the first call; every call leaves it zero again.
+ * workspace: fpm_reduce_workspace(n, grid) bytes, as fpm_lj_forces.
+ * vel      : NULL, or [n] float4 receiving the closing half-kick
+ *            v += dt/2 F (as fpm_lj_forces_kick).
+ * Two launches on `stream`.  Single precision only (the fixed-point unit
+ * 2^-32 is far below FP32 rounding of forces, not below FP64's). */
+fpm_status fpm_lj_forces_half(const fpm_box *box, const fpm_grid *grid, int32_t n, const void *pos, const void *list,
+                              const uint32_t *nn, int32_t cap, double eps, double sigma, double rc, void *force,
+                              double *d_energy, void *acc, size_t acc_bytes, void *workspace, size_t workspace_bytes,
+                              fpm_dev_status *d_status, void *vel, double dt, fpm_stream stream);
+
+/* Bytes of the fixed-point array of fpm_lj_forces_half: three int64 per
+ * particle, n rounded up to even. */
+fpm_status fpm_lj_half_acc_bytes(int32_t n, size_t *bytes);
 
 /* Test hook (the paper has no counterpart): the budget, in SM clock cycles,
  * of the first bounded wait per tile of the force sweeps of fpm_lj_forces,

@@ -173,8 +173,54 @@ __device__ __forceinline__ int seq_cell_x(int x, int ncx, int mode, int *wrap)
     return x;
 }
 
+// The stencil rows of a half-list tile (each pair once): the offsets
+// (dz, dy) = (0, 0), (0, +1), (+1, -1), (+1, 0), (+1, +1), lexicographically
+// after or equal to (0, 0), each kept if it exists (open boundaries) and
+// distinct (an "all"-mode dimension has the single offset 0).  Row 0 is the
+// tile's own row.  Returns the count.
+__device__ __forceinline__ int half_rows(int cy, int cz, const TileCfg &cfg, int *rcy, int *rcz, int *rwy, int *rwz)
+{
+    int k = 0;
+    for (int oz = 0; oz <= 1; ++oz) {
+        if (oz == 1 && cfg.mode[2] == kModeAll) continue;
+        int z = cz + oz, wz = 0;
+        if (z >= cfg.nc[2]) {
+            if (cfg.mode[2] != kModeWrap) continue;
+            z -= cfg.nc[2];
+            wz = 1;
+        }
+        for (int oy = (oz == 0 ? 0 : -1); oy <= 1; ++oy) {
+            if (oy != 0 && cfg.mode[1] == kModeAll) continue;
+            int y = cy + oy, wy = 0;
+            if (y < 0 || y >= cfg.nc[1]) {
+                if (cfg.mode[1] != kModeWrap) continue;
+                if (y < 0) {
+                    y += cfg.nc[1];
+                    wy = -1;
+                } else {
+                    y -= cfg.nc[1];
+                    wy = 1;
+                }
+            }
+            rcy[k] = y;
+            rcz[k] = z;
+            rwy[k] = wy;
+            rwz[k] = wz;
+            ++k;
+        }
+    }
+    return k;
+}
+
 // Computes the geometry of `tile` and its descriptor (in shared memory).  All
-// threads of the block must call it.
+// threads of the block must call it.  HALF: the rows of a half-list tile
+// (half_rows), and every piece staged at an offset of the parity of its
+// first particle index, with a free slot after a piece that ends on an odd
+// index, so that a piece's slots cover the even-aligned index range
+// [gstart & ~1, (gstart + len + 1) & ~1) of a per-particle array (the
+// half-list sweep returns its reactions per piece in that form); the free
+// slots belong to no piece.
+template <bool HALF = false>
 __device__ inline void tile_geometry(const TileCfg &cfg, int tile, const uint32_t *__restrict__ cs, TileGeom &g,
                               TileDesc &d)
 {
@@ -197,20 +243,25 @@ __device__ inline void tile_geometry(const TileCfg &cfg, int tile, const uint32_
             g.seq_start = s;
             g.nseq = e - s;
         }
-        int zc[3], zw[3], yc[3], yw[3], zmid = 0, ymid = 0;
-        const int kz = stencil_rows(cz, cfg.nc[2], cfg.mode[2], zc, zw, &zmid);
-        const int ky = stencil_rows(cy, cfg.nc[1], cfg.mode[1], yc, yw, &ymid);
-        int r = 0;
-        for (int i = 0; i < kz; ++i)
-            for (int j = 0; j < ky; ++j) {
-                g.row_cy[r] = yc[j];
-                g.row_cz[r] = zc[i];
-                g.row_wy[r] = yw[j];
-                g.row_wz[r] = zw[i];
-                if (i == zmid && j == ymid) g.mid_row = r;
-                ++r;
-            }
-        g.nrows = r;
+        if (HALF) {
+            g.nrows = half_rows(cy, cz, cfg, g.row_cy, g.row_cz, g.row_wy, g.row_wz);
+            g.mid_row = 0;
+        } else {
+            int zc[3], zw[3], yc[3], yw[3], zmid = 0, ymid = 0;
+            const int kz = stencil_rows(cz, cfg.nc[2], cfg.mode[2], zc, zw, &zmid);
+            const int ky = stencil_rows(cy, cfg.nc[1], cfg.mode[1], yc, yw, &ymid);
+            int r = 0;
+            for (int i = 0; i < kz; ++i)
+                for (int j = 0; j < ky; ++j) {
+                    g.row_cy[r] = yc[j];
+                    g.row_cz[r] = zc[i];
+                    g.row_wy[r] = yw[j];
+                    g.row_wz[r] = zw[i];
+                    if (i == zmid && j == ymid) g.mid_row = r;
+                    ++r;
+                }
+            g.nrows = r;
+        }
     }
     __syncthreads();
     const int tot = g.nrows * g.nseq;
@@ -227,10 +278,21 @@ __device__ inline void tile_geometry(const TileCfg &cfg, int tile, const uint32_
     if (tid == 0) {
         int o = 0;
         for (int r = 0; r < g.nrows; ++r) {
+            int wprev = 2;
             for (int t = 0; t < g.nseq; ++t) {
+                if (HALF) {
+                    int w;
+                    seq_cell_x(g.seq_start + t, cfg.nc[0], cfg.mode[0], &w);
+                    if (w != wprev) {  // a piece starts here: the previous one ends
+                        if (t > 0 && ((g.start[r][t - 1] + (uint32_t)g.cnt[r][t - 1]) & 1u)) ++o;
+                        if (((uint32_t)o ^ g.start[r][t]) & 1u) ++o;
+                        wprev = w;
+                    }
+                }
                 g.off[r][t] = o;
                 o += g.cnt[r][t];
             }
+            if (HALF && ((g.start[r][g.nseq - 1] + (uint32_t)g.cnt[r][g.nseq - 1]) & 1u)) ++o;
             g.off[r][g.nseq] = o;
         }
         g.M = o;
@@ -258,7 +320,9 @@ __device__ inline void tile_geometry(const TileCfg &cfg, int tile, const uint32_
                 }
                 const int f = rowflags | (w0 > 0 ? kUpX : 0) | (w0 < 0 ? kLoX : 0);
                 if (f & (kUpX | kUpY | kUpZ)) slow = 1;
-                d.piece[r * kPiecesPerRow + p] = Piece{g.off[r][t], g.off[r][t1 + 1] - g.off[r][t], g.start[r][t], f};
+                int len = 0;
+                for (int q = t; q <= t1; ++q) len += g.cnt[r][q];
+                d.piece[r * kPiecesPerRow + p] = Piece{g.off[r][t], len, g.start[r][t], f};
                 ++p;
                 t = t1 + 1;
             }
@@ -356,8 +420,12 @@ __device__ bool stage_positions(const TileDesc &d, const BoxT<T> &box, const V4<
         // copy (or copies) of piece p.  Each issuing lane first orders the
         // block's earlier generic accesses of the buffers (made visible to it by
         // the caller's barrier) before its async copies.
+        // the bytes the copies bring: the pieces' lengths (a half-list tile's
+        // free slots between pieces are not copied)
+        const uint32_t len = lane < kMaxPieces ? (uint32_t)d.piece[lane].len : 0u;
+        const uint32_t staged = __reduce_add_sync(kFull, len);
         if (lane == 0) {
-            const uint32_t bytes = (uint32_t)d.M * (uint32_t)sizeof(V4<T>) * (aux ? 2u : 1u);
+            const uint32_t bytes = staged * (uint32_t)sizeof(V4<T>) * (aux ? 2u : 1u);
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
         }
         __syncwarp();
@@ -432,13 +500,18 @@ template <typename T>
 __device__ __forceinline__ V4<T> staged_global(const TileDesc &d, const BoxT<T> &box, const V4<T> *__restrict__ pos,
                                                int s)
 {
-    int p = 0;
+    int p = -1;
     for (int k = 0; k < kMaxPieces; ++k) {
         const Piece pc = d.piece[k];
         if (pc.len > 0 && s >= pc.soff && s < pc.soff + pc.len) {
             p = k;
             break;
         }
+    }
+    if (p < 0) {  // a free slot of a half-list tile: no particle, never inside any radius
+        V4<T> q;
+        q.x = q.y = q.z = q.w = (T)NAN;
+        return q;
     }
     const Piece pc = d.piece[p];
     V4<T> q = ldg4(pos + pc.gstart + (s - pc.soff));
@@ -550,7 +623,10 @@ __device__ __forceinline__ void for_each_entry(uint32_t m, const uint32_t *__res
 // (entries beyond cap are counted, not stored).  Candidates are tested 32 at
 // a time into a bit mask (one shift-in per test); then only the set bits are
 // appended, in increasing slot order.
-template <bool FAST, bool SMEM, typename T>
+// HALF: a half-list tile; in its own row only the slots after `self` (the
+// rest of the home cell, then the next cell) are candidates, so that each pair
+// is listed once.
+template <bool FAST, bool SMEM, typename T, bool HALF = false>
 __device__ __forceinline__ uint32_t scan_candidates(const TileCfg &cfg, const BoxT<T> &box, const TileGeom &g,
                                                     const TileDesc &d, const V4<T> *__restrict__ pos,
                                                     const V4<T> *__restrict__ st, const V4<T> &pi, int self,
@@ -560,7 +636,7 @@ __device__ __forceinline__ uint32_t scan_candidates(const TileCfg &cfg, const Bo
     uint32_t cnt = 0, pending = 0;
     const uint32_t ucap = (uint32_t)cap;
     for (int r = 0; r < g.nrows; ++r) {
-        const int s0 = g.off[r][t0], s1 = g.off[r][t1 + 1];
+        const int s0 = (HALF && r == g.mid_row) ? self + 1 : g.off[r][t0], s1 = g.off[r][t1 + 1];
         for (int base = s0; base < s1; base += 32) {
             const int e = base + 32 < s1 ? base + 32 : s1;
             uint32_t mask = 0;
@@ -593,7 +669,33 @@ __device__ __forceinline__ uint32_t scan_candidates(const TileCfg &cfg, const Bo
 // geometry and descriptor, the staging of its neighbourhood, and the scan of
 // every home particle (pos_ref[i] := pos[i] when pos_ref is given).  Returns
 // the largest candidate count this thread saw.
+// The free slots of a staged half-list tile (between its pieces) are set to
+// NaN positions, never inside any radius (the copies do not write them).
+// Lanes of warp 0, one per piece; the caller's next barrier publishes them.
 template <typename T>
+__device__ __forceinline__ void fill_free_slots(const TileDesc &d, V4<T> *__restrict__ st)
+{
+    if (threadIdx.x >= (unsigned)kMaxPieces) return;
+    const Piece pc = d.piece[threadIdx.x];
+    if (pc.len == 0) return;
+    const int cand[2] = {pc.soff - 1, pc.soff + pc.len};
+    for (int q = 0; q < 2; ++q) {
+        const int s = cand[q];
+        if (s < 0 || s >= d.M) continue;
+        bool used = false;
+        for (int k = 0; k < kMaxPieces; ++k) {
+            const Piece o = d.piece[k];
+            used = used || (o.len > 0 && s >= o.soff && s < o.soff + o.len);
+        }
+        if (!used) {
+            V4<T> nanv;
+            nanv.x = nanv.y = nanv.z = nanv.w = (T)NAN;
+            st[s] = nanv;
+        }
+    }
+}
+
+template <typename T, bool HALF = false>
 __device__ __forceinline__ uint32_t verlet_tile(const TileCfg &cfg, const BoxT<T> &box, int tile,
                                                 const uint32_t *__restrict__ cs, const V4<T> *__restrict__ pos,
                                                 T rl2, int cap, int64_t ld, int stage_cap, TileGeom &g, TileDesc &d,
@@ -601,7 +703,7 @@ __device__ __forceinline__ uint32_t verlet_tile(const TileCfg &cfg, const BoxT<T
                                                 uint32_t *__restrict__ words, uint32_t *__restrict__ nn,
                                                 V4<T> *__restrict__ pos_ref, fpm_dev_status *st)
 {
-    tile_geometry(cfg, tile, cs, g, d);
+    tile_geometry<HALF>(cfg, tile, cs, g, d);
     if (d.M > kMaxStaged) {  // 16-bit entries cannot address this neighbourhood
         for (uint32_t i = d.h0 + threadIdx.x; i < d.h1; i += blockDim.x) nn[i] = 0u;
         if (threadIdx.x == 0) latch_flag(st, FPM_FLAG_CAPACITY);
@@ -609,6 +711,7 @@ __device__ __forceinline__ uint32_t verlet_tile(const TileCfg &cfg, const BoxT<T
     }
     const bool in_smem = d.M <= stage_cap;
     if (!in_smem) note_spill(st);
+    if (HALF && in_smem) fill_free_slots<T>(d, sp);
     if (in_smem && !stage_positions(d, box, pos, sp, bar, phase, st)) {
         for (uint32_t i = d.h0 + threadIdx.x; i < d.h1; i += blockDim.x) nn[i] = 0u;
         return 0u;
@@ -626,10 +729,13 @@ __device__ __forceinline__ uint32_t verlet_tile(const TileCfg &cfg, const BoxT<T
         const int t1 = th + 1 < g.nseq ? th + 1 : g.nseq - 1;
         uint32_t c;
         if (in_smem) {
-            c = d.slow ? scan_candidates<false, true>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld, i, words)
-                       : scan_candidates<true, true>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld, i, words);
+            c = d.slow ? scan_candidates<false, true, T, HALF>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld,
+                                                              i, words)
+                       : scan_candidates<true, true, T, HALF>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld,
+                                                             i, words);
         } else {
-            c = scan_candidates<false, false>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld, i, words);
+            c = scan_candidates<false, false, T, HALF>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld, i,
+                                                       words);
         }
         nn[i] = c < (uint32_t)cap ? c : (uint32_t)cap;
         if (c > (uint32_t)cap) latch_flag(st, FPM_FLAG_CAPACITY);

@@ -14,6 +14,7 @@ namespace fpm {
 
 // Phase 1, every tile: geometry and descriptor (no staging, little shared
 // memory, so the many empty tiles of a sparse box cost almost nothing).
+template <bool HALF>
 __global__ void __launch_bounds__(128)
     k_tile_desc(TileCfg cfg, const uint32_t *__restrict__ cs, TileDesc *__restrict__ descs, fpm_dev_status *st,
                 const uint32_t *gate)
@@ -22,7 +23,7 @@ __global__ void __launch_bounds__(128)
     __shared__ TileGeom g;
     __shared__ TileDesc d;
     for (int tile = blockIdx.x; tile < cfg.ntiles; tile += gridDim.x) {
-        tile_geometry(cfg, tile, cs, g, d);
+        tile_geometry<HALF>(cfg, tile, cs, g, d);
         const int nw = (int)(sizeof(TileDesc) / 4);
         uint32_t *o = (uint32_t *)(descs + tile);
         const uint32_t *s = (const uint32_t *)&d;
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(1024)
 
 // Phase 3, persistent over the non-empty tiles: stage the neighbourhood and
 // scan each home particle's candidates.
-template <typename T>
+template <typename T, bool HALF>
 __global__ void __launch_bounds__(kTileThreads)
     k_verlet_scan(TileCfg cfg, BoxT<T> box, const V4<T> *__restrict__ pos, const uint32_t *__restrict__ cs, T rl2,
                   int cap, int64_t ld, int stage_cap, const uint32_t *__restrict__ active,
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(kTileThreads)
     uint32_t ahead = 0;
     for (uint32_t k = blockIdx.x; k < ntodo; k = ticket_next(ahead, &s_k)) {
         ahead = ticket_ahead(sched);
-        const uint32_t c = verlet_tile<T>(cfg, box, (int)active[k], cs, pos, rl2, cap, ld, stage_cap, g, d, sp, &bar,
+        const uint32_t c = verlet_tile<T, HALF>(cfg, box, (int)active[k], cs, pos, rl2, cap, ld, stage_cap, g, d, sp, &bar,
                                           phase, words, nn, pos_ref, st);
         maxc = c > maxc ? c : maxc;
     }
@@ -170,7 +171,7 @@ __global__ void k_verlet_check(BoxT<T> box, int n, const V4<T> *__restrict__ pos
     disp_report(over, d2f, st);
 }
 
-template <typename T>
+template <typename T, bool HALF>
 static fpm_status verlet_launch(const fpm_box &b, const fpm_grid &g, int n, const void *pos, const uint32_t *cs,
                                 double r_list, int cap, void *list, uint32_t *nn, void *pos_ref, fpm_dev_status *st,
                                 uint32_t *gate, cudaStream_t stream)
@@ -185,12 +186,12 @@ static fpm_status verlet_launch(const fpm_box &b, const fpm_grid &g, int n, cons
         TileDesc *descs = (TileDesc *)(lb + L.off_tiles);
         uint32_t *active = (uint32_t *)(lb + L.off_active);
         uint32_t *count = (uint32_t *)lb;
-        k_tile_desc<<<grid_cap(cfg.ntiles), 128, 0, stream>>>(cfg, cs, descs, st, gate);
+        k_tile_desc<HALF><<<grid_cap(cfg.ntiles), 128, 0, stream>>>(cfg, cs, descs, st, gate);
         k_tile_compact<<<1, 1024, 0, stream>>>(descs, cfg.ntiles, active, count, gate);
         const size_t smem = (size_t)sc * sizeof(V4<T>);
-        smem_opt_in((const void *)k_verlet_scan<T>);
-        const int blocks = persistent_blocks((const void *)k_verlet_scan<T>, kTileThreads, smem, g, cfg.ntiles);
-        k_verlet_scan<T><<<blocks, kTileThreads, smem, stream>>>(cfg, box, (const V4<T> *)pos, cs, rl2, cap, L.ld, sc,
+        smem_opt_in((const void *)k_verlet_scan<T, HALF>);
+        const int blocks = persistent_blocks((const void *)k_verlet_scan<T, HALF>, kTileThreads, smem, g, cfg.ntiles);
+        k_verlet_scan<T, HALF><<<blocks, kTileThreads, smem, stream>>>(cfg, box, (const V4<T> *)pos, cs, rl2, cap, L.ld, sc,
                                                                  active, count,
                                                                  Sched{(unsigned *)(lb + 16), (unsigned *)(lb + 20)},
                                                                  (uint32_t *)(lb + L.off_words), nn, (V4<T> *)pos_ref, st,
@@ -251,10 +252,10 @@ extern "C" fpm_status fpm_verlet_list_bytes(int32_t n, const fpm_grid *grid, int
     return FPM_OK;
 }
 
-extern "C" fpm_status fpm_verlet_build(const fpm_box *box, const fpm_grid *grid, int32_t n, fpm_prec prec,
-                                       const void *pos, const uint32_t *cell_start, double r_list, int32_t cap,
-                                       void *list, size_t list_bytes, uint32_t *nn, void *pos_ref,
-                                       fpm_dev_status *d_status, uint32_t *d_gate, fpm_stream stream)
+static fpm_status verlet_build(const fpm_box *box, const fpm_grid *grid, int32_t n, fpm_prec prec, const void *pos,
+                               const uint32_t *cell_start, double r_list, int32_t cap, void *list, size_t list_bytes,
+                               uint32_t *nn, void *pos_ref, fpm_dev_status *d_status, uint32_t *d_gate,
+                               fpm_stream stream, bool half)
 {
     fpm_status s = fpm_check_grid(box, grid, "fpm_verlet_build");
     if (s != FPM_OK) return s;
@@ -273,11 +274,36 @@ extern "C" fpm_status fpm_verlet_build(const fpm_box *box, const fpm_grid *grid,
         return fpm_fail(FPM_ERR_WORKSPACE, "fpm_verlet_build: list object %zu < %zu bytes", list_bytes, need);
     if (((uintptr_t)list & 255u) != 0) return fpm_fail(FPM_ERR_INVALID, "fpm_verlet_build: list not 256-B aligned");
     cudaStream_t st = (cudaStream_t)stream;
+    if (half) {
+        if (prec == FPM_F32)
+            return verlet_launch<float, true>(*box, *grid, n, pos, cell_start, r_list, cap, list, nn, pos_ref,
+                                              d_status, d_gate, st);
+        return verlet_launch<double, true>(*box, *grid, n, pos, cell_start, r_list, cap, list, nn, pos_ref, d_status,
+                                           d_gate, st);
+    }
     if (prec == FPM_F32)
-        return verlet_launch<float>(*box, *grid, n, pos, cell_start, r_list, cap, list, nn, pos_ref, d_status, d_gate,
-                                    st);
-    return verlet_launch<double>(*box, *grid, n, pos, cell_start, r_list, cap, list, nn, pos_ref, d_status, d_gate,
-                                 st);
+        return verlet_launch<float, false>(*box, *grid, n, pos, cell_start, r_list, cap, list, nn, pos_ref, d_status,
+                                           d_gate, st);
+    return verlet_launch<double, false>(*box, *grid, n, pos, cell_start, r_list, cap, list, nn, pos_ref, d_status,
+                                        d_gate, st);
+}
+
+extern "C" fpm_status fpm_verlet_build(const fpm_box *box, const fpm_grid *grid, int32_t n, fpm_prec prec,
+                                       const void *pos, const uint32_t *cell_start, double r_list, int32_t cap,
+                                       void *list, size_t list_bytes, uint32_t *nn, void *pos_ref,
+                                       fpm_dev_status *d_status, uint32_t *d_gate, fpm_stream stream)
+{
+    return verlet_build(box, grid, n, prec, pos, cell_start, r_list, cap, list, list_bytes, nn, pos_ref, d_status,
+                        d_gate, stream, false);
+}
+
+extern "C" fpm_status fpm_verlet_build_half(const fpm_box *box, const fpm_grid *grid, int32_t n, fpm_prec prec,
+                                            const void *pos, const uint32_t *cell_start, double r_list, int32_t cap,
+                                            void *list, size_t list_bytes, uint32_t *nn, void *pos_ref,
+                                            fpm_dev_status *d_status, uint32_t *d_gate, fpm_stream stream)
+{
+    return verlet_build(box, grid, n, prec, pos, cell_start, r_list, cap, list, list_bytes, nn, pos_ref, d_status,
+                        d_gate, stream, true);
 }
 
 extern "C" fpm_status fpm_verlet_decode(const fpm_grid *grid, int32_t n, int32_t cap, const void *list,

@@ -104,6 +104,12 @@ _SIG = {
     "fpm_verlet_list_bytes": (_c.c_int, [_c.c_int32, _c.POINTER(fpm_grid), _c.c_int32, _c.POINTER(_c.c_size_t)]),
     "fpm_verlet_build": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _c.c_int, _VP, _VP,
                                     _c.c_double, _c.c_int32, _VP, _c.c_size_t, _VP, _VP, _VP, _VP, _VP]),
+    "fpm_verlet_build_half": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _c.c_int, _VP, _VP,
+                                         _c.c_double, _c.c_int32, _VP, _c.c_size_t, _VP, _VP, _VP, _VP, _VP]),
+    "fpm_lj_forces_half": (_c.c_int, [_c.POINTER(fpm_box), _c.POINTER(fpm_grid), _c.c_int32, _VP, _VP, _VP,
+                                      _c.c_int32, _c.c_double, _c.c_double, _c.c_double, _VP, _VP, _VP, _c.c_size_t,
+                                      _VP, _c.c_size_t, _VP, _VP, _c.c_double, _VP]),
+    "fpm_lj_half_acc_bytes": (_c.c_int, [_c.c_int32, _c.POINTER(_c.c_size_t)]),
     "fpm_verlet_decode": (_c.c_int, [_c.POINTER(fpm_grid), _c.c_int32, _c.c_int32, _VP, _VP, _VP, _VP]),
     "fpm_verlet_check": (_c.c_int, [_c.POINTER(fpm_box), _c.c_int32, _c.c_int, _VP, _VP, _c.c_double, _VP, _VP]),
     "fpm_reduce_workspace": (_c.c_int, [_c.c_int32, _c.POINTER(fpm_grid), _c.POINTER(_c.c_size_t)]),
@@ -323,6 +329,29 @@ def fpm_verlet_build(box, grid, n, prec, pos, cell_start, r_list, cap, list_obj,
                                   float(r_list), int(cap), _ptr(list_obj), _nbytes(list_obj), _ptr(nn),
                                   _ptr(pos_ref), _ptr(d_status), _ptr(d_gate), _stream(stream)))
     _count((3 if n > 0 else 0) + (1 if d_gate is not None else 0))
+
+
+def fpm_verlet_build_half(box, grid, n, prec, pos, cell_start, r_list, cap, list_obj, nn, pos_ref=None,
+                          d_status=None, d_gate=None, stream=None):
+    _check(lib().fpm_verlet_build_half(_c.byref(box), _c.byref(grid), int(n), int(prec), _ptr(pos),
+                                       _ptr(cell_start), float(r_list), int(cap), _ptr(list_obj), _nbytes(list_obj),
+                                       _ptr(nn), _ptr(pos_ref), _ptr(d_status), _ptr(d_gate), _stream(stream)))
+    _count((3 if n > 0 else 0) + (1 if d_gate is not None else 0))
+
+
+def fpm_lj_half_acc_bytes(n: int) -> int:
+    b = _c.c_size_t(0)
+    _check(lib().fpm_lj_half_acc_bytes(int(n), _c.byref(b)))
+    return b.value
+
+
+def fpm_lj_forces_half(box, grid, n, pos, list_obj, nn, cap, eps, sigma, rc, force, d_energy, acc, workspace,
+                       d_status=None, vel=None, dt=0.0, stream=None):
+    _check(lib().fpm_lj_forces_half(_c.byref(box), _c.byref(grid), int(n), _ptr(pos), _ptr(list_obj), _ptr(nn),
+                                    int(cap), float(eps), float(sigma), float(rc), _ptr(force), _ptr(d_energy),
+                                    _ptr(acc), _nbytes(acc), _ptr(workspace), _nbytes(workspace), _ptr(d_status),
+                                    _ptr(vel), float(dt), _stream(stream)))
+    _count(2 if n > 0 else 0)
 
 
 def fpm_verlet_decode(grid, n, cap, list_obj, nn, out, stream=None):

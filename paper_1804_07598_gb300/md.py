@@ -31,7 +31,12 @@ def default_cap(rho: float, r_list: float) -> int:
 
 class LJSystem:
     def __init__(self, pos, vel, L, periodic=(1, 1, 1), eps=1.0, sigma=1.0, rc=2.5, skin=0.3, dt=0.005,
-                 precision="f32", cap=None, device="cuda"):
+                 precision="f32", cap=None, device="cuda", half=False):
+        """half: the symmetric sweep over a half list (each pair once,
+        fpm_verlet_build_half + fpm_lj_forces_half; single precision only)."""
+        if half and precision != "f32":
+            raise ValueError("the half-list sweep is single precision only")
+        self.half = bool(half)
         self.dtype = torch.float32 if precision == "f32" else torch.float64
         self.prec = fpm.FPM_F32 if precision == "f32" else fpm.FPM_F64
         self.device = torch.device(device)
@@ -47,6 +52,10 @@ class LJSystem:
         self.grid = fpm.fpm_grid_make(self.box, self.r_list, n)
         vol = float(np.prod(self.L))
         self.cap = int(cap) if cap else default_cap(max(n, 1) / vol, self.r_list)
+        if self.half and not cap:
+            # a half list holds about half the entries, but its counts spread
+            # more (a particle early in its cell's order lists the rest of it)
+            self.cap = max(32, (4 * self.cap // 5 + 7) // 8 * 8)
         self.ld = fpm.fpm_nbr_ld(n)
         dev, dt_ = self.device, self.dtype
         self.pos = torch.zeros((n, 4), dtype=dt_, device=dev)
@@ -66,6 +75,8 @@ class LJSystem:
         self.ws_cell = torch.zeros(fpm.fpm_celllist_workspace(n, self.grid, self.prec), dtype=torch.uint8, device=dev)
         self.ws_red = torch.zeros(fpm.fpm_reduce_workspace(n, self.grid), dtype=torch.uint8, device=dev)
         self.energy = torch.zeros(3, dtype=torch.float64, device=dev)
+        self.acc = (torch.zeros(fpm.fpm_lj_half_acc_bytes(n) // 8, dtype=torch.int64, device=dev) if self.half
+                    else None)
         self.kin = torch.zeros(4, dtype=torch.float64, device=dev)
         self._body = torch.cuda.Stream(device=dev)  # captures the conditional rebuild
         self._graph = None
@@ -106,8 +117,9 @@ class LJSystem:
         fpm.fpm_celllist_build(self.box, self.grid, self.n, self.prec, self.pos, self.vel, self.ids, self.pos,
                                self.vel, self.ids, self.cell_start, self.perm, self.ws_cell, self.status, gate,
                                stream=stream)
-        fpm.fpm_verlet_build(self.box, self.grid, self.n, self.prec, self.pos, self.cell_start, self.r_list,
-                             self.cap, self.nbr, self.nn, self.pos_ref, self.status, gate, stream=stream)
+        build = fpm.fpm_verlet_build_half if self.half else fpm.fpm_verlet_build
+        build(self.box, self.grid, self.n, self.prec, self.pos, self.cell_start, self.r_list, self.cap, self.nbr,
+              self.nn, self.pos_ref, self.status, gate, stream=stream)
 
     def _gated_rebuild(self):
         """The step's rebuild: a conditional graph node under capture, gated
@@ -119,12 +131,21 @@ class LJSystem:
             self.rebuild(gated=True)
 
     def compute_forces(self):
+        if self.half:
+            fpm.fpm_lj_forces_half(self.box, self.grid, self.n, self.pos, self.nbr, self.nn, self.cap, self.eps,
+                                   self.sigma, self.rc, self.force, self.energy, self.acc, self.ws_red, self.status)
+            return
         fpm.fpm_lj_forces(self.box, self.grid, self.n, self.prec, self.pos, self.nbr, self.nn, self.cap, self.eps,
                           self.sigma, self.rc, self.force, self.energy, self.ws_red, self.status)
 
     def forces_and_kick(self):
         """compute_forces, then the closing half-kick v += dt/2 F, in one
         launch (bit-identical to the two calls)."""
+        if self.half:
+            fpm.fpm_lj_forces_half(self.box, self.grid, self.n, self.pos, self.nbr, self.nn, self.cap, self.eps,
+                                   self.sigma, self.rc, self.force, self.energy, self.acc, self.ws_red, self.status,
+                                   self.vel, self.dt)
+            return
         fpm.fpm_lj_forces_kick(self.box, self.grid, self.n, self.prec, self.pos, self.nbr, self.nn, self.cap,
                                self.eps, self.sigma, self.rc, self.force, self.energy, self.ws_red, self.status,
                                self.vel, self.dt)
