@@ -10,9 +10,12 @@
 // 64-bit integers per staged slot.  One thread per home particle walks its
 // list; the particle's own force accumulates in registers in single
 // precision, and every pair's reaction -F_ij on the neighbour is added to the
-// neighbour's reaction slot as a fixed-point integer (units of 2^-32) by a
-// shared-memory atomic.  At the end of the tile each particle's own force
-// joins its own slot, and every piece of the neighbourhood is returned to the
+// neighbour's reaction slot as a fixed-point integer (units of 2^-32), held in
+// shared memory as two 32-bit sums per component (the multiples of 2^23 units
+// and the rest: native 32-bit shared atomics, where a 64-bit shared atomic
+// add is a compare-and-swap loop).  At the end of the tile each particle's own
+// force joins its own slot, the two sums of every component become one 64-bit
+// integer in place, and every piece of the neighbourhood is returned to the
 // global fixed-point force array with one bulk reduce-add from shared to
 // global memory (cp.reduce.async.bulk ... .add.u64): no per-element global
 // atomics.  Integer addition is exact and order-free, so the forces are
@@ -26,8 +29,46 @@
 
 namespace fpm {
 
-constexpr float kFixScale = 4294967296.0f;       // 2^32 fixed-point units per unit of force
-constexpr float kFixUnscale = 2.3283064365386963e-10f;  // 2^-32
+constexpr float kFixUnscale = 2.3283064365386963e-10f;  // 2^-32: force per fixed-point unit
+
+// Force component x as the fixed-point value x 2^32 split into hi 2^23 + lo:
+// hi = floor(x 2^9) and lo = the rest, rounded to an integer in [0, 2^23]
+// (the rest times 2^23 plus 2^23 lies in [2^23, 2^24], where the float
+// spacing is 1, so the fused multiply-add rounds it to an integer and its
+// bits minus those of 2^23 are that integer).
+__device__ __forceinline__ void fix_split(float x, int &hi, unsigned &lo)
+{
+    const float t = x * 512.0f;
+    const float hf = floorf(t);
+    hi = __float2int_rz(hf);
+    lo = __float_as_uint(__fmaf_rn(t - hf, 8388608.0f, 8388608.0f)) - 0x4B000000u;
+}
+
+__device__ __forceinline__ long long fix_join(int hi, unsigned lo) { return ((long long)hi << 23) + (long long)lo; }
+
+// Adds (x, y, z) to reaction slot s: three (lo, hi) pairs of 32-bit sums in
+// shared memory, or 64-bit integers in global memory.
+template <bool SMEM>
+__device__ __forceinline__ void fix_add(unsigned *R, unsigned long long *g, float x, float y, float z)
+{
+    int h0, h1, h2;
+    unsigned l0, l1, l2;
+    fix_split(x, h0, l0);
+    fix_split(y, h1, l1);
+    fix_split(z, h2, l2);
+    if (SMEM) {
+        atomicAdd(R, l0);
+        atomicAdd((int *)R + 1, h0);
+        atomicAdd(R + 2, l1);
+        atomicAdd((int *)R + 3, h1);
+        atomicAdd(R + 4, l2);
+        atomicAdd((int *)R + 5, h2);
+    } else {
+        atomicAdd(g, (unsigned long long)fix_join(h0, l0));
+        atomicAdd(g + 1, (unsigned long long)fix_join(h1, l1));
+        atomicAdd(g + 2, (unsigned long long)fix_join(h2, l2));
+    }
+}
 
 // The pair term of lj_pair for one half-list entry; returns the force factor
 // g = a / r2 (zero beyond the cutoff) with the separation in dx, dy, dz.
@@ -61,11 +102,10 @@ __device__ __forceinline__ float half_pair(const TileCfg &cfg, const BoxT<float>
 // did not fit, straight into the global array acc.
 template <int SEP, bool SMEM>
 __device__ __forceinline__ void half_sweep(const TileCfg &cfg, const BoxT<float> &box, const TileDesc &d,
-                                           const float4 *__restrict__ pos, const float4 *__restrict__ st,
-                                           unsigned long long *R, unsigned long long *acc, const float4 &pi,
-                                           uint32_t m, const uint32_t *__restrict__ col, int64_t ld,
-                                           const LJParams<float> &P, float q24, float &fx, float &fy, float &fz,
-                                           float &S12, float &S6, uint32_t &np)
+                                           const float4 *__restrict__ pos, const float4 *__restrict__ st, unsigned *R,
+                                           unsigned long long *acc, const float4 &pi, uint32_t m,
+                                           const uint32_t *__restrict__ col, int64_t ld, const LJParams<float> &P,
+                                           float &fx, float &fy, float &fz, float &S12, float &S6, uint32_t &np)
 {
     float4 pim = pi;
     if (SEP == 1) {
@@ -81,28 +121,23 @@ __device__ __forceinline__ void half_sweep(const TileCfg &cfg, const BoxT<float>
         fx += g * dx;
         fy += g * dy;
         fz += g * dz;
-        if (in) {  // the reaction -24 eps g d on the neighbour, in units of 2^-32
-            const float gq = -q24 * g;
-            const unsigned long long rx = (unsigned long long)__float2ll_rn(gq * dx);
-            const unsigned long long ry = (unsigned long long)__float2ll_rn(gq * dy);
-            const unsigned long long rz = (unsigned long long)__float2ll_rn(gq * dz);
-            unsigned long long *dst = SMEM ? R + 3 * s : acc + 3 * (size_t)staged_index(d, s);
-            atomicAdd(dst, rx);
-            atomicAdd(dst + 1, ry);
-            atomicAdd(dst + 2, rz);
+        if (in) {  // the reaction -24 eps g d on the neighbour
+            const float gq = -P.eps24 * g;
+            fix_add<SMEM>(R + 6 * s, SMEM ? nullptr : acc + 3 * (size_t)staged_index(d, s), gq * dx, gq * dy,
+                          gq * dz);
         }
     });
 }
 
 __global__ void __launch_bounds__(kTileThreads)
     k_lj_half_tiles(TileCfg cfg, BoxT<float> box, const float4 *__restrict__ pos, ListView lv,
-                    const uint32_t *__restrict__ nn, int64_t ld, int stage_cap, LJParams<float> P, float q24,
+                    const uint32_t *__restrict__ nn, int64_t ld, int stage_cap, LJParams<float> P,
                     unsigned long long *__restrict__ acc, Sched sched, double *part, double *out,
                     fpm_dev_status *status)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float4 *sp = (float4 *)smem_raw;
-    unsigned long long *R = (unsigned long long *)(smem_raw + (size_t)stage_cap * sizeof(float4));
+    unsigned *R = (unsigned *)(smem_raw + (size_t)stage_cap * sizeof(float4));  // [slot][3][lo, hi]
     __shared__ TileDesc d;
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t s_k;
@@ -122,10 +157,10 @@ __global__ void __launch_bounds__(kTileThreads)
         const bool in_smem = d.M <= stage_cap;
         if (!in_smem) note_spill(status);
         if (in_smem) {
-            // clear the reaction slots (three per staged slot, free slots included)
-            ulonglong2 *r2 = (ulonglong2 *)R;
+            // clear the reaction slots (24 bytes per staged slot, free slots included)
+            uint4 *r4 = (uint4 *)R;
             const int nz = (3 * d.M + 1) / 2;
-            for (int q = threadIdx.x; q < nz; q += blockDim.x) r2[q] = make_ulonglong2(0ull, 0ull);
+            for (int q = threadIdx.x; q < nz; q += blockDim.x) r4[q] = make_uint4(0u, 0u, 0u, 0u);
         }
         if (threadIdx.x == 0) {  // the home cells: the piece of the tile's own row (row 0) seen directly,
                                  // not through a periodic wall (a wall piece may hold a copy of cell a)
@@ -148,28 +183,35 @@ __global__ void __launch_bounds__(kTileThreads)
             uint32_t np = 0;
             if (in_smem) {
                 if (!d.slow)
-                    half_sweep<0, true>(cfg, box, d, pos, sp, R, acc, pi, m, words + i, ld, P, q24, fx, fy, fz, S12,
-                                        S6, np);
+                    half_sweep<0, true>(cfg, box, d, pos, sp, R, acc, pi, m, words + i, ld, P, fx, fy, fz, S12, S6,
+                                        np);
                 else if (!all_mode)
-                    half_sweep<1, true>(cfg, box, d, pos, sp, R, acc, pi, m, words + i, ld, P, q24, fx, fy, fz, S12,
-                                        S6, np);
+                    half_sweep<1, true>(cfg, box, d, pos, sp, R, acc, pi, m, words + i, ld, P, fx, fy, fz, S12, S6,
+                                        np);
                 else
-                    half_sweep<2, true>(cfg, box, d, pos, sp, R, acc, pi, m, words + i, ld, P, q24, fx, fy, fz, S12,
-                                        S6, np);
+                    half_sweep<2, true>(cfg, box, d, pos, sp, R, acc, pi, m, words + i, ld, P, fx, fy, fz, S12, S6,
+                                        np);
             } else {
-                half_sweep<2, false>(cfg, box, d, pos, sp, R, acc, pi, m, words + i, ld, P, q24, fx, fy, fz, S12, S6,
-                                     np);
+                half_sweep<2, false>(cfg, box, d, pos, sp, R, acc, pi, m, words + i, ld, P, fx, fy, fz, S12, S6, np);
             }
             // the particle's own force joins its slot (or its global row)
-            unsigned long long *dst = in_smem ? R + 3 * (s_home + (int)(i - d.h0)) : acc + 3 * (size_t)i;
-            atomicAdd(dst, (unsigned long long)__float2ll_rn(q24 * fx));
-            atomicAdd(dst + 1, (unsigned long long)__float2ll_rn(q24 * fy));
-            atomicAdd(dst + 2, (unsigned long long)__float2ll_rn(q24 * fz));
+            if (in_smem)
+                fix_add<true>(R + 6 * (s_home + (int)(i - d.h0)), nullptr, P.eps24 * fx, P.eps24 * fy, P.eps24 * fz);
+            else
+                fix_add<false>(nullptr, acc + 3 * (size_t)i, P.eps24 * fx, P.eps24 * fy, P.eps24 * fz);
             usum += P.eps4 * (S12 - S6);
             wsum += P.eps24 * (2.0f * S12 - S6);
             npsum += np;
         }
         __syncthreads();  // every reaction of the tile is in R
+        if (in_smem && staged) {  // each component's two 32-bit sums become one 64-bit integer, in place
+            uint2 *cell = (uint2 *)R;
+            for (int q = threadIdx.x; q < 3 * d.M; q += blockDim.x) {
+                const uint2 v = cell[q];
+                ((unsigned long long *)cell)[q] = (unsigned long long)fix_join((int)v.y, v.x);
+            }
+        }
+        __syncthreads();
         if (in_smem && staged && threadIdx.x < (unsigned)kMaxPieces) {
             // piece p's slots cover the even-aligned index range of its particles
             // (tile_geometry<true>): one bulk reduce-add of 24-byte rows per piece
@@ -181,7 +223,7 @@ __global__ void __launch_bounds__(kTileThreads)
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u64 [%0], [%1], %2;" ::"l"(
                                  acc + 3 * (size_t)g0),
-                             "r"(smem_u32(R + 3 * s0)), "r"(bytes)
+                             "r"(smem_u32(R + 6 * s0)), "r"(bytes)
                              : "memory");
                 asm volatile("cp.async.bulk.commit_group;" ::: "memory");
                 issued = true;
@@ -272,14 +314,13 @@ extern "C" fpm_status fpm_lj_forces_half(const fpm_box *box, const fpm_grid *gri
     P.eps4 = (float)(4.0 * eps);
     P.sig2 = (float)(sigma * sigma);
     P.rc2 = (float)(rc * rc);
-    const float q24 = (float)(24.0 * eps) * kFixScale;
     // staged positions and the reaction slots: 16 + 24 bytes per staged slot
     const int sc = stage_capacity(n, *grid, sizeof(float4) + 3 * sizeof(unsigned long long));
     const size_t smem = (size_t)sc * (sizeof(float4) + 3 * sizeof(unsigned long long));
     smem_opt_in((const void *)k_lj_half_tiles);
     const int blocks = persistent_blocks((const void *)k_lj_half_tiles, kTileThreads, smem, *grid, cfg.ntiles);
     k_lj_half_tiles<<<blocks, kTileThreads, smem, st>>>(cfg, make_box<float>(*box), (const float4 *)pos,
-                                                        list_view(list, L), nn, L.ld, sc, P, q24,
+                                                        list_view(list, L), nn, L.ld, sc, P,
                                                         (unsigned long long *)acc, Sched{r.work, r.done}, r.part,
                                                         d_energy, d_status);
     k_lj_half_finish<<<(n + 255) / 256, 256, 0, st>>>(n, (unsigned long long *)acc, (float4 *)force, (float4 *)vel,

@@ -623,20 +623,25 @@ __device__ __forceinline__ void for_each_entry(uint32_t m, const uint32_t *__res
 // (entries beyond cap are counted, not stored).  Candidates are tested 32 at
 // a time into a bit mask (one shift-in per test); then only the set bits are
 // appended, in increasing slot order.
-// HALF: a half-list tile; in its own row only the slots after `self` (the
-// rest of the home cell, then the next cell) are candidates, so that each pair
-// is listed once.
+// HALF: a half-list tile, each pair listed once.  In its own row the
+// candidates are the home cell's particles on one side of `self` and the next
+// cell (th + 1); the home cell is split circularly so that every particle
+// gets the same count: with c particles and self at rank q, the particles at
+// ranks q + 1 .. q + (c - 1)/2 (mod c), and for even c also q + c/2 when
+// q < c/2.  (Taking every later particle instead would give the cell's first
+// particle c - 1 candidates and its last none: uneven lists, idle lanes.)
 template <bool FAST, bool SMEM, typename T, bool HALF = false>
 __device__ __forceinline__ uint32_t scan_candidates(const TileCfg &cfg, const BoxT<T> &box, const TileGeom &g,
                                                     const TileDesc &d, const V4<T> *__restrict__ pos,
                                                     const V4<T> *__restrict__ st, const V4<T> &pi, int self,
-                                                    int t0, int t1, T rl2, int cap, int64_t ld, uint32_t i,
+                                                    int th, int t0, int t1, T rl2, int cap, int64_t ld, uint32_t i,
                                                     uint32_t *__restrict__ words)
 {
     uint32_t cnt = 0, pending = 0;
     const uint32_t ucap = (uint32_t)cap;
-    for (int r = 0; r < g.nrows; ++r) {
-        const int s0 = (HALF && r == g.mid_row) ? self + 1 : g.off[r][t0], s1 = g.off[r][t1 + 1];
+    // tests the staged slots [s0, s1) 32 at a time into a bit mask, then
+    // appends the hits in increasing slot order
+    auto scan_range = [&](int s0, int s1) {
         for (int base = s0; base < s1; base += 32) {
             const int e = base + 32 < s1 ? base + 32 : s1;
             uint32_t mask = 0;
@@ -647,7 +652,7 @@ __device__ __forceinline__ uint32_t scan_candidates(const TileCfg &cfg, const Bo
                 const T r2 = tile_sep<FAST>(pi, pj, box, cfg, dx, dy, dz);
                 mask = (mask << 1) | (r2 < rl2 ? 1u : 0u);
             }
-            if (self >= base && self < e) mask &= ~(1u << (e - 1 - self));
+            if (!HALF && self >= base && self < e) mask &= ~(1u << (e - 1 - self));
             while (mask) {
                 const int bit = 31 - __clz(mask);
                 mask &= ~(1u << bit);
@@ -659,16 +664,24 @@ __device__ __forceinline__ uint32_t scan_candidates(const TileCfg &cfg, const Bo
                 ++cnt;
             }
         }
+    };
+    for (int r = 0; r < g.nrows; ++r) {
+        if (HALF && r == g.mid_row) {
+            const int c = g.cnt[r][th], c0 = g.off[r][th], q = self - c0;
+            const int h = (c - 1) / 2 + (((c & 1) == 0 && q < c / 2) ? 1 : 0);
+            const int end = self + 1 + h;
+            scan_range(self + 1, end < c0 + c ? end : c0 + c);
+            if (end > c0 + c) scan_range(c0, c0 + (end - (c0 + c)));
+            if (t1 > th) scan_range(g.off[r][th + 1], g.off[r][th + 1] + g.cnt[r][th + 1]);
+        } else {
+            scan_range(g.off[r][t0], g.off[r][t1 + 1]);
+        }
     }
     const uint32_t stored = cnt < ucap ? cnt : ucap;
     if (stored & 1u) words[(int64_t)(stored >> 1) * ld + i] = pending;
     return cnt;
 }
 
-// One tile of the Verlet build (all threads of the block call it): its
-// geometry and descriptor, the staging of its neighbourhood, and the scan of
-// every home particle (pos_ref[i] := pos[i] when pos_ref is given).  Returns
-// the largest candidate count this thread saw.
 // The free slots of a staged half-list tile (between its pieces) are set to
 // NaN positions, never inside any radius (the copies do not write them).
 // Lanes of warp 0, one per piece; the caller's next barrier publishes them.
@@ -695,6 +708,10 @@ __device__ __forceinline__ void fill_free_slots(const TileDesc &d, V4<T> *__rest
     }
 }
 
+// One tile of the Verlet build (all threads of the block call it): its
+// geometry and descriptor, the staging of its neighbourhood, and the scan of
+// every home particle (pos_ref[i] := pos[i] when pos_ref is given).  Returns
+// the largest candidate count this thread saw.
 template <typename T, bool HALF = false>
 __device__ __forceinline__ uint32_t verlet_tile(const TileCfg &cfg, const BoxT<T> &box, int tile,
                                                 const uint32_t *__restrict__ cs, const V4<T> *__restrict__ pos,
@@ -729,12 +746,12 @@ __device__ __forceinline__ uint32_t verlet_tile(const TileCfg &cfg, const BoxT<T
         const int t1 = th + 1 < g.nseq ? th + 1 : g.nseq - 1;
         uint32_t c;
         if (in_smem) {
-            c = d.slow ? scan_candidates<false, true, T, HALF>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld,
+            c = d.slow ? scan_candidates<false, true, T, HALF>(cfg, box, g, d, pos, sp, pi, self, th, t0, t1, rl2, cap, ld,
                                                               i, words)
-                       : scan_candidates<true, true, T, HALF>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld,
+                       : scan_candidates<true, true, T, HALF>(cfg, box, g, d, pos, sp, pi, self, th, t0, t1, rl2, cap, ld,
                                                              i, words);
         } else {
-            c = scan_candidates<false, false, T, HALF>(cfg, box, g, d, pos, sp, pi, self, t0, t1, rl2, cap, ld, i,
+            c = scan_candidates<false, false, T, HALF>(cfg, box, g, d, pos, sp, pi, self, th, t0, t1, rl2, cap, ld, i,
                                                        words);
         }
         nn[i] = c < (uint32_t)cap ? c : (uint32_t)cap;
