@@ -48,7 +48,7 @@ FALLBACK_HBM_GBS = 6800.0
 # profiling target `--profile forces`, valid only while its source files hash
 # to `sha` (otherwise the bench line reports the traffic as null).
 NCU_TRAFFIC = {"k_lj_tiles<float>": {"files": ["lj.cu", "lj_pair.cuh", "tiles.cuh", "fpm_common.cuh", "reduce.cuh"],
-                                    "sha": "15d8bde8a2a056d6", "bytes_per_launch": 184146176}}
+                                    "sha": "9413928160f3a1c8", "bytes_per_launch": 183851264}}
 
 
 def parse():
@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--profile", default=None, choices=["forces", "step", "sph", "verlet", "batch", "adjoint",
-                                                         "celllist", "dem", "p2m"],
+                                                         "celllist", "dem", "p2m", "half"],
                     help="profiling target for ncu: build the 1M-atom system, then run --steps force sweeps "
                          "or eager steps (no timing, no JSON line)")
     ap.add_argument("--fp64-steps", type=int, default=100)
@@ -758,7 +758,9 @@ def run_ours(args, ws, rank, local):
                      "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                              "peak_kind": f"{peak_kind} (burst)", "alg_bytes_per_launch": alg_bytes}},
         "e2e": {"value": ws * args.e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h,
+                "transfer": "pinned host buffers in the packed x, y, z layout, copied in three overlapped pieces "
+                            "per direction (copy engines), packed / unpacked on the device; energies copied back"},
         "adjoint": adj,
         "sph": sph,
         "sph_full_run": sph_full,
@@ -912,9 +914,10 @@ def run_profile_target(args):
         return
     wl = inputs.WORKLOADS[WORKLOAD]
     pos, vel, L = inputs.lj_state(wl)
-    s = LJSystem(pos, vel, L, eps=wl.eps, sigma=wl.sigma, rc=wl.rc, skin=wl.skin, dt=wl.dt, precision="f32")
+    s = LJSystem(pos, vel, L, eps=wl.eps, sigma=wl.sigma, rc=wl.rc, skin=wl.skin, dt=wl.dt, precision="f32",
+                 half=(args.profile == "half"))
     for _ in range(args.steps):
-        if args.profile == "forces":
+        if args.profile in ("forces", "half"):
             s.compute_forces()
         elif args.profile == "verlet":
             s.rebuild()

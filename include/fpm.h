@@ -386,10 +386,15 @@ fpm_status fpm_vv_drift_check(const fpm_box *box, int32_t n, fpm_prec prec, doub
                               fpm_stream stream);
 
 /* Transfers in the host's layout: packed (x, y, z) triples (float or double
- * [3n], device memory) to and from the 4-vector state (float4|double4 [n]).
+ * [3n]) to and from the 4-vector state (float4|double4 [n], device memory).
  * unpack writes x, y, z of dst4 and keeps its w; pack writes 3n values.
  * With these, an end-to-end step moves 12 (24) bytes per vector across the
- * host link instead of 16 (32). */
+ * host link instead of 16 (32).  The packed array may be device memory or
+ * page-locked host memory mapped into the device's address space (what
+ * cudaHostAlloc gives under unified addressing): the kernel then reads or
+ * writes the host's buffer directly across the host link, with no separate
+ * copy.  Single precision with a 16-byte aligned packed array moves four
+ * particles per thread in 16-byte words. */
 fpm_status fpm_unpack_xyz(int32_t n, fpm_prec prec, const void *src_xyz, void *dst4, fpm_stream stream);
 fpm_status fpm_pack_xyz(int32_t n, fpm_prec prec, const void *src4, void *dst_xyz, fpm_stream stream);
 

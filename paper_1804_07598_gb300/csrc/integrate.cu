@@ -179,6 +179,40 @@ __global__ void k_pack_xyz(int n, const V4<T> *__restrict__ src, T *__restrict__
     dst[3 * (size_t)i + 2] = v.z;
 }
 
+// Single precision with 16-byte aligned packed arrays: thread t moves
+// particles 4t .. 4t+3, reading or writing their twelve packed values as three
+// 16-byte words, so a warp touches 1536 contiguous bytes of the packed array
+// per instruction triple (full-width transactions, which matters most when
+// the packed array is pinned host memory read or written across the host
+// link).  The last n % 4 particles go through the scalar kernels.
+__global__ void k_unpack_xyz4(int nq, const float4 *__restrict__ src, float4 *__restrict__ dst)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nq) return;
+    const float4 a = src[3 * (size_t)t], b = src[3 * (size_t)t + 1], c = src[3 * (size_t)t + 2];
+    float4 *d = dst + 4 * (size_t)t;
+    float4 p0 = d[0], p1 = d[1], p2 = d[2], p3 = d[3];
+    p0.x = a.x; p0.y = a.y; p0.z = a.z;
+    p1.x = a.w; p1.y = b.x; p1.z = b.y;
+    p2.x = b.z; p2.y = b.w; p2.z = c.x;
+    p3.x = c.y; p3.y = c.z; p3.z = c.w;
+    d[0] = p0;
+    d[1] = p1;
+    d[2] = p2;
+    d[3] = p3;
+}
+
+__global__ void k_pack_xyz4(int nq, const float4 *__restrict__ src, float4 *__restrict__ dst)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nq) return;
+    const float4 *s = src + 4 * (size_t)t;
+    const float4 p0 = s[0], p1 = s[1], p2 = s[2], p3 = s[3];
+    dst[3 * (size_t)t] = make_float4(p0.x, p0.y, p0.z, p1.x);
+    dst[3 * (size_t)t + 1] = make_float4(p1.y, p1.z, p2.x, p2.y);
+    dst[3 * (size_t)t + 2] = make_float4(p2.z, p3.x, p3.y, p3.z);
+}
+
 }  // namespace fpm
 
 extern "C" fpm_status fpm_unpack_xyz(int32_t n, fpm_prec prec, const void *src_xyz, void *dst4, fpm_stream stream)
@@ -188,8 +222,18 @@ extern "C" fpm_status fpm_unpack_xyz(int32_t n, fpm_prec prec, const void *src_x
     if (n == 0) return FPM_OK;
     const unsigned blocks = (unsigned)((n + 255) / 256);
     cudaStream_t st = (cudaStream_t)stream;
-    if (prec == FPM_F32) k_unpack_xyz<float><<<blocks, 256, 0, st>>>(n, (const float *)src_xyz, (float4 *)dst4);
-    else k_unpack_xyz<double><<<blocks, 256, 0, st>>>(n, (const double *)src_xyz, (double4_32a *)dst4);
+    if (prec == FPM_F32 && ((uintptr_t)src_xyz & 15u) == 0) {
+        const int nq = n / 4, r = n - 4 * nq;
+        if (nq > 0)
+            k_unpack_xyz4<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(nq, (const float4 *)src_xyz, (float4 *)dst4);
+        if (r > 0)
+            k_unpack_xyz<float><<<1, 32, 0, st>>>(r, (const float *)src_xyz + 12 * (size_t)nq,
+                                                 (float4 *)dst4 + 4 * (size_t)nq);
+    } else if (prec == FPM_F32) {
+        k_unpack_xyz<float><<<blocks, 256, 0, st>>>(n, (const float *)src_xyz, (float4 *)dst4);
+    } else {
+        k_unpack_xyz<double><<<blocks, 256, 0, st>>>(n, (const double *)src_xyz, (double4_32a *)dst4);
+    }
     return fpm_check_launch("fpm_unpack_xyz");
 }
 
@@ -200,7 +244,17 @@ extern "C" fpm_status fpm_pack_xyz(int32_t n, fpm_prec prec, const void *src4, v
     if (n == 0) return FPM_OK;
     const unsigned blocks = (unsigned)((n + 255) / 256);
     cudaStream_t st = (cudaStream_t)stream;
-    if (prec == FPM_F32) k_pack_xyz<float><<<blocks, 256, 0, st>>>(n, (const float4 *)src4, (float *)dst_xyz);
-    else k_pack_xyz<double><<<blocks, 256, 0, st>>>(n, (const double4_32a *)src4, (double *)dst_xyz);
+    if (prec == FPM_F32 && ((uintptr_t)dst_xyz & 15u) == 0) {
+        const int nq = n / 4, r = n - 4 * nq;
+        if (nq > 0)
+            k_pack_xyz4<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(nq, (const float4 *)src4, (float4 *)dst_xyz);
+        if (r > 0)
+            k_pack_xyz<float><<<1, 32, 0, st>>>(r, (const float4 *)src4 + 4 * (size_t)nq,
+                                               (float *)dst_xyz + 12 * (size_t)nq);
+    } else if (prec == FPM_F32) {
+        k_pack_xyz<float><<<blocks, 256, 0, st>>>(n, (const float4 *)src4, (float *)dst_xyz);
+    } else {
+        k_pack_xyz<double><<<blocks, 256, 0, st>>>(n, (const double4_32a *)src4, (double *)dst_xyz);
+    }
     return fpm_check_launch("fpm_pack_xyz");
 }

@@ -615,11 +615,23 @@ def fpm_batch_lj_forces(batch, d_reps, pos, list_obj, nn, cap, eps, sigma, rc, f
 
 # ------------------------------------------------------------------ host-layout transfers
 
+def _host_or_device_ptr(t):
+    """A device tensor, or a pinned host tensor (mapped into the device's
+    address space): the packed side of fpm_pack_xyz / fpm_unpack_xyz."""
+    if t is not None and not isinstance(t, int) and not t.is_cuda:
+        if not t.is_pinned():
+            raise ValueError("libfpm takes device tensors or pinned host tensors here")
+        if not t.is_contiguous():
+            raise ValueError("libfpm takes contiguous tensors only")
+        return t.data_ptr()
+    return _ptr(t)
+
+
 def fpm_unpack_xyz(n, prec, src_xyz, dst4, stream=None):
-    _check(lib().fpm_unpack_xyz(int(n), int(prec), _ptr(src_xyz), _ptr(dst4), _stream(stream)))
+    _check(lib().fpm_unpack_xyz(int(n), int(prec), _host_or_device_ptr(src_xyz), _ptr(dst4), _stream(stream)))
     _count(1 if n > 0 else 0)
 
 
 def fpm_pack_xyz(n, prec, src4, dst_xyz, stream=None):
-    _check(lib().fpm_pack_xyz(int(n), int(prec), _ptr(src4), _ptr(dst_xyz), _stream(stream)))
+    _check(lib().fpm_pack_xyz(int(n), int(prec), _ptr(src4), _host_or_device_ptr(dst_xyz), _stream(stream)))
     _count(1 if n > 0 else 0)

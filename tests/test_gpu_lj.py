@@ -193,6 +193,20 @@ def test_pack_unpack_xyz(cuda, prec):
     fpm.fpm_unpack_xyz(n, fp, xyz, y4)
     torch.cuda.synchronize()
     assert torch.equal(xyz, x4[:, :3]) and torch.equal(y4, x4)
+    # the packed side in pinned host memory (read and written across the host
+    # link by the kernels), and a packed array that starts off a 16-byte
+    # boundary (the one-particle-per-thread path); n = 100003 leaves a tail of 3
+    hb = torch.zeros(3 * n + 1, dtype=dt_).pin_memory()
+    for off in (0, 1):
+        h = hb[off:off + 3 * n]
+        fpm.fpm_pack_xyz(n, fp, x4, h)
+        torch.cuda.synchronize()
+        assert torch.equal(h.view(n, 3), x4[:, :3].cpu())
+        z4 = torch.full_like(x4, -1.0)
+        z4[:, 3] = w
+        fpm.fpm_unpack_xyz(n, fp, h, z4)
+        torch.cuda.synchronize()
+        assert torch.equal(z4, x4)
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
