@@ -755,6 +755,16 @@ fpm_status fpm_batch_lj_forces(const fpm_batch *batch, const fpm_replica *d_reps
                                double rc, void *force, double *d_energy, void *workspace,
                                size_t workspace_bytes, fpm_dev_status *d_status, fpm_stream stream);
 
+/* fpm_batch_lj_forces and the closing half-kick of velocity Verlet in the same
+ * launch (as fpm_lj_forces_kick): after F_i is written, vel[i] += dt/2 F_i,
+ * bit-identical to fpm_batch_lj_forces followed by fpm_vv_step(half = 1).
+ * vel: [n_total] float4, not aliasing pos or force. */
+fpm_status fpm_batch_lj_forces_kick(const fpm_batch *batch, const fpm_replica *d_reps, const void *pos,
+                                    const void *list, const uint32_t *nn, int32_t cap, double eps, double sigma,
+                                    double rc, void *force, double *d_energy, void *workspace,
+                                    size_t workspace_bytes, fpm_dev_status *d_status, void *vel, double dt,
+                                    fpm_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

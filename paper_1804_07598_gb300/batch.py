@@ -7,8 +7,8 @@ One step (all on the current stream, no host synchronisation):
                                     in which a particle moved > skin/2
     fpm_batch_celllist_build        re-bin and reorder the flagged replicas
     fpm_batch_verlet_build          their tiles and lists; flags cleared
-    fpm_batch_lj_forces             F, and U, W, pairs per replica
-    fpm_vv_step(half=1)             v += dt/2 F
+    fpm_batch_lj_forces_kick        F, and U, W, pairs per replica; then
+                                    v += dt/2 F in the same launch
 """
 from __future__ import annotations
 
@@ -101,12 +101,17 @@ class LJBatch:
         fpm.fpm_batch_lj_forces(self.batch, self.d_reps, self.pos, self.nbr, self.nn, self.cap, self.eps, self.sigma,
                                 self.rc, self.force, self.energy, self.ws_red, self.status)
 
+    def forces_and_kick(self):
+        """compute_forces and the closing half-kick v += dt/2 F in one launch."""
+        fpm.fpm_batch_lj_forces_kick(self.batch, self.d_reps, self.pos, self.nbr, self.nn, self.cap, self.eps,
+                                     self.sigma, self.rc, self.force, self.energy, self.ws_red, self.status,
+                                     self.vel, self.dt)
+
     def _step(self):
         fpm.fpm_batch_drift_check(self.batch, self.d_reps, self.dt, self.pos, self.vel, self.force, self.pos_ref,
                                   self.skin, self.flags)
         self.rebuild(gated=True)
-        self.compute_forces()
-        fpm.fpm_vv_step(self.boxes[0], self.n, fpm.FPM_F32, 1, self.dt, None, self.vel, self.force)
+        self.forces_and_kick()
 
     # -- public -----------------------------------------------------------
     def step(self, nsteps: int = 1):

@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(kTileThreads)
     k_blj_tiles(int ntiles, const fpm_replica *__restrict__ reps, const uint32_t *__restrict__ map,
                 const float4 *__restrict__ pos, ListView lv, const uint32_t *__restrict__ nn, int64_t ld, int stage_cap, LJParams<float> P,
                 float4 *__restrict__ force, Sched sched, double *part, uint32_t *rep_done, double *out,
-                fpm_dev_status *status)
+                fpm_dev_status *status, float4 *__restrict__ vel, float hdt)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float4 *sp = (float4 *)smem_raw;
@@ -391,9 +391,11 @@ __global__ void __launch_bounds__(kTileThreads)
                 float fx = 0.0f, fy = 0.0f, fz = 0.0f, u = 0.0f, w = 0.0f;
                 uint32_t np = 0;
                 if (in_smem) {
-                    if (d.slow)
+                    if (d.slow && (cfg.mode[0] == kModeAll || cfg.mode[1] == kModeAll || cfg.mode[2] == kModeAll))
                         lj_sweep<float, false, true>(cfg, box, d, pos, sp, pi, m, words + i, ld, P, fx, fy, fz, u, w,
                                                      np);
+                    else if (d.slow)
+                        lj_sweep_wall<float>(box, sp, pi, m, words + i, ld, P, fx, fy, fz, u, w, np);
                     else
                         lj_sweep<float, true, true>(cfg, box, d, pos, sp, pi, m, words + i, ld, P, fx, fy, fz, u, w,
                                                     np);
@@ -407,6 +409,13 @@ __global__ void __launch_bounds__(kTileThreads)
                 f.z = P.eps24 * fz;
                 f.w = 0.5f * P.eps4 * u;
                 force[i] = f;
+                if (vel) {  // the closing half-kick of velocity Verlet, v += dt/2 F
+                    float4 v = vel[i];
+                    v.x += hdt * f.x;
+                    v.y += hdt * f.y;
+                    v.z += hdt * f.z;
+                    vel[i] = v;
+                }
                 usum += P.eps4 * u;
                 wsum += P.eps24 * w;
                 npsum += np;
@@ -684,10 +693,10 @@ extern "C" fpm_status fpm_batch_workspace(const fpm_batch *batch, size_t *bytes)
     return FPM_OK;
 }
 
-extern "C" fpm_status fpm_batch_lj_forces(const fpm_batch *batch, const fpm_replica *d_reps, const void *pos,
-                                          const void *list, const uint32_t *nn, int32_t cap, double eps,
-                                          double sigma, double rc, void *force, double *d_energy, void *workspace,
-                                          size_t workspace_bytes, fpm_dev_status *d_status, fpm_stream stream)
+static fpm_status batch_lj(const fpm_batch *batch, const fpm_replica *d_reps, const void *pos, const void *list,
+                           const uint32_t *nn, int32_t cap, double eps, double sigma, double rc, void *force,
+                           double *d_energy, void *workspace, size_t workspace_bytes, fpm_dev_status *d_status,
+                           void *vel, double dt, fpm_stream stream)
 {
     fpm_status s = batch_ok(batch, d_reps, "fpm_batch_lj_forces");
     if (s != FPM_OK) return s;
@@ -719,6 +728,27 @@ extern "C" fpm_status fpm_batch_lj_forces(const fpm_batch *batch, const fpm_repl
         nt, d_reps, (const uint32_t *)((const char *)list + off_map), (const float4 *)pos, list_view(list, L), nn,
         L.ld, sc, P, (float4 *)force,
         Sched{(unsigned *)(w + 16), (unsigned *)(w + 32)}, (double *)(w + 256), (uint32_t *)(w + off_done),
-        d_energy, d_status);
+        d_energy, d_status, (float4 *)vel, (float)(0.5 * dt));
     return fpm_check_launch("fpm_batch_lj_forces");
+}
+
+extern "C" fpm_status fpm_batch_lj_forces(const fpm_batch *batch, const fpm_replica *d_reps, const void *pos,
+                                          const void *list, const uint32_t *nn, int32_t cap, double eps,
+                                          double sigma, double rc, void *force, double *d_energy, void *workspace,
+                                          size_t workspace_bytes, fpm_dev_status *d_status, fpm_stream stream)
+{
+    return batch_lj(batch, d_reps, pos, list, nn, cap, eps, sigma, rc, force, d_energy, workspace, workspace_bytes,
+                    d_status, nullptr, 0.0, stream);
+}
+
+extern "C" fpm_status fpm_batch_lj_forces_kick(const fpm_batch *batch, const fpm_replica *d_reps, const void *pos,
+                                               const void *list, const uint32_t *nn, int32_t cap, double eps,
+                                               double sigma, double rc, void *force, double *d_energy,
+                                               void *workspace, size_t workspace_bytes, fpm_dev_status *d_status,
+                                               void *vel, double dt, fpm_stream stream)
+{
+    if (!batch || (batch->n_total > 0 && !vel) || (vel && (vel == pos || vel == force)))
+        return fpm_fail(FPM_ERR_INVALID, "fpm_batch_lj_forces_kick: null vel, or vel aliases pos or force");
+    return batch_lj(batch, d_reps, pos, list, nn, cap, eps, sigma, rc, force, d_energy, workspace, workspace_bytes,
+                    d_status, vel, dt, stream);
 }

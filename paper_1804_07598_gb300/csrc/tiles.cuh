@@ -630,7 +630,9 @@ __device__ __forceinline__ void for_each_entry(uint32_t m, const uint32_t *__res
 // ranks q + 1 .. q + (c - 1)/2 (mod c), and for even c also q + c/2 when
 // q < c/2.  (Taking every later particle instead would give the cell's first
 // particle c - 1 candidates and its last none: uneven lists, idle lanes.)
-template <bool FAST, bool SMEM, typename T, bool HALF = false>
+// SEP: 0 a tile without wall flags (tile_sep<true>), 1 a tile with wall flags
+// and no "all"-mode dimension (tile_sep_wall), 2 any tile (tile_sep<false>).
+template <int SEP, bool SMEM, typename T, bool HALF = false>
 __device__ __forceinline__ uint32_t scan_candidates(const TileCfg &cfg, const BoxT<T> &box, const TileGeom &g,
                                                     const TileDesc &d, const V4<T> *__restrict__ pos,
                                                     const V4<T> *__restrict__ st, const V4<T> &pi, int self,
@@ -639,6 +641,12 @@ __device__ __forceinline__ uint32_t scan_candidates(const TileCfg &cfg, const Bo
 {
     uint32_t cnt = 0, pending = 0;
     const uint32_t ucap = (uint32_t)cap;
+    V4<T> pim = pi;  // the home coordinates x_i - L of the wall path
+    if (SEP == 1) {
+        pim.x = rsub(pi.x, box.L[0]);
+        pim.y = rsub(pi.y, box.L[1]);
+        pim.z = rsub(pi.z, box.L[2]);
+    }
     // tests the staged slots [s0, s1) 32 at a time into a bit mask, then
     // appends the hits in increasing slot order
     auto scan_range = [&](int s0, int s1) {
@@ -649,7 +657,9 @@ __device__ __forceinline__ uint32_t scan_candidates(const TileCfg &cfg, const Bo
             for (int s = base; s < e; ++s) {
                 const V4<T> pj = SMEM ? st[s] : staged_global(d, box, pos, s);
                 T dx, dy, dz;
-                const T r2 = tile_sep<FAST>(pi, pj, box, cfg, dx, dy, dz);
+                const T r2 = SEP == 0   ? tile_sep<true>(pi, pj, box, cfg, dx, dy, dz)
+                             : SEP == 1 ? tile_sep_wall(pi, pim, pj, dx, dy, dz)
+                                        : tile_sep<false>(pi, pj, box, cfg, dx, dy, dz);
                 mask = (mask << 1) | (r2 < rl2 ? 1u : 0u);
             }
             if (!HALF && self >= base && self < e) mask &= ~(1u << (e - 1 - self));
@@ -734,6 +744,7 @@ __device__ __forceinline__ uint32_t verlet_tile(const TileCfg &cfg, const BoxT<T
         return 0u;
     }
     uint32_t maxc = 0;
+    const bool all_mode = cfg.mode[0] == kModeAll || cfg.mode[1] == kModeAll || cfg.mode[2] == kModeAll;
     for (uint32_t i = d.h0 + threadIdx.x; i < d.h1; i += blockDim.x) {
         const V4<T> pi = pos[i];
         if (pos_ref) pos_ref[i] = pi;
@@ -745,14 +756,15 @@ __device__ __forceinline__ uint32_t verlet_tile(const TileCfg &cfg, const BoxT<T
         const int t0 = th > 0 ? th - 1 : 0;
         const int t1 = th + 1 < g.nseq ? th + 1 : g.nseq - 1;
         uint32_t c;
-        if (in_smem) {
-            c = d.slow ? scan_candidates<false, true, T, HALF>(cfg, box, g, d, pos, sp, pi, self, th, t0, t1, rl2, cap, ld,
-                                                              i, words)
-                       : scan_candidates<true, true, T, HALF>(cfg, box, g, d, pos, sp, pi, self, th, t0, t1, rl2, cap, ld,
-                                                             i, words);
+        if (in_smem && !d.slow) {
+            c = scan_candidates<0, true, T, HALF>(cfg, box, g, d, pos, sp, pi, self, th, t0, t1, rl2, cap, ld, i, words);
+        } else if (in_smem && !all_mode) {
+            c = scan_candidates<1, true, T, HALF>(cfg, box, g, d, pos, sp, pi, self, th, t0, t1, rl2, cap, ld, i, words);
+        } else if (in_smem) {
+            c = scan_candidates<2, true, T, HALF>(cfg, box, g, d, pos, sp, pi, self, th, t0, t1, rl2, cap, ld, i, words);
         } else {
-            c = scan_candidates<false, false, T, HALF>(cfg, box, g, d, pos, sp, pi, self, th, t0, t1, rl2, cap, ld, i,
-                                                       words);
+            c = scan_candidates<2, false, T, HALF>(cfg, box, g, d, pos, sp, pi, self, th, t0, t1, rl2, cap, ld, i,
+                                                   words);
         }
         nn[i] = c < (uint32_t)cap ? c : (uint32_t)cap;
         if (c > (uint32_t)cap) latch_flag(st, FPM_FLAG_CAPACITY);

@@ -172,6 +172,9 @@ _SIG = {
     "fpm_batch_workspace": (_c.c_int, [_c.POINTER(fpm_batch), _c.POINTER(_c.c_size_t)]),
     "fpm_batch_lj_forces": (_c.c_int, [_c.POINTER(fpm_batch), _VP, _VP, _VP, _VP, _c.c_int32, _c.c_double,
                                        _c.c_double, _c.c_double, _VP, _VP, _VP, _c.c_size_t, _VP, _VP]),
+    "fpm_batch_lj_forces_kick": (_c.c_int, [_c.POINTER(fpm_batch), _VP, _VP, _VP, _VP, _c.c_int32, _c.c_double,
+                                            _c.c_double, _c.c_double, _VP, _VP, _VP, _c.c_size_t, _VP, _VP,
+                                            _c.c_double, _VP]),
 }
 
 
@@ -603,6 +606,15 @@ def fpm_batch_workspace(batch) -> int:
     n = _c.c_size_t()
     _check(lib().fpm_batch_workspace(_c.byref(batch), _c.byref(n)))
     return n.value
+
+
+def fpm_batch_lj_forces_kick(batch, d_reps, pos, list_obj, nn, cap, eps, sigma, rc, force, d_energy, workspace,
+                             d_status, vel, dt, stream=None):
+    _check(lib().fpm_batch_lj_forces_kick(_c.byref(batch), _ptr(d_reps), _ptr(pos), _ptr(list_obj), _ptr(nn),
+                                          int(cap), float(eps), float(sigma), float(rc), _ptr(force),
+                                          _ptr(d_energy), _ptr(workspace), _nbytes(workspace), _ptr(d_status),
+                                          _ptr(vel), float(dt), _stream(stream)))
+    _count(1)
 
 
 def fpm_batch_lj_forces(batch, d_reps, pos, list_obj, nn, cap, eps, sigma, rc, force, d_energy=None,

@@ -248,3 +248,21 @@ def test_batch_edge_cases(cuda):
                 continue
             check_lists(b, r, pref, nbr, nn)
             check_forces(b, r, pos, force, energy)
+
+
+def test_batch_forces_kick_equals_split(cuda):
+    """fpm_batch_lj_forces_kick writes the forces and energies of
+    fpm_batch_lj_forces and the velocities of a separate half-kick, bit for
+    bit (replicas with walls on every side and all-pairs replicas included)."""
+    b = LJBatch(small_ensemble())
+    b.compute_forces()
+    torch.cuda.synchronize()
+    f0, e0, v0 = b.force.clone(), b.energy.clone(), b.vel.clone()
+    fpm.fpm_vv_step(b.boxes[0], b.n, fpm.FPM_F32, 1, b.dt, None, b.vel, b.force)
+    v_split = b.vel.clone()
+    b.vel.copy_(v0)
+    b.force.zero_()
+    b.forces_and_kick()
+    torch.cuda.synchronize()
+    b.check_status()
+    assert torch.equal(b.force, f0) and torch.equal(b.energy, e0) and torch.equal(b.vel, v_split)
