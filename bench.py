@@ -70,6 +70,7 @@ def parse():
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--sph-steps", type=int, default=500)
     ap.add_argument("--batch-steps", type=int, default=300)
+    ap.add_argument("--batch-seq-steps", type=int, default=3)
     ap.add_argument("--celllist-builds", type=int, default=50)
     ap.add_argument("--dem-steps", type=int, default=500)
     ap.add_argument("--sph-full", type=int, default=1, help="run the full-length SPH dam break (1) or not (0)")
@@ -482,11 +483,33 @@ def run_ours(args, ws, rank, local):
         runner.backward()
         torch.cuda.synchronize()
         t2 = time.perf_counter()
+        # the reverse sweep (J a and dF/dtheta) alone, on the final state
+        sa = runner.sys
+        hslots = int(sa.nn[: sa.n].sum().item())
+
+        def hvp():
+            fpm.fpm_lj_backward(sa.box, sa.grid, sa.n, sa.prec, sa.pos, sa.nbr, sa.nn, sa.cap, sa.eps, sa.sigma,
+                                sa.rc, runner.avec, 1.0, runner.xbar, runner.theta_steps, sa.ws_red, sa.status)
+
+        for _ in range(3):
+            hvp()
+        k0.record()
+        for _ in range(args.kernel_reps):
+            hvp()
+        k1.record()
+        torch.cuda.synchronize()
+        hvp_us = 1e3 * k0.elapsed_time(k1) / args.kernel_reps
+        hbytes = HVP_BYTES_PER_SLOT * hslots + HVP_BYTES_PER_PARTICLE * sa.n
+        hflop = HVP_FLOP_PER_SLOT * hslots
         adj = {"workload": f"lj_adjoint: {wla.n} particles, FCC 16x16x32, {args.adjoint_steps} steps, "
                            f"checkpoints every 20, loss U + sum|F|^2",
                "forward_s": t1 - t0, "backward_s": t2 - t1, "adjoint_over_forward": (t2 - t1) / (t1 - t0),
                "note": "both passes replay CUDA graphs (one per 20-step segment); backward = segment "
-                       "recomputation keeping per-step states + reverse sweeps (J a and dF/dtheta, FP64 state)"}
+                       "recomputation keeping per-step states + reverse sweeps (J a and dF/dtheta, FP64 state)",
+               "hvp_kernel": {"kernel": "k_lj_hvp_tiles<float>", "launch_us": hvp_us, "list_slots": hslots,
+                              "executed_flop_per_slot": HVP_FLOP_PER_SLOT,
+                              "achieved_tflops": hflop / (hvp_us * 1e-6) / 1e12,
+                              "alg_bytes_per_launch": hbytes, "achieved_gbs": hbytes / (hvp_us * 1e-6) / 1e9}}
         del runner
 
     # SPH dam break (2.13M particles: 1.51M fluid + 0.62M boundary), symplectic
@@ -510,11 +533,26 @@ def run_ours(args, ws, rank, local):
         ss.check_status()
         sms = e0.elapsed_time(e1)
         nlist = int(ss.nn[: ss.n].sum().item())
+        # one rate evaluation alone (the sweep of Eqs. 1-5), on the final state
+        for _ in range(3):
+            ss.rates()
+        k0.record()
+        for _ in range(args.kernel_reps):
+            ss.rates()
+        k1.record()
+        torch.cuda.synchronize()
+        rates_us = 1e3 * k0.elapsed_time(k1) / args.kernel_reps
+        sbytes = SPH_BYTES_PER_SLOT * nlist + SPH_BYTES_PER_PARTICLE * ss.n
+        sflop = SPH_FLOP_PER_SLOT * nlist
         sph = {"workload": f"dam break, dp {inputs.SPH_DP}, {dd['n_fluid']} fluid + {dd['n_boundary']} boundary "
                            f"particles, Wendland C2 h = 1.3 dp, CFL 0.2, two rate evaluations per step",
                "steps_per_s": args.sph_steps / (sms / 1e3), "ms_per_step": sms / args.sph_steps,
                "particle_steps_per_s": ss.n * args.sph_steps / (sms / 1e3), "list_slots": nlist,
-               "simulated_time_s": float(ss.dt.cpu().numpy()[0]) * args.sph_steps}
+               "simulated_time_s": float(ss.dt.cpu().numpy()[0]) * args.sph_steps,
+               "rates_kernel": {"kernel": "k_sph_tiles<0>", "launch_us": rates_us,
+                                "executed_flop_per_slot": SPH_FLOP_PER_SLOT,
+                                "achieved_tflops": sflop / (rates_us * 1e-6) / 1e12,
+                                "alg_bytes_per_launch": sbytes, "achieved_gbs": sbytes / (rates_us * 1e-6) / 1e9}}
         del ss, gs
 
     # the paper's full-length SPH run: the dam break with its fixed obstacle at
@@ -573,6 +611,29 @@ def run_ours(args, ws, rank, local):
             torch.cuda.synchronize()
         bst = bb.check_status()
         bms = e0.elapsed_time(e1)
+        # the same ensemble through the single-system path, one replica after
+        # the other, each step a CUDA-graph replay per replica (FP64, the
+        # precision of the oracle's accuracy, and FP32)
+        seq = {}
+        if args.batch_seq_steps > 0:
+            for sprec in ("f64", "f32"):
+                systems = [LJSystem(p_, v_, L_, precision=sprec) for (p_, v_, L_) in reps]
+                graphs = [s_.capture(steps_per_graph=1) for s_ in systems]
+                for g_ in graphs:
+                    g_.replay()
+                torch.cuda.synchronize()
+                e0.record()
+                for _ in range(args.batch_seq_steps):
+                    for g_ in graphs:
+                        g_.replay()
+                e1.record()
+                torch.cuda.synchronize()
+                for s_ in systems:
+                    s_.check_status()
+                sq_ms = e0.elapsed_time(e1) / args.batch_seq_steps
+                seq[sprec] = {"ms_per_step": sq_ms, "particle_steps_per_s": bb.n / (sq_ms / 1e3)}
+                del systems, graphs
+                torch.cuda.empty_cache()
         bpairs = float(bb.energies()[:, 2].sum())
         bslots = int(bb.nn[: bb.n].sum().item())
         bps = args.batch_steps / (bms / 1e3)
@@ -584,7 +645,11 @@ def run_ours(args, ws, rank, local):
                  "replica_rebuilds_per_step": (bst.nrebuild - nr0) / args.batch_steps,
                  "launches_per_step": batch_launches,
                  "particle_steps_over_fp64_single": bb.n * bps / (fp64_steps_per_s * s.n),
+                 "same_ensemble_replica_by_replica": seq,
+                 "batched_over_fp64_replica_by_replica": (seq["f64"]["ms_per_step"] / (bms / args.batch_steps)
+                                                          if "f64" in seq else None),
                  "autotune": {"config": tuned["config"], "ms_per_step": tuned["ms"],
+                              "cells_per_warp": tuned.get("cells_per_warp"),
                               "candidates": len(tuned.get("trials", [])), "seconds": tuned["seconds"],
                               "cached": tuned["cached"]}}
         del bb, gb
@@ -720,6 +785,11 @@ def run_ours(args, ws, rank, local):
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
+    for kern in ((sph or {}).get("rates_kernel"), (adj or {}).get("hvp_kernel")):
+        if kern:
+            kern["frac_fp32_executed"] = kern["achieved_tflops"] / fp32_peak
+            kern["frac_hbm"] = kern["achieved_gbs"] / peak
+            kern["peaks"] = f"FP32 {fp32_peak:.1f} TFLOP/s (CUDA cores), HBM {peak:.0f} GB/s ({peak_kind})"
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
@@ -777,6 +847,26 @@ def run_ours(args, ws, rank, local):
     }
     print(json.dumps(line), flush=True)
 
+
+# The SPH rate sweep (Eqs. 1-5) per list entry, FP32, an FMA counted as two
+# and a reciprocal or reciprocal square root as one: separation and r^2 8,
+# support test 1, the Wendland gradient factor 9, velocity difference and
+# v.r 8, Drho 2, 1/(rho_i rho_j) 2, mu 4, the viscosity term 4, the pressure
+# coefficient 4, the acceleration 6, max |mu| 1 (every entry evaluated, inside
+# the support or not: the executed work).  Bytes: 2 B of list per entry; per
+# particle position and velocity in (32 B), rates out (16 B).
+SPH_FLOP_PER_SLOT = 49
+SPH_BYTES_PER_SLOT = 2
+SPH_BYTES_PER_PARTICLE = 48
+# The LJ Hessian-vector sweep (fpm_lj_backward) per list entry: separation and
+# r^2 8, cutoff 1, 1/r^2 with its Newton step 5, s2 1, s6 2, s12 1, the force
+# factor g 4, its derivative q 5, the sigma factor 4, a_i - a_j 3, r.(a_i - a_j)
+# 5, q r.da 1, the three sums J a (12), F (6) and dF/dsigma (6), the energy
+# terms 5.  Bytes: 2 B of list per entry; per particle position and a in
+# (32 B), the FP64 adjoint state read and written (64 B).
+HVP_FLOP_PER_SLOT = 69
+HVP_BYTES_PER_SLOT = 2
+HVP_BYTES_PER_PARTICLE = 96
 
 # Algorithmic bytes of one in-place FP32 cell-list build (positions,
 # velocities and ids reordered), per particle: k_bin reads pos/vel/id (36 B)

@@ -688,6 +688,7 @@ typedef struct {
     int32_t max_ncell;
     int32_t stage_cap;
     int32_t sweep_blocks;
+    int32_t sweep_threads;  /* threads per block of the batched force sweep: 128, 256 or 512 (0: 256) */
 } fpm_batch;
 
 /* Plans a batch of R replicas (host only): replica r has counts[r]

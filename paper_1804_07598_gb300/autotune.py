@@ -3,9 +3,12 @@ the device with CUDA events and keeps the fastest, caching the choice in a
 JSON file keyed by GPU name and workload signature.
 
 The knobs are launch shapes only (results do not depend on them): the
-particles per cell tile (tile width in cells along x, `tile_target`) and
-the number of blocks of the persistent tile sweeps (`sweep_blocks`: 0 = as
-many as fit at once, -1 = one block per tile, k > 0 = k blocks).
+particles per cell tile (tile width in cells along x, `tile_target`), the
+number of blocks of the persistent tile sweeps (`sweep_blocks`: 0 = as
+many as fit at once, -1 = one block per tile, k > 0 = k blocks) and, for the
+batched force sweep, its threads per block (`sweep_threads`: 128, 256,
+512).  Tile width and block size together set the cells a warp covers
+(reported as `cells_per_warp`).
 
 Cache file: $FPM_AUTOTUNE_CACHE, else ~/.cache/fpm/autotune.json.
 """
@@ -98,13 +101,16 @@ def tune(key: str, space: dict, apply, measure, use_cache: bool = True) -> dict:
     return {**out, "cached": False, "seconds": time.time() - t0}
 
 
-def tune_batch(system, steps: int = 20, warmup: int = 5, tile_targets=(128, 170, 200, 230),
-               sweep_blocks=None, use_cache: bool = True) -> dict:
-    """Tunes an LJBatch: tile_target (re-plans and rebuilds) x sweep_blocks."""
+def tune_batch(system, steps: int = 20, warmup: int = 5, tile_targets=(128, 170, 230, 300, 420),
+               sweep_blocks=None, sweep_threads=(128, 256, 512), use_cache: bool = True) -> dict:
+    """Tunes an LJBatch: tile_target (re-plans and rebuilds) x sweep_blocks x
+    the force sweep's threads per block (a tile larger than the block takes
+    more than one particle per thread; one much smaller leaves lanes idle)."""
     if sweep_blocks is None:
         sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
         sweep_blocks = (0, -1, 2 * sms, 4 * sms)
-    space = {"tile_target": list(tile_targets), "sweep_blocks": list(sweep_blocks)}
+    space = {"tile_target": list(tile_targets), "sweep_blocks": list(sweep_blocks),
+             "sweep_threads": list(sweep_threads)}
     key = "lj_batch:" + signature({"counts": list(system.counts), "L": [round(float(L[0]), 6) for L in system.L],
                                    "r_list": system.r_list, "cap": system.cap})
 
@@ -112,11 +118,18 @@ def tune_batch(system, steps: int = 20, warmup: int = 5, tile_targets=(128, 170,
         if cfg["tile_target"] != system.tile_target:
             system.plan(cfg["tile_target"], cfg["sweep_blocks"])
         system.set_sweep_blocks(cfg["sweep_blocks"])
+        system.set_sweep_threads(cfg.get("sweep_threads", 0))
 
     def measure():
         return time_steps(system._step, steps, warmup)
 
-    return tune(key, space, apply, measure, use_cache)
+    out = tune(key, space, apply, measure, use_cache)
+    # cells of the tile per warp of the chosen block: the tiles' mean width
+    # in cells over the warps of a block
+    widths = [int(system.reps[r].grid.nc[0]) / max(1, int(system.reps[r].grid.tiles_x)) for r in range(system.R)]
+    threads = out["config"].get("sweep_threads", 256) or 256
+    out["cells_per_warp"] = (sum(widths) / len(widths)) / (threads / 32)
+    return out
 
 
 def tune_system(system, steps: int = 20, warmup: int = 5, cells_per_tile=(6, 8, 10, 13), sweep_blocks=(0, -1),

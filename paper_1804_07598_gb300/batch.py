@@ -63,6 +63,7 @@ class LJBatch:
         tile, 0 = default) and rebuild every replica's lists."""
         reps, b = fpm.fpm_batch_plan(self.boxes, self.counts, self.r_list, tile_target)
         b.sweep_blocks = int(sweep_blocks)
+        b.sweep_threads = self.batch.sweep_threads if hasattr(self, "batch") else 0  # kept across re-plans
         self.reps, self.batch = reps, b
         self.tile_target = int(tile_target)
         raw = np.frombuffer(bytes(reps), dtype=np.uint8).copy()
@@ -87,6 +88,11 @@ class LJBatch:
 
     def set_sweep_blocks(self, blocks: int):
         self.batch.sweep_blocks = int(blocks)
+        self._graph = None
+
+    def set_sweep_threads(self, threads: int):
+        """Threads per block of the force sweep (128, 256 or 512; 0: 256)."""
+        self.batch.sweep_threads = int(threads)
         self._graph = None
 
     # -- pieces ---------------------------------------------------------

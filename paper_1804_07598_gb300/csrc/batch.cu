@@ -26,7 +26,6 @@ namespace fpm {
 constexpr int kBatchCellThreads = 1024;
 constexpr int kBatchMaxCells = 32768;   // cells of one replica (shared-memory counters)
 constexpr int kBatchMaxReplicas = 65535;
-constexpr int kBatchDescBlocks = 2048;  // grid of the descriptor kernel (grid-stride over tiles)
 
 __host__ __device__ inline int rep_ntiles(const fpm_grid &g) { return g.tiles_x * g.nc[1] * g.nc[2]; }
 
@@ -278,35 +277,12 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
-// Descriptors of the tiles on the work list (grid-stride).
-__global__ void __launch_bounds__(128)
-    k_btile_desc(const fpm_replica *__restrict__ reps, const uint32_t *__restrict__ work,
-                 const uint32_t *__restrict__ map, const uint32_t *__restrict__ header,
-                 const uint32_t *__restrict__ cs, TileDesc *__restrict__ descs, fpm_dev_status *st)
-{
-    __shared__ TileGeom g;
-    __shared__ TileDesc d;
-    const uint32_t count = header[0];
-    for (uint32_t k = blockIdx.x; k < count; k += gridDim.x) {
-        const uint32_t tile = work[k];
-        const fpm_replica rp = reps[map[tile]];
-        const TileCfg cfg = make_tile_cfg(rp.box, rp.grid);
-        tile_geometry(cfg, (int)tile - rp.t0, cs + rp.c0, g, d);
-        const int nwd = (int)(sizeof(TileDesc) / 4);
-        uint32_t *o = (uint32_t *)(descs + tile);
-        const uint32_t *s = (const uint32_t *)&d;
-        for (int q = threadIdx.x; q < nwd; q += blockDim.x) o[q] = s[q];
-        if (threadIdx.x == 0 && st && d.h1 > d.h0) atomicMax(&st->max_staged, (uint32_t)d.M);
-        __syncthreads();  // d and g are rewritten for the next tile
-    }
-}
-
 __global__ void __launch_bounds__(kTileThreads)
     k_bverlet_scan(const fpm_replica *__restrict__ reps, const uint32_t *__restrict__ map,
                    const float4 *__restrict__ pos, const uint32_t *__restrict__ cs, float rl2, int cap, int64_t ld,
                    int stage_cap, const uint32_t *__restrict__ work, const uint32_t *__restrict__ count, Sched sched,
                    uint32_t *__restrict__ words, uint32_t *__restrict__ nn, float4 *__restrict__ pos_ref,
-                   fpm_dev_status *st)
+                   TileDesc *__restrict__ descs, fpm_dev_status *st)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float4 *sp = (float4 *)smem_raw;
@@ -337,6 +313,12 @@ __global__ void __launch_bounds__(kTileThreads)
         const uint32_t c = verlet_tile<float>(cfg, box, s_tile, cs + s_c0, pos, rl2, cap, ld, stage_cap, g, d, sp,
                                               &bar, phase, words, nn, pos_ref, st);
         maxc = c > maxc ? c : maxc;
+        // the tile's descriptor, for the force sweep (the geometry the scan computed)
+        const int nwd = (int)(sizeof(TileDesc) / 4);
+        uint32_t *o = (uint32_t *)(descs + work[k]);
+        const uint32_t *dsrc = (const uint32_t *)&d;
+        for (int q = threadIdx.x; q < nwd; q += blockDim.x) o[q] = dsrc[q];
+        if (threadIdx.x == 0 && st && d.h1 > d.h0) atomicMax(&st->max_staged, (uint32_t)d.M);
     }
     const uint32_t m = __reduce_max_sync(kFull, maxc);
     if ((threadIdx.x & 31) == 0 && st && m > 0) atomicMax(&st->max_nn, m);
@@ -345,7 +327,8 @@ __global__ void __launch_bounds__(kTileThreads)
 
 // ---- LJ forces over every tile of the batch ---------------------------------
 
-__global__ void __launch_bounds__(kTileThreads)
+template <int THREADS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS)
     k_blj_tiles(int ntiles, const fpm_replica *__restrict__ reps, const uint32_t *__restrict__ map,
                 const float4 *__restrict__ pos, ListView lv, const uint32_t *__restrict__ nn, int64_t ld, int stage_cap, LJParams<float> P,
                 float4 *__restrict__ force, Sched sched, double *part, uint32_t *rep_done, double *out,
@@ -484,6 +467,8 @@ static fpm_status batch_ok(const fpm_batch *b, const fpm_replica *d_reps, const 
     if (!b || !d_reps || b->R < 1 || b->R > kBatchMaxReplicas || b->n_total < 0 || b->ncell_total < b->R ||
         b->ntiles_total < b->R || b->max_ncell < 1 || b->max_ncell > kBatchMaxCells)
         return fpm_fail(FPM_ERR_INVALID, "%s: bad batch", who);
+    if (b->sweep_threads != 0 && b->sweep_threads != 128 && b->sweep_threads != 256 && b->sweep_threads != 512)
+        return fpm_fail(FPM_ERR_INVALID, "%s: sweep_threads must be 0, 128, 256 or 512", who);
     return FPM_OK;
 }
 
@@ -548,6 +533,7 @@ extern "C" fpm_status fpm_batch_plan(int32_t R, const fpm_box *boxes, const int3
     batch->max_ncell = max_ncell;
     batch->stage_cap = stage;
     batch->sweep_blocks = 0;
+    batch->sweep_threads = 0;
     return FPM_OK;
 }
 
@@ -658,8 +644,6 @@ extern "C" fpm_status fpm_batch_verlet_build(const fpm_batch *batch, const fpm_r
     const int R = batch->R;
     const int nt = batch->ntiles_total;
     k_bwork<<<1, 1024, 0, st>>>(R, d_reps, d_rep_flag, work, map, header, d_status);
-    k_btile_desc<<<std::min(nt, kBatchDescBlocks), 128, 0, st>>>(d_reps, work, map, header, cell_start, descs,
-                                                                d_status);
     const int sc = batch_stage_cap(*batch);
     const size_t smem = (size_t)sc * sizeof(float4);
     smem_opt_in((const void *)k_bverlet_scan);
@@ -670,7 +654,7 @@ extern "C" fpm_status fpm_batch_verlet_build(const fpm_batch *batch, const fpm_r
                                                        (float)(r_list * r_list), cap, L.ld, sc, work, header,
                                                        Sched{(unsigned *)(lb + 16), (unsigned *)(lb + 20)},
                                                        (uint32_t *)(lb + L.off_words), nn, (float4 *)pos_ref,
-                                                       d_status);
+                                                       descs, d_status);
     return fpm_check_launch("fpm_batch_verlet_build");
 }
 
@@ -719,12 +703,14 @@ static fpm_status batch_lj(const fpm_batch *batch, const fpm_replica *d_reps, co
     P.rc2 = (float)(rc * rc);
     const int sc = batch_stage_cap(*batch);
     const size_t smem = (size_t)sc * sizeof(float4);
-    smem_opt_in((const void *)k_blj_tiles);
+    const int threads = batch->sweep_threads == 0 ? 256 : batch->sweep_threads;
+    auto kern = threads == 128 ? k_blj_tiles<128> : threads == 512 ? k_blj_tiles<512> : k_blj_tiles<256>;
+    smem_opt_in((const void *)kern);
     fpm_grid gg{};
     gg.sweep_blocks = batch->sweep_blocks;
     const int nt = batch->ntiles_total;
-    const int blocks = persistent_blocks((const void *)k_blj_tiles, kTileThreads, smem, gg, nt);
-    k_blj_tiles<<<blocks, kTileThreads, smem, (cudaStream_t)stream>>>(
+    const int blocks = persistent_blocks((const void *)kern, threads, smem, gg, nt);
+    kern<<<blocks, threads, smem, (cudaStream_t)stream>>>(
         nt, d_reps, (const uint32_t *)((const char *)list + off_map), (const float4 *)pos, list_view(list, L), nn,
         L.ld, sc, P, (float4 *)force,
         Sched{(unsigned *)(w + 16), (unsigned *)(w + 32)}, (double *)(w + 256), (uint32_t *)(w + off_done),

@@ -134,6 +134,8 @@ class DEMSystem:
         """Capture `steps_per_graph` whole steps into one CUDA graph."""
         torch.cuda.synchronize()
         s = torch.cuda.Stream()
+        while s.cuda_stream == self._body.cuda_stream:  # torch hands out streams from a small pool
+            s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         g = torch.cuda.CUDAGraph()
         with torch.cuda.stream(s):

@@ -55,7 +55,7 @@ class fpm_replica(_c.Structure):
 class fpm_batch(_c.Structure):
     _fields_ = [("R", _c.c_int32), ("n_total", _c.c_int32), ("ncell_total", _c.c_int32),
                 ("ntiles_total", _c.c_int32), ("max_n", _c.c_int32), ("max_ncell", _c.c_int32),
-                ("stage_cap", _c.c_int32), ("sweep_blocks", _c.c_int32)]
+                ("stage_cap", _c.c_int32), ("sweep_blocks", _c.c_int32), ("sweep_threads", _c.c_int32)]
 
 
 class fpm_dev_status(_c.Structure):
@@ -593,7 +593,7 @@ def fpm_batch_verlet_build(batch, d_reps, pos, cell_start, r_list, cap, list_obj
     _check(lib().fpm_batch_verlet_build(_c.byref(batch), _ptr(d_reps), _ptr(pos), _ptr(cell_start), float(r_list),
                                         int(cap), _ptr(list_obj), _nbytes(list_obj), _ptr(nn), _ptr(pos_ref),
                                         _ptr(d_rep_flag), _ptr(d_status), _stream(stream)))
-    _count(3)
+    _count(2)  # the work list, the scan (which also writes the tile descriptors)
 
 
 def fpm_batch_verlet_decode(batch, cap, list_obj, nn, out, stream=None):

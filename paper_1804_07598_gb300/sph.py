@@ -155,6 +155,8 @@ class SPHSystem:
     def capture(self, steps_per_graph: int = 1):
         torch.cuda.synchronize()
         s = torch.cuda.Stream()
+        while s.cuda_stream == self._body.cuda_stream:  # torch hands out streams from a small pool
+            s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         g = torch.cuda.CUDAGraph()
         with torch.cuda.stream(s):

@@ -266,3 +266,25 @@ def test_batch_forces_kick_equals_split(cuda):
     torch.cuda.synchronize()
     b.check_status()
     assert torch.equal(b.force, f0) and torch.equal(b.energy, e0) and torch.equal(b.vel, v_split)
+
+
+@pytest.mark.parametrize("threads", [128, 512])
+def test_batch_sweep_threads(cuda, threads):
+    """The force sweep's block size is a launch shape only: 128 or 512 threads
+    per block give the forces of the default 256 bit for bit (one thread per
+    particle, the same list order) and the energies within rounding (the
+    per-thread partial sums group differently when a tile is larger than the
+    block)."""
+    b = LJBatch(small_ensemble())
+    b.compute_forces()
+    torch.cuda.synchronize()
+    f0, e0 = b.force.clone(), b.energy.clone()
+    b.set_sweep_threads(threads)
+    b.force.zero_()
+    b.compute_forces()
+    torch.cuda.synchronize()
+    b.check_status()
+    assert torch.equal(b.force, f0)
+    e, e0 = b.energy.cpu().numpy(), e0.cpu().numpy()
+    assert np.all(np.abs(e[:, 0] - e0[:, 0]) <= 1e-6 * np.abs(e0[:, 0]))
+    assert np.array_equal(e[:, 2], e0[:, 2])
