@@ -586,7 +586,8 @@ def run_ours(args, ws, rank, local):
         del sf, gf
 
     # batched ensemble: 512 periodic replicas of 256..16384 particles, one
-    # launch per operation, replayed from a CUDA graph, launch shapes autotuned
+    # launch per step (or per operation, whichever the tuner picks), replayed
+    # from a CUDA graph, launch shapes autotuned
     batch = None
     if args.batch_steps > 0:
         from paper_1804_07598_gb300 import autotune
@@ -648,6 +649,10 @@ def run_ours(args, ws, rank, local):
                  "same_ensemble_replica_by_replica": seq,
                  "batched_over_fp64_replica_by_replica": (seq["f64"]["ms_per_step"] / (bms / args.batch_steps)
                                                           if "f64" in seq else None),
+                 "one_launch_step": bb.fused,
+                 "autotune_best_ms": {m: min((t_["ms"] for t_ in tuned.get("trials", [])
+                                              if t_["config"]["shape"][0] == m), default=None)
+                                      for m in ("step", "split")},
                  "autotune": {"config": tuned["config"], "ms_per_step": tuned["ms"],
                               "cells_per_warp": tuned.get("cells_per_warp"),
                               "candidates": len(tuned.get("trials", [])), "seconds": tuned["seconds"],

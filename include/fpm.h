@@ -689,6 +689,8 @@ typedef struct {
     int32_t stage_cap;
     int32_t sweep_blocks;
     int32_t sweep_threads;  /* threads per block of the batched force sweep: 128, 256 or 512 (0: 256) */
+    int32_t step_blocks_per_sm;  /* fpm_batch_step: blocks per SM its registers are bounded for, 2, 3 or 4
+                                    (0: 4); fewer blocks, more registers per thread */
 } fpm_batch;
 
 /* Plans a batch of R replicas (host only): replica r has counts[r]
@@ -708,7 +710,9 @@ fpm_status fpm_batch_drift_check(const fpm_batch *batch, const fpm_replica *d_re
                                  void *vel, const void *force, const void *pos_ref, double skin,
                                  uint32_t *d_rep_flag, fpm_stream stream);
 
-/* Bytes of device workspace of fpm_batch_celllist_build. */
+/* Bytes of device workspace of fpm_batch_celllist_build and fpm_batch_step
+ * (for fpm_batch_step zero-filled once before first use: it holds cell
+ * counters that every step leaves at zero again). */
 fpm_status fpm_batch_celllist_workspace(const fpm_batch *batch, size_t *bytes);
 
 /* Cell lists of the replicas whose d_rep_flag is set (all replicas when
@@ -743,8 +747,8 @@ fpm_status fpm_batch_verlet_build(const fpm_batch *batch, const fpm_replica *d_r
 fpm_status fpm_batch_verlet_decode(const fpm_batch *batch, int32_t cap, const void *list, const uint32_t *nn,
                                    uint32_t *out, fpm_stream stream);
 
-/* Bytes of workspace of fpm_batch_lj_forces (zero-filled once before first
- * use; every call leaves its counters at zero again). */
+/* Bytes of workspace of fpm_batch_lj_forces and fpm_batch_step (zero-filled
+ * once before first use; every call leaves its counters at zero again). */
 fpm_status fpm_batch_workspace(const fpm_batch *batch, size_t *bytes);
 
 /* LJ forces of every replica (as fpm_lj_forces on its own box, single
@@ -765,6 +769,42 @@ fpm_status fpm_batch_lj_forces_kick(const fpm_batch *batch, const fpm_replica *d
                                     double rc, void *force, double *d_energy, void *workspace,
                                     size_t workspace_bytes, fpm_dev_status *d_status, void *vel, double dt,
                                     fpm_stream stream);
+
+/* One velocity-Verlet step of the whole batch in ONE cooperative launch:
+ * the work of fpm_batch_drift_check, fpm_batch_celllist_build and
+ * fpm_batch_verlet_build gated by d_rep_flag, then fpm_batch_lj_forces_kick,
+ * as phases of a persistent kernel separated by grid barriers, with the same
+ * arguments as those four calls (cell_ws: fpm_batch_celllist_workspace bytes;
+ * workspace: fpm_batch_workspace bytes).  The cell lists of the flagged
+ * replicas are built by the whole grid (particles binned with global
+ * counters, a scan per replica, a warp per cell), and the Verlet scans of
+ * their tiles share one ticket queue with the force tiles: the tiles of the
+ * replicas not rebuilt first, those of the rebuilt replicas once every tile
+ * of their replica is scanned.  A step that flags no replica skips the
+ * rebuild phases.  The results (pos, vel, force, ids, perm, cell_start, nn,
+ * the list, pos_ref, d_energy, d_status->nrebuild and max_nn) are those of
+ * the four calls bit for bit when the batch's sweep_threads is 0 or 256; the
+ * flags are clear afterwards.
+ * Preconditions: cell_ws and workspace zero-filled once; the cell lists and
+ * the list built for every replica once with this cell_ws and list
+ * (fpm_batch_celllist_build and fpm_batch_verlet_build, d_rep_flag NULL: the
+ * cell build also records the replica of every particle and cell in cell_ws);
+ * force holds the forces of the current positions.
+ * The grid is every block that fits on the GPU at once (or sweep_blocks when
+ * smaller); a grid that cannot be resident is refused by the launch
+ * (FPM_ERR_CUDA), never run.  The grid barrier's state lives in the list
+ * object (bytes 32..39).  Every wait (grid barrier, scanned-tile count, bulk
+ * copy) is bounded (about 2 s of SM clock); on expiry the kernel latches
+ * FPM_FLAG_TIMEOUT and returns.  The results of that step are then undefined:
+ * zero-fill cell_ws and workspace again and run fpm_batch_celllist_build and
+ * fpm_batch_verlet_build (which resets the barrier) on every replica before
+ * the next step. */
+fpm_status fpm_batch_step(const fpm_batch *batch, const fpm_replica *d_reps, double dt, double skin, double r_list,
+                          int32_t cap, double eps, double sigma, double rc, void *pos, void *vel, void *force,
+                          void *pos_ref, uint32_t *ids, uint32_t *cell_start, uint32_t *perm, void *list,
+                          size_t list_bytes, uint32_t *nn, uint32_t *d_rep_flag, void *cell_ws,
+                          size_t cell_ws_bytes, void *workspace, size_t workspace_bytes, double *d_energy,
+                          fpm_dev_status *d_status, fpm_stream stream);
 
 #ifdef __cplusplus
 }

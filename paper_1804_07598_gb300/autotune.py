@@ -6,7 +6,8 @@ The knobs are launch shapes only (results do not depend on them): the
 particles per cell tile (tile width in cells along x, `tile_target`), the
 number of blocks of the persistent tile sweeps (`sweep_blocks`: 0 = as
 many as fit at once, -1 = one block per tile, k > 0 = k blocks) and, for the
-batched force sweep, its threads per block (`sweep_threads`: 128, 256,
+batched replicas, the one-launch step (its register bound) or the separate
+calls with the force sweep's threads per block (`sweep_threads`: 128, 256,
 512).  Tile width and block size together set the cells a warp covers
 (reported as `cells_per_warp`).
 
@@ -102,23 +103,35 @@ def tune(key: str, space: dict, apply, measure, use_cache: bool = True) -> dict:
 
 
 def tune_batch(system, steps: int = 20, warmup: int = 5, tile_targets=(128, 170, 230, 300, 420),
-               sweep_blocks=None, sweep_threads=(128, 256, 512), use_cache: bool = True) -> dict:
-    """Tunes an LJBatch: tile_target (re-plans and rebuilds) x sweep_blocks x
-    the force sweep's threads per block (a tile larger than the block takes
-    more than one particle per thread; one much smaller leaves lanes idle)."""
+               sweep_blocks=None, sweep_threads=(128, 256, 512), step_blocks=(0,), step_minb=(2, 3, 4),
+               use_cache: bool = True) -> dict:
+    """Tunes an LJBatch: tile_target (re-plans and rebuilds) x the launch
+    shape, one of
+      ["step", blocks, minb]     the one-launch step (fpm_batch_step) on
+                                 `blocks` blocks (0: all that fit at once),
+                                 its registers bounded for minb blocks per SM;
+      ["split", blocks, threads] the four separate calls, the force sweep on
+                                 `blocks` blocks of `threads` threads (a tile
+                                 larger than the block takes more than one
+                                 particle per thread; one much smaller leaves
+                                 lanes idle)."""
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     if sweep_blocks is None:
-        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
         sweep_blocks = (0, -1, 2 * sms, 4 * sms)
-    space = {"tile_target": list(tile_targets), "sweep_blocks": list(sweep_blocks),
-             "sweep_threads": list(sweep_threads)}
+    shapes = [["step", int(b), int(m)] for b in step_blocks for m in step_minb]
+    shapes += [["split", int(b), int(t)] for b in sweep_blocks for t in sweep_threads]
+    space = {"tile_target": list(tile_targets), "shape": shapes}
     key = "lj_batch:" + signature({"counts": list(system.counts), "L": [round(float(L[0]), 6) for L in system.L],
                                    "r_list": system.r_list, "cap": system.cap})
 
     def apply(cfg):
+        mode, blocks, third = cfg["shape"]
         if cfg["tile_target"] != system.tile_target:
-            system.plan(cfg["tile_target"], cfg["sweep_blocks"])
-        system.set_sweep_blocks(cfg["sweep_blocks"])
-        system.set_sweep_threads(cfg.get("sweep_threads", 0))
+            system.plan(cfg["tile_target"], blocks)
+        system.fused = mode == "step"
+        system.set_sweep_blocks(blocks)
+        system.set_sweep_threads(0 if mode == "step" else third)
+        system.set_step_blocks_per_sm(third if mode == "step" else 0)
 
     def measure():
         return time_steps(system._step, steps, warmup)
@@ -127,7 +140,7 @@ def tune_batch(system, steps: int = 20, warmup: int = 5, tile_targets=(128, 170,
     # cells of the tile per warp of the chosen block: the tiles' mean width
     # in cells over the warps of a block
     widths = [int(system.reps[r].grid.nc[0]) / max(1, int(system.reps[r].grid.tiles_x)) for r in range(system.R)]
-    threads = out["config"].get("sweep_threads", 256) or 256
+    threads = (out["config"]["shape"][2] or 256) if out["config"]["shape"][0] == "split" else 256
     out["cells_per_warp"] = (sum(widths) / len(widths)) / (threads / 32)
     return out
 

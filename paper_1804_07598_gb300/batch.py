@@ -2,7 +2,9 @@
 of uneven size (an ensemble of the MD system of Sec. 4.1) advanced together,
 one launch per operation for the whole batch.
 
-One step (all on the current stream, no host synchronisation):
+One step (all on the current stream, no host synchronisation) is one
+launch, fpm_batch_step, whose phases do the work of the four separate calls
+below (fused=False runs those instead; the results are the same bit for bit):
     fpm_batch_drift_check           v += dt/2 F; x += dt v; flag the replicas
                                     in which a particle moved > skin/2
     fpm_batch_celllist_build        re-bin and reorder the flagged replicas
@@ -23,9 +25,11 @@ from .md import default_cap
 
 class LJBatch:
     def __init__(self, replicas, eps=1.0, sigma=1.0, rc=2.5, skin=0.3, dt=0.005, tile_target=0, cap=None,
-                 device="cuda"):
-        """replicas: sequence of (pos [n, >=3], vel [n, >=3], L [3]) per replica."""
+                 device="cuda", fused=True):
+        """replicas: sequence of (pos [n, >=3], vel [n, >=3], L [3]) per replica.
+        fused: a step is the one launch fpm_batch_step (else four calls)."""
         self.device = torch.device(device)
+        self.fused = bool(fused)
         self.eps, self.sigma, self.rc, self.skin, self.dt = float(eps), float(sigma), float(rc), float(skin), float(dt)
         self.r_list = self.rc + self.skin
         self.L = [np.broadcast_to(np.asarray(L, np.float64), (3,)).copy() for (_, _, L) in replicas]
@@ -63,7 +67,9 @@ class LJBatch:
         tile, 0 = default) and rebuild every replica's lists."""
         reps, b = fpm.fpm_batch_plan(self.boxes, self.counts, self.r_list, tile_target)
         b.sweep_blocks = int(sweep_blocks)
-        b.sweep_threads = self.batch.sweep_threads if hasattr(self, "batch") else 0  # kept across re-plans
+        if hasattr(self, "batch"):  # launch-shape choices are kept across re-plans
+            b.sweep_threads = self.batch.sweep_threads
+            b.step_blocks_per_sm = self.batch.step_blocks_per_sm
         self.reps, self.batch = reps, b
         self.tile_target = int(tile_target)
         raw = np.frombuffer(bytes(reps), dtype=np.uint8).copy()
@@ -90,6 +96,12 @@ class LJBatch:
         self.batch.sweep_blocks = int(blocks)
         self._graph = None
 
+    def set_step_blocks_per_sm(self, blocks: int):
+        """Blocks per SM the one-launch step's registers are bounded for
+        (2, 3 or 4; 0: 4)."""
+        self.batch.step_blocks_per_sm = int(blocks)
+        self._graph = None
+
     def set_sweep_threads(self, threads: int):
         """Threads per block of the force sweep (128, 256 or 512; 0: 256)."""
         self.batch.sweep_threads = int(threads)
@@ -114,6 +126,12 @@ class LJBatch:
                                      self.vel, self.dt)
 
     def _step(self):
+        if self.fused:
+            fpm.fpm_batch_step(self.batch, self.d_reps, self.dt, self.skin, self.r_list, self.cap, self.eps,
+                               self.sigma, self.rc, self.pos, self.vel, self.force, self.pos_ref, self.ids,
+                               self.cell_start, self.perm, self.nbr, self.nn, self.flags, self.ws_cell, self.ws_red,
+                               self.energy, self.status)
+            return
         fpm.fpm_batch_drift_check(self.batch, self.d_reps, self.dt, self.pos, self.vel, self.force, self.pos_ref,
                                   self.skin, self.flags)
         self.rebuild(gated=True)

@@ -62,6 +62,20 @@ __device__ __forceinline__ double4_32a ldg4(const double4_32a *p)
     return r;
 }
 
+// Loads of a 4-vector cached at L2 only (coherent with writes made earlier in
+// the same launch by other blocks, once ordered by a barrier or a flag).
+__device__ __forceinline__ float4 ldcg4(const float4 *p) { return __ldcg(p); }
+__device__ __forceinline__ double4_32a ldcg4(const double4_32a *p)
+{
+    const double2 a = __ldcg((const double2 *)p), b = __ldcg((const double2 *)p + 1);
+    double4_32a r;
+    r.x = a.x;
+    r.y = a.y;
+    r.z = b.x;
+    r.w = b.y;
+    return r;
+}
+
 // Small integer flags carried in the unused w component of a staged 4-vector.
 template <typename T> __device__ __forceinline__ T flags_as(int f);
 template <> __device__ __forceinline__ float flags_as<float>(int f) { return __int_as_float(f); }

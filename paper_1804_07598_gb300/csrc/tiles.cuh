@@ -348,6 +348,18 @@ __device__ __forceinline__ void load_desc(const TileDesc *__restrict__ src, Tile
     __syncthreads();
 }
 
+// load_desc for a descriptor that may have been written earlier in the same
+// launch (by another block, ordered by a barrier or a flag): read at L2,
+// never through the read-only path.
+__device__ __forceinline__ void load_desc_cg(const TileDesc *src, TileDesc &dst)
+{
+    const int words = (int)(sizeof(TileDesc) / 4);
+    const uint32_t *s = (const uint32_t *)src;
+    uint32_t *o = (uint32_t *)&dst;
+    for (int k = threadIdx.x; k < words; k += blockDim.x) o[k] = __ldcg(s + k);
+    __syncthreads();
+}
+
 // ---- TMA bulk staging -------------------------------------------------------
 // Every piece is a contiguous run of 16-byte (float4) or 32-byte (double4)
 // records in the sorted position array, so one cp.async.bulk per piece copies
@@ -514,7 +526,7 @@ __device__ __forceinline__ V4<T> staged_global(const TileDesc &d, const BoxT<T> 
         return q;
     }
     const Piece pc = d.piece[p];
-    V4<T> q = ldg4(pos + pc.gstart + (s - pc.soff));
+    V4<T> q = ldcg4(pos + pc.gstart + (s - pc.soff));  // at L2: pos may have been written earlier in the launch
     if (pc.flags & kLoX) q.x = rsub(q.x, box.L[0]);
     if (pc.flags & kLoY) q.y = rsub(q.y, box.L[1]);
     if (pc.flags & kLoZ) q.z = rsub(q.z, box.L[2]);

@@ -55,7 +55,8 @@ class fpm_replica(_c.Structure):
 class fpm_batch(_c.Structure):
     _fields_ = [("R", _c.c_int32), ("n_total", _c.c_int32), ("ncell_total", _c.c_int32),
                 ("ntiles_total", _c.c_int32), ("max_n", _c.c_int32), ("max_ncell", _c.c_int32),
-                ("stage_cap", _c.c_int32), ("sweep_blocks", _c.c_int32), ("sweep_threads", _c.c_int32)]
+                ("stage_cap", _c.c_int32), ("sweep_blocks", _c.c_int32), ("sweep_threads", _c.c_int32),
+                ("step_blocks_per_sm", _c.c_int32)]
 
 
 class fpm_dev_status(_c.Structure):
@@ -175,6 +176,9 @@ _SIG = {
     "fpm_batch_lj_forces_kick": (_c.c_int, [_c.POINTER(fpm_batch), _VP, _VP, _VP, _VP, _c.c_int32, _c.c_double,
                                             _c.c_double, _c.c_double, _VP, _VP, _VP, _c.c_size_t, _VP, _VP,
                                             _c.c_double, _VP]),
+    "fpm_batch_step": (_c.c_int, [_c.POINTER(fpm_batch), _VP, _c.c_double, _c.c_double, _c.c_double, _c.c_int32,
+                                  _c.c_double, _c.c_double, _c.c_double, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP,
+                                  _c.c_size_t, _VP, _VP, _VP, _c.c_size_t, _VP, _c.c_size_t, _VP, _VP, _VP]),
 }
 
 
@@ -614,6 +618,17 @@ def fpm_batch_lj_forces_kick(batch, d_reps, pos, list_obj, nn, cap, eps, sigma, 
                                           int(cap), float(eps), float(sigma), float(rc), _ptr(force),
                                           _ptr(d_energy), _ptr(workspace), _nbytes(workspace), _ptr(d_status),
                                           _ptr(vel), float(dt), _stream(stream)))
+    _count(1)
+
+
+def fpm_batch_step(batch, d_reps, dt, skin, r_list, cap, eps, sigma, rc, pos, vel, force, pos_ref, ids, cell_start,
+                   perm, list_obj, nn, d_rep_flag, cell_ws, workspace, d_energy=None, d_status=None, stream=None):
+    _check(lib().fpm_batch_step(_c.byref(batch), _ptr(d_reps), float(dt), float(skin), float(r_list), int(cap),
+                                float(eps), float(sigma), float(rc), _ptr(pos), _ptr(vel), _ptr(force),
+                                _ptr(pos_ref), _ptr(ids), _ptr(cell_start), _ptr(perm), _ptr(list_obj),
+                                _nbytes(list_obj), _ptr(nn), _ptr(d_rep_flag), _ptr(cell_ws), _nbytes(cell_ws),
+                                _ptr(workspace), _nbytes(workspace), _ptr(d_energy), _ptr(d_status),
+                                _stream(stream)))
     _count(1)
 
 

@@ -288,3 +288,95 @@ def test_batch_sweep_threads(cuda, threads):
     e, e0 = b.energy.cpu().numpy(), e0.cpu().numpy()
     assert np.all(np.abs(e[:, 0] - e0[:, 0]) <= 1e-6 * np.abs(e0[:, 0]))
     assert np.array_equal(e[:, 2], e0[:, 2])
+
+
+def batch_state(b):
+    """Everything a step writes, as host arrays (the list object from byte 64:
+    its header holds launch counters and the grid barrier's generation)."""
+    torch.cuda.synchronize()
+    out = {k: getattr(b, k).cpu().numpy().copy() for k in
+           ("pos", "vel", "force", "pos_ref", "ids", "perm", "cell_start", "nn", "energy", "flags")}
+    nbr = b.nbr.cpu().numpy()
+    out["list"] = nbr[64:].copy()
+    out["nwork"] = nbr[:4].copy()
+    return out
+
+
+@pytest.mark.parametrize("skin,sweep_blocks,minb", [(0.3, 0, 0), (0.05, 0, 2), (0.05, 7, 3)])
+def test_batch_one_launch_step_equals_split(cuda, skin, sweep_blocks, minb):
+    """fpm_batch_step (one cooperative launch: drift, gated cell lists and
+    Verlet lists, forces and the closing kick, separated by grid barriers)
+    leaves every array exactly as the four separate calls do, over eager and
+    graph-captured steps in which replicas rebuild on their own schedule (a
+    small skin rebuilds most replicas most steps), with a grid of a few
+    blocks (each taking many replicas, cells and tiles), and over steps in
+    which no replica is flagged (the rebuild phases skipped)."""
+    reps = small_ensemble(seed=13)
+    a = LJBatch(reps, skin=skin, fused=True)
+    b = LJBatch(reps, skin=skin, fused=False)
+    a.batch.sweep_blocks = sweep_blocks
+    a.set_step_blocks_per_sm(minb)
+    st0 = fpm.read_status(a.status).nrebuild
+    for _ in range(4):
+        a.step(1)
+        b.step(1)
+    sa, sb = batch_state(a), batch_state(b)
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
+    a.capture(steps_per_graph=2)
+    b.capture(steps_per_graph=2)
+    a.run(8)
+    b.run(8)
+    sa, sb = batch_state(a), batch_state(b)
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
+    ta, tb = a.check_status(), b.check_status()
+    assert ta.nrebuild == tb.nrebuild and ta.nrebuild > st0
+    assert ta.max_nn == tb.max_nn
+    assert not sa["flags"].any()
+    # steps in which no replica is flagged (dt = 0: nobody moves)
+    a.dt = b.dt = 0.0
+    for _ in range(2):
+        a.step(1)
+        b.step(1)
+    sa, sb = batch_state(a), batch_state(b)
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
+    assert a.check_status().nrebuild == ta.nrebuild
+
+
+def test_batch_one_launch_step_barrier_timeout(cuda):
+    """A grid barrier that can never complete (its arrival counter planted far
+    past the grid size, so no block is ever the last) gives up after its
+    bounded wait: the launch returns with FPM_FLAG_TIMEOUT latched and the
+    context still usable; after the documented recovery (workspaces
+    zero-filled, full cell and Verlet builds, which reset the barrier) the
+    next steps again equal the separate calls."""
+    reps = small_ensemble(seed=17, extra=2)
+    a = LJBatch(reps, fused=True)
+    b = LJBatch(reps, fused=False)
+    hdr = a.nbr[:64].view(torch.int32)
+    hdr[8] = 1 << 30
+    a.step(1)
+    torch.cuda.synchronize()
+    st = fpm.read_status(a.status)
+    assert st.flags & fpm.FPM_FLAG_TIMEOUT
+    assert fpm.fpm_status_from_device(st) == fpm.FPM_ERR_TIMEOUT
+    for k in ("pos", "vel", "force", "ids"):
+        getattr(a, k).copy_(getattr(b, k))
+    a.status.zero_()
+    a.flags.zero_()
+    a.ws_cell.zero_()
+    a.ws_red.zero_()
+    a.rebuild()
+    a.compute_forces()
+    b.rebuild()
+    b.compute_forces()
+    assert int(hdr[8].item()) == 0
+    for _ in range(3):
+        a.step(1)
+        b.step(1)
+    sa, sb = batch_state(a), batch_state(b)
+    for k in ("pos", "vel", "force", "ids", "energy", "nn", "list"):
+        assert np.array_equal(sa[k], sb[k]), k
+    a.check_status()
