@@ -193,7 +193,25 @@ __device__ __forceinline__ void bcell_gather(uint32_t s, uint32_t e, const BCell
         }
         return;
     }
-    // larger cells: rank of each element = number of smaller indices
+    // larger cells: a slice already in ascending order (a replica of one
+    // cell, ranked in index order) is gathered as it stands
+    bool sorted = true;
+    for (uint32_t e0 = 0; e0 < m && sorted; e0 += 32) {
+        const uint32_t j = e0 + lane;
+        const bool ok = j + 1 >= m || w.tmp[s + j] < w.tmp[s + j + 1];
+        sorted = __all_sync(kFull, ok);
+    }
+    if (sorted) {
+        for (uint32_t j = lane; j < m; j += 32) {
+            const uint32_t slot = s + j, v = w.tmp[slot];
+            pos[slot] = w.spos[v];
+            if (vel) vel[slot] = w.svel[v];
+            if (ids) ids[slot] = w.sid[v];
+            if (perm) perm[slot] = v;
+        }
+        return;
+    }
+    // otherwise: rank of each element = number of smaller indices
     for (uint32_t e0 = 0; e0 < m; e0 += 32) {
         const bool mine = e0 + lane < m;
         const uint32_t v = mine ? w.tmp[s + e0 + lane] : 0xffffffffu;
@@ -240,7 +258,8 @@ __global__ void __launch_bounds__(kBatchCellThreads)
         __syncthreads();
         for (uint32_t k = threadIdx.x; k < n; k += blockDim.x) {
             const uint32_t i = p0 + k;
-            w.rank[i] = atomicAdd(&cnt[bcell_bin(i, box, g, pos, vel, ids, w, st)], 1u);
+            const uint32_t rk = atomicAdd(&cnt[bcell_bin(i, box, g, pos, vel, ids, w, st)], 1u);
+            w.rank[i] = ncell == 1 ? k : rk;  // one cell: the index order is the sorted order
             w.prid[i] = (uint32_t)r;
         }
         __syncthreads();
@@ -288,9 +307,10 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *w
     return off;
 }
 
-// One block: the tile -> replica map of every tile, the work list of the
-// build (every tile of every flagged replica, in replica order), the scan's
-// scheduling counters and the rebuild count.
+// One block: the tile -> replica map of every tile (unless map is null: it
+// never changes), the work list of the build (every tile of every flagged
+// replica, in replica order), the scan's scheduling counters and the rebuild
+// count.
 // (clear: the flags are cleared as they are read, and the one-launch step's
 // grid barrier is reset.  unf, when given, receives the tiles of the
 // replicas NOT flagged, in replica order, and rep_scan[r] is zeroed for
@@ -310,7 +330,8 @@ __device__ void bwork_block(int R, const fpm_replica *__restrict__ reps, uint32_
             if (flag && clear) flag[r] = 0u;
             nr = (uint32_t)rep_ntiles(reps[r].grid);
             t0 = (uint32_t)reps[r].t0;
-            for (uint32_t j = 0; j < nr; ++j) map[t0 + j] = (uint32_t)r;
+            if (map)
+                for (uint32_t j = 0; j < nr; ++j) map[t0 + j] = (uint32_t)r;
             nt = f ? nr : 0u;
             nu = f ? 0u : nr;
             if (f && rep_scan) rep_scan[r] = 0u;
@@ -547,12 +568,14 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
 //   A   drift and per-replica rebuild test (every particle), counting the
 //       flagged replicas (when there are none, B is skipped);
 //   B1  the particles of flagged replicas binned, each with its rank in its
-//       cell from a global counter; the last block writes the work lists;
+//       cell from a global counter (in index order for a replica of one
+//       cell, whose index order is the sorted order);
 //   B2  per flagged replica (a block each): the counters scanned into
 //       cell_start (and zeroed for the next step);
 //   B3  every binned particle's index scattered to its (cell, rank) slot;
 //   B4  per cell of a flagged replica (a warp each): the slice sorted by
-//       particle index and pos / vel / ids / perm gathered into place;
+//       particle index and pos / vel / ids / perm gathered into place; the
+//       last block first writes the work lists;
 //   CD  one ticket queue: first the Verlet scans of the flagged replicas'
 //       tiles (which also write their descriptors), then the force tiles
 //       (forces, the closing half-kick and the energies) of the replicas not
@@ -630,16 +653,32 @@ __device__ bool grid_sync(unsigned *gbar, fpm_dev_status *st)
     return s_ok != 0;
 }
 
+// B1 and B3 take four particles per thread at a time (grid-strided), so the
+// loads of the four start together.
 __device__ __forceinline__ void bstep_bin(const BStepArgs &a)
 {
     const int stride = (int)(gridDim.x * blockDim.x);
-    for (int i = (int)(blockIdx.x * blockDim.x + threadIdx.x); i < a.n; i += stride) {
-        const uint32_t r = __ldcg(a.cw.prid + i);
-        if (__ldcg(a.flag + r) == 0u) continue;
-        const BoxT<float> box = make_box<float>(a.reps[r].box);
-        const GridD g = make_grid(a.reps[r].grid);
-        const uint32_t c = bcell_bin((uint32_t)i, box, g, a.pos, a.vel, a.ids, a.cw, a.status);
-        a.cw.rank[i] = atomicAdd(&a.gcnt[a.reps[r].c0 + (int)c], 1u);
+    for (int i0 = (int)(blockIdx.x * blockDim.x + threadIdx.x); i0 < a.n; i0 += 4 * stride) {
+        uint32_t r[4];
+        bool f[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * stride;
+            r[u] = i < a.n ? __ldcg(a.cw.prid + i) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) f[u] = i0 + u * stride < a.n && __ldcg(a.flag + r[u]) != 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (!f[u]) continue;
+            const int i = i0 + u * stride;
+            const fpm_replica &rp = a.reps[r[u]];
+            const BoxT<float> box = make_box<float>(rp.box);
+            const GridD g = make_grid(rp.grid);
+            const uint32_t c = bcell_bin((uint32_t)i, box, g, a.pos, a.vel, a.ids, a.cw, a.status);
+            // one cell: the index order is the sorted order, and the count is n
+            a.cw.rank[i] = rp.grid.ncell == 1 ? (uint32_t)(i - rp.p0) : atomicAdd(&a.gcnt[rp.c0 + (int)c], 1u);
+        }
     }
 }
 
@@ -648,7 +687,7 @@ __device__ __forceinline__ void bstep_cell_scan(const BStepArgs &a, int r, uint3
     const int ncell = a.reps[r].grid.ncell, c0 = a.reps[r].c0;
     const uint32_t p0 = (uint32_t)a.reps[r].p0;
     for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
-        cnt[c] = __ldcg(a.gcnt + c0 + c);
+        cnt[c] = ncell == 1 ? (uint32_t)a.reps[r].n : __ldcg(a.gcnt + c0 + c);
         a.gcnt[c0 + c] = 0u;
     }
     __syncthreads();
@@ -660,21 +699,37 @@ __device__ __forceinline__ void bstep_cell_scan(const BStepArgs &a, int r, uint3
 __device__ __forceinline__ void bstep_scatter(const BStepArgs &a)
 {
     const int stride = (int)(gridDim.x * blockDim.x);
-    for (int i = (int)(blockIdx.x * blockDim.x + threadIdx.x); i < a.n; i += stride) {
-        const uint32_t r = __ldcg(a.cw.prid + i);
-        if (__ldcg(a.flag + r) == 0u) continue;
-        const uint32_t c = __ldcg(a.cw.cell + i);
-        a.cw.tmp[__ldcg(a.cell_start + a.reps[r].c0 + c) + __ldcg(a.cw.rank + i)] = (uint32_t)i;
+    for (int i0 = (int)(blockIdx.x * blockDim.x + threadIdx.x); i0 < a.n; i0 += 4 * stride) {
+        uint32_t r[4];
+        bool f[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * stride;
+            r[u] = i < a.n ? __ldcg(a.cw.prid + i) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) f[u] = i0 + u * stride < a.n && __ldcg(a.flag + r[u]) != 0u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (!f[u]) continue;
+            const int i = i0 + u * stride;
+            const uint32_t c = __ldcg(a.cw.cell + i);
+            a.cw.tmp[__ldcg(a.cell_start + a.reps[r[u]].c0 + c) + __ldcg(a.cw.rank + i)] = (uint32_t)i;
+        }
     }
 }
 
-// A warp tests 32 cells at once and gathers the flagged ones in turn.
+// Warp w takes the cells w, w + nw, w + 2 nw, ... (nw warps in the grid), so
+// the cells of the flagged replicas, which lie in runs, spread over every
+// warp; it tests 32 of them at once and gathers the flagged ones in turn.
 __device__ __forceinline__ void bstep_gather(const BStepArgs &a)
 {
     const int lane = threadIdx.x & 31;
     const int nw = (int)(gridDim.x * blockDim.x) >> 5;
-    for (int base = ((int)(blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < a.ncell; base += nw * 32) {
-        const int gc = base + lane;
+    const int w = (int)(blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (long long j0 = 0; w + j0 * nw < a.ncell; j0 += 32) {
+        const long long gl = w + (j0 + lane) * nw;
+        const int gc = gl < a.ncell ? (int)gl : a.ncell;
         const bool f = gc < a.ncell && __ldcg(a.flag + __ldcg(a.cw.crid + gc)) != 0u;
         const uint32_t s = f ? __ldcg(a.cell_start + gc) : 0u, e = f ? __ldcg(a.cell_start + gc + 1) : 0u;
         unsigned m = __ballot_sync(kFull, f);
@@ -712,8 +767,6 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_batch_step(BStepArgs a)
     uint32_t ntodo = 0;
     if (rebuild) {
         // B1
-        if (blockIdx.x == gridDim.x - 1)
-            bwork_block(a.R, a.reps, a.flag, a.work, a.map, a.header, a.status, false, wsum, a.unf, a.rep_scan);
         bstep_bin(a);
         if (!grid_sync(a.gbar, a.status)) return;
         // B2
@@ -723,7 +776,10 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_batch_step(BStepArgs a)
         // B3
         bstep_scatter(a);
         if (!grid_sync(a.gbar, a.status)) return;
-        // B4
+        // B4 (the work lists, needed from CD on, by the last block: the
+        // gather's cells are spread thinly enough to hide it)
+        if (blockIdx.x == gridDim.x - 1)
+            bwork_block(a.R, a.reps, a.flag, a.work, nullptr, a.header, a.status, false, wsum, a.unf, a.rep_scan);
         bstep_gather(a);
         if (!grid_sync(a.gbar, a.status)) return;
         for (int r = (int)(blockIdx.x * blockDim.x + threadIdx.x); r < a.R; r += stride) a.flag[r] = 0u;
