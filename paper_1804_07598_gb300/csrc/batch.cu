@@ -434,6 +434,10 @@ __global__ void __launch_bounds__(kTileThreads)
 
 // ---- LJ forces over every tile of the batch ---------------------------------
 
+// Force tiles of at most this many home particles split each list in two
+// (see blj_tile).
+constexpr uint32_t kSplitTile = 128;
+
 // Shared state of a batched force block.
 struct BLjShared {
     TileDesc d;
@@ -478,7 +482,86 @@ __device__ __forceinline__ void blj_tile(uint32_t k, BLjShared &sh, const fpm_re
         if (!in_smem) note_spill(status);
         const bool staged = in_smem ? stage_positions(d, box, pos, sp, bar, phase, status) : true;
         const bool all_mode = cfg.mode[0] == kModeAll || cfg.mode[1] == kModeAll || cfg.mode[2] == kModeAll;
-        for (uint32_t i = d.h0 + threadIdx.x; staged && i < d.h1; i += blockDim.x) {
+        const uint32_t nh = d.h1 - d.h0;
+        if (nh <= kSplitTile) {
+            // A small tile (the small replicas' tiles leave most of a block
+            // idle): each home particle's list in two halves, the even and
+            // the odd words, whose sums are added half 0 + half 1.  With a
+            // lane per half the lane pair 2q, 2q + 1 takes particle q; with
+            // fewer threads one thread takes both halves in turn.  The same
+            // sums either way, whatever the block size.
+            const bool pair = 2u * nh <= blockDim.x;
+            const uint32_t q = pair ? (threadIdx.x >> 1) : threadIdx.x;
+            // half sums of particle i: forces, S12 - S6 and 2 S12 - S6 (u, w), pairs
+            auto half_sums = [&](uint32_t i, uint32_t half, const float4 &pi, uint32_t m, float (&o)[5],
+                                 uint32_t &np) {
+                o[0] = o[1] = o[2] = o[3] = o[4] = 0.0f;
+                np = 0;
+                if (!in_smem)
+                    lj_sweep<float, false, false, 2>(cfg, box, d, pos, sp, pi, m, words + i, ld, P, o[0], o[1], o[2],
+                                                     o[3], o[4], np, half);
+                else if (d.slow && all_mode)
+                    lj_sweep<float, false, true, 2>(cfg, box, d, pos, sp, pi, m, words + i, ld, P, o[0], o[1], o[2],
+                                                    o[3], o[4], np, half);
+                else if (d.slow)
+                    lj_sweep_wall<float, 2>(box, sp, pi, m, words + i, ld, P, o[0], o[1], o[2], o[3], o[4], np, half);
+                else
+                    lj_sweep<float, true, true, 2>(cfg, box, d, pos, sp, pi, m, words + i, ld, P, o[0], o[1], o[2],
+                                                   o[3], o[4], np, half);
+            };
+            if (staged && q < nh) {
+                const uint32_t i = d.h0 + q;
+                const float4 pi = pos[i];
+                const uint32_t m = nn[i];
+                float o[5];
+                uint32_t np;
+                if (pair) {
+                    half_sums(i, threadIdx.x & 1u, pi, m, o, np);
+                    // the lanes of this warp in the branch: a prefix (threadIdx.x < 2 nh)
+                    const uint32_t live = 2u * nh - (threadIdx.x & ~31u);
+                    const unsigned act = live >= 32u ? kFull : ((1u << live) - 1u);
+                    float po[5];
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) po[c] = __shfl_xor_sync(act, o[c], 1);
+                    const uint32_t pnp = __shfl_xor_sync(act, np, 1);
+                    if (threadIdx.x & 1u) {  // the odd lane holds half 1: half 0 + half 1 as below
+#pragma unroll
+                        for (int c = 0; c < 5; ++c) o[c] = po[c] + o[c];
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 5; ++c) o[c] = o[c] + po[c];
+                    }
+                    np += pnp;
+                } else {
+                    float o1[5];
+                    uint32_t np1;
+                    half_sums(i, 0u, pi, m, o, np);
+                    half_sums(i, 1u, pi, m, o1, np1);
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) o[c] = o[c] + o1[c];
+                    np += np1;
+                }
+                if (!pair || (threadIdx.x & 1u) == 0u) {
+                    float4 f;
+                    f.x = P.eps24 * o[0];
+                    f.y = P.eps24 * o[1];
+                    f.z = P.eps24 * o[2];
+                    f.w = 0.5f * P.eps4 * o[3];
+                    force[i] = f;
+                    if (vel) {  // the closing half-kick of velocity Verlet, v += dt/2 F
+                        float4 v = vel[i];
+                        v.x += hdt * f.x;
+                        v.y += hdt * f.y;
+                        v.z += hdt * f.z;
+                        vel[i] = v;
+                    }
+                    usum += P.eps4 * o[3];
+                    wsum += P.eps24 * o[4];
+                    npsum += np;
+                }
+            }
+        }
+        for (uint32_t i = d.h0 + threadIdx.x; staged && nh > kSplitTile && i < d.h1; i += blockDim.x) {
             const float4 pi = pos[i];
             const uint32_t m = nn[i];
             float fx = 0.0f, fy = 0.0f, fz = 0.0f, u = 0.0f, w = 0.0f;

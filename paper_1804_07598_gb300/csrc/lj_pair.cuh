@@ -80,34 +80,38 @@ __device__ __forceinline__ void lj_pair_wall(const V4<T> *__restrict__ st, const
 }
 
 // The LJ sums of one home particle over its list (list words prefetched
-// kLjChunk at a time, see for_each_entry).
+// kLjChunk at a time, see for_each_entry); with kStride = 2 over the words
+// w_first, w_first + 2, ... only (half of the list).
 constexpr uint32_t kLjChunk = 3;
 
-template <typename T, bool FAST, bool SMEM>
+template <typename T, bool FAST, bool SMEM, uint32_t kStride = 1>
 __device__ __forceinline__ void lj_sweep(const TileCfg &cfg, const BoxT<T> &box, const TileDesc &d,
                                          const V4<T> *__restrict__ pos, const V4<T> *__restrict__ st,
                                          const V4<T> &pi, uint32_t m, const uint32_t *__restrict__ col, int64_t ld,
-                                         const LJParams<T> &P, T &fx, T &fy, T &fz, T &u, T &w, uint32_t &np)
+                                         const LJParams<T> &P, T &fx, T &fy, T &fz, T &u, T &w, uint32_t &np,
+                                         uint32_t w_first = 0)
 {
     T S12 = 0, S6 = 0;
-    for_each_entry<kLjChunk>(m, col, ld, [&](int s) {
-        lj_pair<T, FAST, SMEM>(cfg, box, d, pos, st, pi, s, P, fx, fy, fz, S12, S6, np);
-    });
+    for_each_entry<kLjChunk, kStride>(
+        m, col, ld, [&](int s) { lj_pair<T, FAST, SMEM>(cfg, box, d, pos, st, pi, s, P, fx, fy, fz, S12, S6, np); },
+        w_first);
     u += S12 - S6;
     w += (T)2 * S12 - S6;
 }
 
-template <typename T>
+template <typename T, uint32_t kStride = 1>
 __device__ __forceinline__ void lj_sweep_wall(const BoxT<T> &box, const V4<T> *__restrict__ st, const V4<T> &pi,
                                               uint32_t m, const uint32_t *__restrict__ col, int64_t ld,
-                                              const LJParams<T> &P, T &fx, T &fy, T &fz, T &u, T &w, uint32_t &np)
+                                              const LJParams<T> &P, T &fx, T &fy, T &fz, T &u, T &w, uint32_t &np,
+                                              uint32_t w_first = 0)
 {
     V4<T> pim = pi;
     pim.x = rsub(pi.x, box.L[0]);
     pim.y = rsub(pi.y, box.L[1]);
     pim.z = rsub(pi.z, box.L[2]);
     T S12 = 0, S6 = 0;
-    for_each_entry<kLjChunk>(m, col, ld, [&](int s) { lj_pair_wall<T>(st, pi, pim, s, P, fx, fy, fz, S12, S6, np); });
+    for_each_entry<kLjChunk, kStride>(
+        m, col, ld, [&](int s) { lj_pair_wall<T>(st, pi, pim, s, P, fx, fy, fz, S12, S6, np); }, w_first);
     u += S12 - S6;
     w += (T)2 * S12 - S6;
 }
