@@ -47,11 +47,13 @@ __device__ __forceinline__ int replica_of_particle(const fpm_replica *__restrict
 
 // One particle (every lane of the warp calls it; i may be past n).  A
 // replica's flag is set by the first lane that finds it over; nflag, when
-// given, counts the replicas flagged.
+// given, counts the replicas flagged, and flist receives them (in no
+// particular order).
 __device__ __forceinline__ void bdrift_one(int i, int n, int R, const fpm_replica *__restrict__ reps, float hdt,
                                            float dt, float4 *__restrict__ pos, float4 *__restrict__ vel,
                                            const float4 *__restrict__ force, const float4 *__restrict__ ref, float th,
-                                           uint32_t *__restrict__ flag, uint32_t *nflag = nullptr)
+                                           uint32_t *__restrict__ flag, uint32_t *nflag = nullptr,
+                                           uint32_t *flist = nullptr)
 {
     bool over = false;
     if (i < n) {
@@ -73,7 +75,10 @@ __device__ __forceinline__ void bdrift_one(int i, int n, int R, const fpm_replic
     if (!over) return;
     const int r = replica_of_particle(reps, R, (uint32_t)i);
     const unsigned peers = __match_any_sync(m, r);
-    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1 && atomicOr(&flag[r], 1u) == 0u && nflag) atomicAdd(nflag, 1u);
+    if ((int)(threadIdx.x & 31) == __ffs(peers) - 1 && atomicOr(&flag[r], 1u) == 0u && nflag) {
+        const uint32_t q = atomicAdd(nflag, 1u);
+        if (flist) flist[q] = (uint32_t)r;
+    }
 }
 
 __global__ void __launch_bounds__(256)
@@ -648,8 +653,10 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
 // ---- one persistent launch per step ----------------------------------------
 // The whole batched step as phases of one cooperative kernel (all blocks
 // resident at once), separated by grid barriers:
-//   A   drift and per-replica rebuild test (every particle), counting the
-//       flagged replicas (when there are none, B is skipped);
+//   A   drift and per-replica rebuild test (every particle), listing the
+//       flagged replicas (when there are none, B is skipped; B1, B3 and B4
+//       visit only the listed replicas' particles and cells, through prefix
+//       tables each block builds in shared memory);
 //   B1  the particles of flagged replicas binned, each with its rank in its
 //       cell from a global counter (in index order for a replica of one
 //       cell, whose index order is the sorted order);
@@ -696,6 +703,8 @@ struct BStepArgs {
     fpm_dev_status *status;
     unsigned *gbar;   // grid barrier: [0] arrivals, [1] generation (list header bytes 32..39)
     uint32_t *nflag;  // replicas flagged this step (workspace bytes 48..51; zero between steps)
+    uint32_t *flist;  // [R]: the flagged replicas, in the order they were flagged
+    int smem_bytes, cnt_bytes;  // the block's dynamic shared memory; B2's counters at its start
 };
 
 // A barrier over every block of the (cooperative) grid.  Thread 0 of each
@@ -824,6 +833,120 @@ __device__ __forceinline__ void bstep_gather(const BStepArgs &a)
     }
 }
 
+// The flagged replicas as tables in shared memory (the end of the block's
+// dynamic shared memory, clear of B2's counters): fr[q] the replica,
+// pp[q] / cp[q] the particles / cells of fr[0..q) (pp[nf], cp[nf] the
+// totals).  Binning, scatter and gather then visit only the flagged
+// replicas' particles and cells.  All threads call it; returns false (no
+// tables) when they do not fit.
+struct BFlagTab {
+    uint32_t *fr, *pp, *cp;
+    uint32_t nf;
+};
+
+__device__ __forceinline__ bool bstep_tables(const BStepArgs &a, unsigned char *smem_raw, uint32_t nf, uint32_t *wsum,
+                                             BFlagTab &t)
+{
+    const size_t need = (3 * (size_t)nf + 2) * sizeof(uint32_t);
+    if ((size_t)a.cnt_bytes + need + 16 > (size_t)a.smem_bytes) return false;
+    uint32_t *base = (uint32_t *)(smem_raw + (((size_t)a.smem_bytes - need) & ~(size_t)15));  // >= cnt_bytes
+    t.fr = base;
+    t.pp = base + nf;
+    t.cp = base + 2 * nf + 1;
+    t.nf = nf;
+    uint32_t carry_p = 0, carry_c = 0;
+    for (uint32_t b0 = 0; b0 < nf; b0 += blockDim.x) {
+        const uint32_t q = b0 + threadIdx.x;
+        uint32_t r = 0, np = 0, nc = 0;
+        if (q < nf) {
+            r = __ldcg(a.flist + q);
+            np = (uint32_t)a.reps[r].n;
+            nc = (uint32_t)a.reps[r].grid.ncell;
+            t.fr[q] = r;
+        }
+        uint32_t tp, tc;
+        const uint32_t op = block_exclusive_scan(np, wsum, &tp);
+        const uint32_t oc = block_exclusive_scan(nc, wsum, &tc);
+        if (q < nf) {
+            t.pp[q] = carry_p + op;
+            t.cp[q] = carry_c + oc;
+        }
+        carry_p += tp;
+        carry_c += tc;
+    }
+    if (threadIdx.x == 0) {
+        t.pp[nf] = carry_p;
+        t.cp[nf] = carry_c;
+    }
+    __syncthreads();
+    return true;
+}
+
+// The entry q of a prefix table with tab[q] <= j < tab[q + 1].
+__device__ __forceinline__ uint32_t tab_find(const uint32_t *tab, uint32_t nf, uint32_t j)
+{
+    uint32_t lo = 0, hi = nf - 1;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (tab[mid] <= j) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void bstep_bin_tab(const BStepArgs &a, const BFlagTab &t)
+{
+    const uint32_t P = t.pp[t.nf], stride = gridDim.x * blockDim.x;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < P; j += stride) {
+        const uint32_t q = tab_find(t.pp, t.nf, j);
+        const fpm_replica &rp = a.reps[t.fr[q]];
+        const uint32_t k = j - t.pp[q], i = (uint32_t)rp.p0 + k;
+        const BoxT<float> box = make_box<float>(rp.box);
+        const GridD g = make_grid(rp.grid);
+        const uint32_t c = bcell_bin(i, box, g, a.pos, a.vel, a.ids, a.cw, a.status);
+        // one cell: the index order is the sorted order, and the count is n
+        a.cw.rank[i] = rp.grid.ncell == 1 ? k : atomicAdd(&a.gcnt[rp.c0 + (int)c], 1u);
+    }
+}
+
+__device__ __forceinline__ void bstep_scatter_tab(const BStepArgs &a, const BFlagTab &t)
+{
+    const uint32_t P = t.pp[t.nf], stride = gridDim.x * blockDim.x;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < P; j += stride) {
+        const uint32_t q = tab_find(t.pp, t.nf, j);
+        const fpm_replica &rp = a.reps[t.fr[q]];
+        const uint32_t i = (uint32_t)rp.p0 + (j - t.pp[q]);
+        const uint32_t c = __ldcg(a.cw.cell + i);
+        a.cw.tmp[__ldcg(a.cell_start + rp.c0 + c) + __ldcg(a.cw.rank + i)] = i;
+    }
+}
+
+// Warp w takes the flagged cells w, w + nw, ... (nw warps), 32 at a time.
+__device__ __forceinline__ void bstep_gather_tab(const BStepArgs &a, const BFlagTab &t)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t C = t.cp[t.nf];
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (uint64_t j0 = 0; w + j0 * nw < C; j0 += 32) {
+        const uint64_t jl = w + (j0 + lane) * nw;
+        const bool f = jl < C;
+        uint32_t s = 0, e = 0;
+        if (f) {
+            const uint32_t j = (uint32_t)jl, q = tab_find(t.cp, t.nf, j);
+            const int gc = a.reps[t.fr[q]].c0 + (int)(j - t.cp[q]);
+            s = __ldcg(a.cell_start + gc);
+            e = __ldcg(a.cell_start + gc + 1);
+        }
+        unsigned m = __ballot_sync(kFull, f && e > s);
+        while (m) {
+            const int qq = __ffs(m) - 1;
+            m &= m - 1u;
+            bcell_gather(__shfl_sync(kFull, s, qq), __shfl_sync(kFull, e, qq), a.cw, a.pos, a.vel, a.ids, a.perm);
+        }
+    }
+}
+
 // MINB: blocks per SM the register allocation is bounded for (4: 64
 // registers; 2: no bound in practice, half the warps).
 template <int MINB>
@@ -844,26 +967,31 @@ __global__ void __launch_bounds__(kTileThreads, MINB) k_batch_step(BStepArgs a)
     // A
     for (int base = (int)(blockIdx.x * blockDim.x); base < a.n; base += stride)
         bdrift_one(base + (int)threadIdx.x, a.n, a.R, a.reps, a.hdt, a.dt, a.pos, a.vel, a.force, a.pos_ref, a.th,
-                   a.flag, a.nflag);
+                   a.flag, a.nflag, a.flist);
     if (!grid_sync(a.gbar, a.status)) return;
-    const bool rebuild = __ldcg(a.nflag) != 0u;  // the same in every block
+    const uint32_t nf = __ldcg(a.nflag);  // the same in every block
+    const bool rebuild = nf != 0u;
     uint32_t ntodo = 0;
     if (rebuild) {
+        BFlagTab t;
+        const bool tab = bstep_tables(a, smem_raw, nf, wsum, t);  // the same in every block
         // B1
-        bstep_bin(a);
+        if (tab) bstep_bin_tab(a, t);
+        else bstep_bin(a);
         if (!grid_sync(a.gbar, a.status)) return;
         // B2
-        for (int r = blockIdx.x; r < a.R; r += gridDim.x)
-            if (__ldcg(a.flag + r) != 0u) bstep_cell_scan(a, r, cnt, wsum);
+        for (uint32_t q = blockIdx.x; q < nf; q += gridDim.x) bstep_cell_scan(a, (int)__ldcg(a.flist + q), cnt, wsum);
         if (!grid_sync(a.gbar, a.status)) return;
         // B3
-        bstep_scatter(a);
+        if (tab) bstep_scatter_tab(a, t);
+        else bstep_scatter(a);
         if (!grid_sync(a.gbar, a.status)) return;
         // B4 (the work lists, needed from CD on, by the last block: the
         // gather's cells are spread thinly enough to hide it)
         if (blockIdx.x == gridDim.x - 1)
             bwork_block(a.R, a.reps, a.flag, a.work, nullptr, a.header, a.status, false, wsum, a.unf, a.rep_scan);
-        bstep_gather(a);
+        if (tab) bstep_gather_tab(a, t);
+        else bstep_gather(a);
         if (!grid_sync(a.gbar, a.status)) return;
         for (int r = (int)(blockIdx.x * blockDim.x + threadIdx.x); r < a.R; r += stride) a.flag[r] = 0u;
         ntodo = __ldcg(a.header);
@@ -925,9 +1053,10 @@ struct BatchWs {
 
 // Force workspace: counters (bytes 16, 32, 48), the per-tile sums, the
 // per-replica completion counters, and for the one-launch step the tiles of
-// the replicas not rebuilt and the per-replica scanned-tile counters.
+// the replicas not rebuilt, the per-replica scanned-tile counters and the
+// list of the flagged replicas.
 static size_t bws_layout(const fpm_batch &b, size_t *off_done, size_t *off_unf = nullptr,
-                         size_t *off_scan = nullptr)
+                         size_t *off_scan = nullptr, size_t *off_flist = nullptr)
 {
     size_t o = 256 + (size_t)b.ntiles_total * 3 * sizeof(double);
     o = (o + 255) & ~(size_t)255;
@@ -936,6 +1065,8 @@ static size_t bws_layout(const fpm_batch &b, size_t *off_done, size_t *off_unf =
     if (off_unf) *off_unf = o;
     o = (o + (size_t)b.ntiles_total * sizeof(uint32_t) + 255) & ~(size_t)255;
     if (off_scan) *off_scan = o;
+    o = (o + (size_t)b.R * sizeof(uint32_t) + 255) & ~(size_t)255;
+    if (off_flist) *off_flist = o;
     return o + (size_t)b.R * sizeof(uint32_t);
 }
 
@@ -1261,8 +1392,8 @@ extern "C" fpm_status fpm_batch_step(const fpm_batch *batch, const fpm_replica *
     if (!cell_ws || cell_ws_bytes < cneed || ((uintptr_t)cell_ws & 15u) != 0)
         return fpm_fail(FPM_ERR_WORKSPACE, "fpm_batch_step: cell workspace %zu < %zu bytes or not 16-B aligned",
                         cell_ws_bytes, cneed);
-    size_t off_done = 0, off_unf = 0, off_scan = 0;
-    const size_t need = bws_layout(*batch, &off_done, &off_unf, &off_scan);
+    size_t off_done = 0, off_unf = 0, off_scan = 0, off_flist = 0;
+    const size_t need = bws_layout(*batch, &off_done, &off_unf, &off_scan, &off_flist);
     if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 15u) != 0)
         return fpm_fail(FPM_ERR_WORKSPACE, "fpm_batch_step: workspace %zu < %zu bytes or not 16-B aligned",
                         workspace_bytes, need);
@@ -1316,6 +1447,7 @@ extern "C" fpm_status fpm_batch_step(const fpm_batch *batch, const fpm_replica *
     a.status = d_status;
     a.gbar = (unsigned *)(lb + 32);
     a.nflag = (uint32_t *)(w + 48);
+    a.flist = (uint32_t *)(w + off_flist);
 
     // Every block must be resident at once (the grid barriers): the grid is
     // the occupancy limit, or sweep_blocks when that is smaller, and the
@@ -1323,6 +1455,8 @@ extern "C" fpm_status fpm_batch_step(const fpm_batch *batch, const fpm_replica *
     const size_t cnt_bytes = ((size_t)batch->max_ncell + 1) * sizeof(uint32_t);
     const size_t stage_bytes = (size_t)a.stage_cap * sizeof(float4);
     const size_t smem = cnt_bytes > stage_bytes ? cnt_bytes : stage_bytes;
+    a.smem_bytes = (int)smem;
+    a.cnt_bytes = (int)cnt_bytes;
     const int minb = batch->step_blocks_per_sm == 0 ? 4 : batch->step_blocks_per_sm;
     auto kern = minb == 2 ? k_batch_step<2> : minb == 3 ? k_batch_step<3> : k_batch_step<4>;
     smem_opt_in((const void *)kern);
