@@ -916,6 +916,16 @@ __device__ __forceinline__ void bstep_scatter_tab(const BStepArgs &a, const BFla
         const uint32_t q = tab_find(t.pp, t.nf, j);
         const fpm_replica &rp = a.reps[t.fr[q]];
         const uint32_t i = (uint32_t)rp.p0 + (j - t.pp[q]);
+        if (rp.grid.ncell == 1) {
+            // a replica of one cell keeps its index order: its particles go
+            // straight into place here, by every thread, instead of through
+            // one warp in the gather
+            a.pos[i] = __ldcg(a.cw.spos + i);
+            if (a.vel) a.vel[i] = __ldcg(a.cw.svel + i);
+            if (a.ids) a.ids[i] = __ldcg(a.cw.sid + i);
+            if (a.perm) a.perm[i] = i;
+            continue;
+        }
         const uint32_t c = __ldcg(a.cw.cell + i);
         a.cw.tmp[__ldcg(a.cell_start + rp.c0 + c) + __ldcg(a.cw.rank + i)] = i;
     }
@@ -934,9 +944,12 @@ __device__ __forceinline__ void bstep_gather_tab(const BStepArgs &a, const BFlag
         uint32_t s = 0, e = 0;
         if (f) {
             const uint32_t j = (uint32_t)jl, q = tab_find(t.cp, t.nf, j);
-            const int gc = a.reps[t.fr[q]].c0 + (int)(j - t.cp[q]);
-            s = __ldcg(a.cell_start + gc);
-            e = __ldcg(a.cell_start + gc + 1);
+            const fpm_replica &rp = a.reps[t.fr[q]];
+            if (rp.grid.ncell > 1) {  // (a replica of one cell was placed by the scatter)
+                const int gc = rp.c0 + (int)(j - t.cp[q]);
+                s = __ldcg(a.cell_start + gc);
+                e = __ldcg(a.cell_start + gc + 1);
+            }
         }
         unsigned m = __ballot_sync(kFull, f && e > s);
         while (m) {
