@@ -59,3 +59,38 @@ def test_ensemble_statistics():
     assert abs(1000 / L[0] ** 3 - 0.8) < 1e-12
     assert len({tuple(p) for p in np.round(x[:, :3], 9)}) == 1000  # distinct sites
     assert np.allclose(v[:, :3].sum(0), 0, atol=1e-10)
+
+
+def test_step_rejects_bad_arguments(fpm_lib):
+    """fpm_batch_step checks its arguments before any device work: a bad
+    register bound, pos / vel aliasing, no flag array, and a list object or a
+    workspace below the sizes the size queries give.  The pointers are
+    aligned fakes that a valid call would dereference; none is touched."""
+    import ctypes
+    counts = [300, 1200]
+    Ls = [max((c / 0.8) ** (1 / 3), 6.0) for c in counts]
+    reps, b = fpm.fpm_batch_plan(boxes_of(Ls), counts, 2.8, 0)
+    cap = 96
+    lb = fpm.fpm_batch_list_bytes(b, cap)
+    cb = fpm.fpm_batch_celllist_workspace(b)
+    wb = fpm.fpm_batch_workspace(b)
+    # the step's regions: flagged list, scanned-tile counts, tile queue; cell counters, replica ids
+    assert wb >= 256 + 24 * b.ntiles_total + 4 * (3 * b.R + b.ntiles_total)
+    assert cb >= 4 * (7 * b.n_total + 2 * b.ncell_total)
+    P, Q, V, F = 0x100000, 0x200000, 0x300000, 0x400000
+    L, C, W = 0x1000000, 0x2000000, 0x3000000
+
+    def step(batch, pos=P, vel=V, list_bytes=lb, flag=Q, cell_bytes=cb, ws_bytes=wb):
+        return fpm_lib.fpm_batch_step(ctypes.byref(batch), P, 0.005, 0.3, 2.8, cap, 1.0, 1.0, 2.5, pos, vel, F, P,
+                                      None, Q, None, L, list_bytes, Q, flag, C, cell_bytes, W, ws_bytes, None,
+                                      None, None)
+
+    bad_b = fpm.fpm_batch.from_buffer_copy(b)
+    bad_b.step_blocks_per_sm = 1
+    assert step(bad_b) == fpm.FPM_ERR_INVALID
+    assert "step_blocks_per_sm" in fpm.fpm_last_error()
+    assert step(b, vel=P) == fpm.FPM_ERR_INVALID
+    assert step(b, flag=None) == fpm.FPM_ERR_INVALID
+    assert step(b, list_bytes=lb - 4) == fpm.FPM_ERR_WORKSPACE
+    assert step(b, cell_bytes=cb - 4) == fpm.FPM_ERR_WORKSPACE
+    assert step(b, ws_bytes=wb - 4) == fpm.FPM_ERR_WORKSPACE
