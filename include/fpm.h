@@ -675,9 +675,11 @@ typedef struct {
 
 /* Sizes of a batch (host struct, passed by pointer to every batched call).
  * stage_cap and sweep_blocks act as in fpm_grid, for every replica; the
- * plan sets stage_cap to an estimate and sweep_blocks to 0, and the caller
- * may change both between calls (launch-shape choices: results do not
- * depend on them, except that a tile whose neighbourhood exceeds stage_cap
+ * plan sets stage_cap to an estimate and sweep_blocks, sweep_threads and
+ * step_blocks_per_sm to 0, and the caller may change them between calls
+ * (launch-shape choices: lists and forces do not depend on them, and the
+ * per-replica energies only up to the FP32 rounding of the per-tile sums,
+ * which group by block size; a tile whose neighbourhood exceeds stage_cap
  * reads it from global memory and is counted in d_status->spilled). */
 typedef struct {
     int32_t R;
