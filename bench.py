@@ -43,6 +43,7 @@ FLOP_PER_PAIR = 30
 # virial 1, energy 2.  Reported beside the roofline as the executed work.
 FLOP_PER_SLOT = 25
 FALLBACK_HBM_GBS = 6800.0
+P2M_FLOP_PER_PAIR = 10  # M'4 P2M: weight product w_x w_y w_z (2) + four FMAs into the node (8)
 
 # DRAM bytes per launch of the dominant kernel from one ncu capture of the
 # profiling target `--profile forces`, valid only while its source files hash
@@ -747,6 +748,15 @@ def run_ours(args, ws, rank, local):
                "p2m_us": full_us, "bin_us": bin_us, "gather_us": gather_us, "m2p_us": m2p_us,
                "m2p_unbinned_order_us": m2p_unsorted_us,
                "gather_bytes": 32 * npm + 16 * 128 ** 3,
+               # the gather kernel against the FP32 and HBM peaks (fractions
+               # filled in below): per particle-node pair the weight product
+               # (2 multiplies) and four FMAs, 10 FLOP; per particle 32 B
+               # (position, value) and per node 16 B
+               "gather_kernel": {"kernel": "k_p2m", "launch_us": gather_us,
+                                 "alg_flop_per_pair": P2M_FLOP_PER_PAIR,
+                                 "achieved_tflops": P2M_FLOP_PER_PAIR * 64 * npm / (gather_us * 1e-6) / 1e12,
+                                 "alg_bytes_per_launch": 32 * npm + 16 * 128 ** 3,
+                                 "achieved_gbs": (32 * npm + 16 * 128 ** 3) / (gather_us * 1e-6) / 1e9},
                "paper": "the same interpolation: 0.41 s in OpenFPM and 3.4 s in PPM on a single core (context only)"}
         del pm, xp, vp, outp
 
@@ -790,9 +800,9 @@ def run_ours(args, ws, rank, local):
     clocks = clk.summary()
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
-    for kern in ((sph or {}).get("rates_kernel"), (adj or {}).get("hvp_kernel")):
+    for kern in ((sph or {}).get("rates_kernel"), (adj or {}).get("hvp_kernel"), (p2m or {}).get("gather_kernel")):
         if kern:
-            kern["frac_fp32_executed"] = kern["achieved_tflops"] / fp32_peak
+            kern["frac_fp32" if "alg_flop_per_pair" in kern else "frac_fp32_executed"] = kern["achieved_tflops"] / fp32_peak
             kern["frac_hbm"] = kern["achieved_gbs"] / peak
             kern["peaks"] = f"FP32 {fp32_peak:.1f} TFLOP/s (CUDA cores), HBM {peak:.0f} GB/s ({peak_kind})"
 
