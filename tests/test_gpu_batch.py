@@ -380,3 +380,35 @@ def test_batch_one_launch_step_barrier_timeout(cuda):
     for k in ("pos", "vel", "force", "ids", "energy", "nn", "list"):
         assert np.array_equal(sa[k], sb[k]), k
     a.check_status()
+
+
+def test_batch_one_launch_step_many_flagged_replicas(cuda):
+    """Hundreds of replicas flagged in one step, more than the per-block
+    tables of flagged replicas hold in shared memory: the step's binning,
+    scatter and gather then walk every particle and cell of the batch (the
+    replica of each read from the cell workspace) instead, with the same
+    results as the separate calls; tiles beyond the staging capacity read
+    their neighbourhoods from global memory on both sides."""
+    reps = [inputs.replica_state(256, 0.9, 1.0, 900 + r) for r in range(700)]
+    reps += [inputs.replica_state(3000, 0.8, 1.0, 1900 + r) for r in range(20)]
+    a = LJBatch(reps, skin=0.02, fused=True)
+    b = LJBatch(reps, skin=0.02, fused=False)
+    # a small staging capacity (the larger replicas' tiles then read their
+    # neighbourhoods from global memory), which also bounds the tables
+    a.batch.stage_cap = b.batch.stage_cap = 384
+    nr0 = fpm.read_status(a.status).nrebuild
+    for _ in range(3):
+        a.step(1)
+        b.step(1)
+    sa, sb = batch_state(a), batch_state(b)
+    for k in sa:
+        assert np.array_equal(sa[k], sb[k]), k
+    ta = a.check_status()
+    per_step = (ta.nrebuild - nr0) / 3
+    # the tables: 12 B per flagged replica (+ 8 B) after B2's counters, within
+    # the step's dynamic shared memory (the larger of the counters and the staging)
+    stage = min((a.batch.stage_cap + 31) // 32 * 32, 200 * 1024 // 16 // 32 * 32) * 16
+    cnt = (a.batch.max_ncell + 1) * 4
+    capacity = (max(stage, cnt) - cnt - 16 - 8) // 12
+    assert per_step > capacity, (per_step, capacity)
+    assert ta.spilled > 0
