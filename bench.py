@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=8)
     ap.add_argument("--cpu-omp-steps", type=int, default=30)
     ap.add_argument("--adjoint-steps", type=int, default=200)
+    ap.add_argument("--small-steps", type=int, default=2000)
     ap.add_argument("--sph-steps", type=int, default=500)
     ap.add_argument("--batch-steps", type=int, default=300)
     ap.add_argument("--batch-seq-steps", type=int, default=3)
@@ -466,6 +467,32 @@ def run_ours(args, ws, rank, local):
     d2h = h2d + he.numel() * he.element_size()
     s.check_status()
 
+    # the small LJ system (4000 atoms, FCC 10^3 x 4, the 4000-atom config),
+    # FP64 and FP32, replayed from a CUDA graph of one step
+    small = None
+    if args.small_steps > 0:
+        wls = inputs.WORKLOADS["lj_small"]
+        xs_, vs_, Ls_ = inputs.lj_state(wls)
+        small = {"workload": f"lj_small: {xs_.shape[0]} LJ particles (FCC 10^3 x 4), rho 0.8442, T* 0.72, "
+                             "rc 2.5, skin 0.3, dt 0.005, CUDA graph of 1 step"}
+        for sprec in ("f64", "f32"):
+            ss = LJSystem(xs_, vs_, Ls_, eps=wls.eps, sigma=wls.sigma, rc=wls.rc, skin=wls.skin, dt=wls.dt,
+                          precision=sprec)
+            gs = ss.capture(steps_per_graph=1)
+            for _ in range(20):
+                gs.replay()
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(args.small_steps):
+                gs.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            ss.check_status()
+            sms = e0.elapsed_time(e1) / args.small_steps
+            small[sprec] = {"steps_per_s": 1e3 / sms, "ms_per_step": sms,
+                            "tiles": int(ss.grid.tiles_x * ss.grid.nc[1] * ss.grid.nc[2])}
+            del ss, gs
+
     # adjoint / forward cost on the differentiable workload (32,768 particles,
     # 200 NVE steps, checkpoints every 20, FP32 forward, FP64 adjoint state)
     adj = None
@@ -849,6 +876,7 @@ def run_ours(args, ws, rank, local):
                 "d2h_bytes_per_step": d2h,
                 "transfer": "pinned host buffers in the packed x, y, z layout, copied in three overlapped pieces "
                             "per direction (copy engines), packed / unpacked on the device; energies copied back"},
+        "small": small,
         "adjoint": adj,
         "sph": sph,
         "sph_full_run": sph_full,

@@ -89,6 +89,102 @@ __global__ void __launch_bounds__(kTileThreads)
     }
 }
 
+// The sweep for small systems, whose few tiles leave most of the GPU idle:
+// KS threads per home particle (aligned lane groups), thread `part` walking
+// the list words part, part + KS, ...; the KS partial sums are added by a
+// fixed xor-shuffle tree (bit-reproducible; the grouping differs from the
+// one-thread sweep's, so the forces agree with it to rounding).
+template <typename T, uint32_t KS>
+__global__ void __launch_bounds__(kTileThreads)
+    k_lj_tiles_split(TileCfg cfg, BoxT<T> box, const V4<T> *__restrict__ pos, ListView lv,
+                     const uint32_t *__restrict__ nn, int64_t ld, int stage_cap, LJParams<T> P,
+                     V4<T> *__restrict__ force, Sched sched, double *part_sums, double *out, fpm_dev_status *status,
+                     V4<T> *__restrict__ vel, T hdt, long long wait0)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    V4<T> *sp = (V4<T> *)smem_raw;
+    __shared__ TileDesc d;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t s_k;
+    __shared__ bool s_last;
+    stage_init(&bar);
+    uint32_t phase = 0;
+    const uint32_t *__restrict__ words = lv.words;
+    const uint32_t ntodo = *lv.count;
+    const uint32_t part = threadIdx.x % KS, per_pass = blockDim.x / KS;
+    uint32_t ahead = 0;
+    for (uint32_t k = blockIdx.x; k < ntodo; k = ticket_next(ahead, &s_k)) {
+        ahead = ticket_ahead(sched);
+        load_desc(lv.descs + lv.active[k], d);
+        if (d.h0 + threadIdx.x < d.h1) prefetch_home(pos, nn, words, ld, d.h0 + threadIdx.x, 1);
+        const bool in_smem = d.M <= stage_cap;
+        if (!in_smem) note_spill(status);
+        const bool staged =
+            in_smem ? stage_positions(d, box, pos, sp, &bar, phase, status, nullptr, nullptr, wait0) : true;
+        const bool all_mode = cfg.mode[0] == kModeAll || cfg.mode[1] == kModeAll || cfg.mode[2] == kModeAll;
+        T usum = 0, wsum = 0;
+        uint32_t npsum = 0;
+        const uint32_t nh = d.h1 - d.h0;
+        for (uint32_t q0 = 0; staged && q0 < nh; q0 += per_pass) {  // the same trip count in every thread
+            const uint32_t q = q0 + threadIdx.x / KS;
+            const bool act = q < nh;
+            const uint32_t i = d.h0 + (act ? q : 0u);
+            T o[5] = {0, 0, 0, 0, 0};
+            uint32_t np = 0;
+            if (act) {
+                const V4<T> pi = pos[i];
+                const uint32_t m = nn[i];
+                if (!in_smem)
+                    lj_sweep<T, false, false, KS>(cfg, box, d, pos, sp, pi, m, words + i, ld, P, o[0], o[1], o[2],
+                                                  o[3], o[4], np, part);
+                else if (d.slow && all_mode)
+                    lj_sweep<T, false, true, KS>(cfg, box, d, pos, sp, pi, m, words + i, ld, P, o[0], o[1], o[2],
+                                                 o[3], o[4], np, part);
+                else if (d.slow)
+                    lj_sweep_wall<T, KS>(box, sp, pi, m, words + i, ld, P, o[0], o[1], o[2], o[3], o[4], np, part);
+                else
+                    lj_sweep<T, true, true, KS>(cfg, box, d, pos, sp, pi, m, words + i, ld, P, o[0], o[1], o[2], o[3],
+                                                o[4], np, part);
+            }
+#pragma unroll
+            for (uint32_t off = KS / 2; off >= 1; off >>= 1) {
+#pragma unroll
+                for (int c = 0; c < 5; ++c) o[c] += __shfl_xor_sync(kFull, o[c], off);
+                np += __shfl_xor_sync(kFull, np, off);
+            }
+            if (act && part == 0) {
+                V4<T> f;
+                f.x = P.eps24 * o[0];
+                f.y = P.eps24 * o[1];
+                f.z = P.eps24 * o[2];
+                f.w = (T)0.5 * P.eps4 * o[3];
+                force[i] = f;
+                if (vel) {  // the closing half-kick of velocity Verlet, v += dt/2 F
+                    V4<T> v = vel[i];
+                    v.x += hdt * f.x;
+                    v.y += hdt * f.y;
+                    v.z += hdt * f.z;
+                    vel[i] = v;
+                }
+                usum += P.eps4 * o[3];
+                wsum += P.eps24 * o[4];
+                npsum += np;
+            }
+        }
+        if (out) {  // this tile's U, W, pairs (halved: every pair is seen from both sides)
+            const T v[3] = {(T)0.5 * usum, (T)0.5 * wsum, (T)0.5 * (T)npsum};
+            block_sum_store<3>(v, part_sums + (size_t)k * 3);
+        }
+    }
+    if (sched_finish(sched, &s_last) && out) {
+        __threadfence();
+        sum_tile_partials<3>(part_sums, ntodo, out, false, nullptr);
+    }
+}
+
+// Systems of at most this many particles take k_lj_tiles_split.
+constexpr int kSplitMaxN = 65536;
+
 // Budget of the sweep's first wait on a tile's copies (fpm_test_wait_budget).
 static std::atomic<long long> g_first_wait{0};
 
@@ -108,9 +204,25 @@ static fpm_status lj_launch(const fpm_box &b, const fpm_grid &g, int n, const vo
     P.rc2 = (T)(rc * rc);
     const int sc = stage_capacity(n, g, sizeof(V4<T>));
     const size_t smem = (size_t)sc * sizeof(V4<T>);
+    const long long w0 = g_first_wait.load();
+    if (n <= kSplitMaxN) {
+        // threads per home particle: as many as a block holds for a tile of
+        // 1.5x the mean occupancy (the kernel loops over larger tiles)
+        const double per_tile = 1.5 * (double)n / (double)(cfg.ntiles > 0 ? cfg.ntiles : 1);
+        const int ks = per_tile <= 32.0 ? 8 : per_tile <= 64.0 ? 4 : per_tile <= 128.0 ? 2 : 1;
+        if (ks > 1) {
+            auto kern = ks == 8 ? k_lj_tiles_split<T, 8> : ks == 4 ? k_lj_tiles_split<T, 4> : k_lj_tiles_split<T, 2>;
+            smem_opt_in((const void *)kern);
+            const int blocks = persistent_blocks((const void *)kern, kTileThreads, smem, g, cfg.ntiles);
+            kern<<<blocks, kTileThreads, smem, stream>>>(cfg, box, (const V4<T> *)pos, list_view(list, L), nn, L.ld,
+                                                          sc, P, (V4<T> *)force, Sched{r.work, r.done}, r.part,
+                                                          d_energy, status, (V4<T> *)vel, (T)(0.5 * dt),
+                                                          w0 > 0 ? w0 : kWaitCycles);
+            return fpm_check_launch("fpm_lj_forces");
+        }
+    }
     smem_opt_in((const void *)k_lj_tiles<T>);
     const int blocks = persistent_blocks((const void *)k_lj_tiles<T>, kTileThreads, smem, g, cfg.ntiles);
-    const long long w0 = g_first_wait.load();
     k_lj_tiles<T><<<blocks, kTileThreads, smem, stream>>>(cfg, box, (const V4<T> *)pos, list_view(list, L), nn, L.ld,
                                                           sc, P, (V4<T> *)force, Sched{r.work, r.done}, r.part,
                                                           d_energy, status, (V4<T> *)vel, (T)(0.5 * dt),

@@ -29,6 +29,16 @@ def default_cap(rho: float, r_list: float) -> int:
     return max(32, int(math.ceil(1.5 * mean / 8.0)) * 8)
 
 
+# Systems of at most SMALL_N particles take tiles of about SMALL_TILE
+# particles (the library's force sweep splits each list over several threads
+# for such tiles).  Larger systems fill the GPU with the default tiles, which
+# the other tile sweeps (the Verlet scan, the adjoint's Hessian-vector sweep)
+# also run best on: at 32,768 particles the finer tiles cost the adjoint's
+# sweep 36 -> 50 us.
+SMALL_N = 16384
+SMALL_TILE = 40
+
+
 class LJSystem:
     def __init__(self, pos, vel, L, periodic=(1, 1, 1), eps=1.0, sigma=1.0, rc=2.5, skin=0.3, dt=0.005,
                  precision="f32", cap=None, device="cuda", half=False):
@@ -50,6 +60,14 @@ class LJSystem:
         self.r_list = self.rc + self.skin
         self.box = fpm.make_box(self.L, self.periodic)
         self.grid = fpm.fpm_grid_make(self.box, self.r_list, n)
+        if 0 < n <= SMALL_N and not self.half:
+            # a small system has too few tiles of the default width to fill
+            # the GPU: tiles of about SMALL_TILE particles, whose force sweep
+            # gives each home particle several threads (a launch shape only)
+            per_cell = n / max(1, int(self.grid.ncell))
+            w = max(1, int(round(SMALL_TILE / per_cell)))
+            nc0 = int(self.grid.nc[0])
+            self.grid.tiles_x = min(nc0, max(int(self.grid.tiles_x), -(-nc0 // w)))
         vol = float(np.prod(self.L))
         self.cap = int(cap) if cap else default_cap(max(n, 1) / vol, self.r_list)
         if self.half and not cap:
