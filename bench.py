@@ -49,7 +49,7 @@ P2M_FLOP_PER_PAIR = 10  # M'4 P2M: weight product w_x w_y w_z (2) + four FMAs in
 # profiling target `--profile forces`, valid only while its source files hash
 # to `sha` (otherwise the bench line reports the traffic as null).
 NCU_TRAFFIC = {"k_lj_tiles<float>": {"files": ["lj.cu", "lj_pair.cuh", "tiles.cuh", "fpm_common.cuh", "reduce.cuh"],
-                                    "sha": "5eb56c4e67a6e39c", "bytes_per_launch": 183309824}}
+                                    "sha": "6f84c62c261585ef", "bytes_per_launch": 183596288}}
 
 
 def parse():
