@@ -1,7 +1,9 @@
 """GPU parity of the LJ pair sweep, velocity Verlet and the FP64 reductions
 against the oracle, on identical positions.
 
-Tolerances (stated in the north star of this project and derived for FP64):
+Tolerances (the FP32 bounds are this project's stated accuracy targets; the
+FP64 ones follow from the arithmetic: a few ulps per pair term summed over
+~80 terms):
   forces  max_i |F_i - F_i^ref| / RMS(F^ref)  <= 1e-5 (FP32), 1e-12 (FP64)
   U, W    relative                           <= 1e-6 (FP32), 1e-12 (FP64)
   pairs   exact (the cutoff test is taken in the path's precision on both
