@@ -64,6 +64,7 @@ def parse():
                          "or eager steps (no timing, no JSON line)")
     ap.add_argument("--fp64-steps", type=int, default=100)
     ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--e2e-chunks", type=int, default=3, help="pieces of the end-to-end round trip")
     ap.add_argument("--kernel-reps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=8)
@@ -391,7 +392,7 @@ def run_ours(args, ws, rank, local):
         g64.replay()
     e1.record()
     torch.cuda.synchronize()
-    fp64_steps_per_s = args.fp64_steps / (e1_ms := e0.elapsed_time(e1)) * 1e3
+    fp64_steps_per_s = args.fp64_steps / e0.elapsed_time(e1) * 1e3 if args.fp64_steps > 0 else None
     # the FP64 force sweep alone, against the FP64 peak (not measured on this
     # pool: the nominal 1.25 TFLOP/s of GB300)
     nn64 = int(s64.nn[: s64.n].sum().item())
@@ -423,7 +424,7 @@ def run_ours(args, ws, rank, local):
     # input.  Positions and velocities travel as one packed [2, n, 3] array in
     # E2E_CHUNKS pieces: piece k goes back to the device (second stream) as soon
     # as it has reached the host, so the two directions of the link overlap.
-    E2E_CHUNKS = 3
+    E2E_CHUNKS = args.e2e_chunks
     f32 = torch.float32
     hbuf = torch.empty((2, s.n, 3), dtype=f32).pin_memory()
     he = torch.empty(3, dtype=torch.float64).pin_memory()
@@ -673,7 +674,8 @@ def run_ours(args, ws, rank, local):
                  "pair_interactions_per_s": bpairs * bps, "list_slots": bslots,
                  "replica_rebuilds_per_step": (bst.nrebuild - nr0) / args.batch_steps,
                  "launches_per_step": batch_launches,
-                 "particle_steps_over_fp64_single": bb.n * bps / (fp64_steps_per_s * s.n),
+                 "particle_steps_over_fp64_single": (bb.n * bps / (fp64_steps_per_s * s.n)
+                                                     if fp64_steps_per_s else None),
                  "same_ensemble_replica_by_replica": seq,
                  "batched_over_fp64_replica_by_replica": (seq["f64"]["ms_per_step"] / (bms / args.batch_steps)
                                                           if "f64" in seq else None),
@@ -851,8 +853,8 @@ def run_ours(args, ws, rank, local):
         "pairs_per_step": pairs,
         "list_slots_per_step": nn_sum,
         "rebuilds_in_timed_region": int(rebuilds),
-        "fp64_steps_per_s": fp64_steps_per_s * ws,
-        "fp32_over_fp64": steps_per_s / (fp64_steps_per_s * ws),
+        "fp64_steps_per_s": fp64_steps_per_s * ws if fp64_steps_per_s else None,
+        "fp32_over_fp64": steps_per_s / (fp64_steps_per_s * ws) if fp64_steps_per_s else None,
         "fp64_force_kernel": {"launch_us": force64_us, "achieved_tflops": fp64_tflops, "peak_tflops": 1.25,
                               "frac": fp64_tflops / 1.25, "peak_kind": "nominal GB300 FP64 (not measured here)",
                               "work": f"{FLOP_PER_PAIR} FLOP per interacting pair",
@@ -874,7 +876,7 @@ def run_ours(args, ws, rank, local):
                              "peak_kind": f"{peak_kind} (burst)", "alg_bytes_per_launch": alg_bytes}},
         "e2e": {"value": ws * args.e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
-                "transfer": "pinned host buffers in the packed x, y, z layout, copied in three overlapped pieces "
+                "transfer": f"pinned host buffers in the packed x, y, z layout, copied in {args.e2e_chunks} overlapped pieces "
                             "per direction (copy engines), packed / unpacked on the device; energies copied back"},
         "small": small,
         "adjoint": adj,
